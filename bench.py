@@ -1,0 +1,326 @@
+"""Benchmark: two-site H_eff matvec at chi = 2048 (split-BF16 tensor cores vs FP64).
+
+One *step* is a complete 20-step Lanczos ground-state solve of the
+effective Hamiltonian of a spin-1/2 Heisenberg chain at bond dimension 2048
+(d = 2, Dw = 5): every matvec is the split-BF16 tcgen05 contraction (operand
+split, GEMM1, W.W, GEMM2), and the Lanczos inner products, CGS2
+re-orthogonalisation, tridiagonal eigensolve and Ritz vector are FP64 on the
+device.  ``value`` = 20 x (algorithmic matvec flops 6.905e11) / step time.
+
+Inputs are synthetic (seeded N(0,1), channel-symmetrised environments), as
+there is no dataset for this path; psi (134 MB) and the Lanczos basis
+(2.8 GB) are larger than the 126 MB L2, so no explicit flush is needed.
+
+``--impl reference`` times the CPU oracle (the project's FP64 reference
+implementation) on a bounded sample of the same workload: whole rows
+out[a, :, :, :] of the matvec.
+
+Multi-GPU: the path runs as independent replicas (one per rank, no
+collective on the data path); ``value`` sums the ranks' work over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+METRIC = "H_eff matvec GFLOP/s at chi=2048 (split-BF16 vs FP64, error ≤1e-6) + % roofline"
+CHI = 2048
+LANCZOS_STEPS = 20
+SEED = 20251223
+
+
+def heff_flops(chi: int) -> float:
+    return 4.0 * chi ** 3 * 4 * 5 + 2.0 * chi ** 2 * 16 * 25
+
+
+def gemm_flops(chi: int) -> float:
+    """Algorithmic flops of one of the two GEMM launches of a matvec (2 * 4chi * 5chi * chi)."""
+    return 2.0 * (4 * chi) * (5 * chi) * chi
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(HERE, "gpurun_out", f"clocks_rank{device_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "N/A") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[3]) if v.lower() == "active"})
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(r[2] for r in rows)}
+
+
+def dist_info():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+# ---------------------------------------------------------------------------- reference (CPU oracle)
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return
+    from oracle.heff import heff_rows
+    from tci_synth import dense_heff_inputs
+    psi, L, R, W = dense_heff_inputs(CHI, seed=SEED)
+    rows_per_step = 8
+    per_row = heff_flops(CHI) / CHI
+    times = []
+    rng = np.random.default_rng(0)
+    for it in range(args.warmup + args.steps):
+        rows = rng.choice(CHI, size=rows_per_step, replace=False)
+        t0 = time.perf_counter()
+        heff_rows(L, W, R, psi, rows)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    tot = sum(times)
+    value = rows_per_step * per_row * len(times) / tot / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "dense two-site H_eff matvec, Heisenberg MPO, chi=2048, d=2, Dw=5",
+                       "chi": CHI, "seed": SEED, "inputs": "larger than L2"},
+            "cpu_baseline": {"value": value, "unit": "GFLOP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{rows_per_step} random output rows out[a,:,:,:] of the chi=2048 matvec per step"},
+            "e2e": {"value": value, "unit": "GFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU path
+def lanczos_launches(m: int) -> int:
+    """Kernel launches of one m-step Lanczos solve (4 per matvec + vector kernels)."""
+    n = 3  # init scalars, start-vector norm (sumsq + reduce) counted below
+    n = 1 + 2 + 1
+    for j in range(m):
+        n += 4                                      # split, GEMM1, W.W, GEMM2
+        n += 1 + 1 + 1                              # alpha mdot + reduce, three-term
+        groups = (j + 1 + 7) // 8
+        n += 2 * (groups + 1 + groups)              # CGS2: mdot groups + reduce + update groups
+        n += 2 + 1                                  # sumsq + reduce, finish_beta
+        if j + 1 < m:
+            n += 1                                  # next vector
+    n += 2                                          # tridiagonal eigensolve, Ritz vector
+    return n
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    import paper_2512_23917_b300 as tci
+    from tci_synth import dense_heff_inputs
+
+    psi, L, R, W = dense_heff_inputs(CHI, seed=SEED)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    dpsi, dL, dR, dW = t(psi), t(L), t(R), t(W)
+    stream = torch.cuda.current_stream(dev)
+    ctx = tci.Context(dev.index, stream.cuda_stream)
+    plan = tci.HeffPlan(ctx, dL, dW, dR, precision="split_bf16")
+    F = plan.flops
+    x = torch.empty_like(dpsi)
+    out = torch.empty_like(dpsi)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- warm-up, then K timed Lanczos solves
+    for _ in range(args.warmup):
+        plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev.index) as clk:
+        ev0.record(stream)
+        res = None
+        for _ in range(args.steps):
+            res = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    ms_total = ev0.elapsed_time(ev1)
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_total = float(tt.item())
+    ms_step = ms_total / args.steps
+    value = world * LANCZOS_STEPS * F / (ms_step * 1e-3) / 1e9
+
+    # ---- per-stage events of single matvecs (roofline of the GEMM kernel)
+    stages = []
+    for _ in range(5):
+        stages.append(plan.apply_timed(dpsi, out))
+    st = np.median(np.array(stages), axis=0)     # split, GEMM1, WW, GEMM2 (ms)
+    mv_ms = float(st.sum())
+    # matvec-only rate (events around back-to-back applies)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        plan.apply(dpsi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    mv_only_ms = e0.elapsed_time(e1) / 10
+
+    peaks, peak_src = measured_peaks()
+    gemm_ms = 0.5 * (st[1] + st[3])
+    tensor_tflops = 6.0 * gemm_flops(CHI) / (gemm_ms * 1e-3) / 1e12
+    roofline = {"bound": "tensor", "kernel": "k_split_bf16_gemm", "achieved": tensor_tflops,
+                "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": tensor_tflops / peaks["bf16_tflops"],
+                "traffic": None, "peak_source": f"{peak_src} bf16 burst",
+                "flops_per_launch": 6.0 * gemm_flops(CHI),
+                "note": "achieved counts the 6 BF16 piece products per FP64-equivalent multiply-add"}
+
+    # ---- e2e through the C ABI with host buffers (psi in, out back, per step)
+    psi_h = torch.from_numpy(np.ascontiguousarray(psi)).pin_memory().numpy()
+    out_h = torch.empty(psi.shape, dtype=torch.float64).pin_memory().numpy()
+    plan.apply_host(psi_h, out_h)
+    t0 = time.perf_counter()
+    ne2e = 5
+    for _ in range(ne2e):
+        plan.apply_host(psi_h, out_h)
+    e2e_s = (time.perf_counter() - t0) / ne2e
+    e2e = {"value": F / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(psi.nbytes),
+           "d2h_bytes_per_step": int(psi.nbytes), "step": "one matvec via tci_heff_apply_host"}
+
+    # ---- FP64 path (same matvec, native arithmetic) and error vs the oracle
+    extra = {}
+    if rank == 0:
+        plan64 = tci.HeffPlan(ctx, dL, dW, dR, precision="native")
+        out64 = torch.empty_like(dpsi)
+        plan64.apply(dpsi, out64)
+        torch.cuda.synchronize()
+        s64 = plan64.apply_timed(dpsi, out64)
+        fp64_ms = float(sum(s64))
+        extra["fp64_path"] = {"gflops": F / (fp64_ms * 1e-3) / 1e9, "ms_per_matvec": fp64_ms,
+                              "stage_ms": [float(v) for v in s64]}
+        extra["split_vs_fp64_speedup"] = fp64_ms / mv_ms
+        # error of the split matvec against the CPU oracle on sampled rows
+        from oracle.contract import rel_frob_err
+        from oracle.heff import heff_rows
+        rows = list(range(0, CHI, CHI // 16))
+        plan.apply(dpsi, out)
+        torch.cuda.synchronize()
+        o = out.cpu().numpy()
+        extra["rel_frob_err_vs_oracle_sampled"] = rel_frob_err(o[rows], heff_rows(L, W, R, psi, rows))
+        extra["rel_frob_err_fp64_path_sampled"] = rel_frob_err(out64.cpu().numpy()[rows], heff_rows(L, W, R, psi, rows))
+        plan64.close()
+        # cpu baseline: the oracle on a bounded sample of rows
+        r_s = list(range(3, CHI, CHI // 8))
+        t0 = time.perf_counter()
+        heff_rows(L, W, R, psi, r_s)
+        cpu_s = time.perf_counter() - t0
+        cpu_value = len(r_s) * F / CHI / cpu_s / 1e9
+        extra["cpu_baseline"] = {"value": cpu_value, "unit": "GFLOP/s", "cores": len(os.sched_getaffinity(0)),
+                                 "kind": "oracle",
+                                 "sample": f"{len(r_s)} output rows out[a,:,:,:] of the chi=2048 FP64 matvec"}
+
+    clocks = clk.summary()
+    line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "20-step Lanczos on the dense two-site H_eff, Heisenberg MPO, chi=2048, d=2, Dw=5, "
+                                   "split-BF16 matvec (3 pieces, 6 products, FP32 accumulate, FP64 promote every "
+                                   "1024 of K), FP64 Lanczos",
+                       "chi": CHI, "lanczos_steps": LANCZOS_STEPS, "seed": SEED,
+                       "l2": "inputs larger than L2 (psi 134 MB, basis 2.8 GB)", "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "e2e": e2e, "gpu_launches": lanczos_launches(LANCZOS_STEPS) * args.steps,
+            "clocks": clocks, "ritz_value": res["theta"] if res else None,
+            "matvec": {"gflops": F / (mv_only_ms * 1e-3) / 1e9, "ms": mv_only_ms,
+                       "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),
+                                    "gemm2": float(st[3])}}}
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

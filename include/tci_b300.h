@@ -1,0 +1,275 @@
+/*
+ * tci_b300.h -- C ABI of the B300 (sm_103a) tensor-contraction library.
+ *
+ * The tensor handle, the label-based contraction and the manipulation calls
+ * follow the Tensor Computing Interface (TCI) of arXiv 2512.23917, App. C
+ * ("Type system", "Core functions", "Environment variables").  The
+ * effective-Hamiltonian, Lanczos, block-sparse and batched-TEBD entry points
+ * are extensions built on that contraction; each says where its definition
+ * comes from.
+ *
+ * Conventions for every entry point
+ *  - Return value: a tci_status.  TCI_OK on success; otherwise nothing was
+ *    launched for a validation error, and tci_last_error(ctx) holds a one-line
+ *    message.  No C++ exception crosses this boundary.
+ *  - Asynchrony: device work is enqueued on the context's stream and the call
+ *    returns without waiting, except calls that hand a host scalar back
+ *    (tci_norm, tci_normalize, tci_close, tci_lanczos), which synchronise the
+ *    stream before returning.
+ *  - Memory: "device pointer" means memory of the context's device; "host
+ *    pointer" means ordinary host memory (pinned memory is faster but not
+ *    required).  Tensors created by tci_allocate / tci_zeros / tci_copy and
+ *    contraction outputs the library creates are OWNED (freed by
+ *    tci_tensor_free / tci_clear); tci_tensor_wrap creates a BORROWED view
+ *    that the library never frees.
+ *  - Layout: shapes and strides are in elements, row-major when strides are
+ *    omitted (last bond fastest), int64.
+ *  - Thread safety: a context must not be used from two host threads at once.
+ */
+#ifndef TCI_B300_H
+#define TCI_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+typedef enum {
+  TCI_OK = 0,
+  TCI_ERR_INVALID_ARG = 1,     /* NULL pointer, negative size, bad enum          */
+  TCI_ERR_SHAPE = 2,           /* shapes/orders/strides incompatible             */
+  TCI_ERR_LABEL = 3,           /* repeated label in one operand, count mismatch  */
+  TCI_ERR_DTYPE = 4,           /* element types differ or are not supported      */
+  TCI_ERR_UNSUPPORTED = 5,     /* valid request outside what is implemented      */
+  TCI_ERR_ALLOC = 6,           /* device allocation failed                       */
+  TCI_ERR_CUDA = 7,            /* a CUDA runtime/driver call failed              */
+  TCI_ERR_TIMEOUT = 8,         /* a bounded device wait expired (kernel status)  */
+  TCI_ERR_INVALID_CONTEXT = 9  /* NULL or destroyed context                      */
+} tci_status;
+
+/* Element types: TCI elem_t (App. C.1, Tab. II) restricted to real/complex
+ * IEEE types.  Complex values are interleaved (re, im). */
+typedef enum { TCI_F32 = 0, TCI_F64 = 1, TCI_C64 = 2, TCI_C128 = 3 } tci_dtype;
+
+/* Arithmetic used for real contractions (context-wide; see
+ * tci_context_set_precision).
+ *  TCI_PREC_NATIVE     : the element type's own arithmetic (FP64 FMA for F64).
+ *  TCI_PREC_SPLIT_BF16 : each operand is split into three bfloat16 pieces
+ *                        (hi, mid, lo; hi+mid+lo == fl32(x)); the six piece
+ *                        products with i+j <= 2 run on the tcgen05 tensor
+ *                        cores with FP32 accumulation in tensor memory, and
+ *                        K-chunks of the accumulation are promoted to FP64.
+ *  TCI_PREC_SPLIT_BF16_3 : same pieces, only the three products with
+ *                        i+j <= 1 (about 2x faster, ~5e-6 relative error). */
+typedef enum {
+  TCI_PREC_NATIVE = 0,
+  TCI_PREC_SPLIT_BF16 = 1,
+  TCI_PREC_SPLIT_BF16_3 = 2
+} tci_precision;
+
+typedef struct tci_context_s* tci_context;   /* TCI context_handle_t */
+typedef struct tci_tensor_s* tci_tensor;     /* TCI TenT              */
+typedef struct tci_heff_plan_s* tci_heff_plan;
+typedef struct tci_bs_plan_s* tci_bs_plan;
+
+/* TCI "version" (App. C.2, Miscellaneous): specification version "M.m".
+ * Returns a static string; never fails. */
+const char* tci_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char* tci_status_string(tci_status s);
+
+/* Message of the last failed call on ctx (or of the last failed call with a
+ * NULL/invalid context when ctx is NULL).  Static/thread-local storage; valid
+ * until the next call on the same context. */
+const char* tci_last_error(tci_context ctx);
+
+/* ---------------------------------------------------------------- context */
+/* TCI "create_context" (App. C.2, Miscellaneous): bind a context to CUDA
+ * device `device` and stream `stream` (a cudaStream_t; NULL = the legacy
+ * default stream).  Reads TCI_VERBOSE (App. C.3) once: 0 silent, 1 one line
+ * per call on stderr, 2 adds the call's device time (this synchronises).
+ * On failure *ctx is set to NULL.  Errors: INVALID_ARG, CUDA. */
+tci_status tci_create_context(tci_context* ctx, int device, void* stream);
+
+/* TCI "destroy_context": release the context and everything it owns;
+ * *ctx becomes NULL.  Tensors created on it must be freed first. */
+tci_status tci_destroy_context(tci_context* ctx);
+
+/* Change the stream later calls enqueue on (extension of create_context's
+ * implementation-defined parameters). */
+tci_status tci_context_set_stream(tci_context ctx, void* stream);
+
+/* Select the arithmetic of real contractions (see tci_precision).  Plans
+ * (tci_heff_plan_create, tci_bs_plan_create) capture the mode at creation. */
+tci_status tci_context_set_precision(tci_context ctx, tci_precision p);
+tci_status tci_context_get_precision(tci_context ctx, tci_precision* p);
+
+/* Accumulation granularity of the split-BF16 tensor-core GEMM (a tuning
+ * knob of the plan): hi*hi products are accumulated in FP32 tensor memory
+ * for chunk_k of contraction depth, the cross products for xchunk_k, before
+ * being folded into an error-free FP32 double-float sum.  Smaller chunks are
+ * more accurate and cost more epilogue work.  Defaults 128 / 1024.
+ * Errors: INVALID_ARG unless 32 | chunk_k and chunk_k | xchunk_k. */
+tci_status tci_context_set_split_chunks(tci_context ctx, int chunk_k, int xchunk_k);
+
+/* Block the host until all work queued on the context's stream finished;
+ * maps a sticky device error or a kernel timeout status to CUDA/TIMEOUT. */
+tci_status tci_synchronize(tci_context ctx);
+
+/* ---------------------------------------------------------------- tensors */
+/* Borrowed view of existing device memory `data` (TCI TenT, App. C.1):
+ * dtype, order (0..8), shape[order], strides[order] in elements (NULL =
+ * row-major contiguous).  The library never frees `data`.
+ * Errors: INVALID_ARG (order > 8, negative dims/strides, NULL data with
+ * nonzero size), DTYPE. */
+tci_status tci_tensor_wrap(tci_context ctx, tci_dtype dtype, int order, const int64_t* shape,
+                           const int64_t* strides, void* data, tci_tensor* out);
+
+/* TCI "allocate" / "zeros" (App. C.2, Construction): owned, row-major,
+ * uninitialised / zero-filled.  Errors: INVALID_ARG, DTYPE, ALLOC. */
+tci_status tci_allocate(tci_context ctx, tci_dtype dtype, int order, const int64_t* shape,
+                        tci_tensor* out);
+tci_status tci_zeros(tci_context ctx, tci_dtype dtype, int order, const int64_t* shape,
+                     tci_tensor* out);
+
+/* TCI "copy" (deep copy): *out becomes a new owned, row-major tensor with
+ * the same logical elements as `in` (strided inputs are materialised). */
+tci_status tci_copy(tci_context ctx, tci_tensor in, tci_tensor* out);
+
+/* TCI "move": transfer metadata and storage of *from into a new handle
+ * *to; *from is left an empty order-0 tensor with no storage. */
+tci_status tci_move(tci_context ctx, tci_tensor from, tci_tensor* to);
+
+/* TCI "clear": release the storage (if owned) and reset t to an empty
+ * order-0 tensor with no storage. */
+tci_status tci_clear(tci_context ctx, tci_tensor t);
+
+/* Release the handle (and owned storage); *t becomes NULL.  Enqueued work
+ * that uses the storage must have been synchronised by the caller. */
+tci_status tci_tensor_free(tci_tensor* t);
+
+/* Host transfer, the analogue of TCI "to_range" / "assign_from_range"
+ * (App. C.2, Construction) for a contiguous host range in the tensor's
+ * logical row-major element order.  `host` holds size(t) elements of t's
+ * dtype.  tci_to_host synchronises; tci_from_host is stream-ordered but
+ * blocks until `host` may be reused. */
+tci_status tci_to_host(tci_context ctx, tci_tensor t, void* host);
+tci_status tci_from_host(tci_context ctx, tci_tensor t, const void* host);
+
+/* TCI read-only queries (App. C.2): order, shape, size (element count),
+ * size_bytes; plus strides, dtype and the device address of element 0. */
+tci_status tci_order(tci_context ctx, tci_tensor t, int* order);
+tci_status tci_shape(tci_context ctx, tci_tensor t, int64_t* shape);      /* order entries */
+tci_status tci_strides(tci_context ctx, tci_tensor t, int64_t* strides);  /* order entries */
+tci_status tci_size(tci_context ctx, tci_tensor t, int64_t* size);
+tci_status tci_size_bytes(tci_context ctx, tci_tensor t, int64_t* bytes);
+tci_status tci_get_dtype(tci_context ctx, tci_tensor t, tci_dtype* dtype);
+tci_status tci_data(tci_context ctx, tci_tensor t, void** data);
+
+/* TCI "reshape" (App. C.2, Tensor manipulation; Sec. II.B.1):
+ * metadata-only change to `order`/`new_shape` (same element count).  The
+ * element order is the logical row-major order of the current shape; when
+ * the current strides cannot express the new shape (e.g. after a lazy
+ * transpose) the tensor is first materialised row-major on the device
+ * (owned storage).  Errors: SHAPE (element count differs). */
+tci_status tci_reshape(tci_context ctx, tci_tensor t, int order, const int64_t* new_shape);
+/* Out-of-place: *out is a new handle; it shares storage with `in` when no
+ * materialisation is needed (borrowed view) and owns a copy otherwise. */
+tci_status tci_reshape_to(tci_context ctx, tci_tensor in, int order, const int64_t* new_shape,
+                          tci_tensor* out);
+
+/* TCI "transpose" (Eq. 1, Sec. II.B.1; App. C.2): B_{i_pi(0)..} = A_{i_0..}
+ * with new_order[k] = the old bond that becomes bond k.  In place it is
+ * lazy: only shape/stride metadata is permuted; contraction reads the
+ * permuted operand in place.  Errors: INVALID_ARG (not a permutation). */
+tci_status tci_transpose(tci_context ctx, tci_tensor t, const int* new_order);
+/* Out-of-place: *out is a new owned row-major tensor holding the permuted
+ * elements (a device permute-copy). */
+tci_status tci_transpose_to(tci_context ctx, tci_tensor in, const int* new_order, tci_tensor* out);
+
+/* TCI "contract" (App. C.2, Tensor linear algebra; Eq. C_IJ = sum_S A_IS
+ * B_SJ of Sec. II.B.2).  Labels: one char per bond (string API) or int32
+ * lists (tci_contract_l, lengths = the operands' orders and nc).  A label in
+ * both a and b and not in c is summed; c's labels give its bonds and their
+ * order; an empty c label list makes an order-0 (scalar) c.
+ *  *c == NULL      : a new owned row-major c is created.
+ *  *c is a tensor  : it must have c's shape and dtype (else SHAPE/DTYPE,
+ *                    unless owned, in which case it is re-allocated); it may
+ *                    alias a and/or b (the result is computed into scratch
+ *                    first, then placed).
+ * Both operands must have the same dtype.  Real F64/F32 contractions use the
+ * context precision; complex ones use native arithmetic.
+ * Errors: LABEL (repeated label in one operand, count mismatch, dimension
+ * mismatch), UNSUPPORTED (a label in a, b and c at once; a free label missing
+ * from c), DTYPE, ALLOC, CUDA. */
+tci_status tci_contract(tci_context ctx, tci_tensor a, const char* labels_a, tci_tensor b,
+                        const char* labels_b, tci_tensor* c, const char* labels_c);
+tci_status tci_contract_l(tci_context ctx, tci_tensor a, const int32_t* labels_a, tci_tensor b,
+                          const int32_t* labels_b, tci_tensor* c, const int32_t* labels_c, int nc);
+
+/* TCI "norm" (Eq. frob_norm): Frobenius norm in FP64 (deterministic
+ * two-level reduction).  Synchronises.  Any dtype. */
+tci_status tci_norm(tci_context ctx, tci_tensor t, double* out);
+/* TCI "normalize" (in place): scale to unit norm; *old_norm (may be NULL)
+ * receives the previous norm.  Synchronises. */
+tci_status tci_normalize(tci_context ctx, tci_tensor t, double* old_norm);
+/* TCI "scale" (in place): t *= (re + i im) (im ignored for real dtypes). */
+tci_status tci_scale(tci_context ctx, tci_tensor t, double re, double im);
+/* TCI "linear_combine": *out = sum_i coefs[i] ins[i]; coefs are n real
+ * values (NULL = all ones).  All inputs share shape and dtype; *out as for
+ * tci_contract's c. */
+tci_status tci_linear_combine(tci_context ctx, int n, const tci_tensor* ins, const double* coefs,
+                              tci_tensor* out);
+/* TCI "close" (App. C.2, Miscellaneous): *result = shapes equal and
+ * max|a-b| <= eps.  Synchronises. */
+tci_status tci_close(tci_context ctx, tci_tensor a, tci_tensor b, double eps, int* result);
+
+/* ------------------------------------------- two-site effective Hamiltonian
+ * Textbook two-site DMRG H_eff (the paper names DMRG as a target application
+ * in Sec. I; it defines the contraction the matvec is built from):
+ *   out[a,s1,s2,b] = sum L[a,wl,a'] W[wl,wm,s1,t1] W[wm,wr,s2,t2]
+ *                        R[b,wr,b'] psi[a',t1,t2,b']
+ * L: F64 [chiL, Dw, chiL]; R: F64 [chiR, Dw, chiR]; W: F64 [Dw, Dw, d, d]
+ * (s = bra/out, t = ket/in); psi, out: F64 [chiL, d, d, chiR]; all
+ * row-major contiguous device tensors.  The plan copies what it needs (L, R
+ * in the plan's arithmetic, W W pre-contracted), so the caller may free L,
+ * W, R after creation.  Arithmetic: the context precision at creation
+ * (NATIVE = FP64 everywhere; SPLIT_BF16[_3] = tensor-core contraction,
+ * output FP64).  Errors: SHAPE, DTYPE, ALLOC, CUDA. */
+tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
+                                tci_heff_plan* plan);
+tci_status tci_heff_plan_destroy(tci_heff_plan* plan);
+/* out = H_eff psi (async).  psi and out must not overlap. */
+tci_status tci_heff_apply(tci_heff_plan plan, tci_tensor psi, tci_tensor out);
+/* Same with HOST buffers: psi_host and out_host hold chiL*d*d*chiR doubles;
+ * the call copies psi to the device, applies, copies out back and
+ * synchronises. */
+tci_status tci_heff_apply_host(tci_heff_plan plan, const double* psi_host, double* out_host);
+/* tci_heff_apply with CUDA events between its stages, for profiling:
+ * stage_ms[0..3] (host) receive the device time of the operand split (0 on
+ * the FP64 path), GEMM1 (psi R), the W.W step and GEMM2 (L V).
+ * Synchronises. */
+tci_status tci_heff_apply_timed(tci_heff_plan plan, tci_tensor psi, tci_tensor out, float* stage_ms);
+/* Algorithmic flops of one matvec: 2 chiL d^2 chiR Dw (chiL + chiR) + 2 chiL chiR d^4 Dw^2. */
+double tci_heff_flops(tci_heff_plan plan);
+
+/* Lanczos ground state of H_eff (textbook; Golub & Van Loan Sec. 10.1 with
+ * classical Gram-Schmidt applied twice when reorth != 0; Ritz value by Sturm
+ * bisection, Sec. 8.4).  All vector arithmetic in FP64 on the device.
+ * psi0: start vector [chiL,d,d,chiR] F64 (normalised internally, not
+ * modified).  Runs up to nsteps (1..256) steps, stopping early when
+ * beta_j < 1e-12 |alpha_j|.  Outputs (host): *ritz, alpha[nsteps],
+ * beta[nsteps] (entries past *steps_done are 0), *steps_done.  x (may be
+ * NULL): device F64 tensor shaped like psi0 receiving the unit Ritz vector.
+ * Synchronises.  Errors: INVALID_ARG, SHAPE, ALLOC, CUDA. */
+tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reorth, double* ritz,
+                       double* alpha, double* beta, int* steps_done, tci_tensor x);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCI_B300_H */

@@ -1,0 +1,408 @@
+"""Python binding of ``libtci_b300.so`` (ctypes; argument marshalling only).
+
+Every operation runs in the CUDA library; this module only turns torch
+tensors into (pointer, shape, strides, dtype) tuples, passes the current
+torch stream, and raises :class:`TciError` on a non-OK status.  There is no
+fallback: if the shared library is missing this import fails.
+
+Build the library with ``python -m paper_2512_23917_b300.build``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtci_b300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2512_23917_b300.build`")
+
+lib = C.CDLL(LIB_PATH)
+
+# ---------------------------------------------------------------- enums
+F32, F64, C64, C128 = 0, 1, 2, 3
+PREC_NATIVE, PREC_SPLIT_BF16, PREC_SPLIT_BF16_3 = 0, 1, 2
+_PREC = {"native": PREC_NATIVE, "fp64": PREC_NATIVE, "split_bf16": PREC_SPLIT_BF16,
+         "split_bf16_3": PREC_SPLIT_BF16_3}
+STATUS = ["TCI_OK", "TCI_ERR_INVALID_ARG", "TCI_ERR_SHAPE", "TCI_ERR_LABEL", "TCI_ERR_DTYPE",
+          "TCI_ERR_UNSUPPORTED", "TCI_ERR_ALLOC", "TCI_ERR_CUDA", "TCI_ERR_TIMEOUT",
+          "TCI_ERR_INVALID_CONTEXT"]
+
+_p = C.c_void_p
+_i64p = C.POINTER(C.c_int64)
+_i32p = C.POINTER(C.c_int32)
+_dp = C.POINTER(C.c_double)
+
+# (name, restype, argtypes) of every exported entry point
+SIGNATURES = [
+    ("tci_version", C.c_char_p, []),
+    ("tci_status_string", C.c_char_p, [C.c_int]),
+    ("tci_last_error", C.c_char_p, [_p]),
+    ("tci_create_context", C.c_int, [C.POINTER(_p), C.c_int, _p]),
+    ("tci_destroy_context", C.c_int, [C.POINTER(_p)]),
+    ("tci_context_set_stream", C.c_int, [_p, _p]),
+    ("tci_context_set_precision", C.c_int, [_p, C.c_int]),
+    ("tci_context_get_precision", C.c_int, [_p, C.POINTER(C.c_int)]),
+    ("tci_context_set_split_chunks", C.c_int, [_p, C.c_int, C.c_int]),
+    ("tci_synchronize", C.c_int, [_p]),
+    ("tci_tensor_wrap", C.c_int, [_p, C.c_int, C.c_int, _i64p, _i64p, _p, C.POINTER(_p)]),
+    ("tci_allocate", C.c_int, [_p, C.c_int, C.c_int, _i64p, C.POINTER(_p)]),
+    ("tci_zeros", C.c_int, [_p, C.c_int, C.c_int, _i64p, C.POINTER(_p)]),
+    ("tci_copy", C.c_int, [_p, _p, C.POINTER(_p)]),
+    ("tci_move", C.c_int, [_p, _p, C.POINTER(_p)]),
+    ("tci_clear", C.c_int, [_p, _p]),
+    ("tci_tensor_free", C.c_int, [C.POINTER(_p)]),
+    ("tci_to_host", C.c_int, [_p, _p, _p]),
+    ("tci_from_host", C.c_int, [_p, _p, _p]),
+    ("tci_order", C.c_int, [_p, _p, C.POINTER(C.c_int)]),
+    ("tci_shape", C.c_int, [_p, _p, _i64p]),
+    ("tci_strides", C.c_int, [_p, _p, _i64p]),
+    ("tci_size", C.c_int, [_p, _p, _i64p]),
+    ("tci_size_bytes", C.c_int, [_p, _p, _i64p]),
+    ("tci_get_dtype", C.c_int, [_p, _p, C.POINTER(C.c_int)]),
+    ("tci_data", C.c_int, [_p, _p, C.POINTER(_p)]),
+    ("tci_reshape", C.c_int, [_p, _p, C.c_int, _i64p]),
+    ("tci_reshape_to", C.c_int, [_p, _p, C.c_int, _i64p, C.POINTER(_p)]),
+    ("tci_transpose", C.c_int, [_p, _p, C.POINTER(C.c_int)]),
+    ("tci_transpose_to", C.c_int, [_p, _p, C.POINTER(C.c_int), C.POINTER(_p)]),
+    ("tci_contract", C.c_int, [_p, _p, C.c_char_p, _p, C.c_char_p, C.POINTER(_p), C.c_char_p]),
+    ("tci_contract_l", C.c_int, [_p, _p, _i32p, _p, _i32p, C.POINTER(_p), _i32p, C.c_int]),
+    ("tci_norm", C.c_int, [_p, _p, _dp]),
+    ("tci_normalize", C.c_int, [_p, _p, _dp]),
+    ("tci_scale", C.c_int, [_p, _p, C.c_double, C.c_double]),
+    ("tci_linear_combine", C.c_int, [_p, C.c_int, C.POINTER(_p), _dp, C.POINTER(_p)]),
+    ("tci_close", C.c_int, [_p, _p, _p, C.c_double, C.POINTER(C.c_int)]),
+    ("tci_heff_plan_create", C.c_int, [_p, _p, _p, _p, C.POINTER(_p)]),
+    ("tci_heff_plan_destroy", C.c_int, [C.POINTER(_p)]),
+    ("tci_heff_apply", C.c_int, [_p, _p, _p]),
+    ("tci_heff_apply_host", C.c_int, [_p, _p, _p]),
+    ("tci_heff_apply_timed", C.c_int, [_p, _p, _p, C.POINTER(C.c_float)]),
+    ("tci_heff_flops", C.c_double, [_p]),
+    ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
+]
+
+for _name, _res, _args in SIGNATURES:
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class TciError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        self.status_name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{self.status_name}: {msg}")
+
+
+def version() -> str:
+    return lib.tci_version().decode()
+
+
+def _check(status: int, ctx_handle=None):
+    if status != 0:
+        raise TciError(status, lib.tci_last_error(ctx_handle).decode(errors="replace"))
+
+
+def _arr64(vals):
+    vals = list(vals)
+    return (C.c_int64 * max(1, len(vals)))(*vals)
+
+
+_TORCH_DT = None
+
+
+def _dtype_code(t) -> int:
+    import torch
+    m = {torch.float32: F32, torch.float64: F64, torch.complex64: C64, torch.complex128: C128}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported dtype {t.dtype}")
+    return m[t.dtype]
+
+
+class Context:
+    """TCI context bound to a CUDA device and the current torch stream."""
+
+    def __init__(self, device: int = 0, stream=None, precision: str = "native"):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.handle = _p()
+        _check(lib.tci_create_context(C.byref(self.handle), int(device), _p(int(stream))))
+        self.device = device
+        self.set_precision(precision)
+
+    def set_precision(self, precision):
+        code = _PREC[precision] if isinstance(precision, str) else int(precision)
+        _check(lib.tci_context_set_precision(self.handle, code), self.handle)
+
+    def set_split_chunks(self, chunk_k: int, xchunk_k: int):
+        _check(lib.tci_context_set_split_chunks(self.handle, int(chunk_k), int(xchunk_k)), self.handle)
+
+    def set_stream(self, stream: int):
+        _check(lib.tci_context_set_stream(self.handle, _p(int(stream))), self.handle)
+
+    def synchronize(self):
+        _check(lib.tci_synchronize(self.handle), self.handle)
+
+    def close(self):
+        if self.handle:
+            _check(lib.tci_destroy_context(C.byref(self.handle)))
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------ tensors
+    def wrap(self, t) -> "Tensor":
+        """Borrowed TCI tensor view of a CUDA torch tensor (no copy)."""
+        h = _p()
+        _check(lib.tci_tensor_wrap(self.handle, _dtype_code(t), t.dim(), _arr64(t.shape), _arr64(t.stride()),
+                                   _p(t.data_ptr()), C.byref(h)), self.handle)
+        return Tensor(self, h, keepalive=t)
+
+
+class Tensor:
+    """Owner of a TCI tensor handle (borrowed view or library-owned storage)."""
+
+    def __init__(self, ctx: Context, handle, keepalive=None):
+        self.ctx = ctx
+        self.handle = handle
+        self._keep = keepalive
+
+    @property
+    def order(self) -> int:
+        o = C.c_int()
+        _check(lib.tci_order(self.ctx.handle, self.handle, C.byref(o)), self.ctx.handle)
+        return o.value
+
+    @property
+    def shape(self):
+        n = self.order
+        a = (C.c_int64 * max(1, n))()
+        _check(lib.tci_shape(self.ctx.handle, self.handle, a), self.ctx.handle)
+        return tuple(a[:n])
+
+    @property
+    def strides(self):
+        n = self.order
+        a = (C.c_int64 * max(1, n))()
+        _check(lib.tci_strides(self.ctx.handle, self.handle, a), self.ctx.handle)
+        return tuple(a[:n])
+
+    @property
+    def dtype_code(self) -> int:
+        d = C.c_int()
+        _check(lib.tci_get_dtype(self.ctx.handle, self.handle, C.byref(d)), self.ctx.handle)
+        return d.value
+
+    def size(self) -> int:
+        n = C.c_int64()
+        _check(lib.tci_size(self.ctx.handle, self.handle, C.byref(n)), self.ctx.handle)
+        return n.value
+
+    def size_bytes(self) -> int:
+        n = C.c_int64()
+        _check(lib.tci_size_bytes(self.ctx.handle, self.handle, C.byref(n)), self.ctx.handle)
+        return n.value
+
+    def data_ptr(self) -> int:
+        p = _p()
+        _check(lib.tci_data(self.ctx.handle, self.handle, C.byref(p)), self.ctx.handle)
+        return p.value or 0
+
+    def to_numpy(self) -> np.ndarray:
+        npdt = {F32: np.float32, F64: np.float64, C64: np.complex64, C128: np.complex128}[self.dtype_code]
+        out = np.empty(self.shape, dtype=npdt)
+        _check(lib.tci_to_host(self.ctx.handle, self.handle, _p(out.ctypes.data)), self.ctx.handle)
+        return out
+
+    def from_numpy(self, arr: np.ndarray):
+        arr = np.ascontiguousarray(arr)
+        _check(lib.tci_from_host(self.ctx.handle, self.handle, _p(arr.ctypes.data)), self.ctx.handle)
+
+    def reshape_(self, shape):
+        _check(lib.tci_reshape(self.ctx.handle, self.handle, len(shape), _arr64(shape)), self.ctx.handle)
+        return self
+
+    def reshape(self, shape) -> "Tensor":
+        h = _p()
+        _check(lib.tci_reshape_to(self.ctx.handle, self.handle, len(shape), _arr64(shape), C.byref(h)),
+               self.ctx.handle)
+        return Tensor(self.ctx, h, keepalive=self)
+
+    def transpose_(self, order):
+        arr = (C.c_int * max(1, len(order)))(*order)
+        _check(lib.tci_transpose(self.ctx.handle, self.handle, arr), self.ctx.handle)
+        return self
+
+    def transpose(self, order) -> "Tensor":
+        arr = (C.c_int * max(1, len(order)))(*order)
+        h = _p()
+        _check(lib.tci_transpose_to(self.ctx.handle, self.handle, arr, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h)
+
+    def copy(self) -> "Tensor":
+        h = _p()
+        _check(lib.tci_copy(self.ctx.handle, self.handle, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h)
+
+    def move(self) -> "Tensor":
+        h = _p()
+        _check(lib.tci_move(self.ctx.handle, self.handle, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h, keepalive=self._keep)
+
+    def clear(self):
+        _check(lib.tci_clear(self.ctx.handle, self.handle), self.ctx.handle)
+
+    def norm(self) -> float:
+        v = C.c_double()
+        _check(lib.tci_norm(self.ctx.handle, self.handle, C.byref(v)), self.ctx.handle)
+        return v.value
+
+    def normalize_(self) -> float:
+        v = C.c_double()
+        _check(lib.tci_normalize(self.ctx.handle, self.handle, C.byref(v)), self.ctx.handle)
+        return v.value
+
+    def scale_(self, s):
+        s = complex(s)
+        _check(lib.tci_scale(self.ctx.handle, self.handle, s.real, s.imag), self.ctx.handle)
+        return self
+
+    def free(self):
+        if self.handle:
+            _check(lib.tci_tensor_free(C.byref(self.handle)))
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            if self.handle and self.ctx.handle:
+                lib.tci_tensor_free(C.byref(self.handle))
+        except Exception:
+            pass
+
+
+def allocate(ctx: Context, shape, dtype: int = F64, zero: bool = False) -> Tensor:
+    h = _p()
+    fn = lib.tci_zeros if zero else lib.tci_allocate
+    _check(fn(ctx.handle, dtype, len(shape), _arr64(shape), C.byref(h)), ctx.handle)
+    return Tensor(ctx, h)
+
+
+def contract_into(ctx: Context, a: Tensor, la, b: Tensor, lb, c, lc) -> Tensor:
+    """TCI contract with handles; ``c`` is a Tensor (written / re-allocated) or None (new owned)."""
+    h = c.handle if c is not None else _p()
+    if isinstance(la, str):
+        _check(lib.tci_contract(ctx.handle, a.handle, la.encode(), b.handle, lb.encode(), C.byref(h),
+                                lc.encode()), ctx.handle)
+    else:
+        ia = (C.c_int32 * max(1, len(la)))(*la)
+        ib = (C.c_int32 * max(1, len(lb)))(*lb)
+        ic = (C.c_int32 * max(1, len(lc)))(*lc)
+        _check(lib.tci_contract_l(ctx.handle, a.handle, ia, b.handle, ib, C.byref(h), ic, len(lc)), ctx.handle)
+    if c is not None:
+        c.handle = h
+        return c
+    return Tensor(ctx, h)
+
+
+def contract(ctx: Context, a, la, b, lb, lc, out=None):
+    """C = contract(a, la, b, lb, lc) on torch CUDA tensors (string or int labels).
+
+    ``out`` (optional) is a torch tensor of the output shape that receives
+    the result; otherwise one is allocated.  Returns the torch output.
+    """
+    import torch
+    la_l, lb_l, lc_l = list(la), list(lb), list(lc)
+    if out is None:
+        dims = dict(zip(la_l, a.shape))
+        dims.update(zip(lb_l, b.shape))
+        shape = [dims[l] for l in lc_l] if all(l in dims for l in lc_l) else [0]
+        out = torch.empty(shape, dtype=a.dtype, device=a.device)
+    ta, tb, tc = ctx.wrap(a), ctx.wrap(b), ctx.wrap(out)
+    contract_into(ctx, ta, la, tb, lb, tc, lc)
+    return out
+
+
+def linear_combine(ctx: Context, tensors, coefs, out):
+    keep = [ctx.wrap(t) for t in tensors]
+    hs = (_p * len(tensors))(*[k.handle for k in keep])
+    co = (C.c_double * len(tensors))(*coefs) if coefs is not None else None
+    to = ctx.wrap(out)
+    h = to.handle
+    _check(lib.tci_linear_combine(ctx.handle, len(tensors), hs, co, C.byref(h)), ctx.handle)
+    return out
+
+
+def close(ctx: Context, a, b, eps: float) -> bool:
+    r = C.c_int()
+    ta, tb = ctx.wrap(a), ctx.wrap(b)
+    _check(lib.tci_close(ctx.handle, ta.handle, tb.handle, float(eps), C.byref(r)), ctx.handle)
+    return bool(r.value)
+
+
+class HeffPlan:
+    """Two-site H_eff plan (see include/tci_b300.h, tci_heff_plan_create)."""
+
+    def __init__(self, ctx: Context, L, W, R, precision=None):
+        if precision is not None:
+            ctx.set_precision(precision)
+        self.ctx = ctx
+        self.handle = _p()
+        self.chiL, self.chiR = L.shape[0], R.shape[0]
+        tl, tw, tr = ctx.wrap(L), ctx.wrap(W), ctx.wrap(R)
+        _check(lib.tci_heff_plan_create(ctx.handle, tl.handle, tw.handle, tr.handle, C.byref(self.handle)),
+               ctx.handle)
+        self._psi_wrap = {}
+
+    @property
+    def flops(self) -> float:
+        return lib.tci_heff_flops(self.handle)
+
+    def apply(self, psi, out):
+        tp, to = self.ctx.wrap(psi), self.ctx.wrap(out)
+        _check(lib.tci_heff_apply(self.handle, tp.handle, to.handle), self.ctx.handle)
+        return out
+
+    def apply_timed(self, psi, out):
+        """Apply and return the four stage durations in ms (split, GEMM1, W.W, GEMM2)."""
+        ms = (C.c_float * 4)()
+        tp, to = self.ctx.wrap(psi), self.ctx.wrap(out)
+        _check(lib.tci_heff_apply_timed(self.handle, tp.handle, to.handle, ms), self.ctx.handle)
+        return list(ms)
+
+    def apply_host(self, psi_host: np.ndarray, out_host: np.ndarray):
+        assert psi_host.dtype == np.float64 and out_host.dtype == np.float64
+        assert psi_host.flags.c_contiguous and out_host.flags.c_contiguous
+        _check(lib.tci_heff_apply_host(self.handle, _p(psi_host.ctypes.data), _p(out_host.ctypes.data)),
+               self.ctx.handle)
+        return out_host
+
+    def lanczos(self, psi0, nsteps: int, reorth: bool = True, x=None):
+        ritz = C.c_double()
+        alpha = (C.c_double * nsteps)()
+        beta = (C.c_double * nsteps)()
+        k = C.c_int()
+        tp = self.ctx.wrap(psi0)
+        tx = self.ctx.wrap(x) if x is not None else None
+        _check(lib.tci_lanczos(self.handle, tp.handle, int(nsteps), int(bool(reorth)), C.byref(ritz), alpha, beta,
+                               C.byref(k), tx.handle if tx is not None else None), self.ctx.handle)
+        return {"theta": ritz.value, "alpha": np.array(alpha[:k.value]), "beta": np.array(beta[:k.value]),
+                "steps": k.value}
+
+    def close(self):
+        if self.handle:
+            _check(lib.tci_heff_plan_destroy(C.byref(self.handle)))
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,332 @@
+// Two-site DMRG effective Hamiltonian matvec
+//   out[a,s1,s2,b] = sum L[a,wl,a'] W[wl,wm,s1,t1] W[wm,wr,s2,t2] R[b,wr,b'] psi[a',t1,t2,b']
+// evaluated right-to-left as three steps whose GEMMs are all "TN" (both
+// operands K-major, read in place):
+//   GEMM1  U[(a',t1,t2), (b,wr)]   = sum_b'       psi[(a',t1,t2), b'] R[(b,wr), b']
+//   WW     V[(s1,s2,b), (wl,a')]   = sum_{wr,t1,t2} WW[wl,s1,s2,wr,t1,t2] U[(a',t1,t2),(b,wr)]
+//   GEMM2  out[a, (s1,s2,b)]       = sum_{wl,a'}  L[a, (wl,a')] V[(s1,s2,b), (wl,a')]
+// with WW[wl,s1,s2,wr,t1,t2] = sum_wm W[wl,wm,s1,t1] W[wm,wr,s2,t2] formed
+// once per plan.  The W.W step writes V already transposed into GEMM2's
+// K-major layout (and, on the split path, already split into bfloat16
+// pieces), so no transpose is ever materialised for the GEMMs.
+#include <cuda_bf16.h>
+
+#include "heff_plan.cuh"
+
+namespace {
+
+// ------------------------------------------------------------------ WW = W.W
+__global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, double* __restrict__ WW) {
+  // WW index ((((wl*d + s1)*d + s2)*Dw + wr)*d + t1)*d + t2
+  const int n = Dw * d * d * Dw * d * d;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int r = i;
+    const int t2 = r % d; r /= d;
+    const int t1 = r % d; r /= d;
+    const int wr = r % Dw; r /= Dw;
+    const int s2 = r % d; r /= d;
+    const int s1 = r % d; r /= d;
+    const int wl = r;
+    double acc = 0.0;
+    for (int wm = 0; wm < Dw; ++wm)
+      acc += W[((wl * Dw + wm) * d + s1) * d + t1] * W[((wm * Dw + wr) * d + s2) * d + t2];
+    WW[i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ W.W application
+// One block: a' in [a0, a0+ATILE), b in [b0, b0+32).  U rows (a',t) for the
+// tile are staged in shared memory (coalesced 32*Dw-long row segments), then
+// each thread forms the 20 outputs of one (a', b) pair and writes them with
+// a' fastest (coalesced along GEMM2's K dimension).
+template <typename T>
+struct WWArgs {
+  T ww[HEFF_DW * 4 * HEFF_DW * 4];   // [wl][s][wr][t], s = (s1 s2), t = (t1 t2)
+};
+
+template <typename T, typename UT, int ATILE, bool SPLIT>
+__global__ void __launch_bounds__(256) k_ww_apply(const WWArgs<T> args, const UT* __restrict__ U, int64_t chiL,
+                                                  int64_t chiR, void* __restrict__ Vout, int64_t ldv, int64_t plane) {
+  constexpr int Dw = HEFF_DW, D2 = 4, BT = 32;
+  constexpr int ROW = D2 * BT * Dw;   // values per a' in the tile
+  extern __shared__ __align__(16) unsigned char smem_ww[];
+  T* Us = (T*)smem_ww;                // [ATILE][ROW + 1]
+  const int64_t a0 = (int64_t)blockIdx.y * ATILE;
+  const int64_t b0 = (int64_t)blockIdx.x * BT;
+  const int64_t ldu = chiR * Dw;
+  // load: for each (a', t) row, BT*Dw contiguous doubles
+  for (int idx = threadIdx.x; idx < ATILE * D2 * BT * Dw; idx += blockDim.x) {
+    const int col = idx % (BT * Dw);
+    const int rt = idx / (BT * Dw);   // a'_local * D2 + t
+    const int al = rt / D2, t = rt % D2;
+    const int64_t ap = a0 + al;
+    const int64_t gcol = b0 * Dw + col;
+    T v = (T)0;
+    if (ap < chiL && gcol < ldu) v = (T)U[(ap * D2 + t) * ldu + gcol];
+    const int bl = col / Dw, wr = col % Dw;
+    Us[al * (ROW + 1) + (t * BT + bl) * Dw + wr] = v;
+  }
+  __syncthreads();
+  const int al = threadIdx.x % ATILE;
+  const int64_t ap = a0 + al;
+  for (int bl = threadIdx.x / ATILE; bl < BT; bl += 256 / ATILE) {
+    const int64_t b = b0 + bl;
+    if (ap >= chiL || b >= chiR) continue;
+    T in[D2 * Dw];
+#pragma unroll
+    for (int t = 0; t < D2; ++t)
+#pragma unroll
+      for (int wr = 0; wr < Dw; ++wr) in[t * Dw + wr] = Us[al * (ROW + 1) + (t * BT + bl) * Dw + wr];
+#pragma unroll
+    for (int wl = 0; wl < Dw; ++wl) {
+#pragma unroll
+      for (int s = 0; s < D2; ++s) {
+        T acc = (T)0;
+#pragma unroll
+        for (int wr = 0; wr < Dw; ++wr)
+#pragma unroll
+          for (int t = 0; t < D2; ++t) acc += args.ww[((wl * D2 + s) * Dw + wr) * D2 + t] * in[t * Dw + wr];
+        const int64_t off = (s * chiR + b) * ldv + wl * chiL + ap;
+        if (SPLIT) {
+          __nv_bfloat16* V = (__nv_bfloat16*)Vout;
+          const float xf = (float)acc;
+          const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+          const float r1 = xf - __bfloat162float(h);
+          const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+          const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+          V[off] = h;
+          V[plane + off] = m;
+          V[2 * plane + off] = l;
+        } else {
+          ((double*)Vout)[off] = (double)acc;
+        }
+      }
+    }
+  }
+}
+
+template <typename T, typename UT, int ATILE, bool SPLIT>
+tci_status launch_ww(tci_context ctx, const WWArgs<T>& args, const UT* U, int64_t chiL, int64_t chiR, void* V,
+                     int64_t ldv, int64_t plane) {
+  constexpr int ROW = 4 * 32 * HEFF_DW;
+  const size_t smem = (size_t)ATILE * (ROW + 1) * sizeof(T);
+  static bool attr = false;
+  if (!attr) {
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_ww_apply<T, UT, ATILE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  dim3 grid((unsigned)((chiR + 31) / 32), (unsigned)((chiL + ATILE - 1) / ATILE));
+  k_ww_apply<T, UT, ATILE, SPLIT><<<grid, 256, smem, ctx->stream>>>(args, U, chiL, chiR, V, ldv, plane);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
+
+}  // namespace
+
+// ------------------------------------------------------------------ plan
+extern "C" tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
+                                           tci_heff_plan* out) {
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "heff_plan_create");
+  if (!out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: NULL output");
+  *out = nullptr;
+  if (!tci_ten_ok(L) || !tci_ten_ok(W) || !tci_ten_ok(R)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: invalid tensor");
+  if (L->dtype != TCI_F64 || W->dtype != TCI_F64 || R->dtype != TCI_F64)
+    return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_create: L, W, R must be F64");
+  if (L->order != 3 || R->order != 3 || W->order != 4) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L[chi,Dw,chi], W[Dw,Dw,d,d], R[chi,Dw,chi]");
+  const int64_t Dw = W->shape[0], d = W->shape[2];
+  if (Dw != HEFF_DW || W->shape[1] != Dw || d != 2 || W->shape[3] != d)
+    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_plan_create: this build supports Dw = %d, d = 2", HEFF_DW);
+  const int64_t chiL = L->shape[0], chiR = R->shape[0];
+  if (L->shape[1] != Dw || L->shape[2] != chiL || R->shape[1] != Dw || R->shape[2] != chiR || chiL <= 0 || chiR <= 0)
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: inconsistent L/R shapes");
+  if (!tci_is_rowmajor(L) || !tci_is_rowmajor(W) || !tci_is_rowmajor(R))
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L, W, R must be row-major contiguous");
+  vs.info = "chiL=" + std::to_string(chiL) + " chiR=" + std::to_string(chiR);
+
+  tci_heff_plan p = new tci_heff_plan_s();
+  p->magic = kPlanMagic;
+  p->ctx = ctx;
+  p->chiL = chiL;
+  p->chiR = chiR;
+  p->prec = ctx->precision;
+  p->products = ctx->precision == TCI_PREC_SPLIT_BF16_3 ? 3 : 6;
+  p->chunk_k = ctx->split_chunk_k;
+  p->xchunk_k = ctx->split_xchunk_k;
+  const int64_t n_psi = chiL * 4 * chiR;
+  const int64_t nU = chiL * 4 * chiR * Dw;
+  auto fail = [&](tci_status s) {
+    tci_heff_plan pp = p;
+    tci_heff_plan_destroy(&pp);
+    return s;
+  };
+  tci_status s;
+  // WW (FP64) on the device, then a host copy for the kernel arguments
+  double* dWW = nullptr;
+  if ((s = tci_dev_alloc(ctx, sizeof(double) * HEFF_NWW, (void**)&dWW)) != TCI_OK) return fail(s);
+  k_ww_precompute<<<1, 256, 0, ctx->stream>>>((const double*)W->data, (int)Dw, (int)d, dWW);
+  cudaError_t e = cudaMemcpyAsync(p->ww, dWW, sizeof(double) * HEFF_NWW, cudaMemcpyDeviceToHost, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  tci_dev_free(dWW);
+  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "heff_plan_create: WW"));
+
+  const size_t ubytes = (p->prec == TCI_PREC_NATIVE ? sizeof(double) : sizeof(float)) * nU;
+  if ((s = tci_dev_alloc(ctx, ubytes, (void**)&p->U)) != TCI_OK) return fail(s);
+  if (p->prec == TCI_PREC_NATIVE) {
+    if ((s = tci_dev_alloc(ctx, sizeof(double) * chiL * Dw * chiL, (void**)&p->L64)) != TCI_OK) return fail(s);
+    if ((s = tci_dev_alloc(ctx, sizeof(double) * chiR * Dw * chiR, (void**)&p->R64)) != TCI_OK) return fail(s);
+    if ((s = tci_dev_alloc(ctx, sizeof(double) * nU, (void**)&p->V64)) != TCI_OK) return fail(s);
+    e = cudaMemcpyAsync(p->L64, L->data, sizeof(double) * chiL * Dw * chiL, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->R64, R->data, sizeof(double) * chiR * Dw * chiR, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "heff_plan_create: copy L/R"));
+  } else {
+    p->Kp1 = pad8(chiR);
+    p->Kp2 = pad8(Dw * chiL);
+    if ((s = tci_dev_alloc(ctx, 2 * 3 * chiL * p->Kp2, (void**)&p->Lp)) != TCI_OK) return fail(s);
+    if ((s = tci_dev_alloc(ctx, 2 * 3 * chiR * Dw * p->Kp1, (void**)&p->Rp)) != TCI_OK) return fail(s);
+    if ((s = tci_dev_alloc(ctx, 2 * 3 * chiL * 4 * p->Kp1, (void**)&p->psip)) != TCI_OK) return fail(s);
+    if ((s = tci_dev_alloc(ctx, 2 * 3 * 4 * chiR * p->Kp2, (void**)&p->Vp)) != TCI_OK) return fail(s);
+    // padded K columns of V stay zero (the W.W step writes valid columns only)
+    if (p->Kp2 != Dw * chiL) {
+      e = cudaMemsetAsync(p->Vp, 0, 2 * 3 * 4 * chiR * p->Kp2, ctx->stream);
+      if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "heff_plan_create: memset"));
+    }
+    // L as [a, (wl,a')] and R as [(b,wr), b'] : K-major rows of the GEMMs
+    if ((s = tci_launch_split3(ctx, TCI_F64, L->data, chiL, Dw * chiL, Dw * chiL, 1, p->Lp, p->Kp2)) != TCI_OK) return fail(s);
+    if ((s = tci_launch_split3(ctx, TCI_F64, R->data, chiR * Dw, chiR, chiR, 1, p->Rp, p->Kp1)) != TCI_OK) return fail(s);
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "heff_plan_create"));
+  (void)n_psi;
+  *out = p;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
+  if (!pp || !*pp || (*pp)->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_plan_destroy: invalid plan");
+  tci_heff_plan p = *pp;
+  if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
+  void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
+                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part};
+  for (void* b : bufs) tci_dev_free(b);
+  p->magic = 0;
+  delete p;
+  *pp = nullptr;
+  return TCI_OK;
+}
+
+extern "C" double tci_heff_flops(tci_heff_plan p) {
+  if (!p || p->magic != kPlanMagic) return 0.0;
+  const double chiL = (double)p->chiL, chiR = (double)p->chiR, d = 2.0, Dw = HEFF_DW;
+  return 2.0 * chiL * d * d * chiR * Dw * (chiL + chiR) + 2.0 * chiL * chiR * d * d * d * d * Dw * Dw;
+}
+
+// ------------------------------------------------------------------ apply
+static tci_status check_vec(tci_heff_plan p, tci_tensor t, const char* what);
+tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, bool psi_presplit) {
+  tci_context ctx = p->ctx;
+  const int64_t chiL = p->chiL, chiR = p->chiR, Dw = HEFF_DW;
+  if (p->prec == TCI_PREC_NATIVE) {
+    WWArgs<double> args;
+    for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = p->ww[i];
+    TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1));
+    TCI_TRY((launch_ww<double, double, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0)));
+    TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out,
+                            4 * chiR, 1));
+    return TCI_OK;
+  }
+  WWArgs<float> args;
+  for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+  if (!psi_presplit) TCI_TRY(tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1));
+  TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products,
+                              p->chunk_k, p->xchunk_k));
+  TCI_TRY((launch_ww<float, float, 32, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2)));
+  TCI_TRY(tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k,
+                              p->xchunk_k));
+  return TCI_OK;
+}
+
+// Same as tci_heff_apply_raw with CUDA events between the stages (split,
+// GEMM1, W.W, GEMM2); ms[0..3] receive the stage durations.
+static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, float* ms) {
+  tci_context ctx = p->ctx;
+  const int64_t chiL = p->chiL, chiR = p->chiR, Dw = HEFF_DW;
+  cudaEvent_t ev[5];
+  for (auto& e : ev) TCI_CUDA(ctx, cudaEventCreate(&e));
+  tci_status s = TCI_OK;
+  TCI_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  if (p->prec == TCI_PREC_NATIVE) {
+    WWArgs<double> args;
+    for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = p->ww[i];
+    TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+    if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1);
+    TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
+    if (s == TCI_OK) s = launch_ww<double, double, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0);
+    TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+    if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out, 4 * chiR, 1);
+  } else {
+    WWArgs<float> args;
+    for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+    s = tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1);
+    TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products, p->chunk_k, p->xchunk_k);
+    TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
+    if (s == TCI_OK) s = launch_ww<float, float, 32, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2);
+    TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k, p->xchunk_k);
+  }
+  TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
+  TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));
+  for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return s;
+}
+
+extern "C" tci_status tci_heff_apply_timed(tci_heff_plan p, tci_tensor psi, tci_tensor out, float* stage_ms) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply_timed: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (!stage_ms) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_apply_timed: NULL stage_ms");
+  TCI_TRY(check_vec(p, psi, "heff_apply_timed psi"));
+  TCI_TRY(check_vec(p, out, "heff_apply_timed out"));
+  return apply_timed(p, (const double*)psi->data, (double*)out->data, stage_ms);
+}
+
+static tci_status check_vec(tci_heff_plan p, tci_tensor t, const char* what) {
+  tci_context ctx = p->ctx;
+  if (!tci_ten_ok(t)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "%s: invalid tensor", what);
+  if (t->dtype != TCI_F64) return tci_fail(ctx, TCI_ERR_DTYPE, "%s: must be F64", what);
+  if (t->order != 4 || t->shape[0] != p->chiL || t->shape[1] != 2 || t->shape[2] != 2 || t->shape[3] != p->chiR)
+    return tci_fail(ctx, TCI_ERR_SHAPE, "%s: expected [%lld,2,2,%lld]", what, (long long)p->chiL, (long long)p->chiR);
+  if (!tci_is_rowmajor(t)) return tci_fail(ctx, TCI_ERR_SHAPE, "%s: must be row-major contiguous", what);
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_apply(tci_heff_plan p, tci_tensor psi, tci_tensor out) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  TciVerboseScope vs(p->ctx, "heff_apply");
+  TCI_TRY(check_vec(p, psi, "heff_apply psi"));
+  TCI_TRY(check_vec(p, out, "heff_apply out"));
+  if (psi->data == out->data) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_apply: psi and out overlap");
+  return tci_heff_apply_raw(p, (const double*)psi->data, (double*)out->data, false);
+}
+
+extern "C" tci_status tci_heff_apply_host(tci_heff_plan p, const double* psi_host, double* out_host) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply_host: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "heff_apply_host");
+  if (!psi_host || !out_host) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_apply_host: NULL buffer");
+  const size_t bytes = sizeof(double) * p->chiL * 4 * p->chiR;
+  if (!p->d_stage_in) {
+    TCI_TRY(tci_dev_alloc(ctx, bytes, (void**)&p->d_stage_in));
+    TCI_TRY(tci_dev_alloc(ctx, bytes, (void**)&p->d_stage_out));
+  }
+  TCI_CUDA(ctx, cudaMemcpyAsync(p->d_stage_in, psi_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
+  TCI_TRY(tci_heff_apply_raw(p, p->d_stage_in, p->d_stage_out, false));
+  TCI_CUDA(ctx, cudaMemcpyAsync(out_host, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));
+  return tci_synchronize(ctx);
+}

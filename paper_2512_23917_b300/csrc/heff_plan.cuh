@@ -1,0 +1,43 @@
+// H_eff plan object shared by the matvec and the Lanczos driver.
+#pragma once
+
+#include "tci_internal.cuh"
+
+#define HEFF_DW 5
+#define HEFF_NWW (HEFF_DW * 4 * HEFF_DW * 4)
+
+constexpr int kPlanMagic = 0x4eff0001;
+
+struct tci_heff_plan_s {
+  int magic;
+  tci_context ctx;
+  int64_t chiL, chiR;
+  tci_precision prec;
+  int products;
+  int chunk_k;     // split GEMM: K depth per hi*hi accumulation unit
+  int xchunk_k;    // split GEMM: K depth per cross-product accumulation unit
+  double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
+  // intermediates
+  void* U = nullptr;       // [(a',t1,t2), (b,wr)]: FP64 (native) or FP32 (split)
+  // native path
+  double* L64 = nullptr;
+  double* R64 = nullptr;
+  double* V64 = nullptr;   // [(s1,s2,b), (wl,a')]
+  // split path: bfloat16 piece planes [3][rows][Kp]
+  int64_t Kp1 = 0, Kp2 = 0;
+  void* Lp = nullptr;      // [3][chiL][Kp2]
+  void* Rp = nullptr;      // [3][chiR*Dw][Kp1]
+  void* psip = nullptr;    // [3][chiL*4][Kp1]
+  void* Vp = nullptr;      // [3][4*chiR][Kp2]
+  // host-buffer staging
+  double* d_stage_in = nullptr;
+  double* d_stage_out = nullptr;
+  // Lanczos workspace
+  double* lz_V = nullptr;     // basis, capacity lz_cap vectors
+  int lz_cap = 0;
+  double* lz_w = nullptr;
+  double* lz_scal = nullptr;  // device scalars
+  double* lz_part = nullptr;  // reduction partials
+};
+
+tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, bool psi_presplit);

@@ -1,0 +1,479 @@
+// Split-BF16 tensor-core GEMM for sm_103a (tcgen05 + TMA + TMEM), plus the
+// K0 split/pack kernel that feeds it.
+//
+//   C(m, n) = sum_k A(m, k) B(n, k),   A, B given as three bfloat16 planes
+//   (hi, mid, lo) with hi + mid + lo == fl32(x).  The piece products
+//   A_i B_j with i + j <= 2 (6 products) or i + j <= 1 (3 products) run on
+//   the tensor cores with FP32 accumulation in tensor memory (TMEM).
+//
+// Accumulation design.  The FP32 accumulator of tcgen05.mma loses about
+// 2^-25 of its own magnitude (on average, always towards zero) every time
+// an MMA adds into it, so the error of a long accumulation grows linearly
+// with the number of MMAs that add into the same large value.  Therefore:
+//   * the dominant product hi*hi accumulates alone in D1 and D1 is drained
+//     every `chunk_k` of depth (default 128: 8 MMAs per drain);
+//   * the five small cross products (magnitude ~2^-8 of hi*hi) accumulate
+//     in a second accumulator X drained every `xchunk_k` (default 1024);
+//   * drained values are summed error-free in FP32 double-float form
+//     (TwoSum: hi + lo) held in the epilogue threads' registers, and the
+//     result is rounded once when the tile is stored (FP64 or FP32).
+// D1 and X are each double-buffered in TMEM (4 x 128 columns), so draining
+// one buffer overlaps the MMAs that fill the other.
+//
+// Structure: persistent CTAs (one per SM), 128 x 128 output tiles, K staged
+// 32 deep (one 64-byte swizzled row per operand row and piece) through a
+// 4-stage TMA -> mbarrier -> tcgen05.mma pipeline.
+//   warp 0      : TMA producer (one lane)
+//   warp 1      : TMEM allocator + MMA issuer (one lane)
+//   warps 2..9  : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
+//                 columns 64*((w-2)/4)..+63
+// Every wait is bounded (2 s); on expiry the kernel records a status word,
+// lets its in-flight copies and MMAs land, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include "ptx_sm100.cuh"
+#include "tci_internal.cuh"
+
+namespace {
+
+constexpr int TBM = 128;
+constexpr int TBN = 128;
+constexpr int TBK = 32;   // bf16 elements = 64 B rows, SWIZZLE_64B
+constexpr int NSTAGE = 4;
+constexpr int PIECE_A = TBM * TBK * 2;   // 8 KB
+constexpr int PIECE_B = TBN * TBK * 2;   // 8 KB
+constexpr int STAGE_A = 3 * PIECE_A;
+constexpr int STAGE_B = 3 * PIECE_B;
+constexpr int STAGE_BYTES = STAGE_A + STAGE_B;   // 48 KB
+constexpr int TMEM_COLS = 512;                   // D1 x2, X x2 (128 columns each)
+constexpr int NEPI = 8;                          // epilogue warps
+constexpr int NTHREADS = 64 + 32 * NEPI;
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
+constexpr int COLS_PER_WARP = TBN / 2;           // two epilogue warps per TMEM lane quadrant
+
+struct GemmParams {
+  int64_t M, N;
+  void* C;
+  int64_t scm, scn;
+  int out_f32;   // 0: FP64 output, 1: FP32 output
+  int num_m, num_n, num_kb;
+  int kb_d1, kb_x;   // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
+  int products;
+  int* status;
+};
+
+// Error-free sum in FP32: s + e == a + b exactly (Knuth TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float ap = __fsub_rn(s, bp);
+  e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// Wait for one accumulation unit, fold its 32-lane x COLS_PER_WARP slice into
+// the double-float running sum (rh + rl), and release the TMEM buffer.  The
+// compensation rl (|rl| <~ 2^-24 |rh| per drain) is kept as packed bfloat16:
+// rounding it to 8 bits costs ~2^-33 |rh| per drain, far below the target,
+// and halves its register footprint.
+__device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, uint64_t* empty_bar, uint32_t parity,
+                                           volatile int* abort_flag, int lane, float (&rh)[COLS_PER_WARP],
+                                           __nv_bfloat162 (&rl)[COLS_PER_WARP / 2]) {
+  if (!ptx::mbar_wait_bounded(ptx::smem_u32(full_bar), parity, abort_flag, WAIT_LIMIT_NS)) return false;
+  ptx::tc_fence_after();
+#pragma unroll
+  for (int g = 0; g < COLS_PER_WARP / 16; ++g) {
+    uint32_t v[16];
+    ptx::tmem_ld_32x32b_x16(taddr + g * 16, v);
+    ptx::tmem_ld_wait();
+#pragma unroll
+    for (int j = 0; j < 16; j += 2) {
+      float s0, e0, s1, e1;
+      two_sum(rh[g * 16 + j], __uint_as_float(v[j]), s0, e0);
+      two_sum(rh[g * 16 + j + 1], __uint_as_float(v[j + 1]), s1, e1);
+      rh[g * 16 + j] = s0;
+      rh[g * 16 + j + 1] = s1;
+      const float2 c = __bfloat1622float2(rl[(g * 16 + j) / 2]);
+      rl[(g * 16 + j) / 2] = __floats2bfloat162_rn(__fadd_rn(c.x, e0), __fadd_rn(c.y, e1));
+    }
+  }
+  ptx::tc_fence_before();
+  if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(empty_bar));
+  return true;
+}
+
+__global__ void __launch_bounds__(NTHREADS, 1)
+    k_split_bf16_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* empty = full + NSTAGE;
+  uint64_t* d1f = empty + NSTAGE;   // D1 buffer full (MMA -> epilogue)
+  uint64_t* d1e = d1f + 2;          // D1 buffer empty (epilogue -> MMA)
+  uint64_t* xf = d1e + 2;
+  uint64_t* xe = xf + 2;
+  uint64_t* done = xe + 2;
+  uint32_t* tmem_slot = (uint32_t*)(done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NSTAGE; ++s) {
+      ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
+      ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(ptx::smem_u32(&d1f[b]), 1);
+      ptx::mbar_init(ptx::smem_u32(&d1e[b]), NEPI);
+      ptx::mbar_init(ptx::smem_u32(&xf[b]), 1);
+      ptx::mbar_init(ptx::smem_u32(&xe[b]), NEPI);
+    }
+    ptx::mbar_init(ptx::smem_u32(done), 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  if (warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&tmA);
+    ptx::tma_prefetch_desc(&tmB);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const int num_tiles = p.num_m * p.num_n;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued = 0, issued_phase = 0;   // bit s: stage s used / its last phase
+      for (int tile = blockIdx.x; tile < num_tiles && !*abort_flag; tile += gridDim.x) {
+        const int mb = tile % p.num_m, nb = tile / p.num_m;
+        for (int kb = 0; kb < p.num_kb; ++kb) {
+          if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
+          const uint32_t fb = ptx::smem_u32(&full[stage]);
+          ptx::mbar_arrive_expect_tx(fb, STAGE_BYTES);
+          uint8_t* sa = smem + stage * STAGE_BYTES;
+          ptx::tma_load_3d(ptx::smem_u32(sa), &tmA, fb, kb * TBK, mb * TBM, 0);
+          ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &tmB, fb, kb * TBK, nb * TBN, 0);
+          issued |= 1u << stage;
+          issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1;
+          }
+        }
+      }
+      // no copy may still be writing shared memory when the CTA exits
+      for (int s = 0; s < NSTAGE; ++s) {
+        if (!((issued >> s) & 1u)) continue;
+        uint64_t t0 = ptx::globaltimer();
+        while (!ptx::mbar_try_wait(ptx::smem_u32(&full[s]), (issued_phase >> s) & 1u))
+          if (ptx::globaltimer() - t0 > WAIT_LIMIT_NS) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      const uint32_t idesc = ptx::idesc_bf16_f32(TBM, TBN);
+      // cross products (A_i, B_j), i + j in {1, 2}: piece offsets packed in
+      // 4-bit fields (i, j) so the table lives in registers
+      constexpr uint32_t kCI = 0x21010u;   // i of q = 0..4: 0,1,0,1,2
+      constexpr uint32_t kCJ = 0x01201u;   // j of q = 0..4: 1,0,2,1,0
+      const int ncross = p.products == 6 ? 5 : 2;
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
+      bool ok = true;
+      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        uint32_t xbuf = 0;
+        for (int kb = 0; kb < p.num_kb && ok; ++kb) {
+          const bool d1_first = (kb % p.kb_d1) == 0;
+          const bool x_first = (kb % p.kb_x) == 0;
+          const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == p.num_kb;
+          const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == p.num_kb;
+          const uint32_t b1 = u1 & 1;
+          if (d1_first) {
+            if (!ptx::mbar_wait_bounded(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+              ok = false;
+              break;
+            }
+          }
+          if (x_first) {
+            xbuf = ux & 1;
+            if (!ptx::mbar_wait_bounded(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+              ok = false;
+              break;
+            }
+          }
+          if (!ptx::mbar_wait_bounded(ptx::smem_u32(&full[stage]), phase, abort_flag, WAIT_LIMIT_NS)) {
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a0 = ptx::smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t b0 = a0 + STAGE_A;
+          const uint32_t dD1 = tmem + b1 * TBN;
+          const uint32_t dX = tmem + 2 * TBN + xbuf * TBN;
+#pragma unroll
+          for (int ks = 0; ks < TBK / 16; ++ks) {
+            ptx::mma_f16(dD1, ptx::smem_desc_kmajor(a0 + ks * 32, 64), ptx::smem_desc_kmajor(b0 + ks * 32, 64), idesc,
+                         (!d1_first || ks > 0) ? 1u : 0u);
+            for (int q = 0; q < ncross; ++q) {
+              const uint32_t qi = (kCI >> (4 * q)) & 0xFu, qj = (kCJ >> (4 * q)) & 0xFu;
+              const uint64_t ad = ptx::smem_desc_kmajor(a0 + qi * PIECE_A + ks * 32, 64);
+              const uint64_t bd = ptx::smem_desc_kmajor(b0 + qj * PIECE_B + ks * 32, 64);
+              ptx::mma_f16(dX, ad, bd, idesc, (!x_first || ks > 0 || q > 0) ? 1u : 0u);
+            }
+          }
+          ptx::mma_commit(ptx::smem_u32(&empty[stage]));
+          if (++stage == NSTAGE) {
+            stage = 0;
+            phase ^= 1;
+          }
+          if (d1_last) {
+            ptx::mma_commit(ptx::smem_u32(&d1f[b1]));
+            ++u1;
+          }
+          if (x_last) {
+            ptx::mma_commit(ptx::smem_u32(&xf[xbuf]));
+            ++ux;
+          }
+        }
+      }
+      // all issued MMAs complete before TMEM is released
+      ptx::mma_commit(ptx::smem_u32(done));
+      uint64_t t0 = ptx::globaltimer();
+      while (!ptx::mbar_try_wait(ptx::smem_u32(done), 0))
+        if (ptx::globaltimer() - t0 > WAIT_LIMIT_NS) break;
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                    // 0..7
+    const int qd = warp & 3;                    // TMEM lane quadrant of this warp
+    const int c0 = (ew >> 2) * COLS_PER_WARP;   // first column of this warp
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    uint32_t u1 = 0, ux = 0;
+    bool ok = true;
+    float rh[COLS_PER_WARP];
+    __nv_bfloat162 rl2[COLS_PER_WARP / 2];
+    for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+      const int mb = tile % p.num_m, nb = tile / p.num_m;
+#pragma unroll
+      for (int j = 0; j < COLS_PER_WARP; ++j) rh[j] = 0.f;
+#pragma unroll
+      for (int j = 0; j < COLS_PER_WARP / 2; ++j) rl2[j] = __floats2bfloat162_rn(0.f, 0.f);
+      for (int kb = 0; kb < p.num_kb; ++kb) {
+        const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == p.num_kb;
+        const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == p.num_kb;
+        if (d1_last) {
+          ok = drain_unit(tmem + lane_base + (u1 & 1) * TBN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
+                          abort_flag, lane, rh, rl2);
+          ++u1;
+        }
+        if (ok && x_last) {
+          ok = drain_unit(tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0, &xf[ux & 1], &xe[ux & 1], (ux >> 1) & 1,
+                          abort_flag, lane, rh, rl2);
+          ++ux;
+        }
+        if (!ok) break;
+      }
+      if (!ok) break;
+      // store the tile (one rounding of hi + lo)
+      const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
+      const int64_t n0 = (int64_t)nb * TBN + c0;
+      if (row < p.M) {
+        if (p.out_f32) {
+          float* crow = (float*)p.C + row * p.scm;
+          const bool vec = p.scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= p.N;
+#pragma unroll
+          for (int j = 0; j < COLS_PER_WARP; j += 4) {
+            const float2 c01 = __bfloat1622float2(rl2[j / 2]);
+            const float2 c23 = __bfloat1622float2(rl2[j / 2 + 1]);
+            const float4 o = make_float4(rh[j] + c01.x, rh[j + 1] + c01.y, rh[j + 2] + c23.x, rh[j + 3] + c23.y);
+            if (vec) {
+              *(float4*)(crow + n0 + j) = o;
+            } else {
+              if (n0 + j < p.N) crow[(n0 + j) * p.scn] = o.x;
+              if (n0 + j + 1 < p.N) crow[(n0 + j + 1) * p.scn] = o.y;
+              if (n0 + j + 2 < p.N) crow[(n0 + j + 2) * p.scn] = o.z;
+              if (n0 + j + 3 < p.N) crow[(n0 + j + 3) * p.scn] = o.w;
+            }
+          }
+        } else {
+          double* crow = (double*)p.C + row * p.scm;
+          const bool vec = p.scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= p.N;
+#pragma unroll
+          for (int j = 0; j < COLS_PER_WARP; j += 2) {
+            const float2 c = __bfloat1622float2(rl2[j / 2]);
+            const double2 o = make_double2((double)rh[j] + (double)c.x, (double)rh[j + 1] + (double)c.y);
+            if (vec) {
+              *(double2*)(crow + n0 + j) = o;
+            } else {
+              if (n0 + j < p.N) crow[(n0 + j) * p.scn] = o.x;
+              if (n0 + j + 1 < p.N) crow[(n0 + j + 1) * p.scn] = o.y;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, 1);
+  if (warp == 1) {
+    __syncwarp();
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+// ---------------------------------------------------------------- tensor maps
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                      const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                      CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled_t get_encode_fn() {
+  static PFN_encodeTiled_t fn = nullptr;
+  if (!fn) {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_encodeTiled_t)ptr;
+  }
+  return fn;
+}
+
+}  // namespace
+
+// 3-D map over bf16 piece planes [3][rows][Kp] with a {TBK, box_rows, 3} box.
+tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* base, int64_t rows, int64_t Kp,
+                              int box_rows) {
+  PFN_encodeTiled_t enc = get_encode_fn();
+  if (!enc) return tci_fail(ctx, TCI_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
+  if (Kp % 8 != 0 || ((uintptr_t)base & 15)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "piece map: misaligned operand");
+  cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2)};
+  cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 3};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return tci_fail(ctx, TCI_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+  return TCI_OK;
+}
+
+tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
+                               void* C, int out_f32, int64_t scm, int64_t scn, int products, int chunk_k,
+                               int xchunk_k) {
+  if (M <= 0 || N <= 0) return TCI_OK;
+  if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
+  if (Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty K");
+  if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
+    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
+  CUtensorMap ta, tb;
+  TCI_TRY(tci_make_piece_map(ctx, &ta, Ap, M, Kp, TBM));
+  TCI_TRY(tci_make_piece_map(ctx, &tb, Bp, N, Kp, TBN));
+  static bool attr_set = false;
+  if (!attr_set) {
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr_set = true;
+  }
+  GemmParams p;
+  p.M = M;
+  p.N = N;
+  p.C = C;
+  p.scm = scm;
+  p.scn = scn;
+  p.out_f32 = out_f32;
+  p.num_m = (int)((M + TBM - 1) / TBM);
+  p.num_n = (int)((N + TBN - 1) / TBN);
+  p.num_kb = (int)((Kp + TBK - 1) / TBK);
+  p.kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
+  int kx = xchunk_k < TBK ? 1 : xchunk_k / TBK;
+  p.kb_x = (kx + p.kb_d1 - 1) / p.kb_d1 * p.kb_d1;   // X drains line up with D1 drains
+  p.products = products;
+  p.status = ctx->d_status;
+  const int tiles = p.num_m * p.num_n;
+  const int grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
+  k_split_bf16_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(ta, tb, p);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+// ---------------------------------------------------------------- K0 split
+namespace {
+
+// hi + mid + lo == fl32(x) exactly (each residual is exact in FP32).
+__device__ __forceinline__ void split3_f32(float xf, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(xf);
+  float r1 = xf - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  float r2 = r1 - __bfloat162float(m);
+  l = __float2bfloat16_rn(r2);
+}
+
+template <typename T>
+__global__ void k_split3(const T* __restrict__ src, int64_t rows, int64_t K, int64_t sr, int64_t sk,
+                         __nv_bfloat16* __restrict__ out, int64_t Kp) {
+  const int64_t plane = rows * Kp;
+  const int64_t total = rows * Kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / Kp, k = i - r * Kp;
+    __nv_bfloat16 h, m, l;
+    if (k < K) {
+      split3_f32((float)src[r * sr + k * sk], h, m, l);
+    } else {
+      h = m = l = __float2bfloat16_rn(0.f);
+    }
+    out[i] = h;
+    out[plane + i] = m;
+    out[2 * plane + i] = l;
+  }
+}
+
+__global__ void k_narrow(int64_t M, int64_t N, const double* __restrict__ src, float* __restrict__ dst, int64_t sm,
+                         int64_t sn) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M * N; i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m = i / N, n = i - m * N;
+    dst[m * sm + n * sn] = (float)src[i];
+  }
+}
+
+}  // namespace
+
+tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int64_t rows, int64_t K, int64_t sr,
+                             int64_t sk, void* out, int64_t Kp) {
+  int64_t total = rows * Kp;
+  if (total == 0) return TCI_OK;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+  if (dt == TCI_F64)
+    k_split3<double><<<(int)blocks, 256, 0, ctx->stream>>>((const double*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp);
+  else if (dt == TCI_F32)
+    k_split3<float><<<(int)blocks, 256, 0, ctx->stream>>>((const float*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp);
+  else
+    return tci_fail(ctx, TCI_ERR_DTYPE, "split3: real dtype required");
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+tci_status tci_launch_narrow_f64_f32(tci_context ctx, int64_t M, int64_t N, const double* src, float* dst, int64_t sm,
+                                     int64_t sn) {
+  int64_t total = M * N;
+  if (total == 0) return TCI_OK;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
+  k_narrow<<<(int)blocks, 256, 0, ctx->stream>>>(M, N, src, dst, sm, sn);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}

@@ -1,0 +1,127 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/tci_b300.h"
+
+#define TCI_MAX_ORDER 8
+
+struct tci_context_s {
+  int magic;
+  int device;
+  cudaStream_t stream;
+  tci_precision precision;
+  int verbose;
+  int num_sms;
+  int split_chunk_k;    // K depth per hi*hi accumulation unit of the split GEMM
+  int split_xchunk_k;   // K depth per cross-product accumulation unit
+  std::string last_error;
+  // device scratch for reductions and kernel status words (owned)
+  double* d_scalars;   // 64 doubles
+  int* d_status;       // 16 ints: [0] = timeout flag of bounded waits
+  double* h_scalars;   // pinned host mirror, 64 doubles
+};
+
+struct tci_tensor_s {
+  int magic;
+  tci_dtype dtype;
+  int order;
+  int64_t shape[TCI_MAX_ORDER];
+  int64_t strides[TCI_MAX_ORDER];
+  void* data;     // address of element 0
+  void* alloc;    // owned allocation (NULL when borrowed or empty)
+  int device;
+};
+
+constexpr int kCtxMagic = 0x7c1c0de;
+constexpr int kTenMagic = 0x7e115e5;
+
+// ---------------------------------------------------------------- errors
+tci_status tci_fail(tci_context ctx, tci_status s, const char* fmt, ...);
+tci_status tci_cuda_fail(tci_context ctx, cudaError_t e, const char* where);
+bool tci_ctx_ok(tci_context ctx);
+bool tci_ten_ok(tci_tensor t);
+
+#define TCI_CHECK_CTX(ctx)                                                      \
+  do {                                                                          \
+    if (!tci_ctx_ok(ctx)) return tci_fail(nullptr, TCI_ERR_INVALID_CONTEXT, "invalid context"); \
+  } while (0)
+
+#define TCI_CUDA(ctx, call)                                                     \
+  do {                                                                          \
+    cudaError_t _e = (call);                                                    \
+    if (_e != cudaSuccess) return tci_cuda_fail(ctx, _e, #call);                \
+  } while (0)
+
+#define TCI_TRY(call)                                                           \
+  do {                                                                          \
+    tci_status _s = (call);                                                     \
+    if (_s != TCI_OK) return _s;                                                \
+  } while (0)
+
+// ---------------------------------------------------------------- verbose
+// TCI_VERBOSE (App. C.3): one line per call at level >= 1, with device time
+// at level 2.  A scope object logs on destruction.
+struct TciVerboseScope {
+  tci_context ctx;
+  const char* name;
+  std::string info;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  TciVerboseScope(tci_context c, const char* n);
+  ~TciVerboseScope();
+};
+
+// ---------------------------------------------------------------- helpers
+size_t tci_elem_bytes(tci_dtype d);
+int64_t tci_numel(const tci_tensor_s* t);
+bool tci_is_rowmajor(const tci_tensor_s* t);
+void tci_rowmajor_strides(int order, const int64_t* shape, int64_t* strides);
+std::string tci_shape_str(const tci_tensor_s* t);
+
+tci_status tci_dev_alloc(tci_context ctx, size_t bytes, void** p);
+void tci_dev_free(void* p);
+
+// Strided permute-copy on the device (kernel K8): dst is row-major over
+// `shape`; src element (i0..i{n-1}) at offset sum_k i_k * src_strides[k].
+tci_status tci_launch_permute_copy(tci_context ctx, tci_dtype dt, int order, const int64_t* shape,
+                                   const void* src, const int64_t* src_strides, void* dst);
+// Same with an arbitrary destination stride vector (used to scatter results).
+tci_status tci_launch_strided_copy(tci_context ctx, tci_dtype dt, int order, const int64_t* shape,
+                                   const void* src, const int64_t* src_strides, void* dst,
+                                   const int64_t* dst_strides);
+
+// Materialise t row-major into new owned storage (in place on the handle).
+tci_status tci_materialise(tci_context ctx, tci_tensor t);
+
+// FP64 dot / norm helpers used by norm and Lanczos (deterministic order).
+tci_status tci_launch_sumsq(tci_context ctx, tci_dtype dt, const void* x, int64_t n, double* d_out);
+tci_status tci_launch_scale(tci_context ctx, tci_dtype dt, void* x, int64_t n, double re, double im);
+
+// ---------------------------------------------------------------- GEMM
+// C[m*ldcm + n*ldcn] = sum_k A[m*sam + k*sak] * B[n*sbn + k*sbk] (beta = 0),
+// native arithmetic of dtype (FP64 FMA for F64), SIMT tiled kernel.
+tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, int64_t K,
+                           const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbn,
+                           int64_t sbk, void* C, int64_t scm, int64_t scn);
+
+// Split-BF16 tensor-core GEMM (tcgen05).  Operands are given as three
+// bfloat16 piece planes each: A pieces [3][M][Kp] and B pieces [3][N][Kp]
+// (K-major rows, Kp % 8 == 0, plane stride = rows*Kp).  C element (m, n) at
+// C[m*scm + n*scn], FP64 (out_f32 = 0) or FP32 (out_f32 = 1).  products = 6
+// or 3.  chunk_k: K depth of one hi*hi accumulation unit (multiple of 32);
+// xchunk_k: K depth of one cross-product accumulation unit.
+tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp,
+                               const void* Apieces, const void* Bpieces, void* C, int out_f32,
+                               int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k);
+
+// K0: split a strided FP64/FP32 operand into three bfloat16 planes, packed
+// K-major: out[p][r][k] for r < rows, k < Kp (zero for k >= K).  Element
+// (r, k) of the source is at src[r*sr + k*sk] (with an optional 2-level row
+// index r = r1*rows0 + r0 -> offset r1*sr1 + r0*sr0 when rows0 > 0).
+tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int64_t rows,
+                             int64_t K, int64_t sr, int64_t sk, void* out, int64_t Kp);

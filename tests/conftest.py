@@ -16,3 +16,24 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def repo_root():
     return ROOT
+
+
+@pytest.fixture(scope="session")
+def tci():
+    import paper_2512_23917_b300 as m
+    return m
+
+
+@pytest.fixture()
+def ctx(tci):
+    import torch
+    c = tci.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    torch.cuda.synchronize()
+    c.close()
+
+
+def to_dev(x):
+    import numpy as np
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()

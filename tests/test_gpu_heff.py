@@ -1,0 +1,89 @@
+"""GPU parity of the H_eff matvec (FP64 and split-BF16 paths) vs the oracle."""
+import numpy as np
+import pytest
+
+from conftest import to_dev
+from oracle import heff as o_heff
+from oracle.contract import rel_frob_err
+from tci_synth import dense_heff_inputs, heisenberg_mpo, random_tensor
+
+pytestmark = pytest.mark.gpu
+
+
+def run_heff(tci, ctx, L, W, R, psi, precision):
+    import torch
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision=precision)
+    out = torch.empty(psi.shape, dtype=torch.float64, device="cuda")
+    plan.apply(to_dev(psi), out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), plan
+
+
+@pytest.mark.parametrize("chi,chi_r", [(32, 32), (33, 17), (1, 1), (7, 130), (200, 64)])
+def test_heff_fp64_matches_oracle(ctx, tci, chi, chi_r):
+    psi, L, R, W = dense_heff_inputs(chi, seed=20251223, chi_r=chi_r)
+    out, _ = run_heff(tci, ctx, L, W, R, psi, "native")
+    ref = o_heff.heff_apply(L, W, R, psi)
+    assert rel_frob_err(out, ref) < 1e-12
+
+
+@pytest.mark.parametrize("chi,chi_r", [(32, 32), (33, 17), (130, 70), (300, 257)])
+def test_heff_split_bf16_matches_oracle(ctx, tci, chi, chi_r):
+    psi, L, R, W = dense_heff_inputs(chi, seed=1, chi_r=chi_r)
+    out, _ = run_heff(tci, ctx, L, W, R, psi, "split_bf16")
+    ref = o_heff.heff_apply(L, W, R, psi)
+    assert rel_frob_err(out, ref) < 1e-6
+
+
+def test_heff_split3_variant(ctx, tci):
+    psi, L, R, W = dense_heff_inputs(96, seed=2)
+    out, _ = run_heff(tci, ctx, L, W, R, psi, "split_bf16_3")
+    assert rel_frob_err(out, o_heff.heff_apply(L, W, R, psi)) < 3e-5
+
+
+def test_identity_mpo_fp64_returns_psi(ctx, tci):
+    # Dw must be 5 for this build: embed the identity in channel 0 only
+    chi = 24
+    W = np.zeros((5, 5, 2, 2))
+    W[0, 0] = np.eye(2)
+    E = np.zeros((chi, 5, chi))
+    E[:, 0, :] = np.eye(chi)
+    psi = random_tensor([chi, 2, 2, chi], 4)
+    out, _ = run_heff(tci, ctx, E, W, E, psi, "native")
+    np.testing.assert_array_equal(out, psi)
+
+
+@pytest.mark.parametrize("nl,nr", [(4, 4), (3, 5), (5, 5)])
+def test_exact_envs_equal_full_hamiltonian(ctx, tci, nl, nr):
+    from test_oracle_heff import kron_heisenberg
+    W = heisenberg_mpo()
+    L, R = o_heff.left_env(W, nl), o_heff.right_env(W, nr)
+    psi = random_tensor([L.shape[0], 2, 2, R.shape[0]], 6)
+    out, _ = run_heff(tci, ctx, L, W, R, psi, "native")
+    ref = (kron_heisenberg(nl + nr + 2) @ psi.ravel()).reshape(psi.shape)
+    assert rel_frob_err(out, ref) < 1e-13
+
+
+def test_heff_fp64_chi1024_sampled_rows(ctx, tci):
+    psi, L, R, W = dense_heff_inputs(1024, seed=20251223)
+    out, plan = run_heff(tci, ctx, L, W, R, psi, "native")
+    rows = [0, 1, 511, 777, 1023]
+    ref = o_heff.heff_rows(L, W, R, psi, rows)
+    assert rel_frob_err(out[rows], ref) < 1e-12
+    assert plan.flops == o_heff.heff_flops(1024)
+
+
+def test_heff_split_bf16_chi2048_full(ctx, tci):
+    psi, L, R, W = dense_heff_inputs(2048, seed=20251223)
+    out, plan = run_heff(tci, ctx, L, W, R, psi, "split_bf16")
+    ref = o_heff.heff_apply(L, W, R, psi)        # full FP64 matvec (BLAS steps)
+    err = rel_frob_err(out, ref)
+    assert err < 1e-6, err
+
+
+def test_apply_host_matches_device(ctx, tci):
+    psi, L, R, W = dense_heff_inputs(64, seed=3)
+    out, plan = run_heff(tci, ctx, L, W, R, psi, "split_bf16")
+    host_out = np.empty_like(psi)
+    plan.apply_host(np.ascontiguousarray(psi), host_out)
+    np.testing.assert_array_equal(host_out, out)
