@@ -257,6 +257,28 @@ tci_status tci_heff_apply_timed(tci_heff_plan plan, tci_tensor psi, tci_tensor o
 /* Algorithmic flops of one matvec: 2 chiL d^2 chiR Dw (chiL + chiR) + 2 chiL chiR d^4 Dw^2. */
 double tci_heff_flops(tci_heff_plan plan);
 
+/* Allocation-free FP64 H_eff matvec for small bond dimensions.  The paper
+ * has no counterpart; it exists for callers that must not allocate device
+ * memory when they apply H_eff (a memory manager that owns the whole GPU, a
+ * loop where cudaMalloc/cudaFree would synchronise the device, a runtime
+ * without an allocator).  Computes the same out = H_eff psi as
+ * tci_heff_apply on the FP64 path.  All pointers are device pointers on the
+ * current device: L [chiL,5,chiL], W [5,5,2,2], R [chiR,5,chiR], psi and out
+ * [chiL,2,2,chiR], row-major, out not overlapping the inputs; work is
+ * enqueued on `stream` (a cudaStream_t of the current device, NULL = legacy
+ * default stream) and the call returns without waiting.
+ * Intermediates live in one fixed 4 MiB device array built into the library
+ * (held on every GPU that loads it until exit): requests with
+ * 512 + 40*chiL*chiR > 2^19 doubles (chiL*chiR > 13094) are rejected with
+ * TCI_ERR_UNSUPPORTED before anything is launched.  All calls share that
+ * array, so calls whose kernels overlap on the GPU race; serialise them.  The
+ * first call on each device looks up the array's device address (make it
+ * before any stream capture).  Allocates no device memory.
+ * Errors: INVALID_ARG (NULL pointer, non-positive size), UNSUPPORTED, CUDA;
+ * the message is available from tci_last_error(NULL). */
+tci_status tci_heff_apply_noalloc(const double* L, const double* W, const double* R, const double* psi,
+                                  double* out, int64_t chiL, int64_t chiR, void* stream);
+
 /* Lanczos ground state of H_eff (textbook; Golub & Van Loan Sec. 10.1 with
  * classical Gram-Schmidt applied twice when reorth != 0; Ritz value by Sturm
  * bisection, Sec. 8.4).  All vector arithmetic in FP64 on the device.

@@ -81,6 +81,7 @@ SIGNATURES = [
     ("tci_heff_apply_host", C.c_int, [_p, _p, _p]),
     ("tci_heff_apply_timed", C.c_int, [_p, _p, _p, C.POINTER(C.c_float)]),
     ("tci_heff_flops", C.c_double, [_p]),
+    ("tci_heff_apply_noalloc", C.c_int, [_p, _p, _p, _p, _p, C.c_int64, C.c_int64, _p]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
 ]
 
