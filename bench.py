@@ -309,14 +309,39 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_case(args):
+    """Small case for ncu captures: split-BF16 matvecs at --profile-chi."""
+    import torch
+    import paper_2512_23917_b300 as tci
+    from tci_synth import dense_heff_inputs
+    chi = args.profile_chi
+    psi, L, R, W = dense_heff_inputs(chi, seed=SEED)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    dpsi = t(psi)
+    ctx = tci.Context(0)
+    plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="split_bf16")
+    out = torch.empty_like(dpsi)
+    for _ in range(args.warmup + args.steps):
+        plan.apply(dpsi, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "split-BF16 H_eff matvec", "chi": chi, "matvecs": args.warmup + args.steps,
+                      "launches_per_matvec": 4}))
+    plan.close()
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
+    ap.add_argument("--profile-chi", type=int, default=0,
+                    help="run only split-BF16 matvecs at this bond dimension (small case for ncu)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile_chi:
+        run_profile_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -74,6 +74,7 @@ typedef struct tci_context_s* tci_context;   /* TCI context_handle_t */
 typedef struct tci_tensor_s* tci_tensor;     /* TCI TenT              */
 typedef struct tci_heff_plan_s* tci_heff_plan;
 typedef struct tci_bs_plan_s* tci_bs_plan;
+typedef struct tci_tebd_plan_s* tci_tebd_plan;
 
 /* TCI "version" (App. C.2, Miscellaneous): specification version "M.m".
  * Returns a static string; never fails. */
@@ -290,6 +291,63 @@ tci_status tci_heff_apply_noalloc(const double* L, const double* W, const double
  * Synchronises.  Errors: INVALID_ARG, SHAPE, ALLOC, CUDA. */
 tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reorth, double* ritz,
                        double* alpha, double* beta, int* steps_done, tci_tensor x);
+
+/* ------------------------------------------- U(1) block-sparse H_eff
+ * Charge-conserving (U(1)) block-sparse tensors are listed as future work of
+ * TCI (Sec. IV); the operation is the two-site H_eff above applied to the
+ * zero-filled tensors, computed block by block over the charge-allowed
+ * blocks only.  Charges: sector_charge[nsec] (distinct; bond sector i has
+ * dimension sector_dim[i]), phys_charge[2] of the physical states,
+ * mpo_charge[5] of the MPO channels (W[wl,wr,s,t] != 0 only if
+ * phys_charge[s]-phys_charge[t] = mpo_charge[wl]-mpo_charge[wr]).  These four
+ * arrays are HOST pointers.
+ * Packed layouts (device, FP32, each block row-major, blocks back to back):
+ *   psi/out: blocks (ia, t1, t2, ib) for ia = 0.., t1 = 0..1, t2 = 0..1 in
+ *            that nesting order, present iff q_ib = q_ia + c(t1) + c(t2);
+ *            block shape [dim ia, dim ib];
+ *   L, R:    blocks (i, w, j) for i = 0.., w = 0..4, present iff
+ *            q_j = q_i + Delta(w); block shape [dim i, dim j]
+ * (q = sector_charge, c = phys_charge, Delta = mpo_charge).  W is the dense
+ * device F64 MPO [5,5,2,2].  The plan packs L and R into the tensor-core
+ * operand layout once, so the caller may free them after creation.
+ * Arithmetic: the context precision (must be SPLIT_BF16 or SPLIT_BF16_3).
+ * Every block GEMM of one matvec stage runs in a single grouped persistent
+ * launch.  Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision), ALLOC, CUDA. */
+tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const int32_t* sector_charge,
+                                   const int64_t* sector_dim, const int32_t* phys_charge,
+                                   const int32_t* mpo_charge, const float* L_packed,
+                                   const float* R_packed, const double* W, tci_bs_plan* plan);
+tci_status tci_bs_plan_destroy(tci_bs_plan* plan);
+/* out = H_eff psi on packed block-sparse vectors (device FP32, length
+ * tci_bs_psi_size).  Async on the context stream; psi and out must not
+ * overlap. */
+tci_status tci_bs_heff_apply(tci_bs_plan plan, const float* psi, float* out);
+/* Algorithmic flops of one matvec: 2 m n k over every charge-allowed block
+ * product of both GEMM stages plus 2 d^4 Dw^2 per element of every sector
+ * pair that carries an intermediate block.  -1/0 for an invalid plan. */
+double tci_bs_heff_flops(tci_bs_plan plan);
+int64_t tci_bs_psi_size(tci_bs_plan plan);
+
+/* ------------------------------------------- batched TEBD theta
+ * The theta formation and gate application of the paper's iTEBD listing
+ * (App. A), batched over independent bonds:
+ *   theta_i[a,s1,s2,b] = sum_{t1,t2,c} G_i[s1,s2,t1,t2] A_i[a,t1,c] B_i[c,t2,b]
+ * (G's LAST two indices are summed; the listing's "ijkl","jkmn"->"imnl" sums
+ * the gate's FIRST two -- the two agree for symmetric gates.)  complex64,
+ * d = 2.  chi[nbonds] is a HOST array of bond dimensions.  Packed device
+ * layouts (interleaved re/im, bonds back to back, each row-major):
+ * A_i [chi_i,2,chi_i], B_i [chi_i,2,chi_i], G_i [2,2,2,2] (16 values per
+ * bond), theta_i [chi_i,2,2,chi_i].  Arithmetic: the context precision at
+ * plan creation (SPLIT_BF16 or SPLIT_BF16_3): the complex product uses three
+ * real split-BF16 tensor-core GEMMs per bond (3M), all bonds in one grouped
+ * persistent launch.  Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision),
+ * ALLOC, CUDA. */
+tci_status tci_tebd_plan_create(tci_context ctx, int nbonds, const int64_t* chi, tci_tebd_plan* plan);
+tci_status tci_tebd_plan_destroy(tci_tebd_plan* plan);
+/* theta = batched theta(A, B, G); async on the context stream. */
+tci_status tci_tebd_apply(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta);
+/* Algorithmic flops: sum_i 8 chi_i^3 d^2 + 8 chi_i^2 d^4 (8 real flops per complex multiply-add). */
+double tci_tebd_flops(tci_tebd_plan plan);
 
 #ifdef __cplusplus
 }

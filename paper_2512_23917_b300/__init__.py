@@ -82,6 +82,15 @@ SIGNATURES = [
     ("tci_heff_apply_timed", C.c_int, [_p, _p, _p, C.POINTER(C.c_float)]),
     ("tci_heff_flops", C.c_double, [_p]),
     ("tci_heff_apply_noalloc", C.c_int, [_p, _p, _p, _p, _p, C.c_int64, C.c_int64, _p]),
+    ("tci_bs_heff_plan_create", C.c_int, [_p, C.c_int, _i32p, _i64p, _i32p, _i32p, _p, _p, _p, C.POINTER(_p)]),
+    ("tci_bs_plan_destroy", C.c_int, [C.POINTER(_p)]),
+    ("tci_bs_heff_apply", C.c_int, [_p, _p, _p]),
+    ("tci_bs_heff_flops", C.c_double, [_p]),
+    ("tci_bs_psi_size", C.c_int64, [_p]),
+    ("tci_tebd_plan_create", C.c_int, [_p, C.c_int, _i64p, C.POINTER(_p)]),
+    ("tci_tebd_plan_destroy", C.c_int, [C.POINTER(_p)]),
+    ("tci_tebd_apply", C.c_int, [_p, _p, _p, _p, _p]),
+    ("tci_tebd_flops", C.c_double, [_p]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
 ]
 
@@ -400,6 +409,101 @@ class HeffPlan:
     def close(self):
         if self.handle:
             _check(lib.tci_heff_plan_destroy(C.byref(self.handle)))
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class BsHeffPlan:
+    """U(1) block-sparse H_eff plan (see include/tci_b300.h, tci_bs_heff_plan_create).
+
+    ``sector_charge``/``sector_dim`` list the bond sectors; ``L_packed`` and
+    ``R_packed`` are CUDA float32 tensors holding the blocks in the canonical
+    packed order; ``W`` a CUDA float64 [5,5,2,2] tensor.
+    """
+
+    def __init__(self, ctx: Context, sector_charge, sector_dim, phys_charge, mpo_charge, L_packed, R_packed, W,
+                 precision="split_bf16"):
+        ctx.set_precision(precision)
+        self.ctx = ctx
+        self.handle = _p()
+        n = len(sector_charge)
+        qc = (C.c_int32 * n)(*[int(q) for q in sector_charge])
+        qd = (C.c_int64 * n)(*[int(d) for d in sector_dim])
+        pc = (C.c_int32 * len(phys_charge))(*[int(c) for c in phys_charge])
+        mc = (C.c_int32 * len(mpo_charge))(*[int(c) for c in mpo_charge])
+        _check(lib.tci_bs_heff_plan_create(ctx.handle, n, qc, qd, pc, mc, _p(L_packed.data_ptr()),
+                                           _p(R_packed.data_ptr()), _p(W.data_ptr()), C.byref(self.handle)),
+               ctx.handle)
+
+    @property
+    def flops(self) -> float:
+        return lib.tci_bs_heff_flops(self.handle)
+
+    @property
+    def psi_size(self) -> int:
+        return lib.tci_bs_psi_size(self.handle)
+
+    def apply(self, psi_packed, out_packed):
+        _check(lib.tci_bs_heff_apply(self.handle, _p(psi_packed.data_ptr()), _p(out_packed.data_ptr())),
+               self.ctx.handle)
+        return out_packed
+
+    def close(self):
+        if self.handle:
+            _check(lib.tci_bs_plan_destroy(C.byref(self.handle)))
+            self.handle = _p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pack_blocks(blocks: dict, keys) -> np.ndarray:
+    """Concatenate blocks (row-major) in the given key order into one float32 vector."""
+    if not keys:
+        return np.zeros(0, dtype=np.float32)
+    return np.concatenate([np.ascontiguousarray(blocks[k], dtype=np.float32).ravel() for k in keys])
+
+
+def unpack_blocks(vec: np.ndarray, keys, shapes) -> dict:
+    out, off = {}, 0
+    for k in keys:
+        r, c = shapes[k]
+        out[k] = vec[off:off + r * c].reshape(r, c)
+        off += r * c
+    return out
+
+
+class TebdPlan:
+    """Batched TEBD theta plan (see include/tci_b300.h, tci_tebd_plan_create)."""
+
+    def __init__(self, ctx: Context, chis, precision="split_bf16"):
+        ctx.set_precision(precision)
+        self.ctx = ctx
+        self.chis = [int(c) for c in chis]
+        self.handle = _p()
+        arr = (C.c_int64 * len(self.chis))(*self.chis)
+        _check(lib.tci_tebd_plan_create(ctx.handle, len(self.chis), arr, C.byref(self.handle)), ctx.handle)
+
+    @property
+    def flops(self) -> float:
+        return lib.tci_tebd_flops(self.handle)
+
+    def apply(self, A_packed, B_packed, G_packed, theta_packed):
+        _check(lib.tci_tebd_apply(self.handle, _p(A_packed.data_ptr()), _p(B_packed.data_ptr()),
+                                  _p(G_packed.data_ptr()), _p(theta_packed.data_ptr())), self.ctx.handle)
+        return theta_packed
+
+    def close(self):
+        if self.handle:
+            _check(lib.tci_tebd_plan_destroy(C.byref(self.handle)))
             self.handle = _p()
 
     def __del__(self):

@@ -1,0 +1,538 @@
+// U(1) block-sparse two-site H_eff (charge-conserving tensors; the paper
+// names symmetric tensors as future TCI work in Sec. IV).  The result is the
+// dense H_eff of the zero-filled tensors restricted to the allowed blocks;
+// only charge-allowed block products are computed.
+//
+// Blocks and their canonical packed order (each block row-major, blocks
+// concatenated without gaps):
+//   psi/out (ia, t1, t2, ib)  q_ib = q_ia + c(t1) + c(t2)   for ia, t1, t2
+//   L (ia, w, ja), R (ib, w, jb)   q_j = q_i + Delta(w)        for i, w
+// where q are the sector charges, c the physical charges and Delta the MPO
+// channel charges; sector indices follow the caller's sector order.
+//
+// Per matvec (all block GEMMs of a stage in ONE grouped persistent launch):
+//   1. split psi blocks into bfloat16 pieces (K-major, padded to 8)
+//   2. grouped GEMM1: for each psi block P = (ia', t1, t2, ib'):
+//        U_P[a', (wr, b)] = sum_b' psi_P[a', b'] Rg_ib'[(wr, b), b']
+//      Rg_ib' stacks the R blocks (ib(wr), wr, ib') along rows (plan time)
+//   3. W.W tasks, one per sector pair (ja, ib): V[(s1 s2, b), (wl, a')] from
+//      the (t1 t2, wr) sub-blocks of the U_P that exist, written as pieces
+//      straight into GEMM2's K-major operand
+//   4. grouped GEMM2: for each output block O = (ia, s1, s2, ib):
+//        out_O[a, b] = sum_{wl, a'} Lg_ia[a, (wl, a')] Vg_O[b, (wl, a')]
+//      Lg_ia concatenates the L blocks (ia, wl, ja(wl)) along K (plan time)
+#include <cuda_bf16.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <vector>
+
+#include "tci_internal.cuh"
+
+#define BS_DW 5
+#define BS_D 2
+
+constexpr int kBsMagic = 0xb5b5e001;
+
+namespace {
+
+int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
+int64_t al256(int64_t bytes) { return (bytes + 255) / 256 * 256; }
+
+// split FP32 rows into bf16 piece planes [3][rows][Kp] (zero in k >= K)
+struct SplitJob {
+  int64_t src_off;   // element offset of the block in the packed FP32 source
+  int64_t rows, K, ld_src, Kp;
+  int64_t dst_off;   // bf16 element offset of plane 0 in the destination arena
+};
+
+__global__ void k_bs_split(const SplitJob* __restrict__ jobs, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
+  const SplitJob j = jobs[blockIdx.y];
+  const int64_t plane = j.rows * j.Kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / j.Kp, k = i - r * j.Kp;
+    __nv_bfloat16 h, m, l;
+    if (k < j.K) {
+      const float x = src[j.src_off + r * j.ld_src + k];
+      h = __float2bfloat16_rn(x);
+      const float r1 = x - __bfloat162float(h);
+      m = __float2bfloat16_rn(r1);
+      l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    } else {
+      h = m = l = __float2bfloat16_rn(0.f);
+    }
+    __nv_bfloat16* d = dst + j.dst_off;
+    d[i] = h;
+    d[plane + i] = m;
+    d[2 * plane + i] = l;
+  }
+}
+
+// split a FP32 block [rows][K] (row stride ld_src) into the column slice
+// [dst_off + r*dst_ld + k] of bf16 piece planes dst_plane elements apart
+struct SliceJob {
+  int64_t src_off, rows, K, ld_src, dst_off, dst_ld, dst_plane;
+};
+
+__global__ void k_bs_split_slice(const SliceJob* __restrict__ jobs, const float* __restrict__ src,
+                                 __nv_bfloat16* __restrict__ dst) {
+  const SliceJob j = jobs[blockIdx.y];
+  const int64_t n = j.rows * j.K;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / j.K, k = i - r * j.K;
+    const float x = src[j.src_off + r * j.ld_src + k];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    const int64_t o = j.dst_off + r * j.dst_ld + k;
+    dst[o] = h;
+    dst[j.dst_plane + o] = m;
+    dst[2 * j.dst_plane + o] = l;
+  }
+}
+
+template <typename Job>
+tci_status run_jobs(tci_context ctx, const std::vector<Job>& jobs, int64_t max_work,
+                    void (*kern)(const Job*, const float*, __nv_bfloat16*), const float* src, __nv_bfloat16* dst) {
+  if (jobs.empty()) return TCI_OK;
+  Job* dj = nullptr;
+  TCI_TRY(tci_dev_alloc(ctx, sizeof(Job) * jobs.size(), (void**)&dj));
+  cudaError_t e = cudaMemcpy(dj, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_work + 255) / 256)), (unsigned)jobs.size());
+    kern<<<grid, 256, 0, ctx->stream>>>(dj, src, dst);
+    e = cudaStreamSynchronize(ctx->stream);
+  }
+  tci_dev_free(dj);
+  if (e != cudaSuccess) return tci_cuda_fail(ctx, e, "block-sparse pack");
+  return TCI_OK;
+}
+
+// W.W task over a sector pair (ja, ib): inputs U[(a', t), (b, wr)] for the
+// (t, wr) that exist; outputs V[(s, b), (wl, a')] for the (wl, s) that exist.
+struct WWTask {
+  const float* u[4 * BS_DW];   // element (a'=0, b=0) of input (t, wr), or null
+  int64_t ldu[4 * BS_DW];
+  int64_t v[4 * BS_DW];        // bf16 element offset of output (wl, s) (b=0, a'=0) in plane 0, or -1
+  int64_t ldv[4 * BS_DW];      // row stride (b -> b+1) of that output
+  int64_t plane[4 * BS_DW];    // plane stride of that output's piece buffer
+  int64_t na, nb;              // sector dims of a' (ja) and b (ib)
+};
+
+struct WWCoef {
+  float ww[BS_DW * 4 * BS_DW * 4];   // [wl][s][wr][t]
+};
+
+__global__ void __launch_bounds__(256) k_bs_ww(const WWTask* __restrict__ tasks, const WWCoef coef,
+                                               __nv_bfloat16* __restrict__ V) {
+  const WWTask& T = tasks[blockIdx.y];
+  const int64_t n = T.na * T.nb;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / T.na, ap = i - b * T.na;   // a' fastest: coalesced V writes
+    float in[4 * BS_DW];
+#pragma unroll
+    for (int q = 0; q < 4 * BS_DW; ++q) in[q] = T.u[q] ? T.u[q][ap * T.ldu[q] + b] : 0.f;
+#pragma unroll
+    for (int wl = 0; wl < BS_DW; ++wl)
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const int o = wl * 4 + s;
+        if (T.v[o] < 0) continue;
+        float acc = 0.f;
+#pragma unroll
+        for (int wr = 0; wr < BS_DW; ++wr)
+#pragma unroll
+          for (int t = 0; t < 4; ++t) acc = fmaf(coef.ww[((wl * 4 + s) * BS_DW + wr) * 4 + t], in[t * BS_DW + wr], acc);
+        const __nv_bfloat16 h = __float2bfloat16_rn(acc);
+        const float r1 = acc - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        const int64_t off = T.v[o] + b * T.ldv[o] + ap;
+        V[off] = h;
+        V[T.plane[o] + off] = m;
+        V[2 * T.plane[o] + off] = l;
+      }
+  }
+}
+
+__global__ void k_bs_ww_precompute(const double* __restrict__ W, float* __restrict__ out) {
+  // out[((wl*4 + s1*2+s2)*Dw + wr)*4 + t1*2+t2] = sum_wm W[wl,wm,s1,t1] W[wm,wr,s2,t2]
+  for (int i = threadIdx.x; i < BS_DW * 4 * BS_DW * 4; i += blockDim.x) {
+    int r = i;
+    const int t = r % 4; r /= 4;
+    const int wr = r % BS_DW; r /= BS_DW;
+    const int s = r % 4; r /= 4;
+    const int wl = r;
+    const int s1 = s / 2, s2 = s % 2, t1 = t / 2, t2 = t % 2;
+    double acc = 0.0;
+    for (int wm = 0; wm < BS_DW; ++wm)
+      acc += W[((wl * BS_DW + wm) * 2 + s1) * 2 + t1] * W[((wm * BS_DW + wr) * 2 + s2) * 2 + t2];
+    out[i] = (float)acc;
+  }
+}
+
+}  // namespace
+
+struct tci_bs_plan_s {
+  int magic;
+  tci_context ctx;
+  int products, chunk_k, xchunk_k;
+  int64_t psi_elems;          // packed psi/out element count
+  double flops;               // algorithmic flops of one matvec
+  // device buffers
+  void* arena = nullptr;      // bf16 pieces: psi blocks, Rg, Lg, Vg
+  float* U = nullptr;         // GEMM1 outputs
+  float* out_stage = nullptr; // GEMM2 writes here (the group table holds fixed pointers)
+  SplitJob* d_psi_jobs = nullptr;
+  WWTask* d_tasks = nullptr;
+  int n_psi_jobs = 0, n_tasks = 0;
+  int64_t max_psi_plane = 0, max_task_elems = 0;
+  tci_split_group* g1 = nullptr;
+  tci_split_group* g2 = nullptr;
+  WWCoef coef;
+  int64_t n_gemm1 = 0, n_gemm2 = 0;
+};
+
+struct BsBlock {
+  int i, a, b, j;      // psi: (ia, t1, t2, ib); env: (i, w, -, j)
+  int64_t off;         // element offset in the packed buffer
+};
+
+extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const int32_t* sector_charge,
+                                              const int64_t* sector_dim, const int32_t* phys_charge,
+                                              const int32_t* mpo_charge, const float* L_packed,
+                                              const float* R_packed, const double* W, tci_bs_plan* out) {
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "bs_heff_plan_create");
+  if (!out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_plan_create: NULL output");
+  *out = nullptr;
+  if (nsec <= 0 || !sector_charge || !sector_dim || !phys_charge || !mpo_charge || !L_packed || !R_packed || !W)
+    return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_plan_create: NULL argument or no sectors");
+  if (ctx->precision == TCI_PREC_NATIVE)
+    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "bs_heff_plan_create: the block-sparse path runs in a split precision");
+  std::map<int, int> idx;
+  for (int i = 0; i < nsec; ++i) {
+    if (sector_dim[i] <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_plan_create: sector dims must be positive");
+    if (idx.count(sector_charge[i])) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_plan_create: repeated sector charge");
+    idx[sector_charge[i]] = i;
+  }
+  auto sec = [&](int q) {
+    auto it = idx.find(q);
+    return it == idx.end() ? -1 : it->second;
+  };
+  const int64_t* dim = sector_dim;
+  // ---------------------------------------------------------------- block lists
+  std::vector<BsBlock> P, Lb, Rb;   // psi, L, R
+  std::map<long, int> Pidx, Lidx, Ridx;
+  int64_t off = 0;
+  for (int ia = 0; ia < nsec; ++ia)
+    for (int t1 = 0; t1 < BS_D; ++t1)
+      for (int t2 = 0; t2 < BS_D; ++t2) {
+        const int ib = sec(sector_charge[ia] + phys_charge[t1] + phys_charge[t2]);
+        if (ib < 0) continue;
+        Pidx[((long)ia * 4 + t1 * 2 + t2) * 4096 + ib] = (int)P.size();
+        P.push_back({ia, t1, t2, ib, off});
+        off += dim[ia] * dim[ib];
+      }
+  const int64_t psi_elems = off;
+  off = 0;
+  for (int ia = 0; ia < nsec; ++ia)
+    for (int w = 0; w < BS_DW; ++w) {
+      const int j = sec(sector_charge[ia] + mpo_charge[w]);
+      if (j < 0) continue;
+      Lidx[((long)ia * BS_DW + w)] = (int)Lb.size();
+      Lb.push_back({ia, w, 0, j, off});
+      off += dim[ia] * dim[j];
+    }
+  Rb = Lb;   // same structure and packed offsets
+  for (auto& kv : Lidx) Ridx[kv.first] = kv.second;
+
+  tci_bs_plan p = new tci_bs_plan_s();
+  p->magic = kBsMagic;
+  p->ctx = ctx;
+  p->products = ctx->precision == TCI_PREC_SPLIT_BF16_3 ? 3 : 6;
+  p->chunk_k = ctx->split_chunk_k;
+  p->xchunk_k = ctx->split_xchunk_k;
+  p->psi_elems = psi_elems;
+  auto fail = [&](tci_status s) {
+    tci_bs_plan pp = p;
+    tci_bs_plan_destroy(&pp);
+    return s;
+  };
+
+  // ---------------------------------------------------------------- arena layout
+  // Rg[ib'] : rows (wr, b) over R blocks (ib(wr), wr, ib'), K = dim[ib']
+  struct Stack {
+    int64_t rows = 0, K = 0, Kp = 0, off = 0;   // off: bf16 elements (plane 0)
+    std::vector<int64_t> row_off;               // per w (or -1)
+    std::vector<int> blk;                       // block per w (or -1)
+  };
+  std::vector<Stack> Rg(nsec), Lg(nsec);
+  int64_t arena = 0;   // in bf16 elements, each buffer 256-byte aligned
+  auto take = [&](int64_t elems) {
+    const int64_t o = arena;
+    arena += al256(elems * 2) / 2;
+    return o;
+  };
+  std::vector<SliceJob> init_jobs_R;
+  for (int jb = 0; jb < nsec; ++jb) {
+    Stack& S = Rg[jb];
+    S.row_off.assign(BS_DW, -1);
+    S.blk.assign(BS_DW, -1);
+    S.K = dim[jb];
+    S.Kp = pad8(S.K);
+    for (int w = 0; w < BS_DW; ++w) {
+      const int ib = sec(sector_charge[jb] - mpo_charge[w]);   // R block (ib, w, jb): q_jb = q_ib + Delta(w)
+      if (ib < 0) continue;
+      S.row_off[w] = S.rows;
+      S.blk[w] = Ridx[(long)ib * BS_DW + w];
+      S.rows += dim[ib];
+    }
+    if (S.rows) S.off = take(3 * S.rows * S.Kp);
+    for (int w = 0; w < BS_DW; ++w)
+      if (S.blk[w] >= 0) {
+        // rows of R block (ib, w, jb) -> rows [row_off[w], + dim ib) of every plane of the stack
+        const BsBlock& B = Rb[S.blk[w]];
+        init_jobs_R.push_back({B.off, dim[B.i], S.K, S.K, S.off + S.row_off[w] * S.Kp, S.Kp, S.rows * S.Kp});
+      }
+  }
+  for (int ia = 0; ia < nsec; ++ia) {
+    Stack& S = Lg[ia];
+    S.row_off.assign(BS_DW, -1);   // here: K offset of each wl
+    S.blk.assign(BS_DW, -1);
+    S.rows = dim[ia];
+    for (int w = 0; w < BS_DW; ++w) {
+      auto it = Lidx.find((long)ia * BS_DW + w);
+      if (it == Lidx.end()) continue;
+      S.row_off[w] = S.K;
+      S.blk[w] = it->second;
+      S.K += dim[Lb[it->second].j];
+    }
+    S.Kp = pad8(S.K);
+    if (S.K) S.off = take(3 * S.rows * S.Kp);
+  }
+  // psi pieces per block: [3][dim ia][pad8(dim ib)]
+  std::vector<int64_t> Ppiece(P.size());
+  std::vector<SplitJob> psi_jobs;
+  for (size_t k = 0; k < P.size(); ++k) {
+    const BsBlock& B = P[k];
+    const int64_t K = dim[B.j], Kp = pad8(K);
+    Ppiece[k] = take(3 * dim[B.i] * Kp);
+    psi_jobs.push_back({B.off, dim[B.i], K, K, Kp, Ppiece[k]});
+    p->max_psi_plane = std::max(p->max_psi_plane, dim[B.i] * Kp);
+  }
+  // Vg per output block O (same structure as psi): [3][dim ib][Lg[ia].Kp]
+  std::vector<int64_t> Vpiece(P.size());
+  for (size_t k = 0; k < P.size(); ++k) {
+    const BsBlock& O = P[k];
+    Vpiece[k] = take(3 * dim[O.j] * std::max<int64_t>(Lg[O.i].Kp, 8));
+  }
+  // U per psi block: [dim ia'][Rg[ib'].rows] FP32
+  std::vector<int64_t> Uoff(P.size());
+  int64_t uelems = 0;
+  for (size_t k = 0; k < P.size(); ++k) {
+    Uoff[k] = uelems;
+    uelems += (al256(dim[P[k].i] * Rg[P[k].j].rows * 4)) / 4;
+  }
+  tci_status s;
+  if ((s = tci_dev_alloc(ctx, std::max<int64_t>(arena, 8) * 2, &p->arena)) != TCI_OK) return fail(s);
+  if ((s = tci_dev_alloc(ctx, std::max<int64_t>(uelems, 1) * 4, (void**)&p->U)) != TCI_OK) return fail(s);
+  __nv_bfloat16* A = (__nv_bfloat16*)p->arena;
+  cudaError_t e = cudaMemsetAsync(p->arena, 0, std::max<int64_t>(arena, 8) * 2, ctx->stream);
+  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan memset"));
+
+  // ---------------------------------------------------------------- pack R and L pieces (once)
+  {
+    int64_t mx = 0;
+    for (auto& j : init_jobs_R) mx = std::max(mx, j.rows * j.K);
+    if ((s = run_jobs<SliceJob>(ctx, init_jobs_R, mx, k_bs_split_slice, R_packed, A)) != TCI_OK) return fail(s);
+    std::vector<SliceJob> lj;
+    mx = 0;
+    for (int ia = 0; ia < nsec; ++ia) {
+      const Stack& S = Lg[ia];
+      for (int w = 0; w < BS_DW; ++w)
+        if (S.blk[w] >= 0) {
+          const BsBlock& B = Lb[S.blk[w]];
+          lj.push_back({B.off, dim[ia], dim[B.j], dim[B.j], S.off + S.row_off[w], S.Kp, S.rows * S.Kp});
+          mx = std::max(mx, dim[ia] * dim[B.j]);
+        }
+    }
+    if ((s = run_jobs<SliceJob>(ctx, lj, mx, k_bs_split_slice, L_packed, A)) != TCI_OK) return fail(s);
+  }
+
+  // ---------------------------------------------------------------- GEMM1 group
+  std::vector<tci_split_problem> g1;
+  for (size_t k = 0; k < P.size(); ++k) {
+    const BsBlock& B = P[k];
+    const Stack& S = Rg[B.j];
+    if (!S.rows) continue;
+    g1.push_back({A + Ppiece[k], A + S.off, dim[B.i], S.rows, S.Kp, p->U + Uoff[k], 1, S.rows, 1});
+  }
+  if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1)) != TCI_OK) return fail(s);
+  p->n_gemm1 = (int64_t)g1.size();
+  // ---------------------------------------------------------------- W.W tasks
+  std::map<long, int> task_of;   // (ja, ib) -> task
+  std::vector<WWTask> tasks;
+  auto task = [&](int ja, int ib) -> WWTask& {
+    const long key = (long)ja * 4096 + ib;
+    auto it = task_of.find(key);
+    if (it != task_of.end()) return tasks[it->second];
+    WWTask T;
+    memset(&T, 0, sizeof T);
+    for (int q = 0; q < 4 * BS_DW; ++q) T.v[q] = -1;
+    T.na = dim[ja];
+    T.nb = dim[ib];
+    task_of[key] = (int)tasks.size();
+    tasks.push_back(T);
+    return tasks.back();
+  };
+  for (size_t k = 0; k < P.size(); ++k) {           // inputs
+    const BsBlock& B = P[k];                        // (ja, t1, t2, ib')
+    const Stack& S = Rg[B.j];
+    const int t = B.a * 2 + B.b;
+    for (int wr = 0; wr < BS_DW; ++wr) {
+      if (S.blk[wr] < 0) continue;
+      const int ib = Rb[S.blk[wr]].i;
+      WWTask& T = task(B.i, ib);
+      T.u[t * BS_DW + wr] = p->U + Uoff[k] + S.row_off[wr];
+      T.ldu[t * BS_DW + wr] = S.rows;
+    }
+  }
+  for (size_t k = 0; k < P.size(); ++k) {           // outputs
+    const BsBlock& O = P[k];                        // (ia, s1, s2, ib)
+    const Stack& S = Lg[O.i];
+    const int sidx = O.a * 2 + O.b;
+    for (int wl = 0; wl < BS_DW; ++wl) {
+      if (S.blk[wl] < 0) continue;
+      const int ja = Lb[S.blk[wl]].j;
+      auto it = task_of.find((long)ja * 4096 + O.j);
+      if (it == task_of.end()) continue;            // no U feeds this V sub-block: it stays zero
+      WWTask& T = tasks[it->second];
+      T.v[wl * 4 + sidx] = Vpiece[k] + S.row_off[wl];
+      T.ldv[wl * 4 + sidx] = S.Kp;
+      T.plane[wl * 4 + sidx] = dim[O.j] * S.Kp;
+    }
+  }
+  p->n_tasks = (int)tasks.size();
+  for (auto& T : tasks) p->max_task_elems = std::max(p->max_task_elems, T.na * T.nb);
+  if (!tasks.empty()) {
+    if ((s = tci_dev_alloc(ctx, sizeof(WWTask) * tasks.size(), (void**)&p->d_tasks)) != TCI_OK) return fail(s);
+    e = cudaMemcpy(p->d_tasks, tasks.data(), sizeof(WWTask) * tasks.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: tasks"));
+  }
+  // ---------------------------------------------------------------- GEMM2 group
+  std::vector<tci_split_problem> g2;
+  std::vector<int64_t> out_off;
+  for (size_t k = 0; k < P.size(); ++k) {
+    const BsBlock& O = P[k];
+    const Stack& S = Lg[O.i];
+    if (!S.K) continue;
+    // C is filled in per apply (output pointer); store the packed offset for now in C.
+    g2.push_back({A + S.off, A + Vpiece[k], dim[O.i], dim[O.j], S.Kp, (void*)(uintptr_t)(O.off * 4), 1, dim[O.j], 1});
+  }
+  // the group table holds fixed pointers: GEMM2 writes the plan's output staging buffer
+  if ((s = tci_dev_alloc(ctx, std::max<int64_t>(psi_elems, 1) * 4, (void**)&p->out_stage)) != TCI_OK) return fail(s);
+  for (auto& q : g2) q.C = (char*)p->out_stage + (uintptr_t)q.C;
+  // output blocks that no GEMM writes stay zero
+  e = cudaMemsetAsync(p->out_stage, 0, std::max<int64_t>(psi_elems, 1) * 4, ctx->stream);
+  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan memset"));
+  if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2)) != TCI_OK) return fail(s);
+  p->n_gemm2 = (int64_t)g2.size();
+  // psi split jobs
+  p->n_psi_jobs = (int)psi_jobs.size();
+  if (!psi_jobs.empty()) {
+    if ((s = tci_dev_alloc(ctx, sizeof(SplitJob) * psi_jobs.size(), (void**)&p->d_psi_jobs)) != TCI_OK) return fail(s);
+    e = cudaMemcpy(p->d_psi_jobs, psi_jobs.data(), sizeof(SplitJob) * psi_jobs.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: psi jobs"));
+  }
+  // W.W coefficients (FP64 product on the device, FP32 copy for the kernel arguments)
+  {
+    float* d = nullptr;
+    if ((s = tci_dev_alloc(ctx, sizeof(WWCoef), (void**)&d)) != TCI_OK) return fail(s);
+    k_bs_ww_precompute<<<1, 256, 0, ctx->stream>>>(W, d);
+    e = cudaMemcpyAsync(p->coef.ww, d, sizeof(WWCoef), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    tci_dev_free(d);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W"));
+  }
+  // ---------------------------------------------------------------- algorithmic flops
+  {
+    double fl = 0.0;
+    std::map<long, int> ublk;   // sector pairs (ja, ib) carrying U
+    for (size_t k = 0; k < P.size(); ++k) {
+      const BsBlock& B = P[k];
+      const Stack& S = Rg[B.j];
+      for (int w = 0; w < BS_DW; ++w)
+        if (S.blk[w] >= 0) {
+          const int ib = Rb[S.blk[w]].i;
+          fl += 2.0 * dim[B.i] * dim[ib] * dim[B.j];
+          ublk[(long)B.i * 4096 + ib] = 1;
+        }
+    }
+    for (auto& kv : ublk) fl += 2.0 * dim[kv.first / 4096] * dim[kv.first % 4096] * 16.0 * BS_DW * BS_DW;
+    for (size_t k = 0; k < P.size(); ++k) {
+      const BsBlock& O = P[k];
+      const Stack& S = Lg[O.i];
+      for (int w = 0; w < BS_DW; ++w)
+        if (S.blk[w] >= 0) {
+          const int ja = Lb[S.blk[w]].j;
+          if (ublk.count((long)ja * 4096 + O.j)) fl += 2.0 * dim[O.i] * dim[O.j] * dim[ja];
+        }
+    }
+    p->flops = fl;
+  }
+  e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan"));
+  vs.info = "blocks=" + std::to_string(P.size()) + " gemm1=" + std::to_string(p->n_gemm1) +
+            " gemm2=" + std::to_string(p->n_gemm2) + " ww_tasks=" + std::to_string(p->n_tasks);
+  *out = p;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_bs_plan_destroy(tci_bs_plan* pp) {
+  if (!pp || !*pp || (*pp)->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_plan_destroy: invalid plan");
+  tci_bs_plan p = *pp;
+  if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
+  tci_split_group_destroy(p->g1);
+  tci_split_group_destroy(p->g2);
+  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks};
+  for (void* b : bufs) tci_dev_free(b);
+  p->magic = 0;
+  delete p;
+  *pp = nullptr;
+  return TCI_OK;
+}
+
+extern "C" double tci_bs_heff_flops(tci_bs_plan p) {
+  if (!p || p->magic != kBsMagic) return 0.0;
+  return p->flops;
+}
+
+extern "C" int64_t tci_bs_psi_size(tci_bs_plan p) {
+  if (!p || p->magic != kBsMagic) return -1;
+  return p->psi_elems;
+}
+
+extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* out) {
+  if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_heff_apply: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "bs_heff_apply");
+  if (!psi || !out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_apply: NULL buffer");
+  if (p->n_psi_jobs) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
+    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
+  }
+  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
+  if (p->n_tasks) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (p->max_task_elems + 255) / 256)), (unsigned)p->n_tasks);
+    k_bs_ww<<<grid, 256, 0, ctx->stream>>>(p->d_tasks, p->coef, (__nv_bfloat16*)p->arena);
+  }
+  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
+  TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
+  return TCI_OK;
+}

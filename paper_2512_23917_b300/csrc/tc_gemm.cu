@@ -33,6 +33,11 @@
 #include <cuda_bf16.h>
 
 #include "ptx_sm100.cuh"
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
 #include "tci_internal.cuh"
 
 namespace {
@@ -53,16 +58,37 @@ constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 constexpr int COLS_PER_WARP = TBN / 2;           // two epilogue warps per TMEM lane quadrant
 
-struct GemmParams {
-  int64_t M, N;
+// One GEMM of a (possibly grouped) launch.  In a grouped launch the table
+// lives in device memory, sorted by decreasing K so the longest tiles are
+// scheduled first; tiles of problem i are [tile_begin, tile_begin + num_m*num_n).
+struct alignas(64) GemmProblem {
+  CUtensorMap tmA;   // bf16 pieces [3][M][Kp], box {32, 128, 3}
+  CUtensorMap tmB;   // bf16 pieces [3][N][Kp], box {32, 128, 3}
   void* C;
-  int64_t scm, scn;
-  int out_f32;   // 0: FP64 output, 1: FP32 output
-  int num_m, num_n, num_kb;
-  int kb_d1, kb_x;   // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
+  int64_t M, N, scm, scn;
+  int num_m, num_n, num_kb, tile_begin;
+  int out_f32, pad0, pad1, pad2;
+};
+
+struct GemmParams {
+  const GemmProblem* table;   // grouped launches only
+  int nprob, num_tiles;
+  int kb_d1, kb_x;            // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
   int products;
   int* status;
 };
+
+template <bool G>
+__device__ __forceinline__ const GemmProblem* find_problem(int tile, const GemmProblem* single, const GemmParams& p) {
+  if (!G) return single;
+  int lo = 0, hi = p.nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (p.table[mid].tile_begin <= tile) lo = mid;
+    else hi = mid - 1;
+  }
+  return &p.table[lo];
+}
 
 // Error-free sum in FP32: s + e == a + b exactly (Knuth TwoSum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -103,8 +129,9 @@ __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, u
   return true;
 }
 
+template <bool G>
 __global__ void __launch_bounds__(NTHREADS, 1)
-    k_split_bf16_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, GemmParams p) {
+    k_split_bf16_gemm(const __grid_constant__ GemmProblem single, const GemmParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
@@ -135,9 +162,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
-  if (warp == 0 && lane == 0) {
-    ptx::tma_prefetch_desc(&tmA);
-    ptx::tma_prefetch_desc(&tmB);
+  if (!G && warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&single.tmA);
+    ptx::tma_prefetch_desc(&single.tmB);
   }
   if (warp == 1) {
     ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
@@ -148,7 +175,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const int num_tiles = p.num_m * p.num_n;
+  const int num_tiles = p.num_tiles;
 
   if (warp == 0) {
     // ------------------------------------------------------------ producer
@@ -157,14 +184,17 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t phase = 0;
       uint32_t issued = 0, issued_phase = 0;   // bit s: stage s used / its last phase
       for (int tile = blockIdx.x; tile < num_tiles && !*abort_flag; tile += gridDim.x) {
-        const int mb = tile % p.num_m, nb = tile / p.num_m;
-        for (int kb = 0; kb < p.num_kb; ++kb) {
+        const GemmProblem* pr = find_problem<G>(tile, &single, p);
+        const int lt = tile - pr->tile_begin;
+        const int mb = lt % pr->num_m, nb = lt / pr->num_m;
+        const int nkb = pr->num_kb;
+        for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
           const uint32_t fb = ptx::smem_u32(&full[stage]);
           ptx::mbar_arrive_expect_tx(fb, STAGE_BYTES);
           uint8_t* sa = smem + stage * STAGE_BYTES;
-          ptx::tma_load_3d(ptx::smem_u32(sa), &tmA, fb, kb * TBK, mb * TBM, 0);
-          ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &tmB, fb, kb * TBK, nb * TBN, 0);
+          ptx::tma_load_3d(ptx::smem_u32(sa), &pr->tmA, fb, kb * TBK, mb * TBM, 0);
+          ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &pr->tmB, fb, kb * TBK, nb * TBN, 0);
           issued |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == NSTAGE) {
@@ -195,12 +225,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
       bool ok = true;
       for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
+        const int nkb = find_problem<G>(tile, &single, p)->num_kb;
         uint32_t xbuf = 0;
-        for (int kb = 0; kb < p.num_kb && ok; ++kb) {
+        for (int kb = 0; kb < nkb && ok; ++kb) {
           const bool d1_first = (kb % p.kb_d1) == 0;
           const bool x_first = (kb % p.kb_x) == 0;
-          const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == p.num_kb;
-          const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == p.num_kb;
+          const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == nkb;
+          const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == nkb;
           const uint32_t b1 = u1 & 1;
           if (d1_first) {
             if (!ptx::mbar_wait_bounded(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
@@ -267,14 +298,20 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     float rh[COLS_PER_WARP];
     __nv_bfloat162 rl2[COLS_PER_WARP / 2];
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-      const int mb = tile % p.num_m, nb = tile / p.num_m;
+      const GemmProblem* pr = find_problem<G>(tile, &single, p);
+      const int lt = tile - pr->tile_begin;
+      const int mb = lt % pr->num_m, nb = lt / pr->num_m;
+      const int nkb = pr->num_kb;
+      const int64_t PM = pr->M, PN = pr->N, scm = pr->scm, scn = pr->scn;
+      void* const PC = pr->C;
+      const int out_f32 = pr->out_f32;
 #pragma unroll
       for (int j = 0; j < COLS_PER_WARP; ++j) rh[j] = 0.f;
 #pragma unroll
       for (int j = 0; j < COLS_PER_WARP / 2; ++j) rl2[j] = __floats2bfloat162_rn(0.f, 0.f);
-      for (int kb = 0; kb < p.num_kb; ++kb) {
-        const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == p.num_kb;
-        const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == p.num_kb;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const bool d1_last = ((kb + 1) % p.kb_d1) == 0 || kb + 1 == nkb;
+        const bool x_last = ((kb + 1) % p.kb_x) == 0 || kb + 1 == nkb;
         if (d1_last) {
           ok = drain_unit(tmem + lane_base + (u1 & 1) * TBN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
                           abort_flag, lane, rh, rl2);
@@ -291,10 +328,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // store the tile (one rounding of hi + lo)
       const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
       const int64_t n0 = (int64_t)nb * TBN + c0;
-      if (row < p.M) {
-        if (p.out_f32) {
-          float* crow = (float*)p.C + row * p.scm;
-          const bool vec = p.scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= p.N;
+      if (row < PM) {
+        if (out_f32) {
+          float* crow = (float*)PC + row * scm;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
 #pragma unroll
           for (int j = 0; j < COLS_PER_WARP; j += 4) {
             const float2 c01 = __bfloat1622float2(rl2[j / 2]);
@@ -303,15 +340,15 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (vec) {
               *(float4*)(crow + n0 + j) = o;
             } else {
-              if (n0 + j < p.N) crow[(n0 + j) * p.scn] = o.x;
-              if (n0 + j + 1 < p.N) crow[(n0 + j + 1) * p.scn] = o.y;
-              if (n0 + j + 2 < p.N) crow[(n0 + j + 2) * p.scn] = o.z;
-              if (n0 + j + 3 < p.N) crow[(n0 + j + 3) * p.scn] = o.w;
+              if (n0 + j < PN) crow[(n0 + j) * scn] = o.x;
+              if (n0 + j + 1 < PN) crow[(n0 + j + 1) * scn] = o.y;
+              if (n0 + j + 2 < PN) crow[(n0 + j + 2) * scn] = o.z;
+              if (n0 + j + 3 < PN) crow[(n0 + j + 3) * scn] = o.w;
             }
           }
         } else {
-          double* crow = (double*)p.C + row * p.scm;
-          const bool vec = p.scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= p.N;
+          double* crow = (double*)PC + row * scm;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
 #pragma unroll
           for (int j = 0; j < COLS_PER_WARP; j += 2) {
             const float2 c = __bfloat1622float2(rl2[j / 2]);
@@ -319,8 +356,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             if (vec) {
               *(double2*)(crow + n0 + j) = o;
             } else {
-              if (n0 + j < p.N) crow[(n0 + j) * p.scn] = o.x;
-              if (n0 + j + 1 < p.N) crow[(n0 + j + 1) * p.scn] = o.y;
+              if (n0 + j < PN) crow[(n0 + j) * scn] = o.x;
+              if (n0 + j + 1 < PN) crow[(n0 + j + 1) * scn] = o.y;
             }
           }
         }
@@ -372,40 +409,126 @@ tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* bas
   return TCI_OK;
 }
 
+static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int64_t N, int64_t Kp, const void* Ap,
+                               const void* Bp, void* C, int out_f32, int64_t scm, int64_t scn) {
+  if (M <= 0 || N <= 0 || Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty problem");
+  if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
+    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
+  memset(pr, 0, sizeof(*pr));
+  TCI_TRY(tci_make_piece_map(ctx, &pr->tmA, Ap, M, Kp, TBM));
+  TCI_TRY(tci_make_piece_map(ctx, &pr->tmB, Bp, N, Kp, TBN));
+  pr->C = C;
+  pr->M = M;
+  pr->N = N;
+  pr->scm = scm;
+  pr->scn = scn;
+  pr->out_f32 = out_f32;
+  pr->num_m = (int)((M + TBM - 1) / TBM);
+  pr->num_n = (int)((N + TBN - 1) / TBN);
+  pr->num_kb = (int)((Kp + TBK - 1) / TBK);
+  return TCI_OK;
+}
+
+static tci_status common_params(tci_context ctx, GemmParams* gp, int products, int chunk_k, int xchunk_k) {
+  if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[0]) {
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr_set[0] = true;
+  }
+  if (!attr_set[1]) {
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr_set[1] = true;
+  }
+  gp->kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
+  const int kx = xchunk_k < TBK ? 1 : xchunk_k / TBK;
+  gp->kb_x = (kx + gp->kb_d1 - 1) / gp->kb_d1 * gp->kb_d1;   // X drains line up with D1 drains
+  gp->products = products;
+  gp->status = ctx->d_status;
+  return TCI_OK;
+}
+
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
                                void* C, int out_f32, int64_t scm, int64_t scn, int products, int chunk_k,
                                int xchunk_k) {
   if (M <= 0 || N <= 0) return TCI_OK;
-  if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
-  if (Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty K");
-  if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
-    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
-  CUtensorMap ta, tb;
-  TCI_TRY(tci_make_piece_map(ctx, &ta, Ap, M, Kp, TBM));
-  TCI_TRY(tci_make_piece_map(ctx, &tb, Bp, N, Kp, TBN));
-  static bool attr_set = false;
-  if (!attr_set) {
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr_set = true;
+  GemmProblem pr;
+  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_f32, scm, scn));
+  GemmParams gp;
+  memset(&gp, 0, sizeof gp);
+  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k));
+  gp.nprob = 1;
+  gp.num_tiles = pr.num_m * pr.num_n;
+  const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
+  k_split_bf16_gemm<false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+// Grouped launch: build the device table once (plan time), launch many times.
+struct tci_split_group {
+  GemmProblem* d_table = nullptr;
+  int nprob = 0;
+  int num_tiles = 0;
+  int64_t flops_tc = 0;
+};
+
+tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out) {
+  *out = nullptr;
+  std::vector<GemmProblem> host;
+  host.reserve(n);
+  std::vector<int> order;
+  for (int i = 0; i < n; ++i)
+    if (probs[i].M > 0 && probs[i].N > 0 && probs[i].Kp > 0) order.push_back(i);
+  // longest K first (static round-robin then schedules the long tiles early)
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return probs[a].Kp > probs[b].Kp; });
+  int tiles = 0;
+  for (int i : order) {
+    const tci_split_problem& q = probs[i];
+    GemmProblem pr;
+    TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_f32, q.scm, q.scn));
+    pr.tile_begin = tiles;
+    tiles += pr.num_m * pr.num_n;
+    host.push_back(pr);
   }
-  GemmParams p;
-  p.M = M;
-  p.N = N;
-  p.C = C;
-  p.scm = scm;
-  p.scn = scn;
-  p.out_f32 = out_f32;
-  p.num_m = (int)((M + TBM - 1) / TBM);
-  p.num_n = (int)((N + TBN - 1) / TBN);
-  p.num_kb = (int)((Kp + TBK - 1) / TBK);
-  p.kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
-  int kx = xchunk_k < TBK ? 1 : xchunk_k / TBK;
-  p.kb_x = (kx + p.kb_d1 - 1) / p.kb_d1 * p.kb_d1;   // X drains line up with D1 drains
-  p.products = products;
-  p.status = ctx->d_status;
-  const int tiles = p.num_m * p.num_n;
-  const int grid = tiles < ctx->num_sms ? tiles : ctx->num_sms;
-  k_split_bf16_gemm<<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(ta, tb, p);
+  tci_split_group* g = new tci_split_group();
+  g->nprob = (int)host.size();
+  g->num_tiles = tiles;
+  if (g->nprob > 0) {
+    tci_status s = tci_dev_alloc(ctx, sizeof(GemmProblem) * host.size(), (void**)&g->d_table);
+    if (s != TCI_OK) {
+      delete g;
+      return s;
+    }
+    cudaError_t e = cudaMemcpy(g->d_table, host.data(), sizeof(GemmProblem) * host.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      tci_dev_free(g->d_table);
+      delete g;
+      return tci_cuda_fail(ctx, e, "split group table upload");
+    }
+  }
+  *out = g;
+  return TCI_OK;
+}
+
+void tci_split_group_destroy(tci_split_group* g) {
+  if (!g) return;
+  tci_dev_free(g->d_table);
+  delete g;
+}
+
+tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k) {
+  if (!g || g->nprob == 0) return TCI_OK;
+  GemmParams gp;
+  memset(&gp, 0, sizeof gp);
+  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k));
+  gp.table = g->d_table;
+  gp.nprob = g->nprob;
+  gp.num_tiles = g->num_tiles;
+  GemmProblem dummy;
+  memset(&dummy, 0, sizeof dummy);
+  const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
+  k_split_bf16_gemm<true><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }

@@ -119,6 +119,20 @@ tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp
                                const void* Apieces, const void* Bpieces, void* C, int out_f32,
                                int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k);
 
+// Grouped split-BF16 GEMM: all problems run in one persistent launch.
+struct tci_split_problem {
+  const void* Ap;   // bf16 pieces [3][M][Kp], 16-byte aligned
+  const void* Bp;   // bf16 pieces [3][N][Kp], 16-byte aligned
+  int64_t M, N, Kp;
+  void* C;          // element (m, n) at C[m*scm + n*scn]
+  int out_f32;
+  int64_t scm, scn;
+};
+struct tci_split_group;
+tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out);
+void tci_split_group_destroy(tci_split_group* g);
+tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k);
+
 // K0: split a strided FP64/FP32 operand into three bfloat16 planes, packed
 // K-major: out[p][r][k] for r < rows, k < Kp (zero for k >= K).  Element
 // (r, k) of the source is at src[r*sr + k*sk] (with an optional 2-level row

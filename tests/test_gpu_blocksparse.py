@@ -1,0 +1,58 @@
+"""GPU parity of the U(1) block-sparse H_eff (grouped split-BF16) vs the densified FP64 oracle."""
+import numpy as np
+import pytest
+
+from conftest import to_dev
+from oracle import blocksparse as o_bs
+from oracle.contract import rel_frob_err
+from tci_synth import MPO_CHANNEL_CHARGE, PHYS_CHARGE, blocksparse_inputs, blocksparse_structure
+
+pytestmark = pytest.mark.gpu
+
+
+def run_bs(tci, ctx, inp):
+    import torch
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    charges = np.arange(len(dims)) - qmax
+    Lp = to_dev(tci.pack_blocks(inp["L"], st["L"]))
+    Rp = to_dev(tci.pack_blocks(inp["R"], st["R"]))
+    plan = tci.BsHeffPlan(ctx, charges, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE, Lp, Rp, to_dev(inp["W"]))
+    psi = to_dev(tci.pack_blocks(inp["psi"], st["psi"]))
+    assert plan.psi_size == psi.numel()
+    out = torch.full_like(psi, float("nan"))
+    plan.apply(psi, out)
+    torch.cuda.synchronize()
+    shapes = {k: (dims[k[0]], dims[k[3]]) for k in st["psi"]}
+    return tci.unpack_blocks(out.cpu().numpy(), st["psi"], shapes), plan, st
+
+
+def blocks_err(got, ref):
+    num = sum(np.sum((got[k].astype(np.float64) - ref[k]) ** 2) for k in ref)
+    den = sum(np.sum(ref[k] ** 2) for k in ref)
+    return float(np.sqrt(num / den))
+
+
+@pytest.mark.parametrize("total,qmax,sigma,seed", [(64, 5, 2.0, 3), (300, 9, 3.0, 4), (97, 15, 5.0, 5)])
+def test_blocksparse_small_matches_oracle(ctx, tci, total, qmax, sigma, seed):
+    inp = blocksparse_inputs(total=total, seed=seed, qmax=qmax, sigma=sigma)
+    got, plan, st = run_bs(tci, ctx, inp)
+    ref, _ = o_bs.bs_heff_apply(inp)
+    assert blocks_err(got, ref) < 1e-6
+    assert plan.flops == o_bs.bs_flops(inp)
+
+
+def test_blocksparse_config_2048(ctx, tci):
+    inp = blocksparse_inputs(total=2048, seed=20251223)
+    got, plan, st = run_bs(tci, ctx, inp)
+    ref, _ = o_bs.bs_heff_apply(inp)
+    assert blocks_err(got, ref) < 1e-6
+    assert abs(plan.flops - o_bs.bs_flops(inp)) <= 1e-9 * plan.flops
+
+
+def test_blocksparse_repeat_is_deterministic(ctx, tci):
+    inp = blocksparse_inputs(total=200, seed=9, qmax=7, sigma=3.0)
+    a, plan, _ = run_bs(tci, ctx, inp)
+    b, _, _ = run_bs(tci, ctx, inp)
+    for k in a:
+        np.testing.assert_array_equal(a[k], b[k])
