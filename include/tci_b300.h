@@ -113,7 +113,8 @@ tci_status tci_context_get_precision(tci_context ctx, tci_precision* p);
  * knob of the plan): hi*hi products are accumulated in FP32 tensor memory
  * for chunk_k of contraction depth, the cross products for xchunk_k, before
  * being folded into an error-free FP32 double-float sum.  Smaller chunks are
- * more accurate and cost more epilogue work.  Defaults 128 / 1024.
+ * more accurate and cost more epilogue work.  Defaults 256 / 1024 (measured
+ * relative error of the chi = 2048 H_eff matvec: 4.3e-7; 128 / 1024: 2.2e-7).
  * Errors: INVALID_ARG unless 32 | chunk_k and chunk_k | xchunk_k. */
 tci_status tci_context_set_split_chunks(tci_context ctx, int chunk_k, int xchunk_k);
 

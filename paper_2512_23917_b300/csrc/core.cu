@@ -170,7 +170,7 @@ extern "C" tci_status tci_create_context(tci_context* out, int device, void* str
   ctx->device = device;
   ctx->stream = (cudaStream_t)stream;
   ctx->precision = TCI_PREC_NATIVE;
-  ctx->split_chunk_k = 128;
+  ctx->split_chunk_k = 256;
   ctx->split_xchunk_k = 1024;
   const char* v = getenv("TCI_VERBOSE");
   ctx->verbose = v ? atoi(v) : 0;
