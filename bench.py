@@ -165,6 +165,104 @@ def lanczos_launches(m: int) -> int:
     return n
 
 
+def measure_blocksparse(tci, ctx, dev, peaks, with_oracle: bool):
+    """U(1) block-sparse matvec, total chi = 2048, 31 sectors (one grouped launch per GEMM stage)."""
+    import torch
+    from tci_synth import MPO_CHANNEL_CHARGE, PHYS_CHARGE, blocksparse_inputs, blocksparse_structure
+    inp = blocksparse_inputs(total=2048, seed=SEED)
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    plan = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                          t(tci.pack_blocks(inp["L"], st["L"])), t(tci.pack_blocks(inp["R"], st["R"])), t(inp["W"]))
+    psi = t(tci.pack_blocks(inp["psi"], st["psi"]))
+    out = torch.empty_like(psi)
+    for _ in range(3):
+        plan.apply(psi, out)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    e0.record(stream)
+    for _ in range(n):
+        plan.apply(psi, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    stg = np.median(np.array([plan.apply_timed(psi, out) for _ in range(5)]), axis=0)
+    gemm_ms = float(stg[1] + stg[3])
+    ach = plan.tensor_flops / (gemm_ms * 1e-3) / 1e12
+    res = {"workload": "U(1) block-sparse two-site H_eff, total chi=2048, 31 sectors q in [-15,15], FP32 blocks, "
+                       "split-BF16 (6 products)",
+           "gflops": plan.flops / (ms * 1e-3) / 1e9, "ms_per_matvec": ms, "algorithmic_flops": plan.flops,
+           "stage_ms": {"split": float(stg[0]), "gemm1_grouped": float(stg[1]), "ww": float(stg[2]),
+                        "gemm2_grouped": float(stg[3])},
+           "launches_per_matvec": 4,
+           "roofline": {"bound": "tensor", "kernel": "k_split_bf16_gemm<grouped>", "achieved": ach,
+                        "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
+                        "flops_per_launch_pair": plan.tensor_flops}}
+    if with_oracle:
+        from oracle import blocksparse as o_bs
+        ref, _ = o_bs.bs_heff_apply(inp)
+        got = out.cpu().numpy()
+        off, num, den = 0, 0.0, 0.0
+        for k in st["psi"]:
+            r, c = dims[k[0]], dims[k[3]]
+            g = got[off:off + r * c].reshape(r, c).astype(np.float64)
+            off += r * c
+            num += float(np.sum((g - ref[k]) ** 2))
+            den += float(np.sum(ref[k] ** 2))
+        res["rel_frob_err_vs_oracle"] = float(np.sqrt(num / den))
+    plan.close()
+    return res
+
+
+def measure_tebd(tci, ctx, dev, peaks, with_oracle: bool):
+    """256 independent TEBD bonds, chi ~ U{16..512}, complex64 (3M split-BF16, one grouped launch)."""
+    import torch
+    from tci_synth import tebd_inputs
+    chis, A, B, G = tebd_inputs(256, seed=SEED)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    pa = t(np.concatenate([a.ravel() for a in A]))
+    pb = t(np.concatenate([b.ravel() for b in B]))
+    pg = t(np.concatenate([g.ravel() for g in G]))
+    th = torch.empty(sum(4 * c * c for c in chis), dtype=torch.complex64, device=dev)
+    plan = tci.TebdPlan(ctx, chis)
+    for _ in range(3):
+        plan.apply(pa, pb, pg, th)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 10
+    e0.record(stream)
+    for _ in range(n):
+        plan.apply(pa, pb, pg, th)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    stg = np.median(np.array([plan.apply_timed(pa, pb, pg, th) for _ in range(5)]), axis=0)
+    ach = plan.tensor_flops / (float(stg[1]) * 1e-3) / 1e12
+    io_bytes = 8 * sum(2 * c * c * 2 + 4 * c * c for c in chis)
+    res = {"workload": "batched TEBD theta, 256 bonds, chi ~ U{16..512}, d=2, complex64, 3M split-BF16",
+           "gflops": plan.flops / (ms * 1e-3) / 1e9, "ms_per_batch": ms, "algorithmic_flops": plan.flops,
+           "stage_ms": {"split": float(stg[0]), "gemm_grouped": float(stg[1]), "gate": float(stg[2])},
+           "launches_per_batch": 3, "io_bytes": io_bytes,
+           "roofline": {"bound": "tensor", "kernel": "k_split_bf16_gemm<grouped>", "achieved": ach,
+                        "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
+                        "flops_per_launch": plan.tensor_flops}}
+    if with_oracle:
+        from oracle import tebd as o_tebd
+        got = th.cpu().numpy()
+        off, num, den = 0, 0.0, 0.0
+        for c, a, b, g in zip(chis, A, B, G):
+            ref = o_tebd.theta(a, b, g)
+            x = got[off:off + 4 * c * c].reshape(c, 2, 2, c)
+            off += 4 * c * c
+            num += float(np.sum(np.abs(x - ref) ** 2))
+            den += float(np.sum(np.abs(ref) ** 2))
+        res["rel_frob_err_vs_oracle"] = float(np.sqrt(num / den))
+    plan.close()
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_info()
@@ -285,6 +383,10 @@ def run_gpu(args):
                                  "kind": "oracle",
                                  "sample": f"{len(r_s)} output rows out[a,:,:,:] of the chi=2048 FP64 matvec"}
 
+    rows = {}
+    if not args.skip_rows:
+        rows["a7_blocksparse"] = measure_blocksparse(tci, ctx, dev, peaks, rank == 0)
+        rows["a8_tebd"] = measure_tebd(tci, ctx, dev, peaks, rank == 0)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
@@ -300,6 +402,7 @@ def run_gpu(args):
                        "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),
                                     "gemm2": float(st[3])}}}
     line.update(extra)
+    line["rows"] = rows
     if rank == 0:
         print(json.dumps(line), flush=True)
     plan.close()
@@ -338,6 +441,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-rows", action="store_true", help="measure only the headline chi=2048 workload")
     args = ap.parse_args()
     if args.profile_chi:
         run_profile_case(args)

@@ -328,6 +328,13 @@ tci_status tci_bs_heff_apply(tci_bs_plan plan, const float* psi, float* out);
  * pair that carries an intermediate block.  -1/0 for an invalid plan. */
 double tci_bs_heff_flops(tci_bs_plan plan);
 int64_t tci_bs_psi_size(tci_bs_plan plan);
+/* Profiling form of tci_bs_heff_apply: stage_ms[0..3] (host) receive the
+ * device times of the psi split, grouped GEMM1, W.W tasks and grouped GEMM2
+ * (with the output copy).  Synchronises. */
+tci_status tci_bs_heff_apply_timed(tci_bs_plan plan, const float* psi, float* out, float* stage_ms);
+/* BF16 tensor-core flops the two grouped launches execute per matvec
+ * (2 x products x M N Kp summed over block GEMMs). */
+double tci_bs_tensor_flops(tci_bs_plan plan);
 
 /* ------------------------------------------- batched TEBD theta
  * The theta formation and gate application of the paper's iTEBD listing
@@ -349,6 +356,12 @@ tci_status tci_tebd_plan_destroy(tci_tebd_plan* plan);
 tci_status tci_tebd_apply(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta);
 /* Algorithmic flops: sum_i 8 chi_i^3 d^2 + 8 chi_i^2 d^4 (8 real flops per complex multiply-add). */
 double tci_tebd_flops(tci_tebd_plan plan);
+/* Profiling form of tci_tebd_apply: stage_ms[0..2] (host) receive the device
+ * times of the split, the grouped GEMM and the gate kernel.  Synchronises. */
+tci_status tci_tebd_apply_timed(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,
+                                float* stage_ms);
+/* BF16 tensor-core flops the grouped launch executes (3 real GEMMs per bond). */
+double tci_tebd_tensor_flops(tci_tebd_plan plan);
 
 #ifdef __cplusplus
 }

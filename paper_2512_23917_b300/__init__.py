@@ -91,6 +91,10 @@ SIGNATURES = [
     ("tci_tebd_plan_destroy", C.c_int, [C.POINTER(_p)]),
     ("tci_tebd_apply", C.c_int, [_p, _p, _p, _p, _p]),
     ("tci_tebd_flops", C.c_double, [_p]),
+    ("tci_tebd_apply_timed", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(C.c_float)]),
+    ("tci_tebd_tensor_flops", C.c_double, [_p]),
+    ("tci_bs_heff_apply_timed", C.c_int, [_p, _p, _p, C.POINTER(C.c_float)]),
+    ("tci_bs_tensor_flops", C.c_double, [_p]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
 ]
 
@@ -448,6 +452,16 @@ class BsHeffPlan:
     def psi_size(self) -> int:
         return lib.tci_bs_psi_size(self.handle)
 
+    @property
+    def tensor_flops(self) -> float:
+        return lib.tci_bs_tensor_flops(self.handle)
+
+    def apply_timed(self, psi_packed, out_packed):
+        ms = (C.c_float * 4)()
+        _check(lib.tci_bs_heff_apply_timed(self.handle, _p(psi_packed.data_ptr()), _p(out_packed.data_ptr()), ms),
+               self.ctx.handle)
+        return list(ms)
+
     def apply(self, psi_packed, out_packed):
         _check(lib.tci_bs_heff_apply(self.handle, _p(psi_packed.data_ptr()), _p(out_packed.data_ptr())),
                self.ctx.handle)
@@ -495,6 +509,16 @@ class TebdPlan:
     @property
     def flops(self) -> float:
         return lib.tci_tebd_flops(self.handle)
+
+    @property
+    def tensor_flops(self) -> float:
+        return lib.tci_tebd_tensor_flops(self.handle)
+
+    def apply_timed(self, A_packed, B_packed, G_packed, theta_packed):
+        ms = (C.c_float * 3)()
+        _check(lib.tci_tebd_apply_timed(self.handle, _p(A_packed.data_ptr()), _p(B_packed.data_ptr()),
+                                        _p(G_packed.data_ptr()), _p(theta_packed.data_ptr()), ms), self.ctx.handle)
+        return list(ms)
 
     def apply(self, A_packed, B_packed, G_packed, theta_packed):
         _check(lib.tci_tebd_apply(self.handle, _p(A_packed.data_ptr()), _p(B_packed.data_ptr()),

@@ -193,6 +193,7 @@ struct tci_bs_plan_s {
   tci_split_group* g2 = nullptr;
   WWCoef coef;
   int64_t n_gemm1 = 0, n_gemm2 = 0;
+  double tensor_flops = 0.0;
 };
 
 struct BsBlock {
@@ -370,6 +371,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     if (!S.rows) continue;
     g1.push_back({A + Ppiece[k], A + S.off, dim[B.i], S.rows, S.Kp, p->U + Uoff[k], 1, S.rows, 1});
   }
+  for (auto& q : g1) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
   if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1)) != TCI_OK) return fail(s);
   p->n_gemm1 = (int64_t)g1.size();
   // ---------------------------------------------------------------- W.W tasks
@@ -438,6 +440,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   // output blocks that no GEMM writes stay zero
   e = cudaMemsetAsync(p->out_stage, 0, std::max<int64_t>(psi_elems, 1) * 4, ctx->stream);
   if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan memset"));
+  for (auto& q : g2) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
   if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2)) != TCI_OK) return fail(s);
   p->n_gemm2 = (int64_t)g2.size();
   // psi split jobs
@@ -535,4 +538,42 @@ extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* 
   TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
   TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
   return TCI_OK;
+}
+
+// tci_bs_heff_apply with CUDA events between the stages: ms[0..3] = psi split,
+// grouped GEMM1, W.W tasks, grouped GEMM2 (+ the output copy).  Synchronises.
+extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, float* out, float* ms) {
+  if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_heff_apply_timed: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  if (!psi || !out || !ms) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_apply_timed: NULL argument");
+  cudaEvent_t ev[5];
+  for (auto& e : ev) TCI_CUDA(ctx, cudaEventCreate(&e));
+  TCI_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  if (p->n_psi_jobs) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
+    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
+  }
+  TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
+  TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
+  if (p->n_tasks) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (p->max_task_elems + 255) / 256)), (unsigned)p->n_tasks);
+    k_bs_ww<<<grid, 256, 0, ctx->stream>>>(p->d_tasks, p->coef, (__nv_bfloat16*)p->arena);
+  }
+  TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
+  TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
+  TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
+  TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));
+  for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return tci_synchronize(ctx);
+}
+
+// BF16 tensor flops executed by the two grouped launches (all piece products,
+// padded K, full tiles excluded): 2 * products * sum over problems of M N Kp.
+extern "C" double tci_bs_tensor_flops(tci_bs_plan p) {
+  if (!p || p->magic != kBsMagic) return 0.0;
+  return p->tensor_flops;
 }

@@ -35,27 +35,27 @@ __global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, dou
 }
 
 // ------------------------------------------------------------------ W.W application
-// One block: a' in [a0, a0+ATILE), b in [b0, b0+32).  U rows (a',t) for the
-// tile are staged in shared memory (coalesced 32*Dw-long row segments), then
-// each thread forms the 20 outputs of one (a', b) pair and writes them with
-// a' fastest (coalesced along GEMM2's K dimension).
+// One block: a' in [a0, a0+ATILE), b in [b0, b0+BT), one (a', b) pair per
+// thread (ATILE*BT = 256).  The U rows (a', t) of the tile are staged in
+// shared memory (row segments of BT*Dw contiguous values), then each thread
+// forms the 20 outputs of its pair and writes them with a' fastest, which is
+// contiguous along GEMM2's K dimension.
 template <typename T>
 struct WWArgs {
   T ww[HEFF_DW * 4 * HEFF_DW * 4];   // [wl][s][wr][t], s = (s1 s2), t = (t1 t2)
 };
 
-template <typename T, typename UT, int ATILE, bool SPLIT>
-__global__ void __launch_bounds__(256) k_ww_apply(const WWArgs<T> args, const UT* __restrict__ U, int64_t chiL,
-                                                  int64_t chiR, void* __restrict__ Vout, int64_t ldv, int64_t plane) {
-  constexpr int Dw = HEFF_DW, D2 = 4, BT = 32;
-  constexpr int ROW = D2 * BT * Dw;   // values per a' in the tile
-  extern __shared__ __align__(16) unsigned char smem_ww[];
-  T* Us = (T*)smem_ww;                // [ATILE][ROW + 1]
+template <typename T, typename UT, int ATILE, int BT, bool SPLIT>
+__global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<T> args, const UT* __restrict__ U,
+                                                          int64_t chiL, int64_t chiR, void* __restrict__ Vout,
+                                                          int64_t ldv, int64_t plane) {
+  constexpr int Dw = HEFF_DW, D2 = 4;
+  constexpr int ROW = D2 * BT * Dw;   // staged values per a'
+  __shared__ T Us[ATILE][ROW + 1];
   const int64_t a0 = (int64_t)blockIdx.y * ATILE;
   const int64_t b0 = (int64_t)blockIdx.x * BT;
   const int64_t ldu = chiR * Dw;
-  // load: for each (a', t) row, BT*Dw contiguous doubles
-  for (int idx = threadIdx.x; idx < ATILE * D2 * BT * Dw; idx += blockDim.x) {
+  for (int idx = threadIdx.x; idx < ATILE * D2 * BT * Dw; idx += ATILE * BT) {
     const int col = idx % (BT * Dw);
     const int rt = idx / (BT * Dw);   // a'_local * D2 + t
     const int al = rt / D2, t = rt % D2;
@@ -63,60 +63,52 @@ __global__ void __launch_bounds__(256) k_ww_apply(const WWArgs<T> args, const UT
     const int64_t gcol = b0 * Dw + col;
     T v = (T)0;
     if (ap < chiL && gcol < ldu) v = (T)U[(ap * D2 + t) * ldu + gcol];
-    const int bl = col / Dw, wr = col % Dw;
-    Us[al * (ROW + 1) + (t * BT + bl) * Dw + wr] = v;
+    Us[al][t * BT * Dw + col] = v;
   }
   __syncthreads();
-  const int al = threadIdx.x % ATILE;
-  const int64_t ap = a0 + al;
-  for (int bl = threadIdx.x / ATILE; bl < BT; bl += 256 / ATILE) {
-    const int64_t b = b0 + bl;
-    if (ap >= chiL || b >= chiR) continue;
-    T in[D2 * Dw];
+  const int al = threadIdx.x % ATILE, bl = threadIdx.x / ATILE;
+  const int64_t ap = a0 + al, b = b0 + bl;
+  if (ap >= chiL || b >= chiR) return;
+  T in[D2 * Dw];
 #pragma unroll
-    for (int t = 0; t < D2; ++t)
+  for (int t = 0; t < D2; ++t)
 #pragma unroll
-      for (int wr = 0; wr < Dw; ++wr) in[t * Dw + wr] = Us[al * (ROW + 1) + (t * BT + bl) * Dw + wr];
+    for (int wr = 0; wr < Dw; ++wr) in[t * Dw + wr] = Us[al][(t * BT + bl) * Dw + wr];
+  const int64_t rowstep = chiR * ldv;   // s -> s + 1
+  const int64_t base = b * ldv + ap;
+#pragma unroll
+  for (int s = 0; s < D2; ++s) {
 #pragma unroll
     for (int wl = 0; wl < Dw; ++wl) {
+      T acc = (T)0;
 #pragma unroll
-      for (int s = 0; s < D2; ++s) {
-        T acc = (T)0;
+      for (int wr = 0; wr < Dw; ++wr)
 #pragma unroll
-        for (int wr = 0; wr < Dw; ++wr)
-#pragma unroll
-          for (int t = 0; t < D2; ++t) acc += args.ww[((wl * D2 + s) * Dw + wr) * D2 + t] * in[t * Dw + wr];
-        const int64_t off = (s * chiR + b) * ldv + wl * chiL + ap;
-        if (SPLIT) {
-          __nv_bfloat16* V = (__nv_bfloat16*)Vout;
-          const float xf = (float)acc;
-          const __nv_bfloat16 h = __float2bfloat16_rn(xf);
-          const float r1 = xf - __bfloat162float(h);
-          const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-          const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-          V[off] = h;
-          V[plane + off] = m;
-          V[2 * plane + off] = l;
-        } else {
-          ((double*)Vout)[off] = (double)acc;
-        }
+        for (int t = 0; t < D2; ++t) acc += args.ww[((wl * D2 + s) * Dw + wr) * D2 + t] * in[t * Dw + wr];
+      const int64_t off = base + s * rowstep + wl * chiL;
+      if (SPLIT) {
+        __nv_bfloat16* V = (__nv_bfloat16*)Vout;
+        const float xf = (float)acc;
+        const __nv_bfloat16 h = __float2bfloat16_rn(xf);
+        const float r1 = xf - __bfloat162float(h);
+        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+        V[off] = h;
+        V[plane + off] = m;
+        V[2 * plane + off] = l;
+      } else {
+        ((double*)Vout)[off] = (double)acc;
       }
     }
   }
 }
 
-template <typename T, typename UT, int ATILE, bool SPLIT>
+template <typename T, typename UT, int ATILE, int BT, bool SPLIT>
 tci_status launch_ww(tci_context ctx, const WWArgs<T>& args, const UT* U, int64_t chiL, int64_t chiR, void* V,
                      int64_t ldv, int64_t plane) {
-  constexpr int ROW = 4 * 32 * HEFF_DW;
-  const size_t smem = (size_t)ATILE * (ROW + 1) * sizeof(T);
-  static bool attr = false;
-  if (!attr) {
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_ww_apply<T, UT, ATILE, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
-  dim3 grid((unsigned)((chiR + 31) / 32), (unsigned)((chiL + ATILE - 1) / ATILE));
-  k_ww_apply<T, UT, ATILE, SPLIT><<<grid, 256, smem, ctx->stream>>>(args, U, chiL, chiR, V, ldv, plane);
+  dim3 grid((unsigned)((chiR + BT - 1) / BT), (unsigned)((chiL + ATILE - 1) / ATILE));
+  if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: chiL too large");
+  k_ww_apply<T, UT, ATILE, BT, SPLIT><<<grid, ATILE * BT, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv, plane);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
@@ -233,7 +225,7 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, b
     WWArgs<double> args;
     for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = p->ww[i];
     TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1));
-    TCI_TRY((launch_ww<double, double, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0)));
+    TCI_TRY((launch_ww<double, double, 16, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0)));
     TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out,
                             4 * chiR, 1));
     return TCI_OK;
@@ -243,7 +235,7 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, b
   if (!psi_presplit) TCI_TRY(tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1));
   TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products,
                               p->chunk_k, p->xchunk_k));
-  TCI_TRY((launch_ww<float, float, 32, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2)));
+  TCI_TRY((launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2)));
   TCI_TRY(tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k,
                               p->xchunk_k));
   return TCI_OK;
@@ -264,7 +256,7 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
     TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1);
     TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-    if (s == TCI_OK) s = launch_ww<double, double, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0);
+    if (s == TCI_OK) s = launch_ww<double, double, 16, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0);
     TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out, 4 * chiR, 1);
   } else {
@@ -274,7 +266,7 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
     TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products, p->chunk_k, p->xchunk_k);
     TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-    if (s == TCI_OK) s = launch_ww<float, float, 32, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2);
+    if (s == TCI_OK) s = launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2);
     TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k, p->xchunk_k);
   }

@@ -12,7 +12,7 @@
 
 namespace {
 
-constexpr int NB = 592;          // 4 x 148 SMs: blocks of every reduction
+constexpr int NB = 1184;         // 8 x 148 SMs: blocks of every reduction (64 warps per SM)
 constexpr int NT = 256;
 constexpr int MAXM = 256;
 // device scalar layout (doubles)
@@ -29,16 +29,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // part[v*NB + block] = sum over this block's slice of V_v[i] * w[i], v < nv.
+// Each thread walks two grid-stride elements per iteration (independent FP64
+// chains); the per-thread order is fixed, so the result is deterministic.
 template <int G>
 __global__ void __launch_bounds__(NT) k_mdot(const double* __restrict__ V, int64_t ldv, int v0, int nv,
                                              const double* __restrict__ w, int64_t n, double* __restrict__ part,
                                              const double* __restrict__ ctrl) {
   if (ctrl[0] != 0.0) return;
   __shared__ double sh[NT / 32][G];
-  double acc[G];
+  double acc[G], acc2[G];
 #pragma unroll
-  for (int g = 0; g < G; ++g) acc[g] = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
+  for (int g = 0; g < G; ++g) acc[g] = acc2[g] = 0.0;
+  const int64_t stride = (int64_t)NB * NT;
+  int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    const double wi = w[i], wj = w[i + stride];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < nv) {
+        const double* vg = V + (int64_t)(v0 + g) * ldv;
+        acc[g] = fma(vg[i], wi, acc[g]);
+        acc2[g] = fma(vg[i + stride], wj, acc2[g]);
+      }
+  }
+  if (i < n) {
     const double wi = w[i];
 #pragma unroll
     for (int g = 0; g < G; ++g)
@@ -47,7 +61,7 @@ __global__ void __launch_bounds__(NT) k_mdot(const double* __restrict__ V, int64
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
   for (int g = 0; g < G; ++g) {
-    double s = warp_sum(acc[g]);
+    double s = warp_sum(acc[g] + acc2[g]);
     if (lane == 0) sh[wid][g] = s;
   }
   __syncthreads();
@@ -77,7 +91,7 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nv, double* 
   }
 }
 
-// w -= sum_{v<nv} c[v] V_v
+// w -= sum_{v<nv} c[v] V_v   (two elements per thread per iteration)
 template <int G>
 __global__ void __launch_bounds__(NT) k_mupdate(const double* __restrict__ V, int64_t ldv, int v0, int nv,
                                                 const double* __restrict__ c, double* __restrict__ w, int64_t n,
@@ -86,7 +100,21 @@ __global__ void __launch_bounds__(NT) k_mupdate(const double* __restrict__ V, in
   double cc[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) cc[g] = g < nv ? c[v0 + g] : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
+  const int64_t stride = (int64_t)NB * NT;
+  int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
+  for (; i + stride < n; i += 2 * stride) {
+    double s = 0.0, t = 0.0;
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < nv) {
+        const double* vg = V + (int64_t)(v0 + g) * ldv;
+        s = fma(cc[g], vg[i], s);
+        t = fma(cc[g], vg[i + stride], t);
+      }
+    w[i] -= s;
+    w[i + stride] -= t;
+  }
+  if (i < n) {
     double s = 0.0;
 #pragma unroll
     for (int g = 0; g < G; ++g)

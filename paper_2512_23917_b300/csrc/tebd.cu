@@ -110,6 +110,7 @@ struct tci_tebd_plan_s {
   int products, chunk_k, xchunk_k;
   int64_t max_chi;
   double flops;
+  double tensor_flops = 0.0;
   void* arena = nullptr;   // bf16 pieces
   float* P = nullptr;      // P1, P2, P3 per bond
   BondJob* d_jobs = nullptr;
@@ -181,6 +182,7 @@ extern "C" tci_status tci_tebd_plan_create(tci_context ctx, int nbonds, const in
     p->max_chi = std::max(p->max_chi, j.chi);
     const double c = (double)j.chi;
     fl += 8.0 * c * c * c * 4.0 + 8.0 * c * c * 16.0;   // 8 chi^3 d^2 + 8 chi^2 d^4
+    p->tensor_flops += 3.0 * 2.0 * p->products * (2.0 * c) * (2.0 * c) * (double)j.Kp;
   }
   p->flops = fl;
   tci_status s;
@@ -222,4 +224,37 @@ extern "C" tci_status tci_tebd_apply(tci_tebd_plan p, const void* A, const void*
   k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)G, (float2*)theta);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
+}
+
+// tci_tebd_apply with CUDA events between the stages: ms[0..2] = split,
+// grouped GEMM (3 real products per bond), gate.  Synchronises.
+extern "C" tci_status tci_tebd_apply_timed(tci_tebd_plan p, const void* A, const void* B, const void* G, void* theta,
+                                           float* ms) {
+  if (!p || p->magic != kTebdMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "tebd_apply_timed: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  if (!A || !B || !G || !theta || !ms) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "tebd_apply_timed: NULL argument");
+  cudaEvent_t ev[4];
+  for (auto& e : ev) TCI_CUDA(ctx, cudaEventCreate(&e));
+  const int64_t mc = p->max_chi;
+  TCI_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
+  dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
+  k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)A, (const float2*)B, (__nv_bfloat16*)p->arena);
+  TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
+  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k));
+  TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
+  dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
+  k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)G, (float2*)theta);
+  TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
+  TCI_CUDA(ctx, cudaEventSynchronize(ev[3]));
+  for (int i = 0; i < 3; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  return tci_synchronize(ctx);
+}
+
+// BF16 tensor flops executed by the grouped launch: 3 real GEMMs per bond,
+// 2 * products * (2 chi)^2 * pad8(chi) each.
+extern "C" double tci_tebd_tensor_flops(tci_tebd_plan p) {
+  if (!p || p->magic != kTebdMagic) return 0.0;
+  return p->tensor_flops;
 }
