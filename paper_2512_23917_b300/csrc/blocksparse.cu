@@ -125,36 +125,56 @@ struct WWCoef {
   float ww[BS_DW * 4 * BS_DW * 4];   // [wl][s][wr][t]
 };
 
-__global__ void __launch_bounds__(256) k_bs_ww(const WWTask* __restrict__ tasks, const WWCoef coef,
-                                               __nv_bfloat16* __restrict__ V) {
-  const WWTask& T = tasks[blockIdx.y];
-  const int64_t n = T.na * T.nb;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t b = i / T.na, ap = i - b * T.na;   // a' fastest: coalesced V writes
-    float in[4 * BS_DW];
-#pragma unroll
-    for (int q = 0; q < 4 * BS_DW; ++q) in[q] = T.u[q] ? T.u[q][ap * T.ldu[q] + b] : 0.f;
-#pragma unroll
-    for (int wl = 0; wl < BS_DW; ++wl)
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const int o = wl * 4 + s;
-        if (T.v[o] < 0) continue;
-        float acc = 0.f;
-#pragma unroll
-        for (int wr = 0; wr < BS_DW; ++wr)
-#pragma unroll
-          for (int t = 0; t < 4; ++t) acc = fmaf(coef.ww[((wl * 4 + s) * BS_DW + wr) * 4 + t], in[t * BS_DW + wr], acc);
-        const __nv_bfloat16 h = __float2bfloat16_rn(acc);
-        const float r1 = acc - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        const int64_t off = T.v[o] + b * T.ldv[o] + ap;
-        V[off] = h;
-        V[T.plane[o] + off] = m;
-        V[2 * T.plane[o] + off] = l;
-      }
+// One block per (task, 32 a' x 8 b tile).  The tile of every existing input
+// (t, wr) is staged in shared memory with coalesced row reads (8 contiguous
+// b per a' row), then each thread forms the outputs of one (a', b) pair and
+// writes them with a' fastest (contiguous along GEMM2's K dimension).
+struct WWTile {
+  int task;
+  int a0, b0;
+};
+
+constexpr int kWA = 32, kWB = 8;
+
+__global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ tasks, const WWTile* __restrict__ tiles,
+                                                     const WWCoef coef, __nv_bfloat16* __restrict__ V) {
+  __shared__ float Us[4 * BS_DW][kWA][kWB + 1];
+  const WWTile tl = tiles[blockIdx.x];
+  const WWTask& T = tasks[tl.task];
+  for (int idx = threadIdx.x; idx < 4 * BS_DW * kWA * kWB; idx += kWA * kWB) {
+    const int bl = idx % kWB, al = (idx / kWB) % kWA, q = idx / (kWB * kWA);
+    const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
+    float v = 0.f;
+    if (T.u[q] && ap < T.na && b < T.nb) v = T.u[q][ap * T.ldu[q] + b];
+    Us[q][al][bl] = v;
   }
+  __syncthreads();
+  const int al = threadIdx.x % kWA, bl = threadIdx.x / kWA;
+  const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
+  if (ap >= T.na || b >= T.nb) return;
+  float in[4 * BS_DW];
+#pragma unroll
+  for (int q = 0; q < 4 * BS_DW; ++q) in[q] = Us[q][al][bl];
+#pragma unroll
+  for (int wl = 0; wl < BS_DW; ++wl)
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int o = wl * 4 + s;
+      if (T.v[o] < 0) continue;
+      float acc = 0.f;
+#pragma unroll
+      for (int wr = 0; wr < BS_DW; ++wr)
+#pragma unroll
+        for (int t = 0; t < 4; ++t) acc = fmaf(coef.ww[((wl * 4 + s) * BS_DW + wr) * 4 + t], in[t * BS_DW + wr], acc);
+      const __nv_bfloat16 h = __float2bfloat16_rn(acc);
+      const float r1 = acc - __bfloat162float(h);
+      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+      const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+      const int64_t off = T.v[o] + b * T.ldv[o] + ap;
+      V[off] = h;
+      V[T.plane[o] + off] = m;
+      V[2 * T.plane[o] + off] = l;
+    }
 }
 
 __global__ void k_bs_ww_precompute(const double* __restrict__ W, float* __restrict__ out) {
@@ -187,6 +207,8 @@ struct tci_bs_plan_s {
   float* out_stage = nullptr; // GEMM2 writes here (the group table holds fixed pointers)
   SplitJob* d_psi_jobs = nullptr;
   WWTask* d_tasks = nullptr;
+  WWTile* d_tiles = nullptr;
+  int n_tiles = 0;
   int n_psi_jobs = 0, n_tasks = 0;
   int64_t max_psi_plane = 0, max_task_elems = 0;
   tci_split_group* g1 = nullptr;
@@ -194,6 +216,8 @@ struct tci_bs_plan_s {
   WWCoef coef;
   int64_t n_gemm1 = 0, n_gemm2 = 0;
   double tensor_flops = 0.0;
+  tci_graph graph;              // captured split -> GEMM1 -> W.W -> GEMM2
+  const float* cap_psi = nullptr;
 };
 
 struct BsBlock {
@@ -419,10 +443,18 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   }
   p->n_tasks = (int)tasks.size();
   for (auto& T : tasks) p->max_task_elems = std::max(p->max_task_elems, T.na * T.nb);
+  std::vector<WWTile> wtiles;
+  for (int t = 0; t < (int)tasks.size(); ++t)
+    for (int64_t a0 = 0; a0 < tasks[t].na; a0 += kWA)
+      for (int64_t b0 = 0; b0 < tasks[t].nb; b0 += kWB) wtiles.push_back({t, (int)a0, (int)b0});
+  p->n_tiles = (int)wtiles.size();
   if (!tasks.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(WWTask) * tasks.size(), (void**)&p->d_tasks)) != TCI_OK) return fail(s);
     e = cudaMemcpy(p->d_tasks, tasks.data(), sizeof(WWTask) * tasks.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: tasks"));
+    if ((s = tci_dev_alloc(ctx, sizeof(WWTile) * wtiles.size(), (void**)&p->d_tiles)) != TCI_OK) return fail(s);
+    e = cudaMemcpy(p->d_tiles, wtiles.data(), sizeof(WWTile) * wtiles.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W tiles"));
   }
   // ---------------------------------------------------------------- GEMM2 group
   std::vector<tci_split_problem> g2;
@@ -498,9 +530,10 @@ extern "C" tci_status tci_bs_plan_destroy(tci_bs_plan* pp) {
   if (!pp || !*pp || (*pp)->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_plan_destroy: invalid plan");
   tci_bs_plan p = *pp;
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
+  tci_graph_destroy(&p->graph);
   tci_split_group_destroy(p->g1);
   tci_split_group_destroy(p->g2);
-  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks};
+  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles};
   for (void* b : bufs) tci_dev_free(b);
   p->magic = 0;
   delete p;
@@ -518,24 +551,45 @@ extern "C" int64_t tci_bs_psi_size(tci_bs_plan p) {
   return p->psi_elems;
 }
 
+static tci_status bs_launch_all(void* arg) {
+  tci_bs_plan p = (tci_bs_plan)arg;
+  tci_context ctx = p->ctx;
+  if (p->n_psi_jobs) {
+    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
+    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, p->cap_psi, (__nv_bfloat16*)p->arena);
+  }
+  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
+  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
+  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
+  return TCI_OK;
+}
+
 extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* out) {
   if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_heff_apply: invalid plan");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "bs_heff_apply");
   if (!psi || !out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_apply: NULL buffer");
-  if (p->n_psi_jobs) {
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
-    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
+  p->cap_psi = psi;
+  if (!p->graph.exec) {
+    // first call: run eagerly (sets kernel attributes), then capture the sequence
+    TCI_TRY(bs_launch_all(p));
+    if (p->n_psi_jobs) TCI_TRY(tci_graph_capture(ctx, &p->graph, bs_launch_all, p, {(const void*)k_bs_split}));
+  } else {
+    if (p->n_psi_jobs) {
+      const SplitJob* jobs = p->d_psi_jobs;
+      __nv_bfloat16* dst = (__nv_bfloat16*)p->arena;
+      void* args[3] = {(void*)&jobs, (void*)&psi, (void*)&dst};
+      cudaKernelNodeParams kp;
+      TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(p->graph.nodes[0], &kp));
+      kp.kernelParams = args;
+      kp.extra = nullptr;
+      TCI_CUDA(ctx, cudaGraphExecKernelNodeSetParams(p->graph.exec, p->graph.nodes[0], &kp));
+    }
+    TCI_CUDA(ctx, cudaGraphLaunch(p->graph.exec, ctx->stream));
   }
-  TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
-  if (p->n_tasks) {
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (p->max_task_elems + 255) / 256)), (unsigned)p->n_tasks);
-    k_bs_ww<<<grid, 256, 0, ctx->stream>>>(p->d_tasks, p->coef, (__nv_bfloat16*)p->arena);
-  }
-  TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
   TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
   return TCI_OK;
 }
@@ -557,10 +611,7 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-  if (p->n_tasks) {
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (p->max_task_elems + 255) / 256)), (unsigned)p->n_tasks);
-    k_bs_ww<<<grid, 256, 0, ctx->stream>>>(p->d_tasks, p->coef, (__nv_bfloat16*)p->arena);
-  }
+  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
   TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));

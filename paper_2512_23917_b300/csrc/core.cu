@@ -1001,3 +1001,60 @@ extern "C" tci_status tci_close(tci_context ctx, tci_tensor a, tci_tensor b, dou
   *result = ctx->h_scalars[0] <= eps ? 1 : 0;
   return TCI_OK;
 }
+
+// ====================================================================== graphs
+tci_status tci_graph_capture(tci_context ctx, tci_graph* g, tci_status (*body)(void*), void* arg,
+                             const std::vector<const void*>& funcs) {
+  if (!g->cap) TCI_CUDA(ctx, cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking));
+  cudaStream_t saved = ctx->stream;
+  TCI_CUDA(ctx, cudaStreamSynchronize(saved));
+  ctx->stream = g->cap;
+  cudaError_t e = cudaStreamBeginCapture(g->cap, cudaStreamCaptureModeThreadLocal);
+  tci_status s = e == cudaSuccess ? body(arg) : tci_cuda_fail(ctx, e, "cudaStreamBeginCapture");
+  cudaGraph_t graph = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(g->cap, &graph);
+  ctx->stream = saved;
+  if (s != TCI_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e2 != cudaSuccess) return tci_cuda_fail(ctx, e2, "cudaStreamEndCapture");
+  size_t n = 0;
+  TCI_CUDA(ctx, cudaGraphGetNodes(graph, nullptr, &n));
+  std::vector<cudaGraphNode_t> all(n);
+  TCI_CUDA(ctx, cudaGraphGetNodes(graph, all.data(), &n));
+  g->nodes.assign(funcs.size(), nullptr);
+  for (cudaGraphNode_t nd : all) {
+    cudaGraphNodeType ty;
+    TCI_CUDA(ctx, cudaGraphNodeGetType(nd, &ty));
+    if (ty != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeParams kp;
+    TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(nd, &kp));
+    for (size_t i = 0; i < funcs.size(); ++i)
+      if (kp.func == funcs[i] && !g->nodes[i]) g->nodes[i] = nd;
+  }
+  for (auto nd : g->nodes)
+    if (!nd) {
+      cudaGraphDestroy(graph);
+      return tci_fail(ctx, TCI_ERR_CUDA, "graph capture: kernel node not found");
+    }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  if (e != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return tci_cuda_fail(ctx, e, "cudaGraphInstantiate");
+  }
+  g->graph = graph;
+  g->exec = exec;
+  return TCI_OK;
+}
+
+void tci_graph_destroy(tci_graph* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  if (g->cap) cudaStreamDestroy(g->cap);
+  g->exec = nullptr;
+  g->graph = nullptr;
+  g->cap = nullptr;
+  g->nodes.clear();
+}

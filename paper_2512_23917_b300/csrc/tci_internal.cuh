@@ -133,6 +133,22 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
 void tci_split_group_destroy(tci_split_group* g);
 tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k);
 
+// Captured launch sequence of a plan.  The sequence is captured once on a
+// private stream (capture is not possible on the legacy default stream) and
+// replayed on the context stream; kernel nodes whose pointer arguments change
+// per call are updated with cudaGraphExecKernelNodeSetParams.
+struct tci_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cap = nullptr;
+  std::vector<cudaGraphNode_t> nodes;   // kernel nodes in the order of `funcs`
+};
+// Capture `body` (which launches on ctx->stream) into g and locate the kernel
+// nodes of the listed device functions.
+tci_status tci_graph_capture(tci_context ctx, tci_graph* g, tci_status (*body)(void*), void* arg,
+                             const std::vector<const void*>& funcs);
+void tci_graph_destroy(tci_graph* g);
+
 // K0: split a strided FP64/FP32 operand into three bfloat16 planes, packed
 // K-major: out[p][r][k] for r < rows, k < Kp (zero for k >= K).  Element
 // (r, k) of the source is at src[r*sr + k*sk] (with an optional 2-level row

@@ -115,12 +115,16 @@ struct tci_tebd_plan_s {
   float* P = nullptr;      // P1, P2, P3 per bond
   BondJob* d_jobs = nullptr;
   tci_split_group* group = nullptr;
+  tci_graph graph;   // captured split -> grouped GEMM -> gate
+  const void *cA = nullptr, *cB = nullptr, *cG = nullptr;
+  void* cT = nullptr;
 };
 
 extern "C" tci_status tci_tebd_plan_destroy(tci_tebd_plan* pp) {
   if (!pp || !*pp || (*pp)->magic != kTebdMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "tebd_plan_destroy: invalid plan");
   tci_tebd_plan p = *pp;
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
+  tci_graph_destroy(&p->graph);
   tci_split_group_destroy(p->group);
   tci_dev_free(p->arena);
   tci_dev_free(p->P);
@@ -209,20 +213,48 @@ extern "C" double tci_tebd_flops(tci_tebd_plan p) {
   return p->flops;
 }
 
+static tci_status tebd_launch_all(void* arg) {
+  tci_tebd_plan p = (tci_tebd_plan)arg;
+  tci_context ctx = p->ctx;
+  const int64_t mc = p->max_chi;
+  dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
+  k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)p->cA, (const float2*)p->cB, (__nv_bfloat16*)p->arena);
+  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k));
+  dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
+  k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)p->cG, (float2*)p->cT);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
 extern "C" tci_status tci_tebd_apply(tci_tebd_plan p, const void* A, const void* B, const void* G, void* theta) {
   if (!p || p->magic != kTebdMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "tebd_apply: invalid plan");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "tebd_apply");
   if (!A || !B || !G || !theta) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "tebd_apply: NULL buffer");
-  const int64_t mc = p->max_chi;
-  dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
-  k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)A, (const float2*)B, (__nv_bfloat16*)p->arena);
-  TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k));
-  dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
-  k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)G, (float2*)theta);
-  TCI_CUDA(ctx, cudaGetLastError());
+  p->cA = A;
+  p->cB = B;
+  p->cG = G;
+  p->cT = theta;
+  if (!p->graph.exec) {
+    TCI_TRY(tebd_launch_all(p));
+    return tci_graph_capture(ctx, &p->graph, tebd_launch_all, p, {(const void*)k_tebd_split, (const void*)k_tebd_gate});
+  }
+  const BondJob* jobs = p->d_jobs;
+  __nv_bfloat16* arena = (__nv_bfloat16*)p->arena;
+  const float* P = p->P;
+  void* sargs[4] = {(void*)&jobs, (void*)&A, (void*)&B, (void*)&arena};
+  void* gargs[4] = {(void*)&jobs, (void*)&P, (void*)&G, (void*)&theta};
+  void** argv[2] = {sargs, gargs};
+  for (int i = 0; i < 2; ++i) {
+    cudaKernelNodeParams kp;
+    TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(p->graph.nodes[i], &kp));
+    kp.kernelParams = argv[i];
+    kp.extra = nullptr;
+    TCI_CUDA(ctx, cudaGraphExecKernelNodeSetParams(p->graph.exec, p->graph.nodes[i], &kp));
+  }
+  TCI_CUDA(ctx, cudaGraphLaunch(p->graph.exec, ctx->stream));
   return TCI_OK;
 }
 

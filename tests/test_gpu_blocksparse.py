@@ -56,3 +56,25 @@ def test_blocksparse_repeat_is_deterministic(ctx, tci):
     b, _, _ = run_bs(tci, ctx, inp)
     for k in a:
         np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_blocksparse_graph_replay_with_new_buffers(ctx, tci):
+    """Later calls replay a captured CUDA graph; inputs in fresh buffers must be picked up."""
+    import torch
+    inp = blocksparse_inputs(total=120, seed=12, qmax=6, sigma=2.5)
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    plan = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                          to_dev(tci.pack_blocks(inp["L"], st["L"])), to_dev(tci.pack_blocks(inp["R"], st["R"])),
+                          to_dev(inp["W"]))
+    shapes = {k: (dims[k[0]], dims[k[3]]) for k in st["psi"]}
+    rng = np.random.default_rng(5)
+    for call in range(4):
+        psi_blocks = {k: rng.standard_normal(v.shape).astype(np.float32) for k, v in inp["psi"].items()}
+        psi = to_dev(tci.pack_blocks(psi_blocks, st["psi"]))
+        out = torch.full_like(psi, float("nan"))
+        plan.apply(psi, out)
+        torch.cuda.synchronize()
+        got = tci.unpack_blocks(out.cpu().numpy(), st["psi"], shapes)
+        ref, _ = o_bs.bs_heff_apply(dict(inp, psi=psi_blocks))
+        assert blocks_err(got, ref) < 1e-6, call

@@ -58,3 +58,27 @@ def test_tebd_unitary_gate_preserves_norm(ctx, tci):
     plain, _ = run_tebd(tci, ctx, chis, A, B, eye)
     for g_, p_ in zip(got, plain):
         assert abs(np.linalg.norm(g_) - np.linalg.norm(p_)) < 1e-5 * np.linalg.norm(p_)
+
+
+def test_tebd_graph_replay_with_new_buffers(ctx, tci):
+    """Later calls replay a captured CUDA graph with updated pointer arguments."""
+    import torch
+    chis = [9, 33, 70, 5]
+    plan = tci.TebdPlan(ctx, chis)
+    for call, seed in enumerate((21, 22, 23)):
+        _, A, B, G = tebd_inputs(len(chis), seed=seed, chi_lo=1, chi_hi=1)
+        rng = np.random.default_rng(seed)
+        A = [(rng.standard_normal((c, 2, c)) + 1j * rng.standard_normal((c, 2, c))).astype(np.complex64) for c in chis]
+        B = [(rng.standard_normal((c, 2, c)) + 1j * rng.standard_normal((c, 2, c))).astype(np.complex64) for c in chis]
+        G = G[:1] * len(chis)
+        pa = to_dev(np.concatenate([a.ravel() for a in A]))
+        pb = to_dev(np.concatenate([b.ravel() for b in B]))
+        pg = to_dev(np.concatenate([g.ravel() for g in G]))
+        th = torch.full((sum(4 * c * c for c in chis),), complex("nan+nanj"), dtype=torch.complex64, device="cuda")
+        plan.apply(pa, pb, pg, th)
+        torch.cuda.synchronize()
+        th = th.cpu().numpy()
+        off = 0
+        for c, a, b, g in zip(chis, A, B, G):
+            assert rel_frob_err(th[off:off + 4 * c * c].reshape(c, 2, 2, c), o_tebd.theta(a, b, g)) < 1e-5, call
+            off += 4 * c * c
