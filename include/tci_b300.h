@@ -363,6 +363,23 @@ tci_status tci_tebd_apply_timed(tci_tebd_plan plan, const void* A, const void* B
 /* BF16 tensor-core flops the grouped launch executes (3 real GEMMs per bond). */
 double tci_tebd_tensor_flops(tci_tebd_plan plan);
 
+/* ------------------------------------------- autotuner and plan cache
+ * (An implementation facility; the paper has no counterpart.)  Time the
+ * candidate configurations of the split-BF16 tensor-core GEMM on the plan's
+ * own operands -- the hi*hi accumulation chunk (128/256/512, capped by
+ * max_chunk_k: the measured relative error of the chi = 2048 matvec is
+ * 2.2e-7 / 4.3e-7 / 8.8e-7), the cross-product chunk (1024/4096) and the
+ * tile order (m-fastest or groups of 8/16 m-blocks) -- and keep the fastest
+ * in the plan.  Results are cached per (plan kind, shape, device) in memory
+ * and, when TCI_AUTOTUNE_CACHE names a file, in that file (read first, so a
+ * cached shape is not timed again).  chosen (may be NULL) receives 3 ints:
+ * chunk_k, xchunk_k, raster.  The inputs are used as timing data only
+ * (outputs are overwritten).  Synchronises.  Errors: INVALID_ARG, SHAPE, CUDA. */
+tci_status tci_heff_autotune(tci_heff_plan plan, tci_tensor psi, tci_tensor out, int max_chunk_k, int* chosen);
+tci_status tci_bs_autotune(tci_bs_plan plan, const float* psi, int max_chunk_k, int* chosen);
+tci_status tci_tebd_autotune(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,
+                             int max_chunk_k, int* chosen);
+
 #ifdef __cplusplus
 }
 #endif

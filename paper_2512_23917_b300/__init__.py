@@ -95,6 +95,9 @@ SIGNATURES = [
     ("tci_tebd_tensor_flops", C.c_double, [_p]),
     ("tci_bs_heff_apply_timed", C.c_int, [_p, _p, _p, C.POINTER(C.c_float)]),
     ("tci_bs_tensor_flops", C.c_double, [_p]),
+    ("tci_heff_autotune", C.c_int, [_p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
+    ("tci_bs_autotune", C.c_int, [_p, _p, C.c_int, C.POINTER(C.c_int)]),
+    ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
 ]
 
@@ -391,6 +394,13 @@ class HeffPlan:
         _check(lib.tci_heff_apply_timed(self.handle, tp.handle, to.handle, ms), self.ctx.handle)
         return list(ms)
 
+    def autotune(self, psi, out, max_chunk_k: int = 256):
+        """Tune the split GEMM configuration on these operands; returns (chunk_k, xchunk_k, raster)."""
+        ch = (C.c_int * 3)()
+        tp, to = self.ctx.wrap(psi), self.ctx.wrap(out)
+        _check(lib.tci_heff_autotune(self.handle, tp.handle, to.handle, int(max_chunk_k), ch), self.ctx.handle)
+        return tuple(ch)
+
     def apply_host(self, psi_host: np.ndarray, out_host: np.ndarray):
         assert psi_host.dtype == np.float64 and out_host.dtype == np.float64
         assert psi_host.flags.c_contiguous and out_host.flags.c_contiguous
@@ -456,6 +466,11 @@ class BsHeffPlan:
     def tensor_flops(self) -> float:
         return lib.tci_bs_tensor_flops(self.handle)
 
+    def autotune(self, psi_packed, max_chunk_k: int = 256):
+        ch = (C.c_int * 3)()
+        _check(lib.tci_bs_autotune(self.handle, _p(psi_packed.data_ptr()), int(max_chunk_k), ch), self.ctx.handle)
+        return tuple(ch)
+
     def apply_timed(self, psi_packed, out_packed):
         ms = (C.c_float * 4)()
         _check(lib.tci_bs_heff_apply_timed(self.handle, _p(psi_packed.data_ptr()), _p(out_packed.data_ptr()), ms),
@@ -513,6 +528,13 @@ class TebdPlan:
     @property
     def tensor_flops(self) -> float:
         return lib.tci_tebd_tensor_flops(self.handle)
+
+    def autotune(self, A_packed, B_packed, G_packed, theta_packed, max_chunk_k: int = 256):
+        ch = (C.c_int * 3)()
+        _check(lib.tci_tebd_autotune(self.handle, _p(A_packed.data_ptr()), _p(B_packed.data_ptr()),
+                                     _p(G_packed.data_ptr()), _p(theta_packed.data_ptr()), int(max_chunk_k), ch),
+               self.ctx.handle)
+        return tuple(ch)
 
     def apply_timed(self, A_packed, B_packed, G_packed, theta_packed):
         ms = (C.c_float * 3)()

@@ -1,0 +1,177 @@
+// Autotuner and plan cache for the split-BF16 tensor-core GEMM.
+//
+// Tuned per plan on the plan's own operands, timed with CUDA events on the
+// context stream:
+//   chunk_k  in {128, 256, 512} (<= the caller's accuracy cap; the hi*hi
+//            accumulation error grows linearly with it, ~2.9e-8 per 16 of
+//            depth per GEMM, measured on B300),
+//   xchunk_k in {1024, 4096},
+//   raster   in {0 (m-fastest), 8, 16 (m-block groups, n-fastest inside)}
+//            for plans whose GEMMs have many tiles per dimension.
+// Winners are cached in memory per (plan kind, shape, device) and, when the
+// environment variable TCI_AUTOTUNE_CACHE names a file, appended to it as one
+// line "key chunk_k xchunk_k raster ms"; a later process reads the file and
+// reuses the entry without timing.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+
+#include "heff_plan.cuh"
+
+namespace {
+
+std::mutex g_tune_mutex;
+std::map<std::string, std::pair<tci_gemm_cfg, double>> g_tune_cache;
+bool g_file_loaded = false;
+
+void load_cache_file() {
+  if (g_file_loaded) return;
+  g_file_loaded = true;
+  const char* path = getenv("TCI_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "r");
+  if (!f) return;
+  char key[512];
+  tci_gemm_cfg c;
+  double ms = 0.0;
+  while (fscanf(f, "%511s %d %d %d %lf", key, &c.chunk_k, &c.xchunk_k, &c.raster, &ms) == 5)
+    g_tune_cache[key] = {c, ms};
+  fclose(f);
+}
+
+void store_cache_file(const std::string& key, const tci_gemm_cfg& c, double ms) {
+  const char* path = getenv("TCI_AUTOTUNE_CACHE");
+  if (!path || !*path) return;
+  FILE* f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), c.chunk_k, c.xchunk_k, c.raster, ms);
+  fclose(f);
+}
+
+}  // namespace
+
+tci_status tci_autotune(tci_context ctx, const std::string& key_in, int max_chunk_k, bool raster_candidates,
+                        tci_status (*run)(void* arg, const tci_gemm_cfg& cfg), void* arg, tci_gemm_cfg* best,
+                        double* best_ms) {
+  if (max_chunk_k < 128) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "autotune: max_chunk_k must be >= 128");
+  cudaDeviceProp prop;
+  TCI_CUDA(ctx, cudaGetDeviceProperties(&prop, ctx->device));
+  std::string dev = prop.name;
+  for (auto& ch : dev)
+    if (ch == ' ') ch = '_';
+  const std::string key = key_in + "|" + dev + "|cap" + std::to_string(max_chunk_k);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    load_cache_file();
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      *best = it->second.first;
+      if (best_ms) *best_ms = it->second.second;
+      return TCI_OK;
+    }
+  }
+  std::vector<tci_gemm_cfg> cands;
+  const int chunks[3] = {128, 256, 512};
+  const int xchunks[2] = {1024, 4096};
+  const int rasters[3] = {0, 8, 16};
+  for (int c : chunks) {
+    if (c > max_chunk_k) continue;
+    for (int x : xchunks)
+      for (int r : rasters) {
+        if (!raster_candidates && r != 0) continue;
+        tci_gemm_cfg cfg;
+        cfg.chunk_k = c;
+        cfg.xchunk_k = x;
+        cfg.raster = r;
+        cands.push_back(cfg);
+      }
+  }
+  cudaEvent_t e0, e1;
+  TCI_CUDA(ctx, cudaEventCreate(&e0));
+  TCI_CUDA(ctx, cudaEventCreate(&e1));
+  double bms = 1e300;
+  tci_gemm_cfg bcfg = cands.front();
+  tci_status s = TCI_OK;
+  for (const auto& cfg : cands) {
+    if ((s = run(arg, cfg)) != TCI_OK) break;   // warm-up
+    float total = 0.f;
+    const int reps = 3;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < reps && s == TCI_OK; ++r) s = run(arg, cfg);
+    cudaEventRecord(e1, ctx->stream);
+    if (s != TCI_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = tci_cuda_fail(ctx, e, "autotune timing");
+      break;
+    }
+    cudaEventElapsedTime(&total, e0, e1);
+    const double ms = total / reps;
+    if (ms < bms) {
+      bms = ms;
+      bcfg = cfg;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s != TCI_OK) return s;
+  TCI_TRY(tci_synchronize(ctx));
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    g_tune_cache[key] = {bcfg, bms};
+    store_cache_file(key, bcfg, bms);
+  }
+  *best = bcfg;
+  if (best_ms) *best_ms = bms;
+  return TCI_OK;
+}
+
+// ---------------------------------------------------------------- H_eff plans
+namespace {
+struct HeffTuneArg {
+  tci_heff_plan p;
+  const double* psi;
+  double* out;
+};
+
+tci_status heff_run_cfg(void* a, const tci_gemm_cfg& cfg) {
+  HeffTuneArg* t = (HeffTuneArg*)a;
+  t->p->chunk_k = cfg.chunk_k;
+  t->p->xchunk_k = cfg.xchunk_k;
+  t->p->raster = cfg.raster;
+  return tci_heff_apply_raw(t->p, t->psi, t->out, false);
+}
+}  // namespace
+
+extern "C" tci_status tci_heff_autotune(tci_heff_plan p, tci_tensor psi, tci_tensor out, int max_chunk_k, int* chosen) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_autotune: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "heff_autotune");
+  if (!tci_ten_ok(psi) || !tci_ten_ok(out) || psi->dtype != TCI_F64 || out->dtype != TCI_F64 ||
+      tci_numel(psi) != p->chiL * 4 * p->chiR || tci_numel(out) != p->chiL * 4 * p->chiR || !tci_is_rowmajor(psi) ||
+      !tci_is_rowmajor(out))
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_autotune: psi/out must be row-major F64 [chiL,2,2,chiR]");
+  if (p->prec == TCI_PREC_NATIVE) {   // nothing to tune on the FP64 path
+    if (chosen) chosen[0] = chosen[1] = chosen[2] = 0;
+    return TCI_OK;
+  }
+  HeffTuneArg arg{p, (const double*)psi->data, (double*)out->data};
+  const std::string key = "heff|" + std::to_string(p->chiL) + "x" + std::to_string(p->chiR) + "|p" +
+                          std::to_string(p->products);
+  tci_gemm_cfg best;
+  double ms = 0.0;
+  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, heff_run_cfg, &arg, &best, &ms));
+  heff_run_cfg(&arg, best);   // leaves the plan configured with the winner
+  if (chosen) {
+    chosen[0] = best.chunk_k;
+    chosen[1] = best.xchunk_k;
+    chosen[2] = best.raster;
+  }
+  vs.info = "chunk=" + std::to_string(best.chunk_k) + " xchunk=" + std::to_string(best.xchunk_k) +
+            " raster=" + std::to_string(best.raster) + " ms=" + std::to_string(ms);
+  return tci_synchronize(ctx);
+}

@@ -199,6 +199,7 @@ struct tci_bs_plan_s {
   int magic;
   tci_context ctx;
   int products, chunk_k, xchunk_k;
+  int raster = 0;
   int64_t psi_elems;          // packed psi/out element count
   double flops;               // algorithmic flops of one matvec
   // device buffers
@@ -559,10 +560,10 @@ static tci_status bs_launch_all(void* arg) {
     k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, p->cap_psi, (__nv_bfloat16*)p->arena);
   }
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   return TCI_OK;
 }
 
@@ -609,11 +610,11 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
     k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
   }
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
   TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));
@@ -627,4 +628,44 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
 extern "C" double tci_bs_tensor_flops(tci_bs_plan p) {
   if (!p || p->magic != kBsMagic) return 0.0;
   return p->tensor_flops;
+}
+
+// ---------------------------------------------------------------- autotuning
+namespace {
+struct BsTuneArg {
+  tci_bs_plan p;
+  const float* psi;
+};
+tci_status bs_run_cfg(void* a, const tci_gemm_cfg& cfg) {
+  BsTuneArg* t = (BsTuneArg*)a;
+  t->p->chunk_k = cfg.chunk_k;
+  t->p->xchunk_k = cfg.xchunk_k;
+  t->p->raster = cfg.raster;
+  t->p->cap_psi = t->psi;
+  return bs_launch_all(t->p);
+}
+}  // namespace
+
+extern "C" tci_status tci_bs_autotune(tci_bs_plan p, const float* psi, int max_chunk_k, int* chosen) {
+  if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_autotune: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "bs_autotune");
+  if (!psi) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_autotune: NULL psi");
+  BsTuneArg arg{p, psi};
+  const std::string key = "bs|n" + std::to_string(p->psi_elems) + "|g" + std::to_string(p->n_gemm1) + "," +
+                          std::to_string(p->n_gemm2) + "|p" + std::to_string(p->products);
+  tci_gemm_cfg best;
+  double ms = 0.0;
+  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, bs_run_cfg, &arg, &best, &ms));
+  p->chunk_k = best.chunk_k;
+  p->xchunk_k = best.xchunk_k;
+  p->raster = best.raster;
+  tci_graph_destroy(&p->graph);   // the next apply captures the tuned sequence
+  if (chosen) {
+    chosen[0] = best.chunk_k;
+    chosen[1] = best.xchunk_k;
+    chosen[2] = best.raster;
+  }
+  return tci_synchronize(ctx);
 }

@@ -245,7 +245,7 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
       if (s != TCI_OK) return cleanup(s);
       const int products = ctx->precision == TCI_PREC_SPLIT_BF16_3 ? 3 : 6;
       s = tci_gemm_split_bf16(ctx, M, N, Kp, Apc, Bpc, Cp, dt == TCI_F32 ? 1 : 0, scm, scn, products,
-                              ctx->split_chunk_k, ctx->split_xchunk_k);
+                              ctx->split_chunk_k, ctx->split_xchunk_k, 0);
       if (s != TCI_OK) return cleanup(s);
     } else {
       s = tci_gemm_native(ctx, dt, M, N, K, Ap, sam, sak, Bp, sbn, sbk, Cp, scm, scn);

@@ -234,10 +234,10 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, b
   for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
   if (!psi_presplit) TCI_TRY(tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1));
   TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products,
-                              p->chunk_k, p->xchunk_k));
+                              p->chunk_k, p->xchunk_k, p->raster));
   TCI_TRY((launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2)));
   TCI_TRY(tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k,
-                              p->xchunk_k));
+                              p->xchunk_k, p->raster));
   return TCI_OK;
 }
 
@@ -264,11 +264,11 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
     for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
     s = tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1);
     TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products, p->chunk_k, p->xchunk_k);
+    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products, p->chunk_k, p->xchunk_k, p->raster);
     TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
     if (s == TCI_OK) s = launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2);
     TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
-    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k, p->xchunk_k);
+    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k, p->xchunk_k, p->raster);
   }
   TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));

@@ -16,6 +16,7 @@ struct tci_heff_plan_s {
   int products;
   int chunk_k;     // split GEMM: K depth per hi*hi accumulation unit
   int xchunk_k;    // split GEMM: K depth per cross-product accumulation unit
+  int raster = 0;  // split GEMM: tile order (autotuned)
   double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
   // intermediates
   void* U = nullptr;       // [(a',t1,t2), (b,wr)]: FP64 (native) or FP32 (split)

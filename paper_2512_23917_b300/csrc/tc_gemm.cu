@@ -74,10 +74,28 @@ struct alignas(64) GemmProblem {
 struct GemmParams {
   const GemmProblem* table;   // grouped launches only
   int nprob, num_tiles;
+  int raster;                 // 0: m-fastest tile order; G > 0: groups of G m-blocks, n-fastest inside
   int kb_d1, kb_x;            // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
   int products;
   int* status;
 };
+
+// Local tile index -> (m-block, n-block).  With raster G > 0, consecutive
+// tiles sweep G m-blocks by all n-blocks, so concurrently running CTAs share
+// both A rows and B rows in L2.
+__device__ __forceinline__ void tile_coords(int lt, int num_m, int num_n, int raster, int& mb, int& nb) {
+  if (raster <= 0 || raster >= num_m) {
+    mb = lt % num_m;
+    nb = lt / num_m;
+    return;
+  }
+  const int per = raster * num_n;
+  const int first = (lt / per) * raster;
+  const int gsz = min(num_m - first, raster);
+  const int r = lt - (lt / per) * per;
+  mb = first + r % gsz;
+  nb = r / gsz;
+}
 
 template <bool G>
 __device__ __forceinline__ const GemmProblem* find_problem(int tile, const GemmProblem* single, const GemmParams& p) {
@@ -187,7 +205,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       for (int tile = blockIdx.x; tile < num_tiles && !*abort_flag; tile += gridDim.x) {
         const GemmProblem* pr = find_problem<G>(tile, &single, p);
         const int lt = tile - pr->tile_begin;
-        const int mb = lt % pr->num_m, nb = lt / pr->num_m;
+        int mb, nb;
+        tile_coords(lt, pr->num_m, pr->num_n, p.raster, mb, nb);
         const int nkb = pr->num_kb;
         for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
@@ -313,7 +332,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       const GemmProblem* pr = find_problem<G>(tile, &single, p);
       const int lt = tile - pr->tile_begin;
-      const int mb = lt % pr->num_m, nb = lt / pr->num_m;
+      int mb, nb;
+        tile_coords(lt, pr->num_m, pr->num_n, p.raster, mb, nb);
       const int nkb = pr->num_kb;
       const int64_t PM = pr->M, PN = pr->N, scm = pr->scm, scn = pr->scn;
       void* const PC = pr->C;
@@ -445,7 +465,7 @@ static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int6
   return TCI_OK;
 }
 
-static tci_status common_params(tci_context ctx, GemmParams* gp, int products, int chunk_k, int xchunk_k) {
+static tci_status common_params(tci_context ctx, GemmParams* gp, int products, int chunk_k, int xchunk_k, int raster) {
   if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
   static bool attr_set = false;
   if (!attr_set) {
@@ -459,19 +479,20 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
   const int kx = xchunk_k < TBK ? 1 : xchunk_k / TBK;
   gp->kb_x = (kx + gp->kb_d1 - 1) / gp->kb_d1 * gp->kb_d1;   // X drains line up with D1 drains
   gp->products = products;
+  gp->raster = raster;
   gp->status = ctx->d_status;
   return TCI_OK;
 }
 
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
                                void* C, int out_f32, int64_t scm, int64_t scn, int products, int chunk_k,
-                               int xchunk_k) {
+                               int xchunk_k, int raster) {
   if (M <= 0 || N <= 0) return TCI_OK;
   GemmProblem pr;
   TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_f32, scm, scn));
   GemmParams gp;
   memset(&gp, 0, sizeof gp);
-  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k));
+  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
   gp.nprob = 1;
   gp.num_tiles = pr.num_m * pr.num_n;
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
@@ -535,11 +556,12 @@ void tci_split_group_destroy(tci_split_group* g) {
   delete g;
 }
 
-tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k) {
+tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k,
+                                  int raster) {
   if (!g || g->nprob == 0) return TCI_OK;
   GemmParams gp;
   memset(&gp, 0, sizeof gp);
-  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k));
+  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
   gp.table = g->d_table;
   gp.nprob = g->nprob;
   gp.num_tiles = g->num_tiles;

@@ -114,10 +114,27 @@ tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, 
 // (K-major rows, Kp % 8 == 0, plane stride = rows*Kp).  C element (m, n) at
 // C[m*scm + n*scn], FP64 (out_f32 = 0) or FP32 (out_f32 = 1).  products = 6
 // or 3.  chunk_k: K depth of one hi*hi accumulation unit (multiple of 32);
-// xchunk_k: K depth of one cross-product accumulation unit.
+// xchunk_k: K depth of one cross-product accumulation unit.  raster: tile
+// order (0 m-fastest, G > 0 groups of G m-blocks with n fastest inside).
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp,
                                const void* Apieces, const void* Bpieces, void* C, int out_f32,
-                               int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k);
+                               int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k,
+                               int raster);
+
+// Configuration of the split GEMM chosen by the autotuner (or defaults).
+struct tci_gemm_cfg {
+  int chunk_k = 256;
+  int xchunk_k = 1024;
+  int raster = 0;
+};
+// Time candidate configurations with `run` (which must launch the plan's
+// work with the given configuration on ctx->stream) and return the fastest
+// whose chunk_k <= max_chunk_k.  `key` identifies the plan shape in the
+// autotune cache (file named by TCI_AUTOTUNE_CACHE, when set); a cached entry
+// is used without timing.  raster_candidates: whether tile order is tuned.
+tci_status tci_autotune(tci_context ctx, const std::string& key, int max_chunk_k, bool raster_candidates,
+                        tci_status (*run)(void* arg, const tci_gemm_cfg& cfg), void* arg, tci_gemm_cfg* best,
+                        double* best_ms);
 
 // Grouped split-BF16 GEMM: all problems run in one persistent launch.
 struct tci_split_problem {
@@ -131,7 +148,8 @@ struct tci_split_problem {
 struct tci_split_group;
 tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out);
 void tci_split_group_destroy(tci_split_group* g);
-tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k);
+tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k,
+                                  int raster);
 
 // Captured launch sequence of a plan.  The sequence is captured once on a
 // private stream (capture is not possible on the legacy default stream) and

@@ -108,6 +108,7 @@ struct tci_tebd_plan_s {
   tci_context ctx;
   int nbonds;
   int products, chunk_k, xchunk_k;
+  int raster = 0;
   int64_t max_chi;
   double flops;
   double tensor_flops = 0.0;
@@ -220,7 +221,7 @@ static tci_status tebd_launch_all(void* arg) {
   dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)p->cA, (const float2*)p->cB, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k, p->raster));
   dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)p->cG, (float2*)p->cT);
   TCI_CUDA(ctx, cudaGetLastError());
@@ -273,7 +274,7 @@ extern "C" tci_status tci_tebd_apply_timed(tci_tebd_plan p, const void* A, const
   dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)A, (const float2*)B, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k));
+  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)G, (float2*)theta);
@@ -289,4 +290,43 @@ extern "C" tci_status tci_tebd_apply_timed(tci_tebd_plan p, const void* A, const
 extern "C" double tci_tebd_tensor_flops(tci_tebd_plan p) {
   if (!p || p->magic != kTebdMagic) return 0.0;
   return p->tensor_flops;
+}
+
+// ---------------------------------------------------------------- autotuning
+namespace {
+tci_status tebd_run_cfg(void* a, const tci_gemm_cfg& cfg) {
+  tci_tebd_plan p = (tci_tebd_plan)a;
+  p->chunk_k = cfg.chunk_k;
+  p->xchunk_k = cfg.xchunk_k;
+  p->raster = cfg.raster;
+  return tebd_launch_all(p);
+}
+}  // namespace
+
+extern "C" tci_status tci_tebd_autotune(tci_tebd_plan p, const void* A, const void* B, const void* G, void* theta,
+                                        int max_chunk_k, int* chosen) {
+  if (!p || p->magic != kTebdMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "tebd_autotune: invalid plan");
+  tci_context ctx = p->ctx;
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "tebd_autotune");
+  if (!A || !B || !G || !theta) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "tebd_autotune: NULL buffer");
+  p->cA = A;
+  p->cB = B;
+  p->cG = G;
+  p->cT = theta;
+  const std::string key = "tebd|b" + std::to_string(p->nbonds) + "|max" + std::to_string(p->max_chi) + "|f" +
+                          std::to_string((long long)(p->flops / 1e6)) + "|p" + std::to_string(p->products);
+  tci_gemm_cfg best;
+  double ms = 0.0;
+  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, tebd_run_cfg, p, &best, &ms));
+  p->chunk_k = best.chunk_k;
+  p->xchunk_k = best.xchunk_k;
+  p->raster = best.raster;
+  tci_graph_destroy(&p->graph);
+  if (chosen) {
+    chosen[0] = best.chunk_k;
+    chosen[1] = best.xchunk_k;
+    chosen[2] = best.raster;
+  }
+  return tci_synchronize(ctx);
 }
