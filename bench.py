@@ -150,17 +150,15 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU path
 def lanczos_launches(m: int) -> int:
-    """Kernel launches of one m-step Lanczos solve (4 per matvec + vector kernels)."""
-    n = 3  # init scalars, start-vector norm (sumsq + reduce) counted below
-    n = 1 + 2 + 1
+    """Kernel launches of one m-step Lanczos solve with double-float vectors and CGS2 (basis <= 24 vectors)."""
+    n = 4                                           # init scalars, psi0 sum of squares + reduce, start vector
     for j in range(m):
-        n += 4                                      # split, GEMM1, W.W, GEMM2
-        n += 1 + 1 + 1                              # alpha mdot + reduce, three-term
-        groups = (j + 1 + 7) // 8
-        n += 2 * (groups + 1 + groups)              # CGS2: mdot groups + reduce + update groups
-        n += 2 + 1                                  # sumsq + reduce, finish_beta
+        n += 3                                      # GEMM1, W.W, GEMM2 (the split is fused into the next-vector kernel)
+        n += 2 + 1                                  # pass-1 dots + reduce, alpha
+        n += 2 + 2                                  # pass-2 update+dots + reduce, pass-3 update+norm + reduce
+        n += 1                                      # beta / stop test
         if j + 1 < m:
-            n += 1                                  # next vector
+            n += 1                                  # v_{j+1} = w / beta and its bfloat16 pieces
     n += 2                                          # tridiagonal eigensolve, Ritz vector
     return n
 
@@ -320,6 +318,18 @@ def run_gpu(args):
     ms_step = ms_total / args.steps
     value = world * LANCZOS_STEPS * F / (ms_step * 1e-3) / 1e9
 
+    # ---- the same solve with FP64 vector arithmetic (context for the double-float choice)
+    plan.set_lanczos_arith("f64")
+    plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res64 = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lanczos_f64_ms = e0.elapsed_time(e1)
+    plan.set_lanczos_arith("auto")
+
     # ---- per-stage events of single matvecs (roofline of the GEMM kernel)
     stages = []
     for _ in range(5):
@@ -397,13 +407,18 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "20-step Lanczos on the dense two-site H_eff, Heisenberg MPO, chi=2048, d=2, Dw=5, "
-                                   "split-BF16 matvec (3 pieces, 6 products, FP32 accumulate, FP64 promote every "
-                                   "1024 of K), FP64 Lanczos",
+                                   "split-BF16 matvec (3 pieces, 6 products, FP32 tensor-memory accumulation drained "
+                                   "every chunk_k of K into a double-float sum), Lanczos vectors in double-float "
+                                   "(FP32 pairs), scalars FP64",
                        "chi": CHI, "lanczos_steps": LANCZOS_STEPS, "seed": SEED,
                        "l2": "inputs larger than L2 (psi 134 MB, basis 2.8 GB)", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": lanczos_launches(LANCZOS_STEPS) * args.steps,
             "clocks": clocks, "ritz_value": res["theta"] if res else None,
-            "autotune": {"chunk_k": tuned[0], "xchunk_k": tuned[1], "raster": tuned[2], "max_chunk_k": 256},
+            "autotune": {"chunk_k": tuned[0], "xchunk_k": tuned[1], "raster": tuned[2], "max_chunk_k": 256,
+                         "ww_a_per_thread": plan.get_config()[3]},
+            "lanczos_f64_vectors": {"ms_per_step": lanczos_f64_ms, "ritz_value": res64["theta"],
+                                    "ritz_rel_diff_vs_double_float": abs(res64["theta"] - res["theta"]) / abs(res64["theta"])
+                                    if res else None},
             "matvec": {"gflops": F / (mv_only_ms * 1e-3) / 1e9, "ms": mv_only_ms,
                        "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),
                                     "gemm2": float(st[3])}}}

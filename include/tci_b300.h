@@ -281,9 +281,30 @@ double tci_heff_flops(tci_heff_plan plan);
 tci_status tci_heff_apply_noalloc(const double* L, const double* W, const double* R, const double* psi,
                                   double* out, int64_t chiL, int64_t chiR, void* stream);
 
+/* Vector arithmetic of tci_lanczos (extension; the paper has no Lanczos
+ * API).  TCI_LANCZOS_F64: every dot product and vector update in FP64.
+ * TCI_LANCZOS_DF32: vectors held as pairs of FP32 numbers hi + lo
+ * (double-float, Dekker 1971; ~48 significant bits) with error-free
+ * transformations, so the vector passes run on the FP32 pipes (B300 issues
+ * FP64 FMAs at ~1/64 of its FP32 rate); Ritz values agree with the FP64
+ * arithmetic to ~1e-12 relative.  TCI_LANCZOS_AUTO: F64 for a plan made
+ * with TCI_PREC_NATIVE, DF32 for the split-BF16 precisions. */
+typedef enum {
+  TCI_LANCZOS_AUTO = 0,
+  TCI_LANCZOS_F64 = 1,
+  TCI_LANCZOS_DF32 = 2
+} tci_lanczos_arith;
+
+/* Select the vector arithmetic of later tci_lanczos calls on `plan`.
+ * Errors: INVALID_ARG (invalid plan or value), INVALID_CONTEXT. */
+tci_status tci_heff_set_lanczos_arith(tci_heff_plan plan, tci_lanczos_arith arith);
+
 /* Lanczos ground state of H_eff (textbook; Golub & Van Loan Sec. 10.1 with
  * classical Gram-Schmidt applied twice when reorth != 0; Ritz value by Sturm
- * bisection, Sec. 8.4).  All vector arithmetic in FP64 on the device.
+ * bisection, Sec. 8.4).  All vector work runs on the device, in the
+ * arithmetic chosen by tci_heff_set_lanczos_arith (by default FP64 for an
+ * FP64 plan and double-float for a split-BF16 plan); scalars (alpha, beta,
+ * Gram-Schmidt coefficients, the tridiagonal eigenpair) are FP64.
  * psi0: start vector [chiL,d,d,chiR] F64 (normalised internally, not
  * modified).  Runs up to nsteps (1..256) steps, stopping early when
  * beta_j < 1e-12 |alpha_j|.  Outputs (host): *ritz, alpha[nsteps],
@@ -372,10 +393,21 @@ double tci_tebd_tensor_flops(tci_tebd_plan plan);
  * tile order (m-fastest or groups of 8/16 m-blocks) -- and keep the fastest
  * in the plan.  Results are cached per (plan kind, shape, device) in memory
  * and, when TCI_AUTOTUNE_CACHE names a file, in that file (read first, so a
- * cached shape is not timed again).  chosen (may be NULL) receives 3 ints:
- * chunk_k, xchunk_k, raster.  The inputs are used as timing data only
+ * cached shape is not timed again); the W.W kernel variant is timed too
+ * (not cached).  chosen (may be NULL) receives 3 ints: chunk_k, xchunk_k,
+ * raster.  The inputs are used as timing data only
  * (outputs are overwritten).  Synchronises.  Errors: INVALID_ARG, SHAPE, CUDA. */
 tci_status tci_heff_autotune(tci_heff_plan plan, tci_tensor psi, tci_tensor out, int max_chunk_k, int* chosen);
+/* Read / set the configuration of a split-BF16 H_eff plan (extension; no
+ * counterpart in the paper): cfg[0] chunk_k, cfg[1] xchunk_k (as in
+ * tci_context_set_split_chunks), cfg[2] raster (tile order: 0 m-fastest,
+ * G > 0 groups of G m-blocks), cfg[3] a' per thread of the W.W kernel
+ * (2 or 4).  tci_heff_autotune sets all four; set_config lets a caller
+ * replay a known configuration without timing.  For an FP64 plan get
+ * returns zeros and set is rejected.  Errors: INVALID_ARG (invalid plan,
+ * NULL cfg, values outside the rules above), UNSUPPORTED (FP64 plan). */
+tci_status tci_heff_get_config(tci_heff_plan plan, int* cfg);
+tci_status tci_heff_set_config(tci_heff_plan plan, const int* cfg);
 tci_status tci_bs_autotune(tci_bs_plan plan, const float* psi, int max_chunk_k, int* chosen);
 tci_status tci_tebd_autotune(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,
                              int max_chunk_k, int* chosen);

@@ -99,6 +99,9 @@ SIGNATURES = [
     ("tci_bs_autotune", C.c_int, [_p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
+    ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
+    ("tci_heff_get_config", C.c_int, [_p, C.POINTER(C.c_int)]),
+    ("tci_heff_set_config", C.c_int, [_p, C.POINTER(C.c_int)]),
 ]
 
 for _name, _res, _args in SIGNATURES:
@@ -401,12 +404,28 @@ class HeffPlan:
         _check(lib.tci_heff_autotune(self.handle, tp.handle, to.handle, int(max_chunk_k), ch), self.ctx.handle)
         return tuple(ch)
 
+    def get_config(self):
+        """(chunk_k, xchunk_k, raster, W.W a' per thread) of a split-BF16 plan."""
+        cfg = (C.c_int * 4)()
+        _check(lib.tci_heff_get_config(self.handle, cfg), self.ctx.handle)
+        return tuple(cfg)
+
+    def set_config(self, chunk_k: int, xchunk_k: int, raster: int, ww_na: int):
+        cfg = (C.c_int * 4)(int(chunk_k), int(xchunk_k), int(raster), int(ww_na))
+        _check(lib.tci_heff_set_config(self.handle, cfg), self.ctx.handle)
+
     def apply_host(self, psi_host: np.ndarray, out_host: np.ndarray):
         assert psi_host.dtype == np.float64 and out_host.dtype == np.float64
         assert psi_host.flags.c_contiguous and out_host.flags.c_contiguous
         _check(lib.tci_heff_apply_host(self.handle, _p(psi_host.ctypes.data), _p(out_host.ctypes.data)),
                self.ctx.handle)
         return out_host
+
+    LANCZOS_ARITH = {"auto": 0, "f64": 1, "df32": 2}
+
+    def set_lanczos_arith(self, arith: str):
+        """Vector arithmetic of lanczos(): "auto", "f64" or "df32" (double-float FP32 pairs)."""
+        _check(lib.tci_heff_set_lanczos_arith(self.handle, self.LANCZOS_ARITH[arith]), self.ctx.handle)
 
     def lanczos(self, psi0, nsteps: int, reorth: bool = True, x=None):
         ritz = C.c_double()

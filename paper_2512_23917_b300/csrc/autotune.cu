@@ -165,13 +165,43 @@ extern "C" tci_status tci_heff_autotune(tci_heff_plan p, tci_tensor psi, tci_ten
   tci_gemm_cfg best;
   double ms = 0.0;
   TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, heff_run_cfg, &arg, &best, &ms));
-  heff_run_cfg(&arg, best);   // leaves the plan configured with the winner
+  heff_run_cfg(&arg, best);   // leaves the plan configured with the winner (and U, V filled)
+  float ww_ms = 0.f;
+  TCI_TRY(tci_heff_tune_ww(p, &ww_ms));
   if (chosen) {
     chosen[0] = best.chunk_k;
     chosen[1] = best.xchunk_k;
     chosen[2] = best.raster;
   }
   vs.info = "chunk=" + std::to_string(best.chunk_k) + " xchunk=" + std::to_string(best.xchunk_k) +
-            " raster=" + std::to_string(best.raster) + " ms=" + std::to_string(ms);
+            " raster=" + std::to_string(best.raster) + " ms=" + std::to_string(ms) + " ww_na=" + std::to_string(p->ww_na) +
+            " ww_ms=" + std::to_string(ww_ms);
   return tci_synchronize(ctx);
+}
+
+extern "C" tci_status tci_heff_get_config(tci_heff_plan p, int* cfg) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_get_config: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (!cfg) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_get_config: NULL cfg");
+  const bool split = p->prec != TCI_PREC_NATIVE;
+  cfg[0] = split ? p->chunk_k : 0;
+  cfg[1] = split ? p->xchunk_k : 0;
+  cfg[2] = split ? p->raster : 0;
+  cfg[3] = split ? p->ww_na : 0;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_config(tci_heff_plan p, const int* cfg) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_set_config: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (!cfg) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_set_config: NULL cfg");
+  if (p->prec == TCI_PREC_NATIVE) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "heff_set_config: FP64 plan has no configuration");
+  const int c = cfg[0], x = cfg[1], r = cfg[2], na = cfg[3];
+  if (c < 32 || c % 32 != 0 || x < c || x % c != 0 || r < 0 || (na != 2 && na != 4))
+    return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_set_config: need 32 | chunk_k, chunk_k | xchunk_k, raster >= 0, W.W a' per thread 2 or 4");
+  p->chunk_k = c;
+  p->xchunk_k = x;
+  p->raster = r;
+  p->ww_na = na;
+  return TCI_OK;
 }

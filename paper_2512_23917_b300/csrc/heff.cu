@@ -3,6 +3,7 @@
 // evaluated right-to-left as three steps whose GEMMs are all "TN" (both
 // operands K-major, read in place):
 //   GEMM1  U[(a',t1,t2), (b,wr)]   = sum_b'       psi[(a',t1,t2), b'] R[(b,wr), b']
+//          (stored transposed on the split path, U^T[(b,wr), (a',t1,t2)])
 //   WW     V[(s1,s2,b), (wl,a')]   = sum_{wr,t1,t2} WW[wl,s1,s2,wr,t1,t2] U[(a',t1,t2),(b,wr)]
 //   GEMM2  out[a, (s1,s2,b)]       = sum_{wl,a'}  L[a, (wl,a')] V[(s1,s2,b), (wl,a')]
 // with WW[wl,s1,s2,wr,t1,t2] = sum_wm W[wl,wm,s1,t1] W[wm,wr,s2,t2] formed
@@ -14,6 +15,10 @@
 #include "heff_plan.cuh"
 
 namespace {
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
 
 // ------------------------------------------------------------------ WW = W.W
 __global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, double* __restrict__ WW) {
@@ -35,23 +40,23 @@ __global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, dou
 }
 
 // ------------------------------------------------------------------ W.W application
-// One block: a' in [a0, a0+ATILE), b in [b0, b0+BT), one (a', b) pair per
-// thread (ATILE*BT = 256).  The U rows (a', t) of the tile are staged in
-// shared memory (row segments of BT*Dw contiguous values), then each thread
-// forms the 20 outputs of its pair and writes them with a' fastest, which is
-// contiguous along GEMM2's K dimension.
 template <typename T>
 struct WWArgs {
   T ww[HEFF_DW * 4 * HEFF_DW * 4];   // [wl][s][wr][t], s = (s1 s2), t = (t1 t2)
 };
 
-template <typename T, typename UT, int ATILE, int BT, bool SPLIT>
-__global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<T> args, const UT* __restrict__ U,
-                                                          int64_t chiL, int64_t chiR, void* __restrict__ Vout,
-                                                          int64_t ldv, int64_t plane) {
+// FP64 path.  U [(a',t), (b,wr)].  One block: a' in [a0, a0+ATILE), b in
+// [b0, b0+BT), one (a', b) pair per thread (ATILE*BT = 256).  The U rows
+// (a', t) of the tile are staged in shared memory (row segments of BT*Dw
+// contiguous values), then each thread forms the 20 outputs of its pair and
+// writes them with a' fastest, which is contiguous along GEMM2's K dimension.
+template <int ATILE, int BT>
+__global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<double> args, const double* __restrict__ U,
+                                                          int64_t chiL, int64_t chiR, double* __restrict__ V,
+                                                          int64_t ldv) {
   constexpr int Dw = HEFF_DW, D2 = 4;
   constexpr int ROW = D2 * BT * Dw;   // staged values per a'
-  __shared__ T Us[ATILE][ROW + 1];
+  __shared__ double Us[ATILE][ROW + 1];
   const int64_t a0 = (int64_t)blockIdx.y * ATILE;
   const int64_t b0 = (int64_t)blockIdx.x * BT;
   const int64_t ldu = chiR * Dw;
@@ -61,15 +66,15 @@ __global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<T> args
     const int al = rt / D2, t = rt % D2;
     const int64_t ap = a0 + al;
     const int64_t gcol = b0 * Dw + col;
-    T v = (T)0;
-    if (ap < chiL && gcol < ldu) v = (T)U[(ap * D2 + t) * ldu + gcol];
+    double v = 0.0;
+    if (ap < chiL && gcol < ldu) v = U[(ap * D2 + t) * ldu + gcol];
     Us[al][t * BT * Dw + col] = v;
   }
   __syncthreads();
   const int al = threadIdx.x % ATILE, bl = threadIdx.x / ATILE;
   const int64_t ap = a0 + al, b = b0 + bl;
   if (ap >= chiL || b >= chiR) return;
-  T in[D2 * Dw];
+  double in[D2 * Dw];
 #pragma unroll
   for (int t = 0; t < D2; ++t)
 #pragma unroll
@@ -80,38 +85,183 @@ __global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<T> args
   for (int s = 0; s < D2; ++s) {
 #pragma unroll
     for (int wl = 0; wl < Dw; ++wl) {
-      T acc = (T)0;
+      double acc = 0.0;
 #pragma unroll
       for (int wr = 0; wr < Dw; ++wr)
 #pragma unroll
         for (int t = 0; t < D2; ++t) acc += args.ww[((wl * D2 + s) * Dw + wr) * D2 + t] * in[t * Dw + wr];
-      const int64_t off = base + s * rowstep + wl * chiL;
-      if (SPLIT) {
-        __nv_bfloat16* V = (__nv_bfloat16*)Vout;
-        const float xf = (float)acc;
-        const __nv_bfloat16 h = __float2bfloat16_rn(xf);
-        const float r1 = xf - __bfloat162float(h);
-        const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-        V[off] = h;
-        V[plane + off] = m;
-        V[2 * plane + off] = l;
+      V[base + s * rowstep + wl * chiL] = acc;
+    }
+  }
+}
+
+// Split path.  GEMM1 stores U transposed, U^T [(b,wr), (a',t)] (row length
+// 4 chiL), so that one thread reads the NA*4 values (a', t), a' in
+// [a0, a0+NA), of each of its five rows (b, wr) as contiguous float4s and a
+// warp reads 32*NA*16 contiguous bytes per row, with no shared-memory
+// staging.  The thread forms the 20 outputs (s, wl) of its NA pairs (a', b),
+// splits them into bfloat16 pieces and stores NA consecutive a' per piece
+// plane with one vector store (a' is GEMM2's K dimension).  Lanes run along
+// a', so each warp store covers 32*NA*2 contiguous bytes.
+__device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16& m, __nv_bfloat16& l) {
+  h = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h);
+  m = __float2bfloat16_rn(r1);
+  l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+template <int NA>
+__global__ void __launch_bounds__(256) k_ww_split(const WWArgs<float> args, const float* __restrict__ Ut, int64_t chiL,
+                                                  int64_t chiR, __nv_bfloat16* __restrict__ V, int64_t ldv,
+                                                  int64_t plane) {
+  constexpr int Dw = HEFF_DW, D2 = 4;
+  static_assert(NA == 2 || NA == 4, "NA");
+  const int64_t nq = (chiL + NA - 1) / NA;
+  const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t q = idx % nq, b = idx / nq;
+  if (b >= chiR) return;
+  const int64_t a0 = q * NA;
+  const bool full = a0 + NA <= chiL;
+  const int64_t ldu = 4 * chiL;
+  float in[Dw][NA * D2];   // [wr][(a'-a0)*4 + t]
+#pragma unroll
+  for (int wr = 0; wr < Dw; ++wr) {
+    const float* row = Ut + (b * Dw + wr) * ldu + a0 * D2;
+    if (full) {
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const float4 v = __ldg((const float4*)row + j);
+        in[wr][4 * j] = v.x;
+        in[wr][4 * j + 1] = v.y;
+        in[wr][4 * j + 2] = v.z;
+        in[wr][4 * j + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < NA * D2; ++j) in[wr][j] = a0 + j / D2 < chiL ? row[j] : 0.f;
+    }
+  }
+  const bool vec = full && (chiL % NA == 0);
+#pragma unroll
+  for (int s = 0; s < D2; ++s) {
+#pragma unroll
+    for (int wl = 0; wl < Dw; ++wl) {
+      float acc[NA];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) acc[j] = 0.f;
+#pragma unroll
+      for (int wr = 0; wr < Dw; ++wr)
+#pragma unroll
+        for (int t = 0; t < D2; ++t) {
+          const float w = args.ww[((wl * D2 + s) * Dw + wr) * D2 + t];
+#pragma unroll
+          for (int j = 0; j < NA; ++j) acc[j] = fmaf(w, in[wr][j * D2 + t], acc[j]);
+        }
+      __nv_bfloat16 h[NA], m[NA], l[NA];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) split3(acc[j], h[j], m[j], l[j]);
+      const int64_t off = (s * chiR + b) * ldv + wl * chiL + a0;
+      if (vec) {
+        if constexpr (NA == 4) {
+          uint2 ph, pm, pl;
+          ph.x = pack_bf16x2(h[0], h[1]);
+          ph.y = pack_bf16x2(h[2], h[3]);
+          pm.x = pack_bf16x2(m[0], m[1]);
+          pm.y = pack_bf16x2(m[2], m[3]);
+          pl.x = pack_bf16x2(l[0], l[1]);
+          pl.y = pack_bf16x2(l[2], l[3]);
+          *(uint2*)(V + off) = ph;
+          *(uint2*)(V + plane + off) = pm;
+          *(uint2*)(V + 2 * plane + off) = pl;
+        } else {
+          *(uint32_t*)(V + off) = pack_bf16x2(h[0], h[1]);
+          *(uint32_t*)(V + plane + off) = pack_bf16x2(m[0], m[1]);
+          *(uint32_t*)(V + 2 * plane + off) = pack_bf16x2(l[0], l[1]);
+        }
       } else {
-        ((double*)Vout)[off] = (double)acc;
+#pragma unroll
+        for (int j = 0; j < NA; ++j)
+          if (a0 + j < chiL) {
+            V[off + j] = h[j];
+            V[plane + off + j] = m[j];
+            V[2 * plane + off + j] = l[j];
+          }
       }
     }
   }
 }
 
-template <typename T, typename UT, int ATILE, int BT, bool SPLIT>
-tci_status launch_ww(tci_context ctx, const WWArgs<T>& args, const UT* U, int64_t chiL, int64_t chiR, void* V,
-                     int64_t ldv, int64_t plane) {
+tci_status launch_ww_f64(tci_context ctx, const WWArgs<double>& args, const double* U, int64_t chiL, int64_t chiR,
+                         double* V, int64_t ldv) {
+  constexpr int ATILE = 16, BT = 16;
   dim3 grid((unsigned)((chiR + BT - 1) / BT), (unsigned)((chiL + ATILE - 1) / ATILE));
   if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: chiL too large");
-  k_ww_apply<T, UT, ATILE, BT, SPLIT><<<grid, ATILE * BT, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv, plane);
+  k_ww_apply<ATILE, BT><<<grid, ATILE * BT, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
+
+// na: a' per thread (2 or 4; 4 halves the store instructions, 2 doubles the
+// resident warps), chosen by the autotuner.
+tci_status launch_ww_split(tci_context ctx, const WWArgs<float>& args, const float* Ut, int64_t chiL, int64_t chiR,
+                           void* V, int64_t ldv, int64_t plane, int na) {
+  const int64_t threads = (chiL + na - 1) / na * chiR;
+  const int64_t blocks = (threads + 255) / 256;
+  if (blocks > 0x7fffffff) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: too large");
+  if (na == 2)
+    k_ww_split<2><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane);
+  else
+    k_ww_split<4><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+}  // namespace
+
+// Time both W.W variants on the plan's current U (5 launches each) and keep
+// the faster one in p->ww_na.
+tci_status tci_heff_tune_ww(tci_heff_plan p, float* ms_out) {
+  tci_context ctx = p->ctx;
+  if (p->prec == TCI_PREC_NATIVE) return TCI_OK;
+  WWArgs<float> args;
+  for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+  cudaEvent_t e0, e1;
+  TCI_CUDA(ctx, cudaEventCreate(&e0));
+  TCI_CUDA(ctx, cudaEventCreate(&e1));
+  float best = 1e30f;
+  int best_na = p->ww_na;
+  tci_status s = TCI_OK;
+  const int cands[2] = {4, 2};
+  for (int na : cands) {
+    s = launch_ww_split(ctx, args, (const float*)p->U, p->chiL, p->chiR, p->Vp, p->Kp2, 4 * p->chiR * p->Kp2, na);
+    if (s != TCI_OK) break;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < 5 && s == TCI_OK; ++r)
+      s = launch_ww_split(ctx, args, (const float*)p->U, p->chiL, p->chiR, p->Vp, p->Kp2, 4 * p->chiR * p->Kp2, na);
+    cudaEventRecord(e1, ctx->stream);
+    if (s != TCI_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = tci_cuda_fail(ctx, e, "tune W.W");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_na = na;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == TCI_OK) {
+    p->ww_na = best_na;
+    if (ms_out) *ms_out = best / 5.f;
+  }
+  return s;
+}
+
+namespace {
 
 int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 
@@ -202,7 +352,7 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   tci_heff_plan p = *pp;
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
-                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part};
+                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
   for (void* b : bufs) tci_dev_free(b);
   p->magic = 0;
   delete p;
@@ -218,14 +368,15 @@ extern "C" double tci_heff_flops(tci_heff_plan p) {
 
 // ------------------------------------------------------------------ apply
 static tci_status check_vec(tci_heff_plan p, tci_tensor t, const char* what);
-tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, bool psi_presplit) {
+tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, bool psi_presplit, int out_mode) {
   tci_context ctx = p->ctx;
   const int64_t chiL = p->chiL, chiR = p->chiR, Dw = HEFF_DW;
   if (p->prec == TCI_PREC_NATIVE) {
+    if (out_mode != 0 || psi_presplit) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_apply: FP64 plan writes FP64");
     WWArgs<double> args;
     for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = p->ww[i];
     TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1));
-    TCI_TRY((launch_ww<double, double, 16, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0)));
+    TCI_TRY(launch_ww_f64(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL));
     TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out,
                             4 * chiR, 1));
     return TCI_OK;
@@ -233,11 +384,12 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, b
   WWArgs<float> args;
   for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
   if (!psi_presplit) TCI_TRY(tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1));
-  TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products,
+  // GEMM1 stores U transposed: U^T[(b,wr), (a',t)] (m stride 1, n stride 4 chiL)
+  TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, 1, chiL * 4, p->products,
                               p->chunk_k, p->xchunk_k, p->raster));
-  TCI_TRY((launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2)));
-  TCI_TRY(tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k,
-                              p->xchunk_k, p->raster));
+  TCI_TRY(launch_ww_split(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2, p->ww_na));
+  TCI_TRY(tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, out_mode, 4 * chiR, 1, p->products,
+                              p->chunk_k, p->xchunk_k, p->raster));
   return TCI_OK;
 }
 
@@ -256,7 +408,7 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
     TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1);
     TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-    if (s == TCI_OK) s = launch_ww<double, double, 16, 16, false>(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL, 0);
+    if (s == TCI_OK) s = launch_ww_f64(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL);
     TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out, 4 * chiR, 1);
   } else {
@@ -264,9 +416,9 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
     for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
     s = tci_launch_split3(ctx, TCI_F64, psi, chiL * 4, chiR, chiR, 1, p->psip, p->Kp1);
     TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, chiR * Dw, 1, p->products, p->chunk_k, p->xchunk_k, p->raster);
+    if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, 1, chiL * 4, p->products, p->chunk_k, p->xchunk_k, p->raster);
     TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-    if (s == TCI_OK) s = launch_ww<float, float, 32, 8, true>(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2);
+    if (s == TCI_OK) s = launch_ww_split(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2, p->ww_na);
     TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
     if (s == TCI_OK) s = tci_gemm_split_bf16(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, 0, 4 * chiR, 1, p->products, p->chunk_k, p->xchunk_k, p->raster);
   }

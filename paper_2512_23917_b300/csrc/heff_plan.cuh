@@ -17,9 +17,11 @@ struct tci_heff_plan_s {
   int chunk_k;     // split GEMM: K depth per hi*hi accumulation unit
   int xchunk_k;    // split GEMM: K depth per cross-product accumulation unit
   int raster = 0;  // split GEMM: tile order (autotuned)
+  int ww_na = 4;      // split W.W kernel: a' per thread (2 or 4, autotuned)
+  int vec_arith = 0;  // Lanczos vector arithmetic: 0 auto, 1 FP64, 2 double-float (FP32 pairs)
   double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
   // intermediates
-  void* U = nullptr;       // [(a',t1,t2), (b,wr)]: FP64 (native) or FP32 (split)
+  void* U = nullptr;       // FP64 [(a',t1,t2), (b,wr)] (native) or FP32 U^T [(b,wr), (a',t1,t2)] (split)
   // native path
   double* L64 = nullptr;
   double* R64 = nullptr;
@@ -39,6 +41,14 @@ struct tci_heff_plan_s {
   double* lz_w = nullptr;
   double* lz_scal = nullptr;  // device scalars
   double* lz_part = nullptr;  // reduction partials
+  double* lz_x64 = nullptr;   // double-float Lanczos with the FP64 matvec: matvec input / output
+  double* lz_o64 = nullptr;
 };
 
-tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, double* out, bool psi_presplit);
+// out_mode 0: out is FP64; 2 (split precisions only): out is a normalised
+// FP32 pair {hi, lo} per element.  psi_presplit: psi's bfloat16 pieces are
+// already in p->psip (psi is then not read).
+// Time the split W.W kernel variants on the plan's current intermediates and
+// keep the faster (p->ww_na); *ms_out (may be NULL) receives its duration.
+tci_status tci_heff_tune_ww(tci_heff_plan p, float* ms_out);
+tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, bool psi_presplit, int out_mode = 0);

@@ -17,7 +17,8 @@
 //     in a second accumulator X drained every `xchunk_k` (default 1024);
 //   * drained values are summed error-free in FP32 double-float form
 //     (TwoSum: hi + lo) held in the epilogue threads' registers, and the
-//     result is rounded once when the tile is stored (FP64 or FP32).
+//     result is rounded once when the tile is stored (FP64, FP32, or as a
+//     normalised FP32 pair hi + lo for double-float consumers).
 // D1 and X are each double-buffered in TMEM (4 x 128 columns), so draining
 // one buffer overlaps the MMAs that fill the other.
 //
@@ -26,8 +27,8 @@
 // 4-stage TMA -> mbarrier -> tcgen05.mma pipeline.
 //   warp 0      : TMA producer (one lane)
 //   warp 1      : TMEM allocator + MMA issuer (one lane)
-//   warps 2..9  : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
-//                 columns 64*((w-2)/4)..+63
+//   warps 2..17 : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
+//                 columns 32*((w-2)/4)..+31
 // Every wait is bounded (2 s); on expiry the kernel records a status word,
 // lets its in-flight copies and MMAs land, frees TMEM and returns.
 #include <cuda.h>
@@ -68,7 +69,7 @@ struct alignas(64) GemmProblem {
   void* C;
   int64_t M, N, scm, scn;
   int num_m, num_n, num_kb, tile_begin;
-  int out_f32, pad0, pad1, pad2;
+  int out_mode, pad0, pad1, pad2;
 };
 
 struct GemmParams {
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int nkb = pr->num_kb;
       const int64_t PM = pr->M, PN = pr->N, scm = pr->scm, scn = pr->scn;
       void* const PC = pr->C;
-      const int out_f32 = pr->out_f32;
+      const int out_mode = pr->out_mode;
 #pragma unroll
       for (int j = 0; j < COLS_PER_WARP; ++j) rh[j] = 0.f;
 #pragma unroll
@@ -365,7 +366,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
       const int64_t n0 = (int64_t)nb * TBN + c0;
       if (row < PM) {
-        if (out_f32) {
+        if (out_mode == 1) {
           float* crow = (float*)PC + row * scm;
           const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
 #pragma unroll
@@ -380,6 +381,22 @@ __global__ void __launch_bounds__(NTHREADS, 1)
               if (n0 + j + 1 < PN) crow[(n0 + j + 1) * scn] = o.y;
               if (n0 + j + 2 < PN) crow[(n0 + j + 2) * scn] = o.z;
               if (n0 + j + 3 < PN) crow[(n0 + j + 3) * scn] = o.w;
+            }
+          }
+        } else if (out_mode == 2) {
+          float2* crow = (float2*)PC + row * scm;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
+#pragma unroll
+          for (int j = 0; j < COLS_PER_WARP; j += 2) {
+            const float2 c = __bfloat1622float2(rl2[j / 2]);
+            float4 o;
+            two_sum(rh[j], c.x, o.x, o.y);
+            two_sum(rh[j + 1], c.y, o.z, o.w);
+            if (vec) {
+              *(float4*)(crow + n0 + j) = o;
+            } else {
+              if (n0 + j < PN) crow[(n0 + j) * scn] = make_float2(o.x, o.y);
+              if (n0 + j + 1 < PN) crow[(n0 + j + 1) * scn] = make_float2(o.z, o.w);
             }
           }
         } else {
@@ -446,7 +463,7 @@ tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* bas
 }
 
 static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int64_t N, int64_t Kp, const void* Ap,
-                               const void* Bp, void* C, int out_f32, int64_t scm, int64_t scn) {
+                               const void* Bp, void* C, int out_mode, int64_t scm, int64_t scn) {
   if (M <= 0 || N <= 0 || Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty problem");
   if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
     return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
@@ -458,7 +475,7 @@ static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int6
   pr->N = N;
   pr->scm = scm;
   pr->scn = scn;
-  pr->out_f32 = out_f32;
+  pr->out_mode = out_mode;
   pr->num_m = (int)((M + TBM - 1) / TBM);
   pr->num_n = (int)((N + TBN - 1) / TBN);
   pr->num_kb = (int)((Kp + TBK - 1) / TBK);
@@ -485,11 +502,11 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
 }
 
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
-                               void* C, int out_f32, int64_t scm, int64_t scn, int products, int chunk_k,
+                               void* C, int out_mode, int64_t scm, int64_t scn, int products, int chunk_k,
                                int xchunk_k, int raster) {
   if (M <= 0 || N <= 0) return TCI_OK;
   GemmProblem pr;
-  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_f32, scm, scn));
+  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_mode, scm, scn));
   GemmParams gp;
   memset(&gp, 0, sizeof gp);
   TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
@@ -525,7 +542,7 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
   for (int i : order) {
     const tci_split_problem& q = probs[i];
     GemmProblem pr;
-    TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_f32, q.scm, q.scn));
+    TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_mode, q.scm, q.scn));
     pr.tile_begin = tiles;
     tiles += pr.num_m * pr.num_n;
     host.push_back(pr);

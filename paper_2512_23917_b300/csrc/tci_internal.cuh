@@ -112,12 +112,13 @@ tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, 
 // Split-BF16 tensor-core GEMM (tcgen05).  Operands are given as three
 // bfloat16 piece planes each: A pieces [3][M][Kp] and B pieces [3][N][Kp]
 // (K-major rows, Kp % 8 == 0, plane stride = rows*Kp).  C element (m, n) at
-// C[m*scm + n*scn], FP64 (out_f32 = 0) or FP32 (out_f32 = 1).  products = 6
+// C[m*scm + n*scn]: FP64 (out_mode = 0), FP32 (out_mode = 1) or a normalised
+// FP32 pair {hi, lo} per element (out_mode = 2, hi + lo = the result).  products = 6
 // or 3.  chunk_k: K depth of one hi*hi accumulation unit (multiple of 32);
 // xchunk_k: K depth of one cross-product accumulation unit.  raster: tile
 // order (0 m-fastest, G > 0 groups of G m-blocks with n fastest inside).
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp,
-                               const void* Apieces, const void* Bpieces, void* C, int out_f32,
+                               const void* Apieces, const void* Bpieces, void* C, int out_mode,
                                int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k,
                                int raster);
 
@@ -142,7 +143,7 @@ struct tci_split_problem {
   const void* Bp;   // bf16 pieces [3][N][Kp], 16-byte aligned
   int64_t M, N, Kp;
   void* C;          // element (m, n) at C[m*scm + n*scn]
-  int out_f32;
+  int out_mode;
   int64_t scm, scn;
 };
 struct tci_split_group;

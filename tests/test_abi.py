@@ -49,6 +49,11 @@ def test_null_arguments_are_rejected_without_a_device():
     assert b"NULL" in tci.lib.tci_last_error(None)
     # free of a NULL tensor
     assert tci.lib.tci_tensor_free(ctypes.byref(ctypes.c_void_p())) == 1
+    # plan-level setters reject a NULL plan before touching a device
+    cfg = (ctypes.c_int * 4)(256, 1024, 0, 4)
+    assert tci.lib.tci_heff_set_config(None, cfg) == 1
+    assert tci.lib.tci_heff_get_config(None, cfg) == 1
+    assert tci.lib.tci_heff_set_lanczos_arith(None, 2) == 1
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="only meaningful without a GPU")

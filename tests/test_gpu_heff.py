@@ -87,3 +87,20 @@ def test_apply_host_matches_device(ctx, tci):
     host_out = np.empty_like(psi)
     plan.apply_host(np.ascontiguousarray(psi), host_out)
     np.testing.assert_array_equal(host_out, out)
+
+
+@pytest.mark.parametrize("ww_na", [2, 4])
+@pytest.mark.parametrize("chi,chi_r", [(33, 17), (130, 70), (64, 40)])
+def test_heff_split_ww_variants(ctx, tci, chi, chi_r, ww_na):
+    """Both W.W kernel variants (a' per thread 2 / 4), with ragged a' tails and unaligned rows."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(chi, seed=9, chi_r=chi_r)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    c = plan.get_config()
+    plan.set_config(c[0], c[1], c[2], ww_na)
+    assert plan.get_config()[3] == ww_na
+    dpsi = to_dev(psi)
+    out = torch.full_like(dpsi, float("nan"))
+    plan.apply(dpsi, out)
+    torch.cuda.synchronize()
+    assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi)) < 1e-6
