@@ -150,7 +150,7 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU path
 def lanczos_launches(m: int) -> int:
-    """Kernel launches of one m-step Lanczos solve with double-float vectors and CGS2 (basis <= 24 vectors)."""
+    """Kernel launches of one m-step Lanczos solve on a split-BF16 plan with CGS2 (basis <= 24 vectors)."""
     n = 4                                           # init scalars, psi0 sum of squares + reduce, start vector
     for j in range(m):
         n += 3                                      # GEMM1, W.W, GEMM2 (the split is fused into the next-vector kernel)
@@ -318,17 +318,17 @@ def run_gpu(args):
     ms_step = ms_total / args.steps
     value = world * LANCZOS_STEPS * F / (ms_step * 1e-3) / 1e9
 
-    # ---- the same solve with FP64 vector arithmetic (context for the double-float choice)
-    plan.set_lanczos_arith("f64")
+    # ---- the same solve with double-float (FP32 pair) vector arithmetic, an opt-in variant
+    plan.set_lanczos_arith("df32")
     plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    res64 = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    res_df = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
     e1.record(stream)
     torch.cuda.synchronize()
-    lanczos_f64_ms = e0.elapsed_time(e1)
-    plan.set_lanczos_arith("auto")
+    lanczos_df_ms = e0.elapsed_time(e1)
+    plan.set_lanczos_arith("f64")
 
     # ---- per-stage events of single matvecs (roofline of the GEMM kernel)
     stages = []
@@ -408,17 +408,17 @@ def run_gpu(args):
             "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
             "config": {"workload": "20-step Lanczos on the dense two-site H_eff, Heisenberg MPO, chi=2048, d=2, Dw=5, "
                                    "split-BF16 matvec (3 pieces, 6 products, FP32 tensor-memory accumulation drained "
-                                   "every chunk_k of K into a double-float sum), Lanczos vectors in double-float "
-                                   "(FP32 pairs), scalars FP64",
+                                   "every chunk_k of K into a double-float sum), FP64 Lanczos (dots, CGS2, "
+                                   "tridiagonal eigensolve)",
                        "chi": CHI, "lanczos_steps": LANCZOS_STEPS, "seed": SEED,
                        "l2": "inputs larger than L2 (psi 134 MB, basis 2.8 GB)", "parallelism": f"replicas x{world}"},
             "roofline": roofline, "e2e": e2e, "gpu_launches": lanczos_launches(LANCZOS_STEPS) * args.steps,
             "clocks": clocks, "ritz_value": res["theta"] if res else None,
             "autotune": {"chunk_k": tuned[0], "xchunk_k": tuned[1], "raster": tuned[2], "max_chunk_k": 256,
                          "ww_a_per_thread": plan.get_config()[3]},
-            "lanczos_f64_vectors": {"ms_per_step": lanczos_f64_ms, "ritz_value": res64["theta"],
-                                    "ritz_rel_diff_vs_double_float": abs(res64["theta"] - res["theta"]) / abs(res64["theta"])
-                                    if res else None},
+            "lanczos_double_float_vectors": {"ms_per_step": lanczos_df_ms, "ritz_value": res_df["theta"],
+                                             "ritz_rel_diff_vs_fp64": abs(res_df["theta"] - res["theta"]) / abs(res["theta"])
+                                             if res else None},
             "matvec": {"gflops": F / (mv_only_ms * 1e-3) / 1e9, "ms": mv_only_ms,
                        "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),
                                     "gemm2": float(st[3])}}}
@@ -445,11 +445,18 @@ def run_profile_case(args):
     ctx = tci.Context(0)
     plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="split_bf16")
     out = torch.empty_like(dpsi)
-    for _ in range(args.warmup + args.steps):
-        plan.apply(dpsi, out)
-    torch.cuda.synchronize()
-    print(json.dumps({"profile_case": "split-BF16 H_eff matvec", "chi": chi, "matvecs": args.warmup + args.steps,
-                      "launches_per_matvec": 4}))
+    if args.profile_lanczos:
+        for _ in range(args.warmup + args.steps):
+            plan.lanczos(dpsi, LANCZOS_STEPS, True, out)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "20-step split-BF16 Lanczos", "chi": chi,
+                          "solves": args.warmup + args.steps, "launches_per_solve": lanczos_launches(LANCZOS_STEPS)}))
+    else:
+        for _ in range(args.warmup + args.steps):
+            plan.apply(dpsi, out)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile_case": "split-BF16 H_eff matvec", "chi": chi, "matvecs": args.warmup + args.steps,
+                          "launches_per_matvec": 4}))
     plan.close()
     ctx.close()
 
@@ -458,6 +465,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--profile-chi", type=int, default=0,
                     help="run only split-BF16 matvecs at this bond dimension (small case for ncu)")
+    ap.add_argument("--profile-lanczos", action="store_true",
+                    help="with --profile-chi: run 20-step Lanczos solves instead of single matvecs")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

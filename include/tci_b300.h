@@ -287,8 +287,8 @@ tci_status tci_heff_apply_noalloc(const double* L, const double* W, const double
  * (double-float, Dekker 1971; ~48 significant bits) with error-free
  * transformations, so the vector passes run on the FP32 pipes (B300 issues
  * FP64 FMAs at ~1/64 of its FP32 rate); Ritz values agree with the FP64
- * arithmetic to ~1e-12 relative.  TCI_LANCZOS_AUTO: F64 for a plan made
- * with TCI_PREC_NATIVE, DF32 for the split-BF16 precisions. */
+ * arithmetic to ~1e-10 relative or better.  TCI_LANCZOS_AUTO (default):
+ * FP64. */
 typedef enum {
   TCI_LANCZOS_AUTO = 0,
   TCI_LANCZOS_F64 = 1,
@@ -302,9 +302,9 @@ tci_status tci_heff_set_lanczos_arith(tci_heff_plan plan, tci_lanczos_arith arit
 /* Lanczos ground state of H_eff (textbook; Golub & Van Loan Sec. 10.1 with
  * classical Gram-Schmidt applied twice when reorth != 0; Ritz value by Sturm
  * bisection, Sec. 8.4).  All vector work runs on the device, in the
- * arithmetic chosen by tci_heff_set_lanczos_arith (by default FP64 for an
- * FP64 plan and double-float for a split-BF16 plan); scalars (alpha, beta,
- * Gram-Schmidt coefficients, the tridiagonal eigenpair) are FP64.
+ * arithmetic chosen by tci_heff_set_lanczos_arith (FP64 by default);
+ * scalars (alpha, beta, Gram-Schmidt coefficients, the tridiagonal
+ * eigenpair) are FP64.
  * psi0: start vector [chiL,d,d,chiR] F64 (normalised internally, not
  * modified).  Runs up to nsteps (1..256) steps, stopping early when
  * beta_j < 1e-12 |alpha_j|.  Outputs (host): *ritz, alpha[nsteps],

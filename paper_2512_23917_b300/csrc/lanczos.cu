@@ -3,101 +3,354 @@
 // re-orthogonalisation; Sturm-sequence bisection, Sec. 8.4, and inverse
 // iteration for the tridiagonal eigenpair).
 //
-// Two kinds of vector arithmetic:
-//   FP64         every dot and update in FP64 (default for the FP64 matvec);
-//   double-float vectors stored as FP32 pairs hi + lo (~48 significant bits;
-//                default for the split-BF16 matvec, whose own error is ~1e-7).
-//                B300 runs FP64 FMAs at ~1/64 of its FP32 rate: FP64 dots
-//                over HBM-resident vectors are FP64-pipe bound, double-float
-//                ones stay HBM bound.  This variant also fuses the passes:
-//                CGS pass 1 (whose coefficient for v_j is alpha_j and whose
-//                update subsumes the three-term recurrence), pass 2's update
-//                with pass 2's dots, the last update with ||w||^2, and the
-//                normalisation of v_{j+1} with the operand split of the next
-//                matvec.
+// One step j, with the basis V = [v_0 .. v_j] resident in HBM:
+//   w = H v_j                                   (the matvec; its input was
+//                                                prepared with v_j)
+//   pass 1: h = V^T w;  alpha_j = h_j            (one read of V and w)
+//   pass 2: w -= V h, then h' = V^T w            (fused: V read once, w r/w)
+//   pass 3: w -= V h', then ||w||^2              (fused)
+//   beta_j = ||w||;  v_{j+1} = w / beta_j, written with the next matvec's
+//   input (its bfloat16 pieces on a split-BF16 plan) in the same pass.
+// Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
+// = beta_{j-1} up to rounding), so passes 1-3 equal the three-term step
+// followed by two classical Gram-Schmidt passes.  Without re-orthogonal-
+// isation: pass 1 takes only alpha_j and pass 3 subtracts alpha_j v_j +
+// beta_{j-1} v_{j-1}.
 //
-// All scalars (alpha, beta, re-orthogonalisation coefficients, stop flag,
-// step count, Ritz coefficients) stay in device memory; the host enqueues
-// the whole sequence and reads back once at the end.  Reductions are
+// Vector arithmetic (a policy template over the same kernels):
+//   FP64          every product and sum in FP64 (the default);
+//   double-float  vectors held as FP32 pairs hi + lo (~48 significant bits)
+//                 with error-free transformations, so the passes run on the
+//                 FP32 pipes: B300 issues FP64 FMAs at ~1/64 of its FP32
+//                 rate, which makes the FP64 passes FP64-pipe bound.
+//
+// All scalars (alpha, beta, Gram-Schmidt coefficients, stop flag, step
+// count, Ritz coefficients) stay in device memory as FP64; the host enqueues
+// the whole solve and reads back once at the end.  Reductions are
 // deterministic: a fixed grid, a fixed per-thread order and an in-order sum
 // of the block partials.
 #include <cuda_bf16.h>
+
+#include <type_traits>
 
 #include "heff_plan.cuh"
 
 namespace {
 
-constexpr int NB = 1184;         // 8 x 148 SMs: blocks of every reduction (64 warps per SM)
 constexpr int NT = 256;
+constexpr int NBMAX = 1184;      // partial-sum slots per vector (>= any kernel's grid)
 constexpr int MAXM = 256;
+constexpr int GMAX = 20;         // basis vectors per fused pass
 // device scalar layout (doubles)
 constexpr int OFF_ALPHA = 0;
 constexpr int OFF_BETA = MAXM;
-constexpr int OFF_H = 2 * MAXM;          // MAXM + 1 entries
-constexpr int OFF_CTRL = 3 * MAXM + 8;   // [0] stop flag, [1] steps done, [2] theta, [3] sumsq
-constexpr int OFF_Y = 3 * MAXM + 16;
-constexpr int OFF_H2 = 4 * MAXM + 32;    // MAXM + 1 entries (double-float path: pass-2 coefficients)
+constexpr int OFF_H = 2 * MAXM;          // MAXM + 1 entries: pass-1 coefficients
+constexpr int OFF_CTRL = 3 * MAXM + 8;   // [0] stop flag, [1] steps done, [2] theta, [3] sum of squares
+constexpr int OFF_Y = 3 * MAXM + 16;     // Ritz coefficients
+constexpr int OFF_H2 = 4 * MAXM + 32;    // MAXM + 1 entries: pass-2 coefficients
 constexpr int NSCAL = 5 * MAXM + 64;
-constexpr int DF_GMAX = 24;              // basis vectors per fused double-float pass
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
 }
 
-// part[v*NB + block] = sum over this block's slice of V_v[i] * w[i], v < nv.
-// Each thread walks two grid-stride elements per iteration (independent FP64
-// chains); the per-thread order is fixed, so the result is deterministic.
-template <int G>
-__global__ void __launch_bounds__(NT) k_mdot(const double* __restrict__ V, int64_t ldv, int v0, int nv,
-                                             const double* __restrict__ w, int64_t n, double* __restrict__ part,
-                                             const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
+// ---------------------------------------------------------------- double-float
+// A double-float number is the unevaluated sum hi + lo of two FP32 values
+// with |lo| <= ulp(hi)/2 (Dekker, Numer. Math. 18, 1971).  Sums use Knuth's
+// TwoSum (TAOCP vol. 2, Sec. 4.2.2) and products the FMA-exact split
+// a*b = p + e; running sums keep an unnormalised low word.
+
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ float2 df_norm(float h, float l) {
+  float s, e;
+  df_two_sum(h, l, s, e);
+  return make_float2(s, e);
+}
+
+__device__ __forceinline__ float2 df_from_double(double x) {
+  const float h = __double2float_rn(x);
+  return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// x * y as (p, t) with p + t = x*y to ~2^-48 relative
+__device__ __forceinline__ void df_prod(float2 x, float2 y, float& p, float& t) {
+  p = __fmul_rn(x.x, y.x);
+  const float e = __fmaf_rn(x.x, y.x, -p);
+  t = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
+}
+
+// ---------------------------------------------------------------- arithmetic policies
+struct ArithF64 {
+  using V = double;
+  static constexpr int kBlocks = 592;   // FP64-pipe bound: 4 blocks per SM, fewer FP64 reduction adds
+  struct Acc { double s; };
+  struct Coef { double c; };
+  struct Sub { double w, s; };
+  __device__ static Acc zero() { return {0.0}; }
+  __device__ static void acc(Acc& a, V x, V y) { a.s = fma(x, y, a.s); }
+  __device__ static void acc_c(Acc& a, Coef c, V y) { a.s = fma(c.c, y, a.s); }
+  __device__ static double value(const Acc& a) { return a.s; }
+  __device__ static double lane_total(const Acc& a) { return warp_sum(a.s); }   // valid in lane 0
+  __device__ static Coef coef(double c) { return {c}; }
+  __device__ static Sub sub_begin(V w) { return {w, 0.0}; }
+  __device__ static void sub(Sub& t, Coef c, V v) { t.s = fma(c.c, v, t.s); }
+  __device__ static V sub_end(const Sub& t) { return t.w - t.s; }
+  __device__ static V mul(V x, Coef c) { return x * c.c; }
+  __device__ static V from_double(double x) { return x; }
+  __device__ static double to_double(V v) { return v; }
+  __device__ static float f32(V v) { return __double2float_rn(v); }
+};
+
+struct ArithDF {
+  using V = float2;
+  static constexpr int kBlocks = 1184;  // HBM bound: 8 blocks per SM
+  struct Acc { float h, l; };
+  struct Coef { float2 c; };
+  struct Sub { float h, l; };
+  __device__ static Acc zero() { return {0.f, 0.f}; }
+  __device__ static void acc(Acc& a, V x, V y) {
+    float p, t, s, e;
+    df_prod(x, y, p, t);
+    df_two_sum(a.h, p, s, e);
+    a.h = s;
+    a.l = __fadd_rn(a.l, __fadd_rn(e, t));
+  }
+  __device__ static void acc_c(Acc& a, Coef c, V y) { acc(a, c.c, y); }
+  __device__ static double value(const Acc& a) { return (double)a.h + (double)a.l; }
+  __device__ static double lane_total(const Acc& a) {   // double-float tree, one FP64 add at the end
+    float h = a.h, l = a.l;
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_down_sync(0xffffffffu, h, o), l2 = __shfl_down_sync(0xffffffffu, l, o);
+      float s, e;
+      df_two_sum(h, h2, s, e);
+      h = s;
+      l = __fadd_rn(l, __fadd_rn(l2, e));
+    }
+    return (double)h + (double)l;
+  }
+  __device__ static Coef coef(double c) { return {df_from_double(c)}; }
+  __device__ static Sub sub_begin(V w) { return {w.x, w.y}; }
+  __device__ static void sub(Sub& t, Coef c, V v) {
+    float p, q, s, e;
+    df_prod(c.c, v, p, q);
+    df_two_sum(t.h, -p, s, e);
+    t.h = s;
+    t.l = __fadd_rn(t.l, __fsub_rn(e, q));
+  }
+  __device__ static V sub_end(const Sub& t) { return df_norm(t.h, t.l); }
+  __device__ static V mul(V x, Coef c) {
+    float p, t;
+    df_prod(x, c.c, p, t);
+    return df_norm(p, t);
+  }
+  __device__ static V from_double(double x) { return df_from_double(x); }
+  __device__ static double to_double(V v) { return (double)v.x + (double)v.y; }
+  __device__ static float f32(V v) { return v.x; }   // fl32(hi + lo) = hi for a normalised pair
+};
+
+// ---------------------------------------------------------------- vector kernels
+// Per-block partial sums of G accumulators (fixed order): part[g*NBMAX +
+// blockIdx.x] for g < nv.
+template <class A, int G>
+__device__ __forceinline__ void block_partials(const typename A::Acc (&a)[G], int nv, double* part) {
   __shared__ double sh[NT / 32][G];
-  double acc[G], acc2[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) acc[g] = acc2[g] = 0.0;
-  const int64_t stride = (int64_t)NB * NT;
-  int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    const double wi = w[i], wj = w[i + stride];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) {
-        const double* vg = V + (int64_t)(v0 + g) * ldv;
-        acc[g] = fma(vg[i], wi, acc[g]);
-        acc2[g] = fma(vg[i + stride], wj, acc2[g]);
-      }
-  }
-  if (i < n) {
-    const double wi = w[i];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) acc[g] = fma(V[(int64_t)(v0 + g) * ldv + i], wi, acc[g]);
-  }
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-  for (int g = 0; g < G; ++g) {
-    double s = warp_sum(acc[g] + acc2[g]);
-    if (lane == 0) sh[wid][g] = s;
-  }
+  for (int g = 0; g < G; ++g)
+    if (g < nv) {
+      const double s = A::lane_total(a[g]);
+      if (lane == 0) sh[wid][g] = s;
+    }
   __syncthreads();
   if (threadIdx.x < G && threadIdx.x < nv) {
     double s = 0.0;
     for (int k = 0; k < NT / 32; ++k) s += sh[k][threadIdx.x];
-    part[(int64_t)(v0 + threadIdx.x) * NB + blockIdx.x] = s;
+    part[(int64_t)threadIdx.x * NBMAX + blockIdx.x] = s;
   }
 }
 
-// out[v] = sum_b part[v*NB + b] in order; one block per vector.
-__global__ void k_reduce_parts(const double* __restrict__ part, int nv, double* __restrict__ out,
+// partials of <V_{v0+g}, w>, g < nv <= G, into part rows v0 + g
+template <class A, int G>
+__global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
+                                             const typename A::V* __restrict__ w, int64_t n, double* __restrict__ part,
+                                             const double* __restrict__ ctrl) {
+  if (ctrl[0] != 0.0) return;
+  typename A::Acc a[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) a[g] = A::zero();
+  using Vt = typename A::V;
+  const Vt* Vb = V + (int64_t)v0 * ldv;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+    const Vt x = w[i];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < nv) A::acc(a[g], Vb[(int64_t)g * ldv + i], x);
+  }
+  block_partials<A, G>(a, nv, part + (int64_t)v0 * NBMAX);
+}
+
+// w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
+// into part rows v0 + g, or (SUMSQ) partials of ||w||^2 into part_sq.
+template <class A, int G, bool DOTS, bool SUMSQ>
+__global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
+                                               const double* __restrict__ coef, typename A::V* __restrict__ w,
+                                               int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
+                                               const double* __restrict__ ctrl) {
+  using Vt = typename A::V;
+  if (ctrl[0] != 0.0) return;
+  __shared__ typename A::Coef cs[G];
+  if (threadIdx.x < G) cs[threadIdx.x] = A::coef(threadIdx.x < nv ? coef[v0 + threadIdx.x] : 0.0);
+  __syncthreads();
+  constexpr int GD = DOTS ? G : 1;
+  typename A::Acc d[GD];
+#pragma unroll
+  for (int g = 0; g < GD; ++g) d[g] = A::zero();
+  typename A::Acc q = A::zero();
+  const Vt* Vb = V + (int64_t)v0 * ldv;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
+  // software pipeline: the next element's loads are issued before this
+  // element's arithmetic, overlapping their latency within each thread
+  Vt vn[G], xn = Vt();
+  if (i < n) {
+    xn = w[i];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i];
+  }
+  for (; i < n; i += stride) {
+    Vt v[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) v[g] = vn[g];
+    const Vt x = xn;
+    if (i + stride < n) {
+      xn = w[i + stride];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i + stride];
+    }
+    typename A::Sub t = A::sub_begin(x);
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+      if (g < nv) A::sub(t, cs[g], v[g]);
+    const Vt y = A::sub_end(t);
+    w[i] = y;
+    if (DOTS) {
+#pragma unroll
+      for (int g = 0; g < GD; ++g)
+        if (g < nv) A::acc(d[g], v[g], y);
+    }
+    if (SUMSQ) A::acc(q, y, y);
+  }
+  if (DOTS) block_partials<A, GD>(d, nv, part + (int64_t)v0 * NBMAX);
+  if (SUMSQ) {
+    const typename A::Acc qa[1] = {q};
+    block_partials<A, 1>(qa, 1, part_sq);
+  }
+}
+
+__device__ __forceinline__ void split3_store(__nv_bfloat16* o, int64_t plane, float x) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const float r1 = __fsub_rn(x, __bfloat162float(h));
+  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+  const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
+  o[0] = h;
+  o[plane] = m;
+  o[2 * plane] = l;
+}
+
+// Matvec input written next to a new basis vector.
+constexpr int kInNone = 0;     // the matvec reads the FP64 basis vector itself
+constexpr int kInPieces = 1;   // bfloat16 pieces of fl32(v), K-major [3][rows][Kp], zero in k >= cols
+constexpr int kInF64 = 2;      // v as FP64 (double-float basis, FP64 matvec)
+
+template <class A, int MODE>
+__device__ __forceinline__ void emit(typename A::V y, int64_t i, int64_t r, int64_t k, typename A::V* vn,
+                                     __nv_bfloat16* pieces, int64_t Kp, int64_t plane, double* x64) {
+  vn[i] = y;
+  if (MODE == kInPieces) split3_store(pieces + r * Kp + k, plane, A::f32(y));
+  if (MODE == kInF64) x64[i] = A::to_double(y);
+}
+
+// v_{j+1} = w / beta_j (unless stopped); element (r, k) of [rows][cols].
+template <class A, int MODE>
+__global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w, typename A::V* __restrict__ vn,
+                                             int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
+                                             int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
+                                             int j) {
+  if (scal[OFF_CTRL] != 0.0) return;
+  const typename A::Coef c = A::coef(1.0 / scal[OFF_BETA + j]);
+  const int64_t plane = rows * Kp;
+  const int64_t kend = MODE == kInPieces ? Kp : cols;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t k = threadIdx.x; k < kend; k += NT) {
+      if (k < cols) {
+        const int64_t i = r * cols + k;
+        emit<A, MODE>(A::mul(w[i], c), i, r, k, vn, pieces, Kp, plane, x64);
+      } else {
+        split3_store(pieces + r * Kp + k, plane, 0.f);
+      }
+    }
+}
+
+// v_0 = psi / ||psi|| (FP64 sum of squares already in scal[OFF_CTRL + 3])
+template <class A, int MODE>
+__global__ void __launch_bounds__(NT) k_start(const double* __restrict__ psi, typename A::V* __restrict__ v0,
+                                              int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
+                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal) {
+  const double inv = 1.0 / sqrt(scal[OFF_CTRL + 3]);
+  const int64_t plane = rows * Kp;
+  const int64_t kend = MODE == kInPieces ? Kp : cols;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t k = threadIdx.x; k < kend; k += NT) {
+      if (k < cols) {
+        const int64_t i = r * cols + k;
+        emit<A, MODE>(A::from_double(psi[i] * inv), i, r, k, v0, pieces, Kp, plane, x64);
+      } else {
+        split3_store(pieces + r * Kp + k, plane, 0.f);
+      }
+    }
+}
+
+template <class A>
+__global__ void __launch_bounds__(NT) k_from_f64(const double* __restrict__ x, typename A::V* __restrict__ y, int64_t n,
+                                                 const double* __restrict__ ctrl) {
+  if (ctrl[0] != 0.0) return;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+    y[i] = A::from_double(x[i]);
+}
+
+// x = sum_{j<k} y_j v_j (Ritz vector), stored as FP64
+template <class A>
+__global__ void __launch_bounds__(NT) k_ritz(const typename A::V* __restrict__ V, int64_t ldv,
+                                             const double* __restrict__ scal, double* __restrict__ x, int64_t n) {
+  __shared__ typename A::Coef ys[MAXM];
+  const int k = (int)scal[OFF_CTRL + 1];
+  for (int j = threadIdx.x; j < k; j += NT) ys[j] = A::coef(scal[OFF_Y + j]);
+  __syncthreads();
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+    typename A::Acc a = A::zero();
+    for (int j = 0; j < k; ++j) A::acc_c(a, ys[j], V[(int64_t)j * ldv + i]);
+    x[i] = A::value(a);
+  }
+}
+
+// ---------------------------------------------------------------- scalar kernels
+// out[v] = sum_{b < nb} part[v*NBMAX + b] in order; one block per vector.
+__global__ void k_reduce_parts(const double* __restrict__ part, int nv, int nb, double* __restrict__ out,
                                const double* __restrict__ ctrl) {
   if (ctrl[0] != 0.0) return;
   const int v = blockIdx.x;
   if (v >= nv) return;
   __shared__ double sh[32];
   double s = 0.0;
-  for (int b = threadIdx.x; b < NB; b += blockDim.x) s += part[(int64_t)v * NB + b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[(int64_t)v * NBMAX + b];
   s = warp_sum(s);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
   __syncthreads();
@@ -108,58 +361,11 @@ __global__ void k_reduce_parts(const double* __restrict__ part, int nv, double* 
   }
 }
 
-// w -= sum_{v<nv} c[v] V_v   (two elements per thread per iteration)
-template <int G>
-__global__ void __launch_bounds__(NT) k_mupdate(const double* __restrict__ V, int64_t ldv, int v0, int nv,
-                                                const double* __restrict__ c, double* __restrict__ w, int64_t n,
-                                                const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
-  double cc[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) cc[g] = g < nv ? c[v0 + g] : 0.0;
-  const int64_t stride = (int64_t)NB * NT;
-  int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
-  for (; i + stride < n; i += 2 * stride) {
-    double s = 0.0, t = 0.0;
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) {
-        const double* vg = V + (int64_t)(v0 + g) * ldv;
-        s = fma(cc[g], vg[i], s);
-        t = fma(cc[g], vg[i + stride], t);
-      }
-    w[i] -= s;
-    w[i + stride] -= t;
-  }
-  if (i < n) {
-    double s = 0.0;
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) s = fma(cc[g], V[(int64_t)(v0 + g) * ldv + i], s);
-    w[i] -= s;
-  }
-}
-
-// w = w - alpha_j v_j - beta_{j-1} v_{j-1}
-__global__ void __launch_bounds__(NT) k_three_term(double* __restrict__ w, const double* __restrict__ vj,
-                                                   const double* __restrict__ vjm1, int64_t n,
-                                                   const double* __restrict__ scal, int j) {
-  if (scal[OFF_CTRL] != 0.0) return;
-  const double a = scal[OFF_ALPHA + j];
-  const double b = j > 0 ? scal[OFF_BETA + j - 1] : 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
-    double x = w[i] - a * vj[i];
-    if (j > 0) x -= b * vjm1[i];
-    w[i] = x;
-  }
-}
-
-__global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int64_t n, double* __restrict__ part,
-                                              const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
+// FP64 partial sums of squares of psi (the start vector's norm)
+__global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int64_t n, double* __restrict__ part) {
   __shared__ double sh[NT / 32];
   double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) acc = fma(w[i], w[i], acc);
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) acc = fma(w[i], w[i], acc);
   acc = warp_sum(acc);
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
   __syncthreads();
@@ -170,6 +376,14 @@ __global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int6
   }
 }
 
+// alpha_j = <v_j, H v_j> (the pass-1 coefficient of v_j); without
+// re-orthogonalisation the pass-3 coefficients are (beta_{j-1}, alpha_j).
+__global__ void k_post_pass1(double* scal, int j, int reorth) {
+  if (scal[OFF_CTRL] != 0.0) return;
+  scal[OFF_ALPHA + j] = scal[OFF_H + j];
+  if (!reorth && j > 0) scal[OFF_H + j - 1] = scal[OFF_BETA + j - 1];
+}
+
 // beta_j = ||w||, stop test, step counter.
 __global__ void k_finish_beta(double* scal, int j, int m, double tol) {
   if (scal[OFF_CTRL] != 0.0) return;
@@ -178,32 +392,6 @@ __global__ void k_finish_beta(double* scal, int j, int m, double tol) {
   scal[OFF_BETA + j] = b;
   scal[OFF_CTRL + 1] = (double)(j + 1);
   if (j == m - 1 || b < tol * fabs(a)) scal[OFF_CTRL] = 1.0;
-}
-
-// v_{j+1} = w / beta_j (unless stopped)
-__global__ void __launch_bounds__(NT) k_next_vec(const double* __restrict__ w, double* __restrict__ vn, int64_t n,
-                                                 const double* __restrict__ scal, int j) {
-  if (scal[OFF_CTRL] != 0.0) return;
-  const double inv = 1.0 / scal[OFF_BETA + j];
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) vn[i] = w[i] * inv;
-}
-
-// v_0 = psi / ||psi||  (sumsq partial sums already in part[0..NB))
-__global__ void __launch_bounds__(NT) k_start_vec(const double* __restrict__ psi, double* __restrict__ v0, int64_t n,
-                                                  const double* __restrict__ scal) {
-  const double inv = 1.0 / sqrt(scal[OFF_CTRL + 3]);
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) v0[i] = psi[i] * inv;
-}
-
-// x = sum_{j<k} y_j v_j
-__global__ void __launch_bounds__(NT) k_ritz_vec(const double* __restrict__ V, int64_t ldv,
-                                                 const double* __restrict__ scal, double* __restrict__ x, int64_t n) {
-  const int k = (int)scal[OFF_CTRL + 1];
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
-    double s = 0.0;
-    for (int j = 0; j < k; ++j) s = fma(scal[OFF_Y + j], V[(int64_t)j * ldv + i], s);
-    x[i] = s;
-  }
 }
 
 __device__ int sturm_count(const double* a, const double* b, int m, double x) {
@@ -341,410 +529,144 @@ __global__ void k_init_scal(double* scal) {
   for (int i = threadIdx.x; i < NSCAL; i += blockDim.x) scal[i] = 0.0;
 }
 
-// ---------------------------------------------------------------- double-float
-// A double-float number is the unevaluated sum hi + lo of two FP32 values
-// with |lo| <= ulp(hi)/2 (Dekker, Numer. Math. 18, 1971).  Sums use Knuth's
-// TwoSum (TAOCP vol. 2, Sec. 4.2.2) and products the FMA-exact split
-// a*b = p + e; running sums keep an unnormalised low word.
-
-__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bp = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
-}
-
-__device__ __forceinline__ float2 df_norm(float h, float l) {
-  float s, e;
-  df_two_sum(h, l, s, e);
-  return make_float2(s, e);
-}
-
-__device__ __forceinline__ float2 df_from_double(double x) {
-  const float h = __double2float_rn(x);
-  return make_float2(h, __double2float_rn(x - (double)h));
-}
-
-// x * y as (p, t) with p + t = x*y to ~2^-48 relative
-__device__ __forceinline__ void df_prod(float2 x, float2 y, float& p, float& t) {
-  p = __fmul_rn(x.x, y.x);
-  const float e = __fmaf_rn(x.x, y.x, -p);
-  t = __fmaf_rn(x.x, y.y, __fmaf_rn(x.y, y.x, e));
-}
-
-// (h, l) += x * y
-__device__ __forceinline__ void df_acc(float2 x, float2 y, float& h, float& l) {
-  float p, t, s, err;
-  df_prod(x, y, p, t);
-  df_two_sum(h, p, s, err);
-  h = s;
-  l = __fadd_rn(l, __fadd_rn(err, t));
-}
-
-// (h, l) -= x * y
-__device__ __forceinline__ void df_sub(float2 x, float2 y, float& h, float& l) {
-  float p, t, s, err;
-  df_prod(x, y, p, t);
-  df_two_sum(h, -p, s, err);
-  h = s;
-  l = __fadd_rn(l, __fsub_rn(err, t));
-}
-
-__device__ __forceinline__ void split3_store(__nv_bfloat16* o, int64_t plane, float x) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(x);
-  const float r1 = __fsub_rn(x, __bfloat162float(h));
-  const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-  const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(m)));
-  o[0] = h;
-  o[plane] = m;
-  o[2 * plane] = l;
-}
-
-// Per-block partial sums of G double-float accumulators (fixed order):
-// part[g*NB + blockIdx.x] for g < nv.
-template <int G>
-__device__ __forceinline__ void df_block_partials(const float (&h)[G], const float (&l)[G], int nv, double* part) {
-  __shared__ double sh[NT / 32][G];
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll
-  for (int g = 0; g < G; ++g)
-    if (g < nv) {
-      const double s = warp_sum((double)h[g] + (double)l[g]);
-      if (lane == 0) sh[wid][g] = s;
-    }
-  __syncthreads();
-  if (threadIdx.x < G && threadIdx.x < nv) {
-    double s = 0.0;
-    for (int k = 0; k < NT / 32; ++k) s += sh[k][threadIdx.x];
-    part[(int64_t)threadIdx.x * NB + blockIdx.x] = s;
-  }
-}
-
-// part[(v0+g)*NB + block] = partial <V_{v0+g}, w>, g < nv <= G
-template <int G>
-__global__ void __launch_bounds__(NT) k_df_dots(const float2* __restrict__ V, int64_t ldv, int v0, int nv,
-                                                const float2* __restrict__ w, int64_t n, double* __restrict__ part,
-                                                const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
-  float h[G], l[G];
-#pragma unroll
-  for (int g = 0; g < G; ++g) h[g] = l[g] = 0.f;
-  const float2* Vb = V + (int64_t)v0 * ldv;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
-    const float2 x = w[i];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) df_acc(Vb[(int64_t)g * ldv + i], x, h[g], l[g]);
-  }
-  df_block_partials<G>(h, l, nv, part + (int64_t)v0 * NB);
-}
-
-// w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then optionally the partial dots of
-// the new w with the same vectors (part rows v0..) and of ||w||^2 (part_sq).
-template <int G, bool DOTS, bool SUMSQ>
-__global__ void __launch_bounds__(NT) k_df_update(const float2* __restrict__ V, int64_t ldv, int v0, int nv,
-                                                  const double* __restrict__ coef, float2* __restrict__ w, int64_t n,
-                                                  double* __restrict__ part, double* __restrict__ part_sq,
-                                                  const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
-  __shared__ float2 cs[G];
-  if (threadIdx.x < G) cs[threadIdx.x] = threadIdx.x < nv ? df_from_double(coef[v0 + threadIdx.x]) : make_float2(0.f, 0.f);
-  __syncthreads();
-  constexpr int GD = DOTS ? G : 1;
-  float dh[GD], dl[GD];
-#pragma unroll
-  for (int g = 0; g < GD; ++g) dh[g] = dl[g] = 0.f;
-  float qh = 0.f, ql = 0.f;
-  const float2* Vb = V + (int64_t)v0 * ldv;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
-    float2 v[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) v[g] = Vb[(int64_t)g * ldv + i];
-    const float2 x = w[i];
-    float h = x.x, l = x.y;
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) df_sub(cs[g], v[g], h, l);
-    const float2 y = df_norm(h, l);
-    w[i] = y;
-    if (DOTS) {
-#pragma unroll
-      for (int g = 0; g < GD; ++g)
-        if (g < nv) df_acc(v[g], y, dh[g], dl[g]);
-    }
-    if (SUMSQ) df_acc(y, y, qh, ql);
-  }
-  if (DOTS) df_block_partials<GD>(dh, dl, nv, part + (int64_t)v0 * NB);
-  if (SUMSQ) {
-    float qa[1] = {qh}, qb[1] = {ql};
-    if (DOTS) __syncthreads();
-    df_block_partials<1>(qa, qb, 1, part_sq);
-  }
-}
-
-// alpha_j = <v_j, H v_j> (the pass-1 coefficient of v_j); without
-// re-orthogonalisation the update coefficients are (beta_{j-1}, alpha_j).
-__global__ void k_df_post_pass1(double* scal, int j, int reorth) {
-  if (scal[OFF_CTRL] != 0.0) return;
-  scal[OFF_ALPHA + j] = scal[OFF_H + j];
-  if (!reorth && j > 0) scal[OFF_H + j - 1] = scal[OFF_BETA + j - 1];
-}
-
-// Store a new basis vector y (already normalised) at element (r, k) and the
-// matvec's input: bfloat16 pieces of fl32(y) = y.hi (K-major [3][rows][Kp],
-// zero in k >= cols) or, for the FP64 matvec, y as FP64.
-template <bool PIECES>
-__device__ __forceinline__ void df_emit(float2 y, int64_t i, int64_t r, int64_t k, float2* vn, __nv_bfloat16* pieces,
-                                        int64_t Kp, int64_t plane, double* x64) {
-  vn[i] = y;
-  if (PIECES) split3_store(pieces + r * Kp + k, plane, y.x);
-  else x64[i] = (double)y.x + (double)y.y;
-}
-
-// v_{j+1} = w / beta_j (unless stopped), one row (r) per block iteration.
-template <bool PIECES>
-__global__ void __launch_bounds__(NT) k_df_next(const float2* __restrict__ w, float2* __restrict__ vn, int64_t rows,
-                                                int64_t cols, __nv_bfloat16* __restrict__ pieces, int64_t Kp,
-                                                double* __restrict__ x64, const double* __restrict__ scal, int j) {
-  if (scal[OFF_CTRL] != 0.0) return;
-  const float2 c = df_from_double(1.0 / scal[OFF_BETA + j]);
-  const int64_t plane = rows * Kp;
-  const int64_t kend = PIECES ? Kp : cols;
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
-    for (int64_t k = threadIdx.x; k < kend; k += NT) {
-      if (k < cols) {
-        const int64_t i = r * cols + k;
-        float p, t;
-        df_prod(w[i], c, p, t);
-        df_emit<PIECES>(df_norm(p, t), i, r, k, vn, pieces, Kp, plane, x64);
-      } else {
-        split3_store(pieces + r * Kp + k, plane, 0.f);
-      }
-    }
-}
-
-// v_0 = psi / ||psi|| (FP64 sum of squares already in scal[OFF_CTRL + 3])
-template <bool PIECES>
-__global__ void __launch_bounds__(NT) k_df_start(const double* __restrict__ psi, float2* __restrict__ v0, int64_t rows,
-                                                 int64_t cols, __nv_bfloat16* __restrict__ pieces, int64_t Kp,
-                                                 double* __restrict__ x64, const double* __restrict__ scal) {
-  const double inv = 1.0 / sqrt(scal[OFF_CTRL + 3]);
-  const int64_t plane = rows * Kp;
-  const int64_t kend = PIECES ? Kp : cols;
-  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
-    for (int64_t k = threadIdx.x; k < kend; k += NT) {
-      if (k < cols) {
-        const int64_t i = r * cols + k;
-        df_emit<PIECES>(df_from_double(psi[i] * inv), i, r, k, v0, pieces, Kp, plane, x64);
-      } else {
-        split3_store(pieces + r * Kp + k, plane, 0.f);
-      }
-    }
-}
-
-__global__ void __launch_bounds__(NT) k_f64_to_df(const double* __restrict__ x, float2* __restrict__ y, int64_t n,
-                                                  const double* __restrict__ ctrl) {
-  if (ctrl[0] != 0.0) return;
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) y[i] = df_from_double(x[i]);
-}
-
-// x = sum_{j<k} y_j v_j, accumulated in double-float, stored as FP64
-__global__ void __launch_bounds__(NT) k_df_ritz(const float2* __restrict__ V, int64_t ldv,
-                                                const double* __restrict__ scal, double* __restrict__ x, int64_t n) {
-  __shared__ float2 ys[MAXM];
-  const int k = (int)scal[OFF_CTRL + 1];
-  for (int j = threadIdx.x; j < k; j += NT) ys[j] = df_from_double(scal[OFF_Y + j]);
-  __syncthreads();
-  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)NB * NT) {
-    float h = 0.f, l = 0.f;
-    for (int j = 0; j < k; ++j) df_acc(ys[j], V[(int64_t)j * ldv + i], h, l);
-    x[i] = (double)h + (double)l;
-  }
-}
 
 }  // namespace
 
-static tci_status mdot(tci_context ctx, const double* V, int64_t ldv, int nv, const double* w, int64_t n, double* part,
-                       double* out, const double* ctrl) {
-  for (int v0 = 0; v0 < nv; v0 += 8) {
-    const int g = nv - v0 < 8 ? nv - v0 : 8;
-    k_mdot<8><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, g, w, n, part, ctrl);
-  }
-  k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part, nv, out, ctrl);
+// ---------------------------------------------------------------- host side
+namespace {
+
+template <class A>
+void dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
+                 int64_t n, double* part, const double* ctrl) {
+  if (nv <= 8) k_dots<A, 8><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+  else if (nv <= 16) k_dots<A, 16><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+  else k_dots<A, GMAX><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+}
+
+// out[0..nv) = <V_{v0+v}, w>
+template <class A>
+tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
+                    int64_t n, double* part, double* out, const double* ctrl) {
+  for (int g0 = 0; g0 < nv; g0 += GMAX) dots_launch<A>(ctx, V, ldv, v0 + g0, nv - g0 < GMAX ? nv - g0 : GMAX, w, n, part, ctrl);
+  k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, A::kBlocks, out, ctrl);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
 
-static tci_status mupdate(tci_context ctx, const double* V, int64_t ldv, int nv, const double* c, double* w, int64_t n,
-                          const double* ctrl) {
-  for (int v0 = 0; v0 < nv; v0 += 8) {
-    const int g = nv - v0 < 8 ? nv - v0 : 8;
-    k_mupdate<8><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, g, c, w, n, ctrl);
-  }
-  TCI_CUDA(ctx, cudaGetLastError());
-  return TCI_OK;
-}
-
-// ---------------------------------------------------------------- double-float host helpers
-template <int G>
-static void df_dots_launch(tci_context ctx, const float2* V, int64_t ldv, int v0, int nv, const float2* w, int64_t n,
-                           double* part, const double* ctrl) {
-  k_df_dots<G><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
-}
-
-// out[0..nv) = <V_v, w>
-static tci_status df_dots(tci_context ctx, const float2* V, int64_t ldv, int v0, int nv, const float2* w, int64_t n,
-                          double* part, double* out, const double* ctrl) {
-  for (int g0 = 0; g0 < nv; g0 += DF_GMAX) {
-    const int g = nv - g0 < DF_GMAX ? nv - g0 : DF_GMAX;
-    if (g <= 8) df_dots_launch<8>(ctx, V, ldv, v0 + g0, g, w, n, part, ctrl);
-    else if (g <= 16) df_dots_launch<16>(ctx, V, ldv, v0 + g0, g, w, n, part, ctrl);
-    else df_dots_launch<DF_GMAX>(ctx, V, ldv, v0 + g0, g, w, n, part, ctrl);
-  }
-  k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NB, nv, out, ctrl);
-  TCI_CUDA(ctx, cudaGetLastError());
-  return TCI_OK;
-}
-
-template <bool DOTS, bool SUMSQ>
-static void df_update_launch(tci_context ctx, const float2* V, int64_t ldv, int v0, int nv, const double* coef,
-                             float2* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
+template <class A, bool DOTS, bool SUMSQ>
+void update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
+                   typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
   if (nv <= 8)
-    k_df_update<8, DOTS, SUMSQ><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    k_update<A, 8, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
   else if (nv <= 16)
-    k_df_update<16, DOTS, SUMSQ><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    k_update<A, 16, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
   else
-    k_df_update<DF_GMAX, DOTS, SUMSQ><<<NB, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    k_update<A, GMAX, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
 }
 
 // w -= sum_{v0 <= v < v0+nv} coef[v] V_v; then dots_out[0..nv) = <V_v, w>
-// (when dots_out) and *sumsq_out = ||w||^2 (when sumsq_out).  One fused
-// pass for nv <= DF_GMAX; larger sets update group by group and take the
-// dots in a separate pass.
-static tci_status df_update(tci_context ctx, const float2* V, int64_t ldv, int v0, int nv, const double* coef,
-                            float2* w, int64_t n, double* part, double* dots_out, double* sumsq_out,
-                            const double* ctrl) {
-  double* part_sq = part + (int64_t)MAXM * NB;
-  if (nv <= DF_GMAX) {
-    if (dots_out && !sumsq_out) df_update_launch<true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    else if (!dots_out && sumsq_out) df_update_launch<false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    else if (!dots_out && !sumsq_out) df_update_launch<false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    else return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (dots and sumsq in one pass)");
-    if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NB, nv, dots_out, ctrl);
+// (when dots_out) or *sumsq_out = ||w||^2 (when sumsq_out).  One fused pass
+// for nv <= GMAX; a larger basis is updated group by group and its dots
+// taken in a separate pass.
+template <class A>
+tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
+                      typename A::V* w, int64_t n, double* part, double* dots_out, double* sumsq_out,
+                      const double* ctrl) {
+  double* part_sq = part + (int64_t)MAXM * NBMAX;
+  if (dots_out && sumsq_out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (dots and sumsq in one pass)");
+  if (nv <= GMAX) {
+    if (dots_out) update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    else if (sumsq_out) update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    else update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, A::kBlocks, dots_out, ctrl);
   } else {
-    for (int g0 = 0; g0 < nv; g0 += DF_GMAX) {
-      const int g = nv - g0 < DF_GMAX ? nv - g0 : DF_GMAX;
-      const bool last = g0 + g == nv;
-      if (last && sumsq_out) df_update_launch<false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
-      else df_update_launch<false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+    for (int g0 = 0; g0 < nv; g0 += GMAX) {
+      const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
+      if (g0 + g == nv && sumsq_out) update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+      else update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
     }
-    if (dots_out) TCI_TRY(df_dots(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl));
+    if (dots_out) TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl));
   }
-  if (sumsq_out) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, sumsq_out, ctrl);
+  if (sumsq_out) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, A::kBlocks, sumsq_out, ctrl);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
 
-// The double-float Lanczos iteration (same recurrence as the FP64 one; see
-// the file header for the fused pass structure).
-static tci_status lanczos_df(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol) {
+template <class A, int MODE>
+void launch_start(tci_context ctx, const double* psi0, typename A::V* v0, int64_t rows, int64_t cols,
+                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S) {
+  const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
+  k_start<A, MODE><<<blocks, NT, 0, ctx->stream>>>(psi0, v0, rows, cols, pieces, Kp, x64, S);
+}
+
+template <class A, int MODE>
+void launch_next(tci_context ctx, const typename A::V* w, typename A::V* vn, int64_t rows, int64_t cols,
+                 __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j) {
+  const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
+  k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j);
+}
+
+// The Lanczos iteration in arithmetic A with matvec input mode MODE
+// (kInPieces for a split-BF16 plan; kInNone for FP64 vectors on an FP64
+// plan; kInF64 for double-float vectors on an FP64 plan).
+template <class A, int MODE>
+tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol) {
+  using Vt = typename A::V;
   tci_context ctx = p->ctx;
   const int64_t n = p->chiL * 4 * p->chiR;
   const int64_t ldv = (n + 31) / 32 * 32;
   const int64_t rows = p->chiL * 4, cols = p->chiR;
-  const bool split = p->prec != TCI_PREC_NATIVE;
-  if (!split) {
+  constexpr bool kDF = std::is_same<Vt, float2>::value;
+  if (MODE == kInF64) {
     if (!p->lz_x64) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_x64));
     if (!p->lz_o64) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_o64));
   }
   double* S = p->lz_scal;
   double* ctrl = S + OFF_CTRL;
-  float2* V = (float2*)p->lz_V;
-  float2* w = (float2*)p->lz_w;
+  Vt* V = (Vt*)p->lz_V;
+  Vt* w = (Vt*)p->lz_w;
   double* part = p->lz_part;
-  __nv_bfloat16* pieces = (__nv_bfloat16*)p->psip;
-  const int Kp = (int)(split ? p->Kp1 : 0);
-  const int rblocks = (int)(rows < (int64_t)NB * 8 ? rows : (int64_t)NB * 8);
+  __nv_bfloat16* pieces = MODE == kInPieces ? (__nv_bfloat16*)p->psip : nullptr;
+  const int64_t Kp = MODE == kInPieces ? p->Kp1 : 0;
 
   k_init_scal<<<1, 256, 0, ctx->stream>>>(S);
-  k_sumsq<<<NB, NT, 0, ctx->stream>>>(psi0, n, part, ctrl);
-  k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, ctrl + 3, ctrl);
-  if (split) k_df_start<true><<<rblocks, NT, 0, ctx->stream>>>(psi0, V, rows, cols, pieces, Kp, nullptr, S);
-  else k_df_start<false><<<rblocks, NT, 0, ctx->stream>>>(psi0, V, rows, cols, nullptr, 0, p->lz_x64, S);
+  k_sumsq<<<NBMAX, NT, 0, ctx->stream>>>(psi0, n, part);
+  k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
+  launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S);
   TCI_CUDA(ctx, cudaGetLastError());
   for (int j = 0; j < nsteps; ++j) {
-    // w = H v_j (the matvec's input was prepared with v_j)
-    if (split) {
-      TCI_TRY(tci_heff_apply_raw(p, nullptr, w, true, 2));
+    Vt* vj = V + (int64_t)j * ldv;
+    // w = H v_j
+    if (MODE == kInPieces) {
+      TCI_TRY(tci_heff_apply_raw(p, nullptr, w, true, kDF ? 2 : 0));
+    } else if (MODE == kInNone) {
+      TCI_TRY(tci_heff_apply_raw(p, (const double*)vj, w, false, 0));
     } else {
       TCI_TRY(tci_heff_apply_raw(p, p->lz_x64, p->lz_o64, false, 0));
-      k_f64_to_df<<<NB, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
+      k_from_f64<A><<<A::kBlocks, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
     }
     if (reorth) {
-      TCI_TRY(df_dots(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl));
-      k_df_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1);
-      TCI_TRY(df_update(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, nullptr, ctrl));
-      TCI_TRY(df_update(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, ctrl));
+      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl));
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1);
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, nullptr, ctrl));
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, ctrl));
     } else {
-      TCI_TRY(df_dots(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl));
-      k_df_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0);
+      TCI_TRY(run_dots<A>(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl));
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0);
       const int v0 = j > 0 ? j - 1 : 0;
-      TCI_TRY(df_update(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl));
+      TCI_TRY(run_update<A>(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl));
     }
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
-    if (j + 1 < nsteps) {
-      float2* vn = V + (int64_t)(j + 1) * ldv;
-      if (split) k_df_next<true><<<rblocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, nullptr, S, j);
-      else k_df_next<false><<<rblocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, nullptr, 0, p->lz_x64, S, j);
-    }
+    if (j + 1 < nsteps) launch_next<A, MODE>(ctx, w, V + (int64_t)(j + 1) * ldv, rows, cols, pieces, Kp, p->lz_x64, S, j);
     TCI_CUDA(ctx, cudaGetLastError());
   }
   k_tridiag_lowest<<<1, NT, 0, ctx->stream>>>(S);
-  if (x) k_df_ritz<<<NB, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
+  if (x) k_ritz<A><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
 
-// The FP64 Lanczos iteration: three-term recurrence, then (reorth) two
-// classical Gram-Schmidt passes against the whole basis.
-static tci_status lanczos_f64(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol) {
-  tci_context ctx = p->ctx;
-  const int64_t n = p->chiL * 4 * p->chiR;
-  const int64_t ldv = (n + 31) / 32 * 32;
-  double* S = p->lz_scal;
-  double* ctrl = S + OFF_CTRL;
-  double* V = p->lz_V;
-  double* w = p->lz_w;
-  double* part = p->lz_part;
-  k_init_scal<<<1, 256, 0, ctx->stream>>>(S);
-  // v0 = psi0 / ||psi0||
-  k_sumsq<<<NB, NT, 0, ctx->stream>>>(psi0, n, part, ctrl);
-  k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, ctrl + 3, ctrl);
-  k_start_vec<<<NB, NT, 0, ctx->stream>>>(psi0, V, n, S);
-  TCI_CUDA(ctx, cudaGetLastError());
-  for (int j = 0; j < nsteps; ++j) {
-    double* vj = V + (int64_t)j * ldv;
-    TCI_TRY(tci_heff_apply_raw(p, vj, w, false));   // FP64 out
-    // alpha_j = <v_j, w>
-    TCI_TRY(mdot(ctx, vj, ldv, 1, w, n, part, S + OFF_ALPHA + j, ctrl));
-    k_three_term<<<NB, NT, 0, ctx->stream>>>(w, vj, j > 0 ? V + (int64_t)(j - 1) * ldv : vj, n, S, j);
-    if (reorth) {
-      for (int pass = 0; pass < 2; ++pass) {
-        TCI_TRY(mdot(ctx, V, ldv, j + 1, w, n, part, S + OFF_H, ctrl));
-        TCI_TRY(mupdate(ctx, V, ldv, j + 1, S + OFF_H, w, n, ctrl));
-      }
-    }
-    k_sumsq<<<NB, NT, 0, ctx->stream>>>(w, n, part, ctrl);
-    k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, ctrl + 3, ctrl);
-    k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
-    if (j + 1 < nsteps) k_next_vec<<<NB, NT, 0, ctx->stream>>>(w, V + (int64_t)(j + 1) * ldv, n, S, j);
-    TCI_CUDA(ctx, cudaGetLastError());
-  }
-  k_tridiag_lowest<<<1, NT, 0, ctx->stream>>>(S);
-  if (x) k_ritz_vec<<<NB, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
-  TCI_CUDA(ctx, cudaGetLastError());
-  return TCI_OK;
-}
+}  // namespace
 
 extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, int reorth, double* ritz, double* alpha,
                                   double* beta, int* steps_done, tci_tensor x) {
@@ -776,17 +698,22 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   }
   if (!p->lz_w) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_w));
   if (!p->lz_scal) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * NSCAL, (void**)&p->lz_scal));
-  if (!p->lz_part) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * (int64_t)NB * (MAXM + 1), (void**)&p->lz_part));
+  if (!p->lz_part) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * (int64_t)NBMAX * (MAXM + 1), (void**)&p->lz_part));
   double* S = p->lz_scal;
   double* ctrl = S + OFF_CTRL;
   const double tol = 1e-12;
-  int arith = p->vec_arith;
-  if (arith == TCI_LANCZOS_AUTO) arith = p->prec == TCI_PREC_NATIVE ? TCI_LANCZOS_F64 : TCI_LANCZOS_DF32;
+  const int arith = p->vec_arith == TCI_LANCZOS_DF32 ? TCI_LANCZOS_DF32 : TCI_LANCZOS_F64;
+  const bool split = p->prec != TCI_PREC_NATIVE;
   vs.info = arith == TCI_LANCZOS_DF32 ? "double-float vectors" : "FP64 vectors";
   const double* psi = (const double*)psi0->data;
   double* xd = x ? (double*)x->data : nullptr;
-  if (arith == TCI_LANCZOS_DF32) TCI_TRY(lanczos_df(p, psi, nsteps, reorth, xd, tol));
-  else TCI_TRY(lanczos_f64(p, psi, nsteps, reorth, xd, tol));
+  if (arith == TCI_LANCZOS_DF32) {
+    if (split) TCI_TRY((lanczos_run<ArithDF, kInPieces>(p, psi, nsteps, reorth, xd, tol)));
+    else TCI_TRY((lanczos_run<ArithDF, kInF64>(p, psi, nsteps, reorth, xd, tol)));
+  } else {
+    if (split) TCI_TRY((lanczos_run<ArithF64, kInPieces>(p, psi, nsteps, reorth, xd, tol)));
+    else TCI_TRY((lanczos_run<ArithF64, kInNone>(p, psi, nsteps, reorth, xd, tol)));
+  }
   TCI_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctrl, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   std::vector<double> ab(2 * MAXM);
   TCI_CUDA(ctx, cudaMemcpyAsync(ab.data(), S, 2 * MAXM * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
