@@ -27,6 +27,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -38,6 +39,12 @@ METRIC = "H_eff matvec GFLOP/s at chi=2048 (split-BF16 vs FP64, error ≤1e-6) +
 CHI = 2048
 LANCZOS_STEPS = 20
 SEED = 20251223
+
+
+# DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec, the mean
+# of GEMM1 (1443 MB) and GEMM2 (1668 MB) from one ncu capture of this kernel build
+# (profiles/dram_heff_chi2048.md).  Set to None whenever the kernel changes.
+GEMM_DRAM_BYTES_PER_LAUNCH = 1.556e9
 
 
 def heff_flops(chi: int) -> float:
@@ -67,11 +74,11 @@ class ClockSampler:
     def __init__(self, device_index: int):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(HERE, "gpurun_out", f"clocks_rank{device_index}.csv")
+        fd, self.path = tempfile.mkstemp(prefix=f"tci_clocks_rank{device_index}_", suffix=".csv")
+        os.close(fd)
 
     def __enter__(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
@@ -102,6 +109,10 @@ class ClockSampler:
                              parts[5:9]))
             except ValueError:
                 continue
+        try:
+            os.unlink(self.path)
+        except OSError:
+            pass
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -350,7 +361,8 @@ def run_gpu(args):
     tensor_tflops = 6.0 * gemm_flops(CHI) / (gemm_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "kernel": "k_split_bf16_gemm", "achieved": tensor_tflops,
                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": tensor_tflops / peaks["bf16_tflops"],
-                "traffic": None, "peak_source": f"{peak_src} bf16 burst",
+                "traffic": GEMM_DRAM_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch (DRAM read + write)",
+                "peak_source": f"{peak_src} bf16 burst",
                 "flops_per_launch": 6.0 * gemm_flops(CHI),
                 "note": "achieved counts the 6 BF16 piece products per FP64-equivalent multiply-add"}
 
@@ -445,17 +457,19 @@ def run_profile_case(args):
     ctx = tci.Context(0)
     plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="split_bf16")
     out = torch.empty_like(dpsi)
+    tuned = plan.autotune(dpsi, out, max_chunk_k=256)   # the configuration the bench runs
     if args.profile_lanczos:
         for _ in range(args.warmup + args.steps):
             plan.lanczos(dpsi, LANCZOS_STEPS, True, out)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": "20-step split-BF16 Lanczos", "chi": chi,
+        print(json.dumps({"profile_case": "20-step split-BF16 Lanczos", "chi": chi, "config": plan.get_config(),
                           "solves": args.warmup + args.steps, "launches_per_solve": lanczos_launches(LANCZOS_STEPS)}))
     else:
         for _ in range(args.warmup + args.steps):
             plan.apply(dpsi, out)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_case": "split-BF16 H_eff matvec", "chi": chi, "matvecs": args.warmup + args.steps,
+        print(json.dumps({"profile_case": "split-BF16 H_eff matvec", "chi": chi, "config": plan.get_config(),
+                          "matvecs": args.warmup + args.steps,
                           "launches_per_matvec": 4}))
     plan.close()
     ctx.close()

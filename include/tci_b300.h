@@ -138,6 +138,38 @@ tci_status tci_allocate(tci_context ctx, tci_dtype dtype, int order, const int64
 tci_status tci_zeros(tci_context ctx, tci_dtype dtype, int order, const int64_t* shape,
                      tci_tensor* out);
 
+/* TCI "eye" (App. C.2, Tensor construction): *out = a new owned n x n
+ * identity tensor (ones on the main diagonal, zeros elsewhere) of dtype.
+ * Errors: INVALID_ARG (n < 0, NULL out), DTYPE, ALLOC, CUDA. */
+tci_status tci_eye(tci_context ctx, tci_dtype dtype, int64_t n, tci_tensor* out);
+
+/* TCI "fill" (App. C.2, Tensor construction): *out = a new owned row-major
+ * tensor of the given shape with every element equal to re + i im (im is
+ * ignored for real dtypes).  Errors: as tci_allocate. */
+tci_status tci_fill(tci_context ctx, tci_dtype dtype, int order, const int64_t* shape, double re, double im,
+                    tci_tensor* out);
+
+/* TCI "cplx_conj" (App. C.2, Tensor manipulation): elementwise complex
+ * conjugation.  In place: t is conjugated (a real tensor is left unchanged;
+ * a lazy layout is materialised first).  _to: *out = a new owned conjugated
+ * copy (a deep copy for real dtypes).  Errors: INVALID_ARG, ALLOC, CUDA. */
+tci_status tci_cplx_conj(tci_context ctx, tci_tensor t);
+tci_status tci_cplx_conj_to(tci_context ctx, tci_tensor in, tci_tensor* out);
+
+/* TCI "to_cplx" (App. C.2, Tensor manipulation): *out = a new owned complex
+ * tensor of in's shape (F32 -> C64, F64 -> C128, zero imaginary parts); a
+ * complex input gives a deep copy.  Errors: INVALID_ARG, ALLOC, CUDA. */
+tci_status tci_to_cplx(tci_context ctx, tci_tensor in, tci_tensor* out);
+
+/* TCI "diag" (App. C.2, Tensor linear algebra): a first-order input of
+ * length n becomes the n x n matrix with it on the main diagonal; a
+ * second-order input [d0, d1] gives its main diagonal, of length
+ * min(d0, d1).  In place: t's shape and storage are replaced.  _to: *out is
+ * a new owned tensor.  Errors: SHAPE (order other than 1 or 2), INVALID_ARG,
+ * ALLOC, CUDA. */
+tci_status tci_diag(tci_context ctx, tci_tensor t);
+tci_status tci_diag_to(tci_context ctx, tci_tensor in, tci_tensor* out);
+
 /* TCI "copy" (deep copy): *out becomes a new owned, row-major tensor with
  * the same logical elements as `in` (strided inputs are materialised). */
 tci_status tci_copy(tci_context ctx, tci_tensor in, tci_tensor* out);

@@ -14,10 +14,12 @@ linear-algebra operations (Sec. II.B.2): matricise A to [I, S] and B to
 output's bond order.  ``contract_bruteforce`` is the sum written out
 element by element and exists to pin ``contract``.
 
-Readings where the paper is silent (listed in the design doc as well):
-* a label in both operands *and* in the output (a batch/Hadamard bond) and a
-  label in one operand that is absent from the output (an implicit partial
-  sum) are not covered by the specification -> ``UnsupportedLabels``.
+Readings where the paper is silent:
+* a label in both operands *and* in the output (a batch bond) is read as
+  "for every value of that label, contract the slices": C_{IJB} =
+  sum_S A_{ISB} B_{SJB}, the same definition applied slice by slice;
+* a label in one operand that is absent from the output (an implicit partial
+  sum) is not covered by the specification -> ``UnsupportedLabels``.
 """
 from __future__ import annotations
 
@@ -41,7 +43,11 @@ def _as_list(labels):
 
 
 def classify(shape_a, la, shape_b, lb, lc):
-    """Return (I, S, J, dims) label groups after validating the label lists."""
+    """Return (I, S, J, Bt, dims) label groups after validating the label lists.
+
+    I: free bonds of a, J: free bonds of b, S: summed bonds (in a and b, not
+    in c), Bt: batch bonds (in a, b and c); orders follow a (I, S, Bt) and b (J).
+    """
     la, lb, lc = _as_list(la), _as_list(lb), _as_list(lc)
     if len(la) != len(shape_a) or len(lb) != len(shape_b):
         raise LabelError("label count differs from tensor order")
@@ -57,12 +63,10 @@ def classify(shape_a, la, shape_b, lb, lc):
     S = [l for l in la if l in lb and l not in lc]
     I = [l for l in la if l not in lb]
     J = [l for l in lb if l not in la]
-    batch = [l for l in la if l in lb and l in lc]
-    if batch:
-        raise UnsupportedLabels("label shared by both operands and the output")
-    if sorted(map(str, lc)) != sorted(map(str, I + J)):
-        raise UnsupportedLabels("output labels must be exactly the free bonds of a and b")
-    return I, S, J, dims
+    Bt = [l for l in la if l in lb and l in lc]
+    if sorted(map(str, lc)) != sorted(map(str, I + J + Bt)):
+        raise UnsupportedLabels("output labels must be exactly the free and batch bonds of a and b")
+    return I, S, J, Bt, dims
 
 
 def contract(A, la, B, lb, lc):
@@ -70,16 +74,17 @@ def contract(A, la, B, lb, lc):
     A = np.asarray(A)
     B = np.asarray(B)
     la, lb, lc = _as_list(la), _as_list(lb), _as_list(lc)
-    I, S, J, dims = classify(A.shape, la, B.shape, lb, lc)
-    dI = [dims[l] for l in I]
-    dS = [dims[l] for l in S]
-    dJ = [dims[l] for l in J]
-    nI, nS, nJ = int(np.prod(dI, dtype=np.int64)), int(np.prod(dS, dtype=np.int64)), int(np.prod(dJ, dtype=np.int64))
-    Am = np.transpose(A, [la.index(l) for l in I + S]).reshape(nI, nS)
-    Bm = np.transpose(B, [lb.index(l) for l in S + J]).reshape(nS, nJ)
-    Cm = Am @ Bm
-    C = Cm.reshape(dI + dJ)
-    perm = [(I + J).index(l) for l in lc]
+    I, S, J, Bt, dims = classify(A.shape, la, B.shape, lb, lc)
+    size = lambda labels: int(np.prod([dims[l] for l in labels], dtype=np.int64))
+    nI, nS, nJ, nB = size(I), size(S), size(J), size(Bt)
+    # matricise every batch slice: A -> [Bt][I, S], B -> [Bt][S, J]
+    Am = np.transpose(A, [la.index(l) for l in Bt + I + S]).reshape(nB, nI, nS)
+    Bm = np.transpose(B, [lb.index(l) for l in Bt + S + J]).reshape(nB, nS, nJ)
+    Cm = np.empty((nB, nI, nJ), dtype=np.result_type(A.dtype, B.dtype))
+    for t in range(nB):                   # one matrix product per batch slice
+        Cm[t] = Am[t] @ Bm[t]
+    C = Cm.reshape([dims[l] for l in Bt + I + J])
+    perm = [(Bt + I + J).index(l) for l in lc]
     return np.transpose(C, perm).copy()
 
 
@@ -88,7 +93,7 @@ def contract_bruteforce(A, la, B, lb, lc):
     A = np.asarray(A)
     B = np.asarray(B)
     la, lb, lc = _as_list(la), _as_list(lb), _as_list(lc)
-    I, S, J, dims = classify(A.shape, la, B.shape, lb, lc)
+    I, S, J, Bt, dims = classify(A.shape, la, B.shape, lb, lc)
     out_shape = tuple(dims[l] for l in lc)
     dtype = np.result_type(A.dtype, B.dtype)
     C = np.zeros(out_shape, dtype=dtype)

@@ -100,6 +100,13 @@ SIGNATURES = [
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
+    ("tci_eye", C.c_int, [_p, C.c_int, C.c_int64, C.POINTER(_p)]),
+    ("tci_fill", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.POINTER(_p)]),
+    ("tci_cplx_conj", C.c_int, [_p, _p]),
+    ("tci_cplx_conj_to", C.c_int, [_p, _p, C.POINTER(_p)]),
+    ("tci_to_cplx", C.c_int, [_p, _p, C.POINTER(_p)]),
+    ("tci_diag", C.c_int, [_p, _p]),
+    ("tci_diag_to", C.c_int, [_p, _p, C.POINTER(_p)]),
     ("tci_heff_get_config", C.c_int, [_p, C.POINTER(C.c_int)]),
     ("tci_heff_set_config", C.c_int, [_p, C.POINTER(C.c_int)]),
 ]
@@ -295,6 +302,29 @@ class Tensor:
         _check(lib.tci_scale(self.ctx.handle, self.handle, s.real, s.imag), self.ctx.handle)
         return self
 
+    def cplx_conj_(self):
+        _check(lib.tci_cplx_conj(self.ctx.handle, self.handle), self.ctx.handle)
+        return self
+
+    def cplx_conj(self) -> "Tensor":
+        h = _p()
+        _check(lib.tci_cplx_conj_to(self.ctx.handle, self.handle, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h)
+
+    def to_cplx(self) -> "Tensor":
+        h = _p()
+        _check(lib.tci_to_cplx(self.ctx.handle, self.handle, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h)
+
+    def diag_(self):
+        _check(lib.tci_diag(self.ctx.handle, self.handle), self.ctx.handle)
+        return self
+
+    def diag(self) -> "Tensor":
+        h = _p()
+        _check(lib.tci_diag_to(self.ctx.handle, self.handle, C.byref(h)), self.ctx.handle)
+        return Tensor(self.ctx, h)
+
     def free(self):
         if self.handle:
             _check(lib.tci_tensor_free(C.byref(self.handle)))
@@ -306,6 +336,19 @@ class Tensor:
                 lib.tci_tensor_free(C.byref(self.handle))
         except Exception:
             pass
+
+
+def eye(ctx: Context, n: int, dtype: int = F64) -> Tensor:
+    h = _p()
+    _check(lib.tci_eye(ctx.handle, dtype, int(n), C.byref(h)), ctx.handle)
+    return Tensor(ctx, h)
+
+
+def fill(ctx: Context, shape, value, dtype: int = F64) -> Tensor:
+    h = _p()
+    v = complex(value)
+    _check(lib.tci_fill(ctx.handle, dtype, len(shape), _arr64(shape), v.real, v.imag, C.byref(h)), ctx.handle)
+    return Tensor(ctx, h)
 
 
 def allocate(ctx: Context, shape, dtype: int = F64, zero: bool = False) -> Tensor:

@@ -1,7 +1,7 @@
 // TCI "contract" (App. C.2; Sec. II.B.2: C_IJ = sum_S A_IS B_SJ).
 //
-// Planner: labels are classified into M (free in a), N (free in b) and K
-// (shared, summed) groups; adjacent modes of a group that are contiguous with
+// Planner: labels are classified into M (free in a), N (free in b), K
+// (shared, summed) and batch (in a, b and c) groups; adjacent modes of a group that are contiguous with
 // respect to each other in every tensor carrying them are coalesced.  When a
 // group reduces to at most one mode per operand, the operand is read in place
 // through its strides (no transpose is materialised); otherwise it is packed
@@ -92,17 +92,18 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
   int64_t cshape[TCI_MAX_ORDER];
   for (int i = 0; i < nc; ++i) {
     int ia = find(la, a->order, lc[i]), ib = find(lb, b->order, lc[i]);
-    if (ia >= 0 && ib >= 0) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "contract: label in a, b and c (batch bond) is not in the specification");
     if (ia < 0 && ib < 0) return tci_fail(ctx, TCI_ERR_LABEL, "contract: output label not found in a or b");
+    if (ia >= 0 && ib >= 0 && a->shape[ia] != b->shape[ib])
+      return tci_fail(ctx, TCI_ERR_LABEL, "contract: bond dimension mismatch on a batch label");
     cshape[i] = ia >= 0 ? a->shape[ia] : b->shape[ib];
   }
-  Group gm, gn, gk;
-  // K group in a's bond order; dims must agree
+  Group gm, gn, gk, gb;
+  // K group (shared, not in c) in a's bond order; dims must agree
   for (int i = 0; i < a->order; ++i) {
     int ib = find(lb, b->order, la[i]);
     if (ib >= 0) {
       if (a->shape[i] != b->shape[ib]) return tci_fail(ctx, TCI_ERR_LABEL, "contract: bond dimension mismatch on a shared label");
-      gk.modes.push_back({a->shape[i], a->strides[i], b->strides[ib], 0});
+      if (find(lc, nc, la[i]) < 0) gk.modes.push_back({a->shape[i], a->strides[i], b->strides[ib], 0});
     } else if (find(lc, nc, la[i]) < 0) {
       return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "contract: free label of a missing from c");
     }
@@ -133,16 +134,16 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
 
   for (int i = 0; i < nc; ++i) {
     int ia = find(la, a->order, lc[i]);
-    if (ia >= 0) gm.modes.push_back({a->shape[ia], a->strides[ia], 0, cstr[i]});
-    else {
-      int ib = find(lb, b->order, lc[i]);
-      gn.modes.push_back({b->shape[ib], 0, b->strides[ib], cstr[i]});
-    }
+    int ib = find(lb, b->order, lc[i]);
+    if (ia >= 0 && ib >= 0) gb.modes.push_back({a->shape[ia], a->strides[ia], b->strides[ib], cstr[i]});
+    else if (ia >= 0) gm.modes.push_back({a->shape[ia], a->strides[ia], 0, cstr[i]});
+    else gn.modes.push_back({b->shape[ib], 0, b->strides[ib], cstr[i]});
   }
   coalesce(gm, true, false, true);
   coalesce(gn, false, true, true);
   coalesce(gk, true, true, false);
-  const int64_t M = gm.size(), N = gn.size(), K = gk.size();
+  coalesce(gb, true, true, true);
+  const int64_t M = gm.size(), N = gn.size(), K = gk.size(), NB = gb.size();
   int64_t numel_c = 1;
   for (int i = 0; i < nc; ++i) numel_c *= cshape[i];
 
@@ -162,8 +163,58 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
   };
   const size_t eb = tci_elem_bytes(dt);
 
-  // K == 0 (a shared bond of dimension 0): c = 0
-  if (M * N > 0 && K == 0) {
+  if (!gb.modes.empty()) {
+    // ----- batch bonds (labels in a, b and c): one product per batch slice.
+    // Operands are packed to [batch][M][K] and [batch][N][K], the slices run
+    // as one batched launch of the native-arithmetic GEMM (any precision
+    // setting), and the [batch][M][N] result is scattered into c.
+    if (NB * M * N > 0) {
+      auto pack3 = [&](tci_tensor t, const Group& g1, void** out) -> tci_status {
+        int ord = 0;
+        int64_t shp[3 * TCI_MAX_ORDER], str[3 * TCI_MAX_ORDER];
+        const Group* gs[3] = {&gb, &g1, &gk};
+        for (const Group* g : gs)
+          for (auto& m : g->modes) {
+            shp[ord] = m.dim;
+            str[ord] = t == a ? m.sa : m.sb;
+            ++ord;
+          }
+        if (ord > TCI_MAX_ORDER) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "contract: too many non-coalescible modes");
+        TCI_TRY(tci_dev_alloc(ctx, (size_t)(NB * g1.size() * K) * eb, out));
+        scratch.push_back(*out);
+        if (ord == 0) {   // every bond of size 1: a single element
+          TCI_CUDA(ctx, cudaMemcpyAsync(*out, t->data, eb, cudaMemcpyDeviceToDevice, ctx->stream));
+          return TCI_OK;
+        }
+        return tci_launch_permute_copy(ctx, dt, ord, shp, t->data, str, *out);
+      };
+      void *Apk = nullptr, *Bpk = nullptr, *Ck = nullptr;
+      tci_status s = TCI_OK;
+      if (K > 0) {
+        s = pack3(a, gm, &Apk);
+        if (s == TCI_OK) s = pack3(b, gn, &Bpk);
+      }
+      if (s == TCI_OK) s = tci_dev_alloc(ctx, (size_t)(NB * M * N) * eb, &Ck);
+      if (s != TCI_OK) return cleanup(s);
+      scratch.push_back(Ck);
+      if (K == 0) cudaMemsetAsync(Ck, 0, (size_t)(NB * M * N) * eb, ctx->stream);
+      else s = tci_gemm_native_batched(ctx, dt, NB, M, N, K, Apk, M * K, K, 1, Bpk, N * K, K, 1, Ck, M * N, N, 1);
+      if (s != TCI_OK) return cleanup(s);
+      int ord = 0;
+      int64_t shp[3 * TCI_MAX_ORDER], sst[3 * TCI_MAX_ORDER], dst[3 * TCI_MAX_ORDER];
+      const Group* gs[3] = {&gb, &gm, &gn};
+      for (const Group* g : gs)
+        for (auto& m : g->modes) {
+          shp[ord] = m.dim;
+          dst[ord] = m.sc;
+          ++ord;
+        }
+      tci_rowmajor_strides(ord, shp, sst);
+      s = tci_launch_strided_copy(ctx, dt, ord, shp, Ck, sst, cdata, dst);
+      if (s != TCI_OK) return cleanup(s);
+    }
+  } else if (M * N > 0 && K == 0) {
+    // K == 0 (a shared bond of dimension 0): c = 0
     if (reuse && !tci_is_rowmajor(c)) {
       // zero through a strided scatter of a zero buffer
       void* z = nullptr;

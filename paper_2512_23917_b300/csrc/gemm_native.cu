@@ -1,4 +1,5 @@
-// Native-arithmetic strided GEMM (SIMT): C(m,n) = sum_k A(m,k) B(n,k).
+// Native-arithmetic strided GEMM (SIMT): C(m,n) = sum_k A(m,k) B(n,k),
+// optionally batched (blockIdx.z; each operand advances by its batch stride).
 // Operands are read in place through arbitrary (m,k)/(n,k) strides, so a
 // permuted operand needs no materialised transpose.  FP64 on B300 has no
 // fast tensor-core path, so a register-tiled FMA kernel is the FP64 roof.
@@ -29,8 +30,12 @@ constexpr int NT = (BM / TM) * (BN / TN);   // 256 threads
 template <typename T, int ACONT, int BCONT>
 __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64_t K, const T* __restrict__ A,
                                                      int64_t sam, int64_t sak, const T* __restrict__ B, int64_t sbn,
-                                                     int64_t sbk, T* __restrict__ C, int64_t scm, int64_t scn) {
+                                                     int64_t sbk, T* __restrict__ C, int64_t scm, int64_t scn,
+                                                     int64_t sab, int64_t sbb, int64_t scb) {
   __shared__ T As[BK][BM + 1];
+  A += (int64_t)blockIdx.z * sab;
+  B += (int64_t)blockIdx.z * sbb;
+  C += (int64_t)blockIdx.z * scb;
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
@@ -86,33 +91,47 @@ __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64
 }
 
 template <typename T>
-tci_status launch(tci_context ctx, int64_t M, int64_t N, int64_t K, const void* A, int64_t sam, int64_t sak,
-                  const void* B, int64_t sbn, int64_t sbk, void* C, int64_t scm, int64_t scn) {
+tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
+                  int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C, int64_t scb,
+                  int64_t scm, int64_t scn) {
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
   int ac = (sak == 1 || sam != 1) ? 0 : 1;
   int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
-  const T* a = (const T*)A;
-  const T* b = (const T*)B;
-  T* c = (T*)C;
-  if (ac == 0 && bc == 0) k_gemm_strided<T, 0, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn);
-  else if (ac == 0 && bc == 1) k_gemm_strided<T, 0, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn);
-  else if (ac == 1 && bc == 0) k_gemm_strided<T, 1, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn);
-  else k_gemm_strided<T, 1, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn);
-  TCI_CUDA(ctx, cudaGetLastError());
+  for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
+    grid.z = (unsigned)(nbatch - b0 < 65535 ? nbatch - b0 : 65535);
+    const T* a = (const T*)A + b0 * sab;
+    const T* b = (const T*)B + b0 * sbb;
+    T* c = (T*)C + b0 * scb;
+    if (ac == 0 && bc == 0)
+      k_gemm_strided<T, 0, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+    else if (ac == 0 && bc == 1)
+      k_gemm_strided<T, 0, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+    else if (ac == 1 && bc == 0)
+      k_gemm_strided<T, 1, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+    else
+      k_gemm_strided<T, 1, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+    TCI_CUDA(ctx, cudaGetLastError());
+  }
   return TCI_OK;
 }
 
 }  // namespace
 
-tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, int64_t K, const void* A, int64_t sam,
-                           int64_t sak, const void* B, int64_t sbn, int64_t sbk, void* C, int64_t scm, int64_t scn) {
-  if (M == 0 || N == 0) return TCI_OK;
+tci_status tci_gemm_native_batched(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
+                                   const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
+                                   int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn) {
+  if (nbatch <= 0 || M == 0 || N == 0) return TCI_OK;
   switch (dt) {
-    case TCI_F32: return launch<float>(ctx, M, N, K, A, sam, sak, B, sbn, sbk, C, scm, scn);
-    case TCI_F64: return launch<double>(ctx, M, N, K, A, sam, sak, B, sbn, sbk, C, scm, scn);
-    case TCI_C64: return launch<float2>(ctx, M, N, K, A, sam, sak, B, sbn, sbk, C, scm, scn);
-    case TCI_C128: return launch<double2>(ctx, M, N, K, A, sam, sak, B, sbn, sbk, C, scm, scn);
+    case TCI_F32: return launch<float>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
+    case TCI_F64: return launch<double>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
+    case TCI_C64: return launch<float2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
+    case TCI_C128: return launch<double2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
   }
   return tci_fail(ctx, TCI_ERR_DTYPE, "gemm: bad dtype");
+}
+
+tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, int64_t K, const void* A, int64_t sam,
+                           int64_t sak, const void* B, int64_t sbn, int64_t sbk, void* C, int64_t scm, int64_t scn) {
+  return tci_gemm_native_batched(ctx, dt, 1, M, N, K, A, 0, sam, sak, B, 0, sbn, sbk, C, 0, scm, scn);
 }

@@ -1,4 +1,4 @@
-// H_eff plan object shared by the matvec and the Lanczos driver.
+// H_eff plan object shared by the matvec and the Lanczos solver.
 #pragma once
 
 #include "tci_internal.cuh"

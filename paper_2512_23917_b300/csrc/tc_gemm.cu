@@ -258,14 +258,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           cx = x_last ? 0 : cx + 1;
           const uint32_t b1 = u1 & 1;
           if (d1_first) {
-            if (!ptx::mbar_wait_bounded(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+            if (!ptx::mbar_wait_spin(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
               ok = false;
               break;
             }
           }
           if (x_first) {
             xbuf = ux & 1;
-            if (!ptx::mbar_wait_bounded(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+            if (!ptx::mbar_wait_spin(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
               ok = false;
               break;
             }

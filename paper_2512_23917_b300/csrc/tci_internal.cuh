@@ -108,6 +108,10 @@ tci_status tci_launch_scale(tci_context ctx, tci_dtype dt, void* x, int64_t n, d
 tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, int64_t K,
                            const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbn,
                            int64_t sbk, void* C, int64_t scm, int64_t scn);
+// Batched form: nbatch independent products, operand x of batch t at x + t*sxb.
+tci_status tci_gemm_native_batched(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
+                                   const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
+                                   int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn);
 
 // Split-BF16 tensor-core GEMM (tcgen05).  Operands are given as three
 // bfloat16 piece planes each: A pieces [3][M][Kp] and B pieces [3][N][Kp]

@@ -149,7 +149,7 @@ def test_error_codes(ctx, tci):
         tci.contract(ctx, a, "ii", b, "ij", "j")
     assert ei.value.status_name == "TCI_ERR_LABEL"
     with pytest.raises(tci.TciError) as ei:
-        tci.contract(ctx, a, "ij", b, "jk", "ijk")
+        tci.contract(ctx, a, "ij", b, "kl", "il")          # free bonds j, k missing from c
     assert ei.value.status_name == "TCI_ERR_UNSUPPORTED"
     with pytest.raises(tci.TciError) as ei:
         tci.contract(ctx, a, "ij", torch.zeros(4, 4, dtype=torch.float64, device="cuda"), "jk", "ik")
@@ -169,3 +169,36 @@ def test_empty_and_degenerate(ctx, tci):
     b = torch.ones(0, 3, dtype=torch.float64, device="cuda")
     out = tci.contract(ctx, a, "ik", b, "kj", "ij")
     assert torch.all(out == 0) and tuple(out.shape) == (4, 3)
+
+
+BATCH_PATTERNS = [
+    ("ij", "jk", "ijk", {"i": 33, "j": 17, "k": 29}),                    # batch bond j
+    ("bij", "bjk", "bik", {"b": 70, "i": 31, "j": 45, "k": 19}),          # batched matrix product
+    ("ibj", "jkb", "kbi", {"i": 9, "b": 130, "j": 65, "k": 2}),           # batch in the middle, permuted output
+    ("ab", "ab", "ab", {"a": 300, "b": 257}),                             # elementwise product
+    ("abc", "cbd", "bad", {"a": 20, "b": 3, "c": 40, "d": 26}),           # one batch, one summed
+    ("aij", "ajk", "aik", {"a": 70000, "i": 2, "j": 3, "k": 2}),          # > 65535 batch slices
+    ("ij", "ij", "i", {"i": 5, "j": 0}),                                  # summed bond of size 0: zeros
+]
+
+
+@pytest.mark.parametrize("la,lb,lc,dims", BATCH_PATTERNS)
+@pytest.mark.parametrize("dtype", [np.float64, np.complex128, np.float32])
+@pytest.mark.parametrize("prec", ["native", "split_bf16"])
+def test_contract_batch_bonds_match_oracle(ctx, tci, la, lb, lc, dims, dtype, prec):
+    """Labels in a, b and c: one product per batch slice (native arithmetic in every precision)."""
+    ctx.set_precision(prec)
+    try:
+        A = random_tensor([dims[c] for c in la], 3, dtype)
+        B = random_tensor([dims[c] for c in lb], 4, dtype)
+        wide = np.complex128 if np.iscomplexobj(A) else np.float64
+        ref = o_contract(A.astype(wide), la, B.astype(wide), lb, lc)
+        out = tci.contract(ctx, to_dev(A), la, to_dev(B), lb, lc).cpu().numpy()
+    finally:
+        ctx.set_precision("native")
+    assert out.shape == ref.shape
+    if ref.size == 0 or not np.any(ref):
+        assert np.all(out == 0)
+        return
+    tol = 1e-13 if dtype in (np.float64, np.complex128) else 2e-6
+    assert rel_frob_err(out, ref) < tol

@@ -78,9 +78,24 @@ def test_label_errors():
     with pytest.raises(LabelError):
         contract(A, "ij", random_tensor([4, 4], 3), "jk", "ik")   # dim mismatch
     with pytest.raises(UnsupportedLabels):
-        contract(A, "ij", B, "jk", "ijk")          # batch label j kept in output
-    with pytest.raises(UnsupportedLabels):
         contract(A, "ij", B, "kl", "il")           # free bonds j, k dropped
+    with pytest.raises(UnsupportedLabels):
+        contract(A, "ij", B, "jk", "k")            # free bond i of a missing from c
+
+
+@pytest.mark.parametrize("la,lb,lc,shapes", [
+    ("ij", "jk", "ijk", ([3, 4], [4, 5])),                   # batch bond j (Hadamard along j, outer in i, k)
+    ("bij", "bjk", "bik", ([4, 3, 5], [4, 5, 2])),           # batched matrix product
+    ("ibj", "jkb", "kbi", ([3, 4, 2], [2, 5, 4])),           # batch bond in the middle, permuted output
+    ("ab", "ab", "ab", ([3, 4], [3, 4])),                    # elementwise product (all bonds batch)
+    ("abc", "cbd", "bad", ([2, 3, 4], [4, 3, 5])),           # one batch, one summed, permuted
+])
+def test_batch_bonds_match_bruteforce_and_einsum(la, lb, lc, shapes):
+    A = random_tensor(shapes[0], 11) + 1j * random_tensor(shapes[0], 12)
+    B = random_tensor(shapes[1], 13)
+    ref = contract_bruteforce(A, la, B, lb, lc)
+    np.testing.assert_allclose(contract(A, la, B, lb, lc), ref, rtol=1e-13, atol=1e-13)
+    np.testing.assert_allclose(np.einsum(f"{la},{lb}->{lc}", A, B), ref, rtol=1e-13, atol=1e-13)
 
 
 def test_norm_and_close_examples():
