@@ -126,6 +126,23 @@ def dist_info():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def aggregate_replicas(ms_local: float, units_local: float, device=None):
+    """(slowest rank's time, summed work of all ranks) over the initialised process group.
+
+    The path runs as independent replicas (no collective on the data path); the
+    whole-job rate is the work of all ranks over the slowest rank's time.
+    """
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local, units_local
+    t_ms = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    t_units = torch.tensor([units_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t_ms, op=dist.ReduceOp.MAX)
+    dist.all_reduce(t_units, op=dist.ReduceOp.SUM)
+    return float(t_ms.item()), float(t_units.item())
+
+
 # ---------------------------------------------------------------------------- reference (CPU oracle)
 def run_reference(args):
     rank, world, _ = dist_info()
@@ -320,14 +337,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    ms_total = ev0.elapsed_time(ev1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_total = float(tt.item())
+    ms_total, flops_all = aggregate_replicas(ev0.elapsed_time(ev1), args.steps * LANCZOS_STEPS * F, dev)
     ms_step = ms_total / args.steps
-    value = world * LANCZOS_STEPS * F / (ms_step * 1e-3) / 1e9
+    value = flops_all / (ms_total * 1e-3) / 1e9
 
     # ---- the same solve with double-float (FP32 pair) vector arithmetic, an opt-in variant
     plan.set_lanczos_arith("df32")

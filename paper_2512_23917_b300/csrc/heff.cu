@@ -110,18 +110,19 @@ __device__ __forceinline__ void split3(float x, __nv_bfloat16& h, __nv_bfloat16&
   l = __float2bfloat16_rn(r1 - __bfloat162float(m));
 }
 
+// Only a' in [a_begin, a_end) is processed (a row range of psi).
 template <int NA>
 __global__ void __launch_bounds__(256) k_ww_split(const WWArgs<float> args, const float* __restrict__ Ut, int64_t chiL,
                                                   int64_t chiR, __nv_bfloat16* __restrict__ V, int64_t ldv,
-                                                  int64_t plane) {
+                                                  int64_t plane, int64_t a_begin, int64_t a_end) {
   constexpr int Dw = HEFF_DW, D2 = 4;
   static_assert(NA == 2 || NA == 4, "NA");
-  const int64_t nq = (chiL + NA - 1) / NA;
+  const int64_t nq = (a_end - a_begin + NA - 1) / NA;
   const int64_t idx = (int64_t)blockIdx.x * 256 + threadIdx.x;
   const int64_t q = idx % nq, b = idx / nq;
   if (b >= chiR) return;
-  const int64_t a0 = q * NA;
-  const bool full = a0 + NA <= chiL;
+  const int64_t a0 = a_begin + q * NA;
+  const bool full = a0 + NA <= a_end;
   const int64_t ldu = 4 * chiL;
   float in[Dw][NA * D2];   // [wr][(a'-a0)*4 + t]
 #pragma unroll
@@ -138,10 +139,10 @@ __global__ void __launch_bounds__(256) k_ww_split(const WWArgs<float> args, cons
       }
     } else {
 #pragma unroll
-      for (int j = 0; j < NA * D2; ++j) in[wr][j] = a0 + j / D2 < chiL ? row[j] : 0.f;
+      for (int j = 0; j < NA * D2; ++j) in[wr][j] = a0 + j / D2 < a_end ? row[j] : 0.f;
     }
   }
-  const bool vec = full && (chiL % NA == 0);
+  const bool vec = full && (chiL % NA == 0) && (a_begin % NA == 0);
 #pragma unroll
   for (int s = 0; s < D2; ++s) {
 #pragma unroll
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(256) k_ww_split(const WWArgs<float> args, cons
       } else {
 #pragma unroll
         for (int j = 0; j < NA; ++j)
-          if (a0 + j < chiL) {
+          if (a0 + j < a_end) {
             V[off + j] = h[j];
             V[plane + off + j] = m[j];
             V[2 * plane + off + j] = l[j];
@@ -204,14 +205,18 @@ tci_status launch_ww_f64(tci_context ctx, const WWArgs<double>& args, const doub
 // na: a' per thread (2 or 4; 4 halves the store instructions, 2 doubles the
 // resident warps), chosen by the autotuner.
 tci_status launch_ww_split(tci_context ctx, const WWArgs<float>& args, const float* Ut, int64_t chiL, int64_t chiR,
-                           void* V, int64_t ldv, int64_t plane, int na) {
-  const int64_t threads = (chiL + na - 1) / na * chiR;
+                           void* V, int64_t ldv, int64_t plane, int na, int64_t a_begin = 0, int64_t a_end = -1) {
+  if (a_end < 0) a_end = chiL;
+  if (a_begin < 0 || a_end > chiL || a_begin >= a_end) return TCI_OK;
+  const int64_t threads = (a_end - a_begin + na - 1) / na * chiR;
   const int64_t blocks = (threads + 255) / 256;
   if (blocks > 0x7fffffff) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: too large");
   if (na == 2)
-    k_ww_split<2><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane);
+    k_ww_split<2><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane,
+                                                             a_begin, a_end);
   else
-    k_ww_split<4><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane);
+    k_ww_split<4><<<(unsigned)blocks, 256, 0, ctx->stream>>>(args, Ut, chiL, chiR, (__nv_bfloat16*)V, ldv, plane,
+                                                             a_begin, a_end);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
@@ -354,6 +359,12 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
                   p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
   for (void* b : bufs) tci_dev_free(b);
+  for (int i = 0; i < 8; ++i) {
+    if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
+    if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
+  }
+  if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
+  if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
   p->magic = 0;
   delete p;
   *pp = nullptr;
@@ -458,6 +469,65 @@ extern "C" tci_status tci_heff_apply(tci_heff_plan p, tci_tensor psi, tci_tensor
   return tci_heff_apply_raw(p, (const double*)psi->data, (double*)out->data, false);
 }
 
+// Host-buffer matvec on a split-BF16 plan with the copies overlapped: psi
+// is copied in chunks of a' rows on one copy stream while the compute stream
+// splits each arrived chunk, runs GEMM1 on its rows and W.W on its a' range;
+// GEMM2 then runs in chunks of output rows a, each copied back on a second
+// copy stream as soon as it is done.
+static tci_status apply_host_pipelined(tci_heff_plan p, const double* psi_host, double* out_host) {
+  tci_context ctx = p->ctx;
+  const int64_t chiL = p->chiL, chiR = p->chiR, Dw = HEFF_DW;
+  if (!p->s_h2d) {
+    TCI_CUDA(ctx, cudaStreamCreateWithFlags(&p->s_h2d, cudaStreamNonBlocking));
+    TCI_CUDA(ctx, cudaStreamCreateWithFlags(&p->s_d2h, cudaStreamNonBlocking));
+    for (int i = 0; i < 8; ++i) {
+      TCI_CUDA(ctx, cudaEventCreateWithFlags(&p->ev_in[i], cudaEventDisableTiming));
+      TCI_CUDA(ctx, cudaEventCreateWithFlags(&p->ev_out[i], cudaEventDisableTiming));
+    }
+  }
+  const int nch = chiL >= 256 ? 4 : 1;
+  int64_t bnd[5];
+  for (int c = 0; c <= nch; ++c) bnd[c] = c == nch ? chiL : (c * chiL / nch) / 8 * 8;
+  WWArgs<float> args;
+  for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+  // psi rows (a', t1, t2) of a' in [a0, a1) in, as they arrive
+  for (int c = 0; c < nch; ++c) {
+    const int64_t r0 = 4 * bnd[c] * chiR, n = 4 * (bnd[c + 1] - bnd[c]) * chiR;
+    if (n == 0) continue;
+    TCI_CUDA(ctx, cudaMemcpyAsync(p->d_stage_in + r0, psi_host + r0, n * sizeof(double), cudaMemcpyHostToDevice,
+                                  p->s_h2d));
+    TCI_CUDA(ctx, cudaEventRecord(p->ev_in[c], p->s_h2d));
+  }
+  __nv_bfloat16* psip = (__nv_bfloat16*)p->psip;
+  for (int c = 0; c < nch; ++c) {
+    const int64_t a0 = bnd[c], a1 = bnd[c + 1];
+    if (a1 == a0) continue;
+    TCI_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, p->ev_in[c], 0));
+    TCI_TRY(tci_launch_split3(ctx, TCI_F64, p->d_stage_in + 4 * a0 * chiR, 4 * (a1 - a0), chiR, chiR, 1,
+                              psip + 4 * a0 * p->Kp1, p->Kp1, 4 * chiL));
+    TCI_TRY(tci_gemm_split_bf16_sub(ctx, 4 * (a1 - a0), chiR * Dw, p->Kp1, psip + 4 * a0 * p->Kp1, 4 * chiL, p->Rp,
+                                    chiR * Dw, (float*)p->U + 4 * a0, 1, 1, chiL * 4, p->products, p->chunk_k,
+                                    p->xchunk_k, p->raster));
+    TCI_TRY(launch_ww_split(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2, p->ww_na, a0,
+                            a1));
+  }
+  // output rows a in [a0, a1) out, as they are done
+  const __nv_bfloat16* Lp = (const __nv_bfloat16*)p->Lp;
+  for (int c = 0; c < nch; ++c) {
+    const int64_t a0 = bnd[c], a1 = bnd[c + 1];
+    if (a1 == a0) continue;
+    TCI_TRY(tci_gemm_split_bf16_sub(ctx, a1 - a0, 4 * chiR, p->Kp2, Lp + a0 * p->Kp2, chiL, p->Vp, 4 * chiR,
+                                    p->d_stage_out + a0 * 4 * chiR, 0, 4 * chiR, 1, p->products, p->chunk_k,
+                                    p->xchunk_k, p->raster));
+    TCI_CUDA(ctx, cudaEventRecord(p->ev_out[c], ctx->stream));
+    TCI_CUDA(ctx, cudaStreamWaitEvent(p->s_d2h, p->ev_out[c], 0));
+    TCI_CUDA(ctx, cudaMemcpyAsync(out_host + a0 * 4 * chiR, p->d_stage_out + a0 * 4 * chiR,
+                                  (a1 - a0) * 4 * chiR * sizeof(double), cudaMemcpyDeviceToHost, p->s_d2h));
+  }
+  TCI_CUDA(ctx, cudaStreamSynchronize(p->s_d2h));
+  return tci_synchronize(ctx);
+}
+
 extern "C" tci_status tci_heff_apply_host(tci_heff_plan p, const double* psi_host, double* out_host) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply_host: invalid plan");
   tci_context ctx = p->ctx;
@@ -469,6 +539,7 @@ extern "C" tci_status tci_heff_apply_host(tci_heff_plan p, const double* psi_hos
     TCI_TRY(tci_dev_alloc(ctx, bytes, (void**)&p->d_stage_in));
     TCI_TRY(tci_dev_alloc(ctx, bytes, (void**)&p->d_stage_out));
   }
+  if (p->prec != TCI_PREC_NATIVE) return apply_host_pipelined(p, psi_host, out_host);
   TCI_CUDA(ctx, cudaMemcpyAsync(p->d_stage_in, psi_host, bytes, cudaMemcpyHostToDevice, ctx->stream));
   TCI_TRY(tci_heff_apply_raw(p, p->d_stage_in, p->d_stage_out, false));
   TCI_CUDA(ctx, cudaMemcpyAsync(out_host, p->d_stage_out, bytes, cudaMemcpyDeviceToHost, ctx->stream));

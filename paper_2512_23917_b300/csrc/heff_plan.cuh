@@ -32,9 +32,11 @@ struct tci_heff_plan_s {
   void* Rp = nullptr;      // [3][chiR*Dw][Kp1]
   void* psip = nullptr;    // [3][chiL*4][Kp1]
   void* Vp = nullptr;      // [3][4*chiR][Kp2]
-  // host-buffer staging
+  // host-buffer staging (copies overlapped with the compute on two copy streams)
   double* d_stage_in = nullptr;
   double* d_stage_out = nullptr;
+  cudaStream_t s_h2d = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_in[8] = {}, ev_out[8] = {};
   // Lanczos workspace
   double* lz_V = nullptr;     // basis, capacity lz_cap vectors
   int lz_cap = 0;

@@ -445,14 +445,17 @@ PFN_encodeTiled_t get_encode_fn() {
 
 }  // namespace
 
-// 3-D map over bf16 piece planes [3][rows][Kp] with a {TBK, box_rows, 3} box.
+// 3-D map over bf16 piece planes [3][rows][Kp] with a {TBK, box_rows, 3} box;
+// the planes are plane_rows * Kp elements apart (plane_rows >= rows; a row
+// range of a larger piece matrix passes its own base and the full count).
 tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* base, int64_t rows, int64_t Kp,
-                              int box_rows) {
+                              int box_rows, int64_t plane_rows) {
   PFN_encodeTiled_t enc = get_encode_fn();
   if (!enc) return tci_fail(ctx, TCI_ERR_CUDA, "cuTensorMapEncodeTiled entry point unavailable");
   if (Kp % 8 != 0 || ((uintptr_t)base & 15)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "piece map: misaligned operand");
+  if (plane_rows < rows) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "piece map: plane stride below the row count");
   cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, 3};
-  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(rows * Kp * 2)};
+  cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)(plane_rows * Kp * 2)};
   cuuint32_t box[3] = {(cuuint32_t)TBK, (cuuint32_t)box_rows, 3};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
@@ -463,13 +466,14 @@ tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* bas
 }
 
 static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int64_t N, int64_t Kp, const void* Ap,
-                               const void* Bp, void* C, int out_mode, int64_t scm, int64_t scn) {
+                               const void* Bp, void* C, int out_mode, int64_t scm, int64_t scn,
+                               int64_t a_plane_rows = 0, int64_t b_plane_rows = 0) {
   if (M <= 0 || N <= 0 || Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty problem");
   if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
     return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
   memset(pr, 0, sizeof(*pr));
-  TCI_TRY(tci_make_piece_map(ctx, &pr->tmA, Ap, M, Kp, TBM));
-  TCI_TRY(tci_make_piece_map(ctx, &pr->tmB, Bp, N, Kp, TBN));
+  TCI_TRY(tci_make_piece_map(ctx, &pr->tmA, Ap, M, Kp, TBM, a_plane_rows > 0 ? a_plane_rows : M));
+  TCI_TRY(tci_make_piece_map(ctx, &pr->tmB, Bp, N, Kp, TBN, b_plane_rows > 0 ? b_plane_rows : N));
   pr->C = C;
   pr->M = M;
   pr->N = N;
@@ -504,9 +508,16 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
 tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
                                void* C, int out_mode, int64_t scm, int64_t scn, int products, int chunk_k,
                                int xchunk_k, int raster) {
+  return tci_gemm_split_bf16_sub(ctx, M, N, Kp, Ap, M, Bp, N, C, out_mode, scm, scn, products, chunk_k, xchunk_k,
+                                 raster);
+}
+
+tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap,
+                                   int64_t a_plane_rows, const void* Bp, int64_t b_plane_rows, void* C, int out_mode,
+                                   int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k, int raster) {
   if (M <= 0 || N <= 0) return TCI_OK;
   GemmProblem pr;
-  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_mode, scm, scn));
+  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_mode, scm, scn, a_plane_rows, b_plane_rows));
   GemmParams gp;
   memset(&gp, 0, sizeof gp);
   TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
@@ -607,8 +618,7 @@ __device__ __forceinline__ void split3_f32(float xf, __nv_bfloat16& h, __nv_bflo
 
 template <typename T>
 __global__ void k_split3(const T* __restrict__ src, int64_t rows, int64_t K, int64_t sr, int64_t sk,
-                         __nv_bfloat16* __restrict__ out, int64_t Kp) {
-  const int64_t plane = rows * Kp;
+                         __nv_bfloat16* __restrict__ out, int64_t Kp, int64_t plane) {
   const int64_t total = rows * Kp;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / Kp, k = i - r * Kp;
@@ -635,15 +645,16 @@ __global__ void k_narrow(int64_t M, int64_t N, const double* __restrict__ src, f
 }  // namespace
 
 tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int64_t rows, int64_t K, int64_t sr,
-                             int64_t sk, void* out, int64_t Kp) {
+                             int64_t sk, void* out, int64_t Kp, int64_t plane_rows) {
   int64_t total = rows * Kp;
   if (total == 0) return TCI_OK;
+  const int64_t plane = (plane_rows > 0 ? plane_rows : rows) * Kp;
   int64_t blocks = (total + 255) / 256;
   if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
   if (dt == TCI_F64)
-    k_split3<double><<<(int)blocks, 256, 0, ctx->stream>>>((const double*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp);
+    k_split3<double><<<(int)blocks, 256, 0, ctx->stream>>>((const double*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp, plane);
   else if (dt == TCI_F32)
-    k_split3<float><<<(int)blocks, 256, 0, ctx->stream>>>((const float*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp);
+    k_split3<float><<<(int)blocks, 256, 0, ctx->stream>>>((const float*)src, rows, K, sr, sk, (__nv_bfloat16*)out, Kp, plane);
   else
     return tci_fail(ctx, TCI_ERR_DTYPE, "split3: real dtype required");
   TCI_CUDA(ctx, cudaGetLastError());

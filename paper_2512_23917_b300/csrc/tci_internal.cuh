@@ -125,6 +125,13 @@ tci_status tci_gemm_split_bf16(tci_context ctx, int64_t M, int64_t N, int64_t Kp
                                const void* Apieces, const void* Bpieces, void* C, int out_mode,
                                int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k,
                                int raster);
+// Same on row ranges of larger piece matrices: the A / B planes are
+// a_plane_rows*Kp / b_plane_rows*Kp elements apart (Apieces, Bpieces point at
+// the first row of the range in plane 0).
+tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Apieces,
+                                   int64_t a_plane_rows, const void* Bpieces, int64_t b_plane_rows, void* C,
+                                   int out_mode, int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k,
+                                   int raster);
 
 // Configuration of the split GEMM chosen by the autotuner (or defaults).
 struct tci_gemm_cfg {
@@ -173,8 +180,9 @@ tci_status tci_graph_capture(tci_context ctx, tci_graph* g, tci_status (*body)(v
 void tci_graph_destroy(tci_graph* g);
 
 // K0: split a strided FP64/FP32 operand into three bfloat16 planes, packed
-// K-major: out[p][r][k] for r < rows, k < Kp (zero for k >= K).  Element
-// (r, k) of the source is at src[r*sr + k*sk] (with an optional 2-level row
-// index r = r1*rows0 + r0 -> offset r1*sr1 + r0*sr0 when rows0 > 0).
+// K-major: out[p*plane + r*Kp + k] for r < rows, k < Kp (zero for k >= K),
+// plane = plane_rows*Kp (plane_rows = 0: rows; a row range of a larger piece
+// matrix passes its own out and the full row count).  Element (r, k) of the
+// source is at src[r*sr + k*sk].
 tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int64_t rows,
-                             int64_t K, int64_t sr, int64_t sk, void* out, int64_t Kp);
+                             int64_t K, int64_t sr, int64_t sk, void* out, int64_t Kp, int64_t plane_rows = 0);

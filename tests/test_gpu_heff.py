@@ -81,12 +81,18 @@ def test_heff_split_bf16_chi2048_full(ctx, tci):
     assert err < 1e-6, err
 
 
-def test_apply_host_matches_device(ctx, tci):
-    psi, L, R, W = dense_heff_inputs(64, seed=3)
-    out, plan = run_heff(tci, ctx, L, W, R, psi, "split_bf16")
-    host_out = np.empty_like(psi)
+@pytest.mark.parametrize("chi,chi_r,prec", [(64, 64, "split_bf16"), (300, 257, "split_bf16"), (264, 40, "split_bf16"),
+                                            (40, 33, "native")])
+def test_apply_host_matches_device(ctx, tci, chi, chi_r, prec):
+    """Host-buffer matvec (copies overlapped with compute in chunks of rows for chi >= 256) == device matvec."""
+    psi, L, R, W = dense_heff_inputs(chi, seed=3, chi_r=chi_r)
+    out, plan = run_heff(tci, ctx, L, W, R, psi, prec)
+    host_out = np.full_like(psi, np.nan)
     plan.apply_host(np.ascontiguousarray(psi), host_out)
     np.testing.assert_array_equal(host_out, out)
+    host_out2 = np.full_like(psi, np.nan)
+    plan.apply_host(np.ascontiguousarray(psi), host_out2)      # repeated call reuses the staging buffers
+    np.testing.assert_array_equal(host_out2, out)
 
 
 @pytest.mark.parametrize("ww_na", [2, 4])
