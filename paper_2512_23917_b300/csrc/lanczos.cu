@@ -31,6 +31,8 @@
 // of the block partials.
 #include <cuda_bf16.h>
 
+#include <map>
+#include <mutex>
 #include <type_traits>
 
 #include "heff_plan.cuh"
@@ -38,7 +40,7 @@
 namespace {
 
 constexpr int NT = 256;
-constexpr int NBMAX = 1184;      // partial-sum slots per vector (>= any kernel's grid)
+constexpr int NBMAX = 1184;      // partial-sum slots per vector (>= any pass's grid: one wave, <= 8 x 148)
 constexpr int MAXM = 256;
 constexpr int GMAX = 20;         // basis vectors per fused pass
 // device scalar layout (doubles)
@@ -88,7 +90,6 @@ __device__ __forceinline__ void df_prod(float2 x, float2 y, float& p, float& t) 
 // ---------------------------------------------------------------- arithmetic policies
 struct ArithF64 {
   using V = double;
-  static constexpr int kBlocks = 592;   // FP64-pipe bound: 4 blocks per SM, fewer FP64 reduction adds
   struct Acc { double s; };
   struct Coef { double c; };
   struct Sub { double w, s; };
@@ -109,7 +110,6 @@ struct ArithF64 {
 
 struct ArithDF {
   using V = float2;
-  static constexpr int kBlocks = 1184;  // HBM bound: 8 blocks per SM
   struct Acc { float h, l; };
   struct Coef { float2 c; };
   struct Sub { float h, l; };
@@ -535,33 +535,68 @@ __global__ void k_init_scal(double* scal) {
 // ---------------------------------------------------------------- host side
 namespace {
 
+// Grid of a vector pass: one full wave, i.e. the SM count times the blocks
+// of NT threads that fit on one SM (from the kernel's registers and shared
+// memory), capped at NBMAX partial-sum slots.  Fixed per kernel and device,
+// so the reductions stay deterministic.
+int wave_grid(tci_context ctx, const void* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair(kernel, ctx->device);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, NT, 0) != cudaSuccess || occ < 1) occ = 1;
+  int g = occ * ctx->num_sms;
+  if (g > NBMAX) g = NBMAX;
+  cache[key] = g;
+  return g;
+}
+
+template <class A, int G>
+int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
+                  int64_t n, double* part, const double* ctrl) {
+  const int grid = wave_grid(ctx, (const void*)k_dots<A, G>);
+  k_dots<A, G><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+  return grid;
+}
+
 template <class A>
-void dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                 int64_t n, double* part, const double* ctrl) {
-  if (nv <= 8) k_dots<A, 8><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
-  else if (nv <= 16) k_dots<A, 16><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
-  else k_dots<A, GMAX><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+int dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
+                int64_t n, double* part, const double* ctrl) {
+  if (nv <= 8) return dots_launch_g<A, 8>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
+  if (nv <= 16) return dots_launch_g<A, 16>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
+  return dots_launch_g<A, GMAX>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
 }
 
 // out[0..nv) = <V_{v0+v}, w>
 template <class A>
 tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
                     int64_t n, double* part, double* out, const double* ctrl) {
-  for (int g0 = 0; g0 < nv; g0 += GMAX) dots_launch<A>(ctx, V, ldv, v0 + g0, nv - g0 < GMAX ? nv - g0 : GMAX, w, n, part, ctrl);
-  k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, A::kBlocks, out, ctrl);
+  for (int g0 = 0; g0 < nv; g0 += GMAX) {
+    const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
+    const int grid = dots_launch<A>(ctx, V, ldv, v0 + g0, g, w, n, part, ctrl);
+    k_reduce_parts<<<g, 256, 0, ctx->stream>>>(part + (int64_t)(v0 + g0) * NBMAX, g, grid, out + g0, ctrl);
+  }
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
 
+template <class A, int G, bool DOTS, bool SUMSQ>
+int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
+                    typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
+  const int grid = wave_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ>);
+  k_update<A, G, DOTS, SUMSQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+  return grid;
+}
+
 template <class A, bool DOTS, bool SUMSQ>
-void update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
-                   typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
-  if (nv <= 8)
-    k_update<A, 8, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-  else if (nv <= 16)
-    k_update<A, 16, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-  else
-    k_update<A, GMAX, DOTS, SUMSQ><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
+                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
+  if (nv <= 8) return update_launch_g<A, 8, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+  if (nv <= 16) return update_launch_g<A, 16, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+  return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
 }
 
 // w -= sum_{v0 <= v < v0+nv} coef[v] V_v; then dots_out[0..nv) = <V_v, w>
@@ -574,20 +609,27 @@ tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int 
                       const double* ctrl) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
   if (dots_out && sumsq_out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (dots and sumsq in one pass)");
+  int sq_grid = 0;
   if (nv <= GMAX) {
-    if (dots_out) update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    else if (sumsq_out) update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    else update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, A::kBlocks, dots_out, ctrl);
+    if (dots_out) {
+      const int grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+      k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
+    } else if (sumsq_out) {
+      sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    } else {
+      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+    }
   } else {
     for (int g0 = 0; g0 < nv; g0 += GMAX) {
       const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
-      if (g0 + g == nv && sumsq_out) update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
-      else update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+      if (g0 + g == nv && sumsq_out)
+        sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+      else
+        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
     }
     if (dots_out) TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl));
   }
-  if (sumsq_out) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, A::kBlocks, sumsq_out, ctrl);
+  if (sumsq_out) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, sq_grid, sumsq_out, ctrl);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
@@ -643,7 +685,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       TCI_TRY(tci_heff_apply_raw(p, (const double*)vj, w, false, 0));
     } else {
       TCI_TRY(tci_heff_apply_raw(p, p->lz_x64, p->lz_o64, false, 0));
-      k_from_f64<A><<<A::kBlocks, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
+      k_from_f64<A><<<NBMAX, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
     }
     if (reorth) {
       TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl));
@@ -661,7 +703,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     TCI_CUDA(ctx, cudaGetLastError());
   }
   k_tridiag_lowest<<<1, NT, 0, ctx->stream>>>(S);
-  if (x) k_ritz<A><<<A::kBlocks, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
+  if (x) k_ritz<A><<<NBMAX, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
