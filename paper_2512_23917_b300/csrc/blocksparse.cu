@@ -121,6 +121,8 @@ struct WWTask {
   int64_t na, nb;              // sector dims of a' (ja) and b (ib)
 };
 
+static_assert(sizeof(WWTask) % sizeof(int64_t) == 0, "WWTask is copied as int64 words");
+
 struct WWCoef {
   float ww[BS_DW * 4 * BS_DW * 4];   // [wl][s][wr][t]
 };
@@ -139,8 +141,14 @@ constexpr int kWA = 32, kWB = 8;
 __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ tasks, const WWTile* __restrict__ tiles,
                                                      const WWCoef coef, __nv_bfloat16* __restrict__ V) {
   __shared__ float Us[4 * BS_DW][kWA][kWB + 1];
+  __shared__ WWTask T;   // the task's pointers and strides, read once per block
   const WWTile tl = tiles[blockIdx.x];
-  const WWTask& T = tasks[tl.task];
+  {
+    const int64_t* src = (const int64_t*)&tasks[tl.task];
+    int64_t* dst = (int64_t*)&T;
+    for (int i = threadIdx.x; i < (int)(sizeof(WWTask) / sizeof(int64_t)); i += blockDim.x) dst[i] = src[i];
+  }
+  __syncthreads();
   for (int idx = threadIdx.x; idx < 4 * BS_DW * kWA * kWB; idx += kWA * kWB) {
     const int bl = idx % kWB, al = (idx / kWB) % kWA, q = idx / (kWB * kWA);
     const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
