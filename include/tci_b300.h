@@ -118,6 +118,17 @@ tci_status tci_context_get_precision(tci_context ctx, tci_precision* p);
  * Errors: INVALID_ARG unless 32 | chunk_k and chunk_k | xchunk_k. */
 tci_status tci_context_set_split_chunks(tci_context ctx, int chunk_k, int xchunk_k);
 
+/* Limit of each bounded device wait of the tensor-core kernels (extension;
+ * the paper has no counterpart), in nanoseconds; 0 restores the default of
+ * 2 s.  A wait that expires makes the kernel record a status word, let its
+ * in-flight copies and MMAs land, free its tensor memory and return; the
+ * next synchronising call reports TCI_ERR_TIMEOUT (once) and the context
+ * stays usable.  Tiny limits exist to exercise that path in tests.  Plans
+ * that replay a captured CUDA graph (block-sparse, TEBD) keep the limit in
+ * force when their graph was captured.
+ * Errors: INVALID_CONTEXT. */
+tci_status tci_context_set_wait_limit(tci_context ctx, uint64_t limit_ns);
+
 /* Block the host until all work queued on the context's stream finished;
  * maps a sticky device error or a kernel timeout status to CUDA/TIMEOUT. */
 tci_status tci_synchronize(tci_context ctx);

@@ -100,6 +100,7 @@ SIGNATURES = [
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
+    ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
     ("tci_eye", C.c_int, [_p, C.c_int, C.c_int64, C.POINTER(_p)]),
     ("tci_fill", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.POINTER(_p)]),
     ("tci_cplx_conj", C.c_int, [_p, _p]),
@@ -167,6 +168,10 @@ class Context:
 
     def set_split_chunks(self, chunk_k: int, xchunk_k: int):
         _check(lib.tci_context_set_split_chunks(self.handle, int(chunk_k), int(xchunk_k)), self.handle)
+
+    def set_wait_limit(self, limit_ns: int):
+        """Limit of the bounded device waits (ns; 0 = default 2 s)."""
+        _check(lib.tci_context_set_wait_limit(self.handle, int(limit_ns)), self.handle)
 
     def set_stream(self, stream: int):
         _check(lib.tci_context_set_stream(self.handle, _p(int(stream))), self.handle)

@@ -231,6 +231,12 @@ extern "C" tci_status tci_context_set_split_chunks(tci_context ctx, int chunk_k,
   return TCI_OK;
 }
 
+extern "C" tci_status tci_context_set_wait_limit(tci_context ctx, uint64_t limit_ns) {
+  TCI_CHECK_CTX(ctx);
+  ctx->wait_limit_ns = limit_ns;
+  return TCI_OK;
+}
+
 extern "C" tci_status tci_context_get_precision(tci_context ctx, tci_precision* p) {
   TCI_CHECK_CTX(ctx);
   if (!p) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "get_precision: NULL output");

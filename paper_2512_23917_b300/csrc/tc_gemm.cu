@@ -29,8 +29,9 @@
 //   warp 1      : TMEM allocator + MMA issuer (one lane)
 //   warps 2..17 : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
 //                 columns 32*((w-2)/4)..+31
-// Every wait is bounded (2 s); on expiry the kernel records a status word,
-// lets its in-flight copies and MMAs land, frees TMEM and returns.
+// Every wait is bounded (2 s, or the context's wait limit); on expiry the
+// kernel records a status word, lets its in-flight copies and MMAs land
+// (those final drains always allow 2 s), frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -79,6 +80,7 @@ struct GemmParams {
   int kb_d1, kb_x;            // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
   int products;
   int* status;
+  uint64_t wait_ns;           // limit of every wait on work in flight (the final drains keep WAIT_LIMIT_NS)
 };
 
 // Local tile index -> (m-block, n-block).  With raster G > 0, consecutive
@@ -124,9 +126,12 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // rounding it to 8 bits costs ~2^-33 |rh| per drain, far below the target,
 // and halves its register footprint.
 __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, uint64_t* empty_bar, uint32_t parity,
-                                           volatile int* abort_flag, int lane, float (&rh)[COLS_PER_WARP],
-                                           __nv_bfloat162 (&rl)[COLS_PER_WARP / 2]) {
-  if (!ptx::mbar_wait_bounded(ptx::smem_u32(full_bar), parity, abort_flag, WAIT_LIMIT_NS)) return false;
+                                           volatile int* abort_flag, uint64_t wait_ns, int lane,
+                                           float (&rh)[COLS_PER_WARP], __nv_bfloat162 (&rl)[COLS_PER_WARP / 2]) {
+  // the lanes agree before the warp-collective tensor-memory loads: a wait
+  // that expired in any lane aborts the whole warp
+  const bool got = ptx::mbar_wait_bounded(ptx::smem_u32(full_bar), parity, abort_flag, wait_ns);
+  if (!__all_sync(0xffffffffu, got)) return false;
   ptx::tc_fence_after();
 #pragma unroll
   for (int g = 0; g < COLS_PER_WARP / 16; ++g) {
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         tile_coords(lt, pr->num_m, pr->num_n, p.raster, mb, nb);
         const int nkb = pr->num_kb;
         for (int kb = 0; kb < nkb; ++kb) {
-          if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, WAIT_LIMIT_NS)) break;
+          if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, p.wait_ns)) break;
           const uint32_t fb = ptx::smem_u32(&full[stage]);
           ptx::mbar_arrive_expect_tx(fb, STAGE_BYTES);
           uint8_t* sa = smem + stage * STAGE_BYTES;
@@ -258,19 +263,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           cx = x_last ? 0 : cx + 1;
           const uint32_t b1 = u1 & 1;
           if (d1_first) {
-            if (!ptx::mbar_wait_spin(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+            if (!ptx::mbar_wait_spin(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, p.wait_ns)) {
               ok = false;
               break;
             }
           }
           if (x_first) {
             xbuf = ux & 1;
-            if (!ptx::mbar_wait_spin(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, WAIT_LIMIT_NS)) {
+            if (!ptx::mbar_wait_spin(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, p.wait_ns)) {
               ok = false;
               break;
             }
           }
-          if (!ptx::mbar_wait_spin(ptx::smem_u32(&full[stage]), phase, abort_flag, WAIT_LIMIT_NS)) {
+          if (!ptx::mbar_wait_spin(ptx::smem_u32(&full[stage]), phase, abort_flag, p.wait_ns)) {
             ok = false;
             break;
           }
@@ -351,12 +356,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         cx = x_last ? 0 : cx + 1;
         if (d1_last) {
           ok = drain_unit(tmem + lane_base + (u1 & 1) * TBN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
-                          abort_flag, lane, rh, rl2);
+                          abort_flag, p.wait_ns, lane, rh, rl2);
           ++u1;
         }
         if (ok && x_last) {
           ok = drain_unit(tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0, &xf[ux & 1], &xe[ux & 1], (ux >> 1) & 1,
-                          abort_flag, lane, rh, rl2);
+                          abort_flag, p.wait_ns, lane, rh, rl2);
           ++ux;
         }
         if (!ok) break;
@@ -502,6 +507,7 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
   gp->products = products;
   gp->raster = raster;
   gp->status = ctx->d_status;
+  gp->wait_ns = ctx->wait_limit_ns ? ctx->wait_limit_ns : WAIT_LIMIT_NS;
   return TCI_OK;
 }
 

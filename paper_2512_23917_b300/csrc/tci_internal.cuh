@@ -20,6 +20,7 @@ struct tci_context_s {
   int num_sms;
   int split_chunk_k;    // K depth per hi*hi accumulation unit of the split GEMM
   int split_xchunk_k;   // K depth per cross-product accumulation unit
+  uint64_t wait_limit_ns = 0;   // bounded device waits of the tensor-core kernels (0: 2 s)
   std::string last_error;
   // device scratch for reductions and kernel status words (owned)
   double* d_scalars;   // 64 doubles
