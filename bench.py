@@ -457,6 +457,29 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_profile_tebd(args):
+    """The batched TEBD theta workload (256 bonds) applied warmup + steps times, for ncu captures."""
+    import torch
+    import paper_2512_23917_b300 as tci
+    from tci_synth import tebd_inputs
+    chis, A, B, G = tebd_inputs(256, seed=SEED)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    pa = t(np.concatenate([a.ravel() for a in A]))
+    pb = t(np.concatenate([b.ravel() for b in B]))
+    pg = t(np.concatenate([g.ravel() for g in G]))
+    th = torch.empty(sum(4 * c * c for c in chis), dtype=torch.complex64, device="cuda")
+    ctx = tci.Context(0, precision="split_bf16")
+    plan = tci.TebdPlan(ctx, chis)
+    tuned = plan.autotune(pa, pb, pg, th, max_chunk_k=256)
+    for _ in range(args.warmup + args.steps):
+        plan.apply(pa, pb, pg, th)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "batched TEBD theta, 256 bonds", "config": list(tuned),
+                      "batches": args.warmup + args.steps, "launches_per_batch": 3}))
+    plan.close()
+    ctx.close()
+
+
 def run_profile_case(args):
     """Small case for ncu captures: split-BF16 matvecs at --profile-chi."""
     import torch
@@ -493,13 +516,16 @@ def main():
                     help="run only split-BF16 matvecs at this bond dimension (small case for ncu)")
     ap.add_argument("--profile-lanczos", action="store_true",
                     help="with --profile-chi: run 20-step Lanczos solves instead of single matvecs")
+    ap.add_argument("--profile-tebd", action="store_true", help="run only the batched TEBD workload (for ncu)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-rows", action="store_true", help="measure only the headline chi=2048 workload")
     args = ap.parse_args()
-    if args.profile_chi:
+    if args.profile_tebd:
+        run_profile_tebd(args)
+    elif args.profile_chi:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)
