@@ -25,7 +25,8 @@ def sturm_count(alpha, beta, x: float) -> int:
 
     LDL^T pivots q_0 = alpha_0 - x, q_i = alpha_i - x - beta_{i-1}^2 / q_{i-1};
     the count of negative pivots equals the count of eigenvalues below x
-    (Sylvester inertia).  A zero pivot is nudged to a tiny negative value.
+    (Sylvester inertia).  A zero pivot is replaced by a tiny negative value
+    as soon as it appears (so it is counted and divides the next pivot).
     """
     m = len(alpha)
     cnt = 0
@@ -35,9 +36,9 @@ def sturm_count(alpha, beta, x: float) -> int:
         if i == 0:
             q = alpha[0] - x
         else:
-            if q == 0.0:
-                q = -tiny
             q = alpha[i] - x - beta[i - 1] * beta[i - 1] / q
+        if q == 0.0:
+            q = -tiny
         if q < 0.0:
             cnt += 1
     return cnt

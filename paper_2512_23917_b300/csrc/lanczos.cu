@@ -394,16 +394,15 @@ __global__ void k_finish_beta(double* scal, int j, int m, double tol) {
   if (j == m - 1 || b < tol * fabs(a)) scal[OFF_CTRL] = 1.0;
 }
 
+// Negative LDL^T pivots of T - x I = eigenvalues of T below x (Sylvester
+// inertia); a zero pivot is replaced by a tiny negative value as soon as it
+// appears, so it is counted and divides the next pivot.
 __device__ int sturm_count(const double* a, const double* b, int m, double x) {
   int cnt = 0;
   double q = 1.0;
   for (int i = 0; i < m; ++i) {
-    if (i == 0) {
-      q = a[0] - x;
-    } else {
-      if (q == 0.0) q = -2.2250738585072014e-308;
-      q = a[i] - x - b[i - 1] * b[i - 1] / q;
-    }
+    q = i == 0 ? a[0] - x : a[i] - x - b[i - 1] * b[i - 1] / q;
+    if (q == 0.0) q = -2.2250738585072014e-308;
     if (q < 0.0) ++cnt;
   }
   return cnt;

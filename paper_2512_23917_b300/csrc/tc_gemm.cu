@@ -640,14 +640,6 @@ __global__ void k_split3(const T* __restrict__ src, int64_t rows, int64_t K, int
   }
 }
 
-__global__ void k_narrow(int64_t M, int64_t N, const double* __restrict__ src, float* __restrict__ dst, int64_t sm,
-                         int64_t sn) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M * N; i += (int64_t)gridDim.x * blockDim.x) {
-    int64_t m = i / N, n = i - m * N;
-    dst[m * sm + n * sn] = (float)src[i];
-  }
-}
-
 }  // namespace
 
 tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int64_t rows, int64_t K, int64_t sr,
@@ -667,13 +659,3 @@ tci_status tci_launch_split3(tci_context ctx, tci_dtype dt, const void* src, int
   return TCI_OK;
 }
 
-tci_status tci_launch_narrow_f64_f32(tci_context ctx, int64_t M, int64_t N, const double* src, float* dst, int64_t sm,
-                                     int64_t sn) {
-  int64_t total = M * N;
-  if (total == 0) return TCI_OK;
-  int64_t blocks = (total + 255) / 256;
-  if (blocks > (int64_t)ctx->num_sms * 16) blocks = (int64_t)ctx->num_sms * 16;
-  k_narrow<<<(int)blocks, 256, 0, ctx->stream>>>(M, N, src, dst, sm, sn);
-  TCI_CUDA(ctx, cudaGetLastError());
-  return TCI_OK;
-}

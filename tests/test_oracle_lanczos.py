@@ -89,3 +89,14 @@ def test_lanczos_deterministic():
     r1 = lanczos.lanczos(mv, psi, 20)
     r2 = lanczos.lanczos(mv, psi, 20)
     assert r1["theta"] == r2["theta"]
+
+
+def test_sturm_count_with_an_exact_zero_pivot():
+    """x equal to alpha_0 makes the first pivot exactly zero; the count must stay right.
+
+    T = [[-1/4, 1/2], [1/2, -1/4]] has eigenvalues -3/4 and 1/4: one lies below -1/4.
+    """
+    from oracle.lanczos import lowest_eigenvalue_bisect, sturm_count
+    alpha, beta = [-0.25, -0.25], [0.5]
+    assert sturm_count(alpha, beta, -0.25) == 1
+    assert abs(lowest_eigenvalue_bisect(alpha, beta) + 0.75) < 1e-15
