@@ -324,6 +324,46 @@ double tci_heff_flops(tci_heff_plan plan);
 tci_status tci_heff_apply_noalloc(const double* L, const double* W, const double* R, const double* psi,
                                   double* out, int64_t chiL, int64_t chiR, void* stream);
 
+/* TCI "svd" (App. C.2, Tensor linear algebra): a (F64 or F32) is
+ * matricised with its first num_of_bds_as_row bonds as the row index
+ * (I x J) and factored as U S V^T, s_0 >= ... >= s_{kappa-1} >= 0,
+ * kappa = min(I, J).  *u = [d_0..d_{k-1}, kappa], *s = [kappa],
+ * *v_dag = [kappa, d_k..d_{r-1}]: new owned tensors of a's dtype (a handle
+ * already in *u, *s or *v_dag is freed first).  Computed on the device by
+ * one-sided Jacobi in FP64; the singular vectors of zero singular values are
+ * zero vectors.  Synchronises.  Errors: INVALID_ARG, SHAPE (k outside
+ * 1..order-1), UNSUPPORTED (complex dtype), ALLOC, TIMEOUT (no convergence
+ * in 60 sweeps), CUDA. */
+tci_status tci_svd(tci_context ctx, tci_tensor a, int num_of_bds_as_row, tci_tensor* u, tci_tensor* s,
+                   tci_tensor* v_dag);
+
+/* TCI "trunc_svd" (App. C.2, form (2); form (1) is chi_min = 1,
+ * target_trunc_err = 0): as tci_svd, keeping chi singular values chosen by
+ * the paper's rules -- (a) drop s_i < s_min; (b) keep at least chi_min, or
+ * all that remain after (a) if fewer; (c) add values in descending order
+ * until the truncation error sum_{i >= chi} s_i^2 / sum_i s_i^2 <=
+ * target_trunc_err or chi = chi_max (chi_max caps chi_min).  *trunc_err
+ * (may be NULL) receives that error.  Errors: as tci_svd, and INVALID_ARG
+ * when chi_min or chi_max < 1. */
+tci_status tci_trunc_svd(tci_context ctx, tci_tensor a, int num_of_bds_as_row, tci_tensor* u, tci_tensor* s,
+                         tci_tensor* v_dag, double* trunc_err, int64_t chi_min, int64_t chi_max,
+                         double target_trunc_err, double s_min);
+
+/* Two-site finite DMRG (extension; the paper names DMRG as a target of TCI,
+ * Sec. I; textbook sweep, Schollwoeck 2011 Secs. 6.2-6.4) for an open chain
+ * of nsites sites with the uniform MPO W (device F64 [Dw, Dw, 2, 2], row-major;
+ * left boundary vector = its last channel, right boundary = its first), from
+ * the Neel product state.  Each bond update: H_eff plan + tci_lanczos
+ * (lanczos_steps, started from the current two-site tensor) + tci_trunc_svd
+ * (chi_min 1, chi_max, target 0, s_min); the environments follow with
+ * tci_contract.  The context's precision applies to every step.
+ * energies[nsweeps] (host) receives the last Ritz value of each sweep,
+ * max_trunc_err[nsweeps] (host, may be NULL) the largest truncation error of
+ * each sweep.  Synchronises.  Errors: SHAPE, INVALID_ARG, and those of the
+ * calls it makes. */
+tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_t chi_max, int nsweeps, int lanczos_steps,
+                    double s_min, double* energies, double* max_trunc_err);
+
 /* Vector arithmetic of tci_lanczos (extension; the paper has no Lanczos
  * API).  TCI_LANCZOS_F64: every dot product and vector update in FP64.
  * TCI_LANCZOS_DF32: vectors held as pairs of FP32 numbers hi + lo

@@ -101,6 +101,10 @@ SIGNATURES = [
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
     ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
+    ("tci_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
+    ("tci_trunc_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), _dp, C.c_int64,
+                                C.c_int64, C.c_double, C.c_double]),
+    ("tci_dmrg", C.c_int, [_p, _p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_double, _dp, _dp]),
     ("tci_eye", C.c_int, [_p, C.c_int, C.c_int64, C.POINTER(_p)]),
     ("tci_fill", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.POINTER(_p)]),
     ("tci_cplx_conj", C.c_int, [_p, _p]),
@@ -341,6 +345,35 @@ class Tensor:
                 lib.tci_tensor_free(C.byref(self.handle))
         except Exception:
             pass
+
+
+def svd(ctx: Context, t: Tensor, num_of_bds_as_row: int):
+    """TCI svd of a tensor handle: (u, s, v_dag) as new Tensors."""
+    hu, hs, hv = _p(), _p(), _p()
+    _check(lib.tci_svd(ctx.handle, t.handle, int(num_of_bds_as_row), C.byref(hu), C.byref(hs), C.byref(hv)),
+           ctx.handle)
+    return Tensor(ctx, hu), Tensor(ctx, hs), Tensor(ctx, hv)
+
+
+def trunc_svd(ctx: Context, t: Tensor, num_of_bds_as_row: int, chi_min: int, chi_max: int,
+              target_trunc_err: float = 0.0, s_min: float = 0.0):
+    """TCI trunc_svd: (u, s, v_dag, trunc_err)."""
+    hu, hs, hv = _p(), _p(), _p()
+    err = C.c_double()
+    _check(lib.tci_trunc_svd(ctx.handle, t.handle, int(num_of_bds_as_row), C.byref(hu), C.byref(hs), C.byref(hv),
+                             C.byref(err), int(chi_min), int(chi_max), float(target_trunc_err), float(s_min)),
+           ctx.handle)
+    return Tensor(ctx, hu), Tensor(ctx, hs), Tensor(ctx, hv), err.value
+
+
+def dmrg(ctx: Context, W, nsites: int, chi_max: int, nsweeps: int, lanczos_steps: int = 20, s_min: float = 1e-12):
+    """Two-site DMRG on the device (W: CUDA float64 [Dw, Dw, 2, 2]); returns (energies, max truncation errors)."""
+    e = (C.c_double * nsweeps)()
+    te = (C.c_double * nsweeps)()
+    tw = ctx.wrap(W)
+    _check(lib.tci_dmrg(ctx.handle, tw.handle, int(nsites), int(chi_max), int(nsweeps), int(lanczos_steps),
+                        float(s_min), e, te), ctx.handle)
+    return list(e), list(te)
 
 
 def eye(ctx: Context, n: int, dtype: int = F64) -> Tensor:
