@@ -457,6 +457,37 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_dmrg(args):
+    """Two-site DMRG sweeps (open Heisenberg chain) on the device and in the oracle, one JSON line."""
+    import torch
+    import paper_2512_23917_b300 as tci
+    from oracle import dmrg as o_dmrg
+    from tci_synth import heisenberg_mpo
+    n, chi, sweeps = args.dmrg_sites, args.dmrg_chi, args.dmrg_sweeps
+    W = torch.from_numpy(heisenberg_mpo()).cuda()
+    ctx = tci.Context(0, precision=args.dmrg_precision)
+    tci.dmrg(ctx, W, n, chi, 1)                       # warm-up (allocator, kernels)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e, terr = tci.dmrg(ctx, W, n, chi, sweeps)
+    gpu_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oe, _ = o_dmrg.dmrg(heisenberg_mpo(), n, chi, sweeps)
+    cpu_s = time.perf_counter() - t0
+    line = {"metric": "two-site DMRG sweep time, open Heisenberg chain", "value": 1e3 * gpu_s / sweeps,
+            "unit": "ms per sweep", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"two-site DMRG, {n} sites, chi_max {chi}, {sweeps} sweeps from the Neel state, "
+                                   f"20-step Lanczos per bond, {args.dmrg_precision} precision",
+                       "sites": n, "chi_max": chi, "sweeps": sweeps},
+            "energies": e, "max_trunc_err": terr, "energy_per_site": e[-1] / n,
+            "oracle_energy": oe[-1], "rel_diff_vs_oracle": abs(e[-1] - oe[-1]) / abs(oe[-1]),
+            "cpu_baseline": {"value": 1e3 * cpu_s / sweeps, "unit": "ms per sweep",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"the same {sweeps} sweeps in the numpy oracle"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_profile_tebd(args):
     """The batched TEBD theta workload (256 bonds) applied warmup + steps times, for ncu captures."""
     import torch
@@ -517,13 +548,20 @@ def main():
     ap.add_argument("--profile-lanczos", action="store_true",
                     help="with --profile-chi: run 20-step Lanczos solves instead of single matvecs")
     ap.add_argument("--profile-tebd", action="store_true", help="run only the batched TEBD workload (for ncu)")
+    ap.add_argument("--dmrg", action="store_true", help="time two-site DMRG sweeps (device vs oracle) instead")
+    ap.add_argument("--dmrg-sites", type=int, default=32)
+    ap.add_argument("--dmrg-chi", type=int, default=64)
+    ap.add_argument("--dmrg-sweeps", type=int, default=3)
+    ap.add_argument("--dmrg-precision", default="native", choices=["native", "split_bf16"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--skip-rows", action="store_true", help="measure only the headline chi=2048 workload")
     args = ap.parse_args()
-    if args.profile_tebd:
+    if args.dmrg:
+        run_dmrg(args)
+    elif args.profile_tebd:
         run_profile_tebd(args)
     elif args.profile_chi:
         run_profile_case(args)
