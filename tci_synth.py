@@ -201,3 +201,22 @@ def tebd_inputs(nbonds: int = 256, seed: int = DEFAULT_SEED, chi_lo: int = 16, c
         B.append((rng.standard_normal((c, d, c)) + 1j * rng.standard_normal((c, d, c))).astype(np.complex64))
         G.append(haar_unitary(d * d, rng).reshape(d, d, d, d).astype(np.complex64))
     return [int(c) for c in chis], A, B, G
+
+
+def tfim_bond_hamiltonian(J: float = 1.0, g: float = 0.5) -> np.ndarray:
+    """Two-site term h[(s1 s2), (t1 t2)] of the transverse-field Ising chain (the model of the
+    paper's App. A): J on the diagonal for equal spins, -J for opposite ones, -g/2 between
+    states that differ by one spin flip (so H = sum_bonds h = J sum ZZ - g sum X)."""
+    h = np.diag([J, -J, -J, J]).astype(np.float64)
+    for i, j in ((0, 1), (0, 2), (1, 0), (1, 3), (2, 0), (2, 3), (3, 1), (3, 2)):
+        h[i, j] = -0.5 * g
+    return h
+
+
+def itebd_initial_state(chi: int, seed: int = DEFAULT_SEED, d: int = 2):
+    """Random two-site unit cell as in App. A: Gamma_A, Gamma_B [chi, d, chi] and Lambda_A,
+    Lambda_B [chi], entries uniform in [-1, 1) (numpy PCG64 from ``seed``)."""
+    rng = np.random.default_rng(seed)
+    gam = [rng.uniform(-1.0, 1.0, (chi, d, chi)) for _ in range(2)]
+    lam = [rng.uniform(-1.0, 1.0, chi) for _ in range(2)]
+    return gam, lam
