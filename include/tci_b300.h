@@ -364,6 +364,23 @@ tci_status tci_trunc_svd(tci_context ctx, tci_tensor a, int num_of_bds_as_row, t
 tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_t chi_max, int nsweeps, int lanczos_steps,
                     double s_min, double* energies, double* max_trunc_err);
 
+/* iTEBD ground-state iteration of the paper's App. A (extension: the
+ * application of Sec. III A as one call).  h: device F64 two-site term
+ * h[(s1 s2), (t1 t2)] ([4, 4] or [2, 2, 2, 2], row-major); the gate
+ * u = exp(-dt h) is formed on the device.  gamma_a, gamma_b [chi_l, 2, chi_r]
+ * and lambda_a, lambda_b [chi] (device F64, row-major) are the two-site unit
+ * cell; they are updated in place (their storage is replaced by arrays the
+ * handles then own, with the bond dimensions the truncation chose).  Each of
+ * niters iterations forms Theta = L_B Gamma_A L_A Gamma_B L_B, applies u,
+ * truncates with tci_trunc_svd (chi_min 1, chi, target 0, s_min), normalises
+ * Lambda_A and re-gauges with 1/Lambda_B, alternating A and B.  energies[i]
+ * (host) = -log ||Theta'||^2 / (2 dt), the energy per site estimate;
+ * trunc_errs[i] (host, may be NULL) the truncation error.  Synchronises.
+ * Errors: SHAPE, INVALID_ARG, and those of the calls it makes. */
+tci_status tci_itebd(tci_context ctx, tci_tensor h, double dt, tci_tensor gamma_a, tci_tensor gamma_b,
+                     tci_tensor lambda_a, tci_tensor lambda_b, int64_t chi, double s_min, int niters,
+                     double* energies, double* trunc_errs);
+
 /* Vector arithmetic of tci_lanczos (extension; the paper has no Lanczos
  * API).  TCI_LANCZOS_F64: every dot product and vector update in FP64.
  * TCI_LANCZOS_DF32: vectors held as pairs of FP32 numbers hi + lo

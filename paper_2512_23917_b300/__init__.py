@@ -105,6 +105,7 @@ SIGNATURES = [
     ("tci_trunc_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), _dp, C.c_int64,
                                 C.c_int64, C.c_double, C.c_double]),
     ("tci_dmrg", C.c_int, [_p, _p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_double, _dp, _dp]),
+    ("tci_itebd", C.c_int, [_p, _p, C.c_double, _p, _p, _p, _p, C.c_int64, C.c_double, C.c_int, _dp, _dp]),
     ("tci_eye", C.c_int, [_p, C.c_int, C.c_int64, C.POINTER(_p)]),
     ("tci_fill", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.POINTER(_p)]),
     ("tci_cplx_conj", C.c_int, [_p, _p]),
@@ -374,6 +375,26 @@ def dmrg(ctx: Context, W, nsites: int, chi_max: int, nsweeps: int, lanczos_steps
     _check(lib.tci_dmrg(ctx.handle, tw.handle, int(nsites), int(chi_max), int(nsweeps), int(lanczos_steps),
                         float(s_min), e, te), ctx.handle)
     return list(e), list(te)
+
+
+def itebd(ctx: Context, h, dt: float, gammas, lambdas, chi: int, niters: int, s_min: float = 1e-10):
+    """App. A iTEBD on the device.  h: numpy [4, 4]; gammas / lambdas: numpy arrays of the unit cell.
+
+    Returns (energies, truncation errors, final gammas, final lambdas) as numpy arrays.
+    """
+    ht = allocate(ctx, [4, 4], F64)
+    ht.from_numpy(np.asarray(h, dtype=np.float64).reshape(4, 4))
+    cell = []
+    for a in list(gammas) + list(lambdas):
+        t = allocate(ctx, np.shape(a), F64)
+        t.from_numpy(np.asarray(a, dtype=np.float64))
+        cell.append(t)
+    e = (C.c_double * max(1, niters))()
+    te = (C.c_double * max(1, niters))()
+    _check(lib.tci_itebd(ctx.handle, ht.handle, float(dt), cell[0].handle, cell[1].handle, cell[2].handle,
+                         cell[3].handle, int(chi), float(s_min), int(niters), e, te), ctx.handle)
+    out = [t.to_numpy() for t in cell]
+    return list(e[:niters]), list(te[:niters]), out[:2], out[2:]
 
 
 def eye(ctx: Context, n: int, dtype: int = F64) -> Tensor:
