@@ -220,3 +220,40 @@ def itebd_initial_state(chi: int, seed: int = DEFAULT_SEED, d: int = 2):
     gam = [rng.uniform(-1.0, 1.0, (chi, d, chi)) for _ in range(2)]
     lam = [rng.uniform(-1.0, 1.0, chi) for _ in range(2)]
     return gam, lam
+
+
+def heavy_hex_graph(rows: int = 4, cols: int = 9):
+    """A heavy-hex patch: a brick-wall lattice of rows x cols degree-<=3 vertices (horizontal bonds
+    along each row, a vertical bond below (r, c) when r + c is even) with one extra degree-2 vertex
+    inserted on every bond.  Returns (n_vertices, edges) with edges (u, v), u < v, in a fixed order."""
+    def vid(r, c):
+        return r * cols + c
+    base = []
+    for r in range(rows):
+        for c in range(cols):
+            if c + 1 < cols:
+                base.append((vid(r, c), vid(r, c + 1)))
+            if r + 1 < rows and (r + c) % 2 == 0:
+                base.append((vid(r, c), vid(r + 1, c)))
+    n = rows * cols
+    edges = []
+    for u, v in base:
+        edges.append((u, n))
+        edges.append((v, n))
+        n += 1
+    return n, sorted((min(a, b), max(a, b)) for a, b in edges)
+
+
+def bp_tns_inputs(n: int, edges, chi: int, seed: int = DEFAULT_SEED, d: int = 2):
+    """Random real TNS on a graph for belief propagation: site tensor V_i[s, b_1 .. b_k] with d
+    physical states and one bond of dimension chi per neighbour (neighbours in ascending order),
+    entries standard normal; messages M_{i->j} start as the identity / sqrt(chi) (unit Frobenius
+    norm).  Messages are listed per edge e = (u, v): index 2e is u->v, 2e + 1 is v->u."""
+    rng = np.random.default_rng(seed)
+    deg = [0] * n
+    for u, v in edges:
+        deg[u] += 1
+        deg[v] += 1
+    V = [rng.standard_normal((d,) + (chi,) * deg[i]) for i in range(n)]
+    M = [np.eye(chi) / np.sqrt(chi) for _ in range(2 * len(edges))]
+    return V, M
