@@ -488,6 +488,80 @@ def run_dmrg(args):
     ctx.close()
 
 
+def bp_flops(n, edges, V):
+    """Algorithmic flops of one BP iteration: a message leaving site i costs 2 |V_i| sum_q chi_q."""
+    deg = [0] * n
+    for u, v in edges:
+        deg[u] += 1
+        deg[v] += 1
+    return sum(deg[i] * 2.0 * V[i].size * sum(V[i].shape[1:]) for i in range(n))
+
+
+def run_bp(args):
+    """App. B belief propagation on a heavy-hex TNS on the device and in the oracle, one JSON line."""
+    import paper_2512_23917_b300 as tci
+    from oracle import bp as o_bp
+    from tci_synth import bp_tns_inputs, heavy_hex_graph
+    n, edges = heavy_hex_graph(6, 11)
+    chi, iters = args.bp_chi, args.bp_iters
+    V, M = bp_tns_inputs(n, edges, chi, SEED)
+    ctx = tci.Context(0)
+    tci.bp(ctx, n, edges, V, M, 2)                       # warm-up (allocator, kernels)
+    t0 = time.perf_counter()
+    got, res = tci.bp(ctx, n, edges, V, M, iters)
+    gpu_s = time.perf_counter() - t0
+    n_cpu = max(1, min(iters, args.bp_oracle_iters))
+    t0 = time.perf_counter()
+    ref, rres = o_bp.bp(n, edges, V, M, n_cpu)
+    cpu_s = time.perf_counter() - t0
+    fl = bp_flops(n, edges, V)
+    line = {"metric": "BP iteration time, heavy-hex TNS", "value": 1e3 * gpu_s / iters, "unit": "ms per iteration",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": f"BP message iteration on a {n}-qubit heavy-hex patch ({len(edges)} bonds, "
+                                   f"{2 * len(edges)} messages), random real TNS, d=2, chi {chi}, {iters} iterations",
+                       "sites": n, "bonds": len(edges), "chi": chi, "iterations": iters},
+            "gflops_per_s": fl / (gpu_s / iters) / 1e9, "flops_per_iteration": fl,
+            "residual_last": res[-1], "oracle_residual_at_sample_end": rres[-1],
+            "device_residual_at_sample_end": res[n_cpu - 1],
+            "cpu_baseline": {"value": 1e3 * cpu_s / n_cpu, "unit": "ms per iteration",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"the first {n_cpu} iterations in the numpy oracle"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def run_itebd(args):
+    """App. A iTEBD on the TFIM (J = 1, g) on the device and in the oracle, one JSON line."""
+    import paper_2512_23917_b300 as tci
+    from oracle import itebd as o_itebd
+    from tci_synth import itebd_initial_state, tfim_bond_hamiltonian
+    chi, n, g, dt = args.itebd_chi, args.itebd_iters, args.itebd_g, args.itebd_dt
+    h = tfim_bond_hamiltonian(1.0, g)
+    gam, lam = itebd_initial_state(chi, SEED)
+    ctx = tci.Context(0)
+    tci.itebd(ctx, h, dt, gam, lam, chi, 20)              # warm-up (allocator, kernels)
+    t0 = time.perf_counter()
+    e, terr, _, _ = tci.itebd(ctx, h, dt, gam, lam, chi, n)
+    gpu_s = time.perf_counter() - t0
+    n_cpu = min(n, 400)
+    t0 = time.perf_counter()
+    oe, _, _ = o_itebd.itebd(h, dt, gam, lam, chi, n_cpu)
+    cpu_s = time.perf_counter() - t0
+    exact = o_itebd.tfim_exact_energy(1.0, g)
+    line = {"metric": "iTEBD iteration time, TFIM", "value": 1e3 * gpu_s / n, "unit": "ms per iteration",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": f"iTEBD two-site unit cell, TFIM J=1 g={g}, chi {chi}, dt {dt}, {n} iterations "
+                                   f"from a random cell", "chi": chi, "iterations": n, "g": g, "dt": dt},
+            "energy_per_site": e[-1], "exact_energy_per_site": exact, "abs_err_vs_exact": abs(e[-1] - exact),
+            "oracle_energy_at_sample_end": oe[-1], "device_energy_at_sample_end": e[n_cpu - 1],
+            "max_trunc_err": max(terr) if terr else 0.0,
+            "cpu_baseline": {"value": 1e3 * cpu_s / n_cpu, "unit": "ms per iteration",
+                             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+                             "sample": f"the first {n_cpu} iterations in the numpy oracle"}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_profile_tebd(args):
     """The batched TEBD theta workload (256 bonds) applied warmup + steps times, for ncu captures."""
     import torch
@@ -553,6 +627,15 @@ def main():
     ap.add_argument("--dmrg-chi", type=int, default=64)
     ap.add_argument("--dmrg-sweeps", type=int, default=3)
     ap.add_argument("--dmrg-precision", default="native", choices=["native", "split_bf16"])
+    ap.add_argument("--itebd", action="store_true", help="time App. A iTEBD iterations (device vs oracle) instead")
+    ap.add_argument("--itebd-chi", type=int, default=64)
+    ap.add_argument("--itebd-iters", type=int, default=2000)
+    ap.add_argument("--itebd-g", type=float, default=1.0)
+    ap.add_argument("--itebd-dt", type=float, default=0.01)
+    ap.add_argument("--bp", action="store_true", help="time App. B BP iterations on a heavy-hex TNS (device vs oracle)")
+    ap.add_argument("--bp-chi", type=int, default=32)
+    ap.add_argument("--bp-iters", type=int, default=20)
+    ap.add_argument("--bp-oracle-iters", type=int, default=3)
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
@@ -561,6 +644,10 @@ def main():
     args = ap.parse_args()
     if args.dmrg:
         run_dmrg(args)
+    elif args.itebd:
+        run_itebd(args)
+    elif args.bp:
+        run_bp(args)
     elif args.profile_tebd:
         run_profile_tebd(args)
     elif args.profile_chi:

@@ -21,7 +21,11 @@
  *    required).  Tensors created by tci_allocate / tci_zeros / tci_copy and
  *    contraction outputs the library creates are OWNED (freed by
  *    tci_tensor_free / tci_clear); tci_tensor_wrap creates a BORROWED view
- *    that the library never frees.
+ *    that the library never frees.  Owned memory is stream-ordered: it comes
+ *    from a per-device pool on the context's stream and is released in order
+ *    on the stream it was allocated on (which must still exist when the
+ *    tensor is freed).  Work another stream does on an owned tensor must be
+ *    complete, or waited for by that stream, before the tensor is freed.
  *  - Layout: shapes and strides are in elements, row-major when strides are
  *    omitted (last bond fastest), int64.
  *  - Thread safety: a context must not be used from two host threads at once.
@@ -248,9 +252,10 @@ tci_status tci_transpose_to(tci_context ctx, tci_tensor in, const int* new_order
  *                    first, then placed).
  * Both operands must have the same dtype.  Real F64/F32 contractions use the
  * context precision; complex ones use native arithmetic.
+ * A label in a, b and c at once is a batch bond: every slice of it is
+ * contracted on its own (C_IJB = sum_S A_ISB B_SJB), in native arithmetic.
  * Errors: LABEL (repeated label in one operand, count mismatch, dimension
- * mismatch), UNSUPPORTED (a label in a, b and c at once; a free label missing
- * from c), DTYPE, ALLOC, CUDA. */
+ * mismatch), UNSUPPORTED (a free label missing from c), DTYPE, ALLOC, CUDA. */
 tci_status tci_contract(tci_context ctx, tci_tensor a, const char* labels_a, tci_tensor b,
                         const char* labels_b, tci_tensor* c, const char* labels_c);
 tci_status tci_contract_l(tci_context ctx, tci_tensor a, const int32_t* labels_a, tci_tensor b,
@@ -380,6 +385,25 @@ tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_t chi_max, 
 tci_status tci_itebd(tci_context ctx, tci_tensor h, double dt, tci_tensor gamma_a, tci_tensor gamma_b,
                      tci_tensor lambda_a, tci_tensor lambda_b, int64_t chi, double s_min, int niters,
                      double* energies, double* trunc_errs);
+
+/* Belief propagation on the norm network of a tensor-network state (App. B;
+ * extension: the message iteration as one call).  Graph: nsites vertices and
+ * nedges edges (host int64 pairs edges[2e], edges[2e + 1], distinct
+ * vertices).  sites[i] (device F64, row-major) is V_i[s, b_1 .. b_k]: the
+ * physical bond first, then one bond per neighbour in ascending neighbour
+ * order (k = degree of i, at most 6).  messages[2e] is the message u -> v of
+ * edge e = (u, v), messages[2e + 1] the message v -> u; each is an F64
+ * [chi_e, chi_e] matrix (ket bond index, bra bond index), updated in place.
+ * One iteration replaces every message, from the previous set, by
+ *   M_{i->j}[b, b'] = sum V_i[s, .., b, ..] V_i[s, .., b', ..] prod_{k != j} M_{k->i}
+ * normalised to unit Frobenius norm.  Messages with the same site shape and
+ * outgoing bond run as one batched contraction.  Iterations stop after
+ * niters or once the residual max_m ||M_new - M_old||_F is <= tol;
+ * residuals[it] (host, may be NULL; niters entries) and *iters_done (may be
+ * NULL) report them.  Synchronises.  Errors: INVALID_ARG, SHAPE, DTYPE and
+ * those of the calls it makes. */
+tci_status tci_bp(tci_context ctx, int nsites, int nedges, const int64_t* edges, const tci_tensor* sites,
+                  tci_tensor* messages, int niters, double tol, int* iters_done, double* residuals);
 
 /* Vector arithmetic of tci_lanczos (extension; the paper has no Lanczos
  * API).  TCI_LANCZOS_F64: every dot product and vector update in FP64.

@@ -105,6 +105,8 @@ SIGNATURES = [
     ("tci_trunc_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), _dp, C.c_int64,
                                 C.c_int64, C.c_double, C.c_double]),
     ("tci_dmrg", C.c_int, [_p, _p, C.c_int, C.c_int64, C.c_int, C.c_int, C.c_double, _dp, _dp]),
+    ("tci_bp", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.POINTER(_p), C.POINTER(_p), C.c_int, C.c_double,
+                        C.POINTER(C.c_int), _dp]),
     ("tci_itebd", C.c_int, [_p, _p, C.c_double, _p, _p, _p, _p, C.c_int64, C.c_double, C.c_int, _dp, _dp]),
     ("tci_eye", C.c_int, [_p, C.c_int, C.c_int64, C.POINTER(_p)]),
     ("tci_fill", C.c_int, [_p, C.c_int, C.c_int, C.POINTER(C.c_int64), C.c_double, C.c_double, C.POINTER(_p)]),
@@ -395,6 +397,29 @@ def itebd(ctx: Context, h, dt: float, gammas, lambdas, chi: int, niters: int, s_
                          cell[3].handle, int(chi), float(s_min), int(niters), e, te), ctx.handle)
     out = [t.to_numpy() for t in cell]
     return list(e[:niters]), list(te[:niters]), out[:2], out[2:]
+
+
+def bp(ctx: Context, n: int, edges, sites, messages, niters: int, tol: float = 0.0):
+    """App. B belief propagation on the device.  sites / messages: numpy arrays (messages per edge e:
+    2e = u -> v, 2e + 1 = v -> u).  Returns (messages as numpy arrays, residual per iteration)."""
+    st = []
+    for a in sites:
+        t = allocate(ctx, np.shape(a), F64)
+        t.from_numpy(np.asarray(a, dtype=np.float64))
+        st.append(t)
+    mt = []
+    for a in messages:
+        t = allocate(ctx, np.shape(a), F64)
+        t.from_numpy(np.asarray(a, dtype=np.float64))
+        mt.append(t)
+    ed = (C.c_int64 * max(1, 2 * len(edges)))(*[int(x) for e in edges for x in e])
+    sh = (_p * max(1, len(st)))(*[t.handle for t in st])
+    mh = (_p * max(1, len(mt)))(*[t.handle for t in mt])
+    res = (C.c_double * max(1, niters))()
+    done = C.c_int()
+    _check(lib.tci_bp(ctx.handle, int(n), len(edges), ed, sh, mh, int(niters), float(tol), C.byref(done), res),
+           ctx.handle)
+    return [t.to_numpy() for t in mt], list(res[:done.value])
 
 
 def eye(ctx: Context, n: int, dtype: int = F64) -> Tensor:

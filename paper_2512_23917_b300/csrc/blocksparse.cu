@@ -99,7 +99,7 @@ tci_status run_jobs(tci_context ctx, const std::vector<Job>& jobs, int64_t max_w
   if (jobs.empty()) return TCI_OK;
   Job* dj = nullptr;
   TCI_TRY(tci_dev_alloc(ctx, sizeof(Job) * jobs.size(), (void**)&dj));
-  cudaError_t e = cudaMemcpy(dj, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpyAsync(dj, jobs.data(), sizeof(Job) * jobs.size(), cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess) {
     dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (max_work + 255) / 256)), (unsigned)jobs.size());
     kern<<<grid, 256, 0, ctx->stream>>>(dj, src, dst);
@@ -459,10 +459,12 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   p->n_tiles = (int)wtiles.size();
   if (!tasks.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(WWTask) * tasks.size(), (void**)&p->d_tasks)) != TCI_OK) return fail(s);
-    e = cudaMemcpy(p->d_tasks, tasks.data(), sizeof(WWTask) * tasks.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->d_tasks, tasks.data(), sizeof(WWTask) * tasks.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: tasks"));
     if ((s = tci_dev_alloc(ctx, sizeof(WWTile) * wtiles.size(), (void**)&p->d_tiles)) != TCI_OK) return fail(s);
-    e = cudaMemcpy(p->d_tiles, wtiles.data(), sizeof(WWTile) * wtiles.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->d_tiles, wtiles.data(), sizeof(WWTile) * wtiles.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W tiles"));
   }
   // ---------------------------------------------------------------- GEMM2 group
@@ -488,7 +490,8 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   p->n_psi_jobs = (int)psi_jobs.size();
   if (!psi_jobs.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(SplitJob) * psi_jobs.size(), (void**)&p->d_psi_jobs)) != TCI_OK) return fail(s);
-    e = cudaMemcpy(p->d_psi_jobs, psi_jobs.data(), sizeof(SplitJob) * psi_jobs.size(), cudaMemcpyHostToDevice);
+    e = cudaMemcpyAsync(p->d_psi_jobs, psi_jobs.data(), sizeof(SplitJob) * psi_jobs.size(),
+                        cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: psi jobs"));
   }
   // W.W coefficients (FP64 product on the device, FP32 copy for the kernel arguments)

@@ -169,14 +169,14 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
     // as one batched launch of the native-arithmetic GEMM (any precision
     // setting), and the [batch][M][N] result is scattered into c.
     if (NB * M * N > 0) {
-      auto pack3 = [&](tci_tensor t, const Group& g1, void** out) -> tci_status {
+      auto pack3 = [&](tci_tensor t, bool is_a, const Group& g1, void** out) -> tci_status {
         int ord = 0;
         int64_t shp[3 * TCI_MAX_ORDER], str[3 * TCI_MAX_ORDER];
         const Group* gs[3] = {&gb, &g1, &gk};
         for (const Group* g : gs)
           for (auto& m : g->modes) {
             shp[ord] = m.dim;
-            str[ord] = t == a ? m.sa : m.sb;
+            str[ord] = is_a ? m.sa : m.sb;   // not t == a: a and b may be one tensor
             ++ord;
           }
         if (ord > TCI_MAX_ORDER) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "contract: too many non-coalescible modes");
@@ -191,8 +191,8 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
       void *Apk = nullptr, *Bpk = nullptr, *Ck = nullptr;
       tci_status s = TCI_OK;
       if (K > 0) {
-        s = pack3(a, gm, &Apk);
-        if (s == TCI_OK) s = pack3(b, gn, &Bpk);
+        s = pack3(a, true, gm, &Apk);
+        if (s == TCI_OK) s = pack3(b, false, gn, &Bpk);
       }
       if (s == TCI_OK) s = tci_dev_alloc(ctx, (size_t)(NB * M * N) * eb, &Ck);
       if (s != TCI_OK) return cleanup(s);
@@ -235,15 +235,15 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
       bool direct = g1.modes.size() <= 1 && g2.modes.size() <= 1;
       if (direct) {
         *ptr = t->data;
-        *s1 = g1.modes.empty() ? 0 : (t == a ? g1.modes[0].sa : g1.modes[0].sb);
-        *s2 = g2.modes.empty() ? 0 : (t == a ? g2.modes[0].sa : g2.modes[0].sb);
+        *s1 = g1.modes.empty() ? 0 : (g1_is_m ? g1.modes[0].sa : g1.modes[0].sb);
+        *s2 = g2.modes.empty() ? 0 : (g1_is_m ? g2.modes[0].sa : g2.modes[0].sb);
         return TCI_OK;
       }
       // pack [g1 modes..., g2 modes...] row-major
       int ord = 0;
       int64_t shp[2 * TCI_MAX_ORDER], str[2 * TCI_MAX_ORDER];
-      for (auto& m : g1.modes) { shp[ord] = m.dim; str[ord] = (t == a ? m.sa : m.sb); ++ord; }
-      for (auto& m : g2.modes) { shp[ord] = m.dim; str[ord] = (t == a ? m.sa : m.sb); ++ord; }
+      for (auto& m : g1.modes) { shp[ord] = m.dim; str[ord] = (g1_is_m ? m.sa : m.sb); ++ord; }
+      for (auto& m : g2.modes) { shp[ord] = m.dim; str[ord] = (g1_is_m ? m.sa : m.sb); ++ord; }
       if (ord > TCI_MAX_ORDER) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "contract: too many non-coalescible modes");
       void* p = nullptr;
       TCI_TRY(tci_dev_alloc(ctx, (size_t)(g1.size() * g2.size()) * eb, &p));

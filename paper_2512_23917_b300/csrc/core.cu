@@ -9,6 +9,8 @@
 #include <string.h>
 
 #include <chrono>
+#include <mutex>
+#include <unordered_map>
 
 #include "tci_internal.cuh"
 
@@ -136,10 +138,85 @@ std::string tci_shape_str(const tci_tensor_s* t) {
   return s;
 }
 
+// ---------------------------------------------------------------- device memory
+// Library allocations are stream-ordered: they come from one memory pool per
+// device (cudaMallocFromPoolAsync on the context's stream) and are returned
+// with cudaFreeAsync on the stream they were allocated on, so the temporaries
+// of a call never synchronise the device the way cudaMalloc / cudaFree do.
+// The pool keeps up to kPoolKeepBytes of freed memory for reuse; more is
+// released to the driver at the next synchronisation.  Memory allocated while
+// the context's stream is being captured into a graph, or without a context,
+// comes from plain cudaMalloc.
+namespace {
+
+constexpr uint64_t kPoolKeepBytes = 8ull << 30;
+constexpr int kMaxDevices = 64;
+
+struct DevicePools {
+  std::mutex mu;
+  cudaMemPool_t pool[kMaxDevices] = {};
+  std::unordered_map<void*, cudaStream_t> stream_of;   // live pool allocations
+};
+
+DevicePools& device_pools() {
+  static DevicePools* p = new DevicePools();   // never destroyed: frees may run during exit
+  return *p;
+}
+
+cudaMemPool_t pool_of(int device) {
+  if (device < 0 || device >= kMaxDevices) return nullptr;
+  DevicePools& dp = device_pools();
+  std::lock_guard<std::mutex> lk(dp.mu);
+  if (!dp.pool[device]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = kPoolKeepBytes;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    dp.pool[device] = pool;
+  }
+  return dp.pool[device];
+}
+
+}  // namespace
+
 tci_status tci_dev_alloc(tci_context ctx, size_t bytes, void** p) {
   *p = nullptr;
   if (bytes == 0) return TCI_OK;
-  cudaError_t e = cudaMalloc(p, bytes);
+  cudaError_t e = cudaSuccess;
+  if (tci_ctx_ok(ctx)) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      cs = cudaStreamCaptureStatusActive;
+    }
+    cudaMemPool_t pool = cs == cudaStreamCaptureStatusNone ? pool_of(ctx->device) : nullptr;
+    if (pool) {
+      e = cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
+      if (e == cudaErrorMemoryAllocation) {   // give cached memory back and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(ctx->stream);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
+      }
+      if (e == cudaSuccess) {
+        DevicePools& dp = device_pools();
+        std::lock_guard<std::mutex> lk(dp.mu);
+        dp.stream_of[*p] = ctx->stream;
+        return TCI_OK;
+      }
+      cudaGetLastError();
+      *p = nullptr;
+      return tci_fail(ctx, TCI_ERR_ALLOC, "device allocation of %zu bytes: %s", bytes, cudaGetErrorString(e));
+    }
+  }
+  e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     cudaGetLastError();
     *p = nullptr;
@@ -149,7 +226,23 @@ tci_status tci_dev_alloc(tci_context ctx, size_t bytes, void** p) {
 }
 
 void tci_dev_free(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  cudaStream_t s = nullptr;
+  bool pooled = false;
+  {
+    DevicePools& dp = device_pools();
+    std::lock_guard<std::mutex> lk(dp.mu);
+    auto it = dp.stream_of.find(p);
+    if (it != dp.stream_of.end()) {
+      s = it->second;
+      pooled = true;
+      dp.stream_of.erase(it);
+    }
+  }
+  if (pooled)
+    cudaFreeAsync(p, s);
+  else
+    cudaFree(p);
 }
 
 static bool valid_dtype(int d) { return d >= 0 && d <= 3; }

@@ -20,21 +20,6 @@
 
 namespace {
 
-struct Owned {
-  tci_tensor t = nullptr;
-  ~Owned() {
-    if (t) tci_tensor_free(&t);
-  }
-  void reset(tci_tensor x) {
-    if (t) tci_tensor_free(&t);
-    t = x;
-  }
-  tci_tensor release() {
-    tci_tensor x = t;
-    t = nullptr;
-    return x;
-  }
-};
 
 tci_status contract3(tci_context ctx, tci_tensor a, const char* la, tci_tensor b, const char* lb, const char* lc,
                      tci_tensor* out) {
@@ -44,7 +29,7 @@ tci_status contract3(tci_context ctx, tci_tensor a, const char* la, tci_tensor b
 
 // L'[b, w', b'] = sum A[a, s, b] L[a, w, a'] W[w, w', s, t] A[a', t, b']
 tci_status update_left(tci_context ctx, tci_tensor L, tci_tensor A, tci_tensor W, tci_tensor* out) {
-  Owned t1, t2;
+  TciOwned t1, t2;
   TCI_TRY(contract3(ctx, L, "awx", A, "xty", "awty", &t1.t));
   TCI_TRY(contract3(ctx, t1.t, "awty", W, "wvst", "avsy", &t2.t));
   return contract3(ctx, A, "asb", t2.t, "avsy", "bvy", out);
@@ -52,7 +37,7 @@ tci_status update_left(tci_context ctx, tci_tensor L, tci_tensor A, tci_tensor W
 
 // R'[a, w, a'] = sum A[a, s, b] W[w, w', s, t] R[b, w', b'] A[a', t, b']
 tci_status update_right(tci_context ctx, tci_tensor R, tci_tensor A, tci_tensor W, tci_tensor* out) {
-  Owned t1, t2;
+  TciOwned t1, t2;
   TCI_TRY(contract3(ctx, R, "bvy", A, "xty", "bvxt", &t1.t));
   TCI_TRY(contract3(ctx, t1.t, "bvxt", W, "wvst", "bwsx", &t2.t));
   return contract3(ctx, A, "asb", t2.t, "bwsx", "awx", out);
@@ -80,7 +65,7 @@ extern "C" tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_
   const int N = nsites;
   const int64_t Dw = W->shape[0];
   vs.info = "N=" + std::to_string(N) + " chi_max=" + std::to_string(chi_max);
-  std::vector<Owned> A(N), L(N + 1), R(N + 2);
+  std::vector<TciOwned> A(N), L(N + 1), R(N + 2);
   const int64_t site_shape[3] = {1, 2, 1};
   for (int k = 0; k < N; ++k) TCI_TRY(unit_tensor(ctx, site_shape, k % 2, &A[k].t));
   const int64_t env_shape[3] = {1, Dw, 1};
@@ -89,7 +74,7 @@ extern "C" tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_
   for (int k = N - 1; k >= 1; --k) TCI_TRY(update_right(ctx, R[k + 1].t, A[k].t, W, &R[k].t));
 
   auto solve = [&](int k, tci_tensor* ground, double* theta) -> tci_status {
-    Owned psi, x;
+    TciOwned psi, x;
     tci_heff_plan plan = nullptr;
     TCI_TRY(contract3(ctx, A[k].t, "abc", A[k + 1].t, "cde", "abde", &psi.t));
     TCI_TRY(tci_allocate(ctx, TCI_F64, 4, psi.t->shape, &x.t));
@@ -106,7 +91,7 @@ extern "C" tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_
     for (int dir = 0; dir < 2; ++dir) {
       for (int step = 0; step < N - 1; ++step) {
         const int k = dir == 0 ? step : N - 2 - step;
-        Owned x, u, s, vt, sd;
+        TciOwned x, u, s, vt, sd;
         TCI_TRY(solve(k, &x.t, &theta));
         double terr = 0.0;
         TCI_TRY(tci_trunc_svd(ctx, x.t, 2, &u.t, &s.t, &vt.t, &terr, 1, chi_max, 0.0, s_min));

@@ -490,6 +490,9 @@ static tci_status apply_host_pipelined(tci_heff_plan p, const double* psi_host, 
   for (int c = 0; c <= nch; ++c) bnd[c] = c == nch ? chiL : (c * chiL / nch) / 8 * 8;
   WWArgs<float> args;
   for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+  // the copy stream starts after the compute stream's earlier work (staging buffers are stream-ordered)
+  TCI_CUDA(ctx, cudaEventRecord(p->ev_in[7], ctx->stream));
+  TCI_CUDA(ctx, cudaStreamWaitEvent(p->s_h2d, p->ev_in[7], 0));
   // psi rows (a', t1, t2) of a' in [a0, a1) in, as they arrive
   for (int c = 0; c < nch; ++c) {
     const int64_t r0 = 4 * bnd[c] * chiR, n = 4 * (bnd[c + 1] - bnd[c]) * chiR;

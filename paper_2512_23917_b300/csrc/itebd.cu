@@ -17,16 +17,6 @@
 
 namespace {
 
-struct Owned {
-  tci_tensor t = nullptr;
-  ~Owned() {
-    if (t) tci_tensor_free(&t);
-  }
-  void reset(tci_tensor x) {
-    if (t) tci_tensor_free(&t);
-    t = x;
-  }
-};
 
 // u = exp(-dt h) for a 4 x 4 h (one thread): scale by 2^-s so ||A||_1 <= 1/2,
 // Taylor series to degree 18, then square s times.
@@ -88,10 +78,8 @@ tci_status contract_new(tci_context ctx, tci_tensor a, const char* la, tci_tenso
 
 // Replace dst's metadata and storage by src's (src is consumed).
 void take_storage(tci_context ctx, tci_tensor dst, tci_tensor src) {
-  if (dst->alloc) {
-    cudaStreamSynchronize(ctx->stream);
-    tci_dev_free(dst->alloc);
-  }
+  (void)ctx;
+  tci_dev_free(dst->alloc);   // stream-ordered: after the work already queued on it
   dst->dtype = src->dtype;
   dst->order = src->order;
   for (int i = 0; i < src->order; ++i) {
@@ -100,6 +88,7 @@ void take_storage(tci_context ctx, tci_tensor dst, tci_tensor src) {
   }
   dst->data = src->data;
   dst->alloc = src->alloc;
+  dst->device = src->device;
   src->alloc = nullptr;
   tci_tensor_free(&src);
 }
@@ -128,14 +117,14 @@ extern "C" tci_status tci_itebd(tci_context ctx, tci_tensor h, double dt, tci_te
   if (chi < 1 || niters < 0 || !(dt > 0.0) || (niters > 0 && !energies))
     return tci_fail(ctx, TCI_ERR_INVALID_ARG, "itebd: need chi >= 1, dt > 0, niters >= 0 and an energy buffer");
   vs.info = "chi=" + std::to_string(chi) + " iters=" + std::to_string(niters);
-  Owned u;
+  TciOwned u;
   const int64_t ushape[4] = {2, 2, 2, 2};
   TCI_TRY(tci_allocate(ctx, TCI_F64, 4, ushape, &u.t));
   k_expm4<<<1, 32, 0, ctx->stream>>>((const double*)h->data, dt, (double*)u.t->data);
   TCI_CUDA(ctx, cudaGetLastError());
   for (int i = 0; i < niters; ++i) {
     const int A = i % 2, B = (i + 1) % 2;
-    Owned la, lb, t1, t2, t3, t4, th, ua, sa, vb, linv, linvd;
+    TciOwned la, lb, t1, t2, t3, t4, th, ua, sa, vb, linv, linvd;
     TCI_TRY(tci_diag_to(ctx, Lm[A], &la.t));
     TCI_TRY(tci_diag_to(ctx, Lm[B], &lb.t));
     TCI_TRY(contract_new(ctx, lb.t, "ij", G[A], "jkl", "ikl", &t1.t));

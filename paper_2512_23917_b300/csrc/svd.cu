@@ -308,11 +308,9 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
       chi = remain;
     } else {
       chi = cmin;
-      auto err_of = [&](int64_t c) {
-        double t = 0.0;
-        for (int64_t i = c; i < n; ++i) t += sorted[i] * sorted[i];
-        return tot > 0.0 ? t / tot : 0.0;
-      };
+      std::vector<double> tail(n + 1, 0.0);   // tail[c] = sum_{i >= c} s_i^2
+      for (int64_t i = n - 1; i >= 0; --i) tail[i] = tail[i + 1] + sorted[i] * sorted[i];
+      auto err_of = [&](int64_t c) { return tot > 0.0 ? tail[c] / tot : 0.0; };
       while (chi < std::min(chi_max, remain) && err_of(chi) > target) ++chi;
     }
   }

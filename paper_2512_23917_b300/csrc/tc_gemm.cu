@@ -573,7 +573,8 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
       delete g;
       return s;
     }
-    cudaError_t e = cudaMemcpy(g->d_table, host.data(), sizeof(GemmProblem) * host.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaMemcpyAsync(g->d_table, host.data(), sizeof(GemmProblem) * host.size(),
+                                   cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) {
       tci_dev_free(g->d_table);
       delete g;

@@ -87,6 +87,27 @@ std::string tci_shape_str(const tci_tensor_s* t);
 tci_status tci_dev_alloc(tci_context ctx, size_t bytes, void** p);
 void tci_dev_free(void* p);
 
+// Owning holder of a tensor handle for host drivers (freed on scope exit).
+struct TciOwned {
+  tci_tensor t = nullptr;
+  TciOwned() = default;
+  TciOwned(const TciOwned&) = delete;
+  TciOwned& operator=(const TciOwned&) = delete;
+  TciOwned(TciOwned&& o) noexcept : t(o.t) { o.t = nullptr; }
+  ~TciOwned() {
+    if (t) tci_tensor_free(&t);
+  }
+  void reset(tci_tensor x) {
+    if (t) tci_tensor_free(&t);
+    t = x;
+  }
+  tci_tensor release() {
+    tci_tensor x = t;
+    t = nullptr;
+    return x;
+  }
+};
+
 // Strided permute-copy on the device (kernel K8): dst is row-major over
 // `shape`; src element (i0..i{n-1}) at offset sum_k i_k * src_strides[k].
 tci_status tci_launch_permute_copy(tci_context ctx, tci_dtype dt, int order, const int64_t* shape,

@@ -194,7 +194,7 @@ extern "C" tci_status tci_tebd_plan_create(tci_context ctx, int nbonds, const in
   if ((s = tci_dev_alloc(ctx, arena * 2, &p->arena)) != TCI_OK) return fail(s);
   if ((s = tci_dev_alloc(ctx, pels * 4, (void**)&p->P)) != TCI_OK) return fail(s);
   if ((s = tci_dev_alloc(ctx, sizeof(BondJob) * nbonds, (void**)&p->d_jobs)) != TCI_OK) return fail(s);
-  cudaError_t e = cudaMemcpy(p->d_jobs, jobs.data(), sizeof(BondJob) * nbonds, cudaMemcpyHostToDevice);
+  cudaError_t e = cudaMemcpyAsync(p->d_jobs, jobs.data(), sizeof(BondJob) * nbonds, cudaMemcpyHostToDevice, ctx->stream);
   if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "tebd plan: jobs"));
   std::vector<tci_split_problem> probs;
   __nv_bfloat16* A = (__nv_bfloat16*)p->arena;

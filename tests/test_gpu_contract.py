@@ -202,3 +202,14 @@ def test_contract_batch_bonds_match_oracle(ctx, tci, la, lb, lc, dims, dtype, pr
         return
     tol = 1e-13 if dtype in (np.float64, np.complex128) else 2e-6
     assert rel_frob_err(out, ref) < tol
+
+
+@pytest.mark.parametrize("la,lb,lc,shape", [("sab", "sAb", "aA", (3, 5, 4)),       # plain: Gram matrix
+                                            ("zsa", "zsA", "zaA", (6, 2, 7)),      # batch bond z
+                                            ("zsab", "zsAb", "zaA", (4, 2, 3, 5))])
+def test_contract_one_tensor_as_both_operands(ctx, tci, la, lb, lc, shape):
+    """The same handle passed as a and b: each operand keeps its own strides."""
+    A = random_tensor(list(shape), 8)
+    t = ctx.wrap(to_dev(A))
+    out = tci.contract_into(ctx, t, la, t, lb, None, lc).to_numpy()
+    np.testing.assert_allclose(out, o_contract(A, la, A, lb, lc), atol=1e-12)
