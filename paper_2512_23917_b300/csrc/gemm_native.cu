@@ -3,6 +3,11 @@
 // Operands are read in place through arbitrary (m,k)/(n,k) strides, so a
 // permuted operand needs no materialised transpose.  FP64 on B300 has no
 // fast tensor-core path, so a register-tiled FMA kernel is the FP64 roof.
+// When the output has too few tiles to fill the SMs and K is long (a batch
+// of small Gram-like products), K is split: each split writes a partial
+// product and a second kernel adds the partials in split order.
+#include <algorithm>
+
 #include "tci_internal.cuh"
 
 namespace {
@@ -17,6 +22,10 @@ __device__ __forceinline__ float2 fma_(float2 a, float2 b, float2 c) {
 __device__ __forceinline__ double2 fma_(double2 a, double2 b, double2 c) {
   return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
 }
+__device__ __forceinline__ float add_(float a, float b) { return a + b; }
+__device__ __forceinline__ double add_(double a, double b) { return a + b; }
+__device__ __forceinline__ float2 add_(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 add_(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 template <typename T> __device__ __forceinline__ T zero_();
 template <> __device__ __forceinline__ float zero_<float>() { return 0.f; }
 template <> __device__ __forceinline__ double zero_<double>() { return 0.0; }
@@ -31,11 +40,14 @@ template <typename T, int ACONT, int BCONT>
 __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64_t K, const T* __restrict__ A,
                                                      int64_t sam, int64_t sak, const T* __restrict__ B, int64_t sbn,
                                                      int64_t sbk, T* __restrict__ C, int64_t scm, int64_t scn,
-                                                     int64_t sab, int64_t sbb, int64_t scb) {
+                                                     int64_t sab, int64_t sbb, int64_t scb, int nsplit,
+                                                     int64_t kchunk, int64_t scs) {
   __shared__ T As[BK][BM + 1];
-  A += (int64_t)blockIdx.z * sab;
-  B += (int64_t)blockIdx.z * sbb;
-  C += (int64_t)blockIdx.z * scb;
+  const int64_t bz = blockIdx.z / nsplit, split = blockIdx.z % nsplit;
+  A += bz * sab;
+  B += bz * sbb;
+  C += bz * scb + split * scs;
+  const int64_t kb = split * kchunk, ke = kb + kchunk < K ? kb + kchunk : K;
   __shared__ T Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid % (BN / TN), ty = tid / (BN / TN);
@@ -46,14 +58,14 @@ __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = zero_<T>();
 
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kb; k0 < ke; k0 += BK) {
 #pragma unroll
     for (int r = 0; r < (BM * BK) / NT; ++r) {
       int e = tid + r * NT;
       int kk, mm;
       if (ACONT == 0) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
       int64_t gm = m0 + mm, gk = k0 + kk;
-      As[kk][mm] = (gm < M && gk < K) ? A[gm * sam + gk * sak] : zero_<T>();
+      As[kk][mm] = (gm < M && gk < ke) ? A[gm * sam + gk * sak] : zero_<T>();
     }
 #pragma unroll
     for (int r = 0; r < (BN * BK) / NT; ++r) {
@@ -61,7 +73,7 @@ __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64
       int kk, nn;
       if (BCONT == 0) { kk = e % BK; nn = e / BK; } else { nn = e % BN; kk = e / BN; }
       int64_t gn = n0 + nn, gk = k0 + kk;
-      Bs[kk][nn] = (gn < N && gk < K) ? B[gn * sbn + gk * sbk] : zero_<T>();
+      Bs[kk][nn] = (gn < N && gk < ke) ? B[gn * sbn + gk * sbk] : zero_<T>();
     }
     __syncthreads();
 #pragma unroll
@@ -90,6 +102,19 @@ __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64
   }
 }
 
+// C[b, m, n] = sum_s part[s][b][m][n] (splits added in order)
+template <typename T>
+__global__ void k_split_sum(const T* __restrict__ part, int nsplit, int64_t nb, int64_t M, int64_t N,
+                            T* __restrict__ C, int64_t scb, int64_t scm, int64_t scn) {
+  const int64_t per = nb * M * N;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x) {
+    T acc = part[i];
+    for (int s = 1; s < nsplit; ++s) acc = add_(acc, part[s * per + i]);
+    const int64_t b = i / (M * N), r = i - b * (M * N), m = r / N, n = r - m * N;
+    C[b * scb + m * scm + n * scn] = acc;
+  }
+}
+
 template <typename T>
 tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
                   int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C, int64_t scb,
@@ -98,22 +123,58 @@ tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t
   if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
   int ac = (sak == 1 || sam != 1) ? 0 : 1;
   int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
-  for (int64_t b0 = 0; b0 < nbatch; b0 += 65535) {
-    grid.z = (unsigned)(nbatch - b0 < 65535 ? nbatch - b0 : 65535);
+  // split K when the tiles cannot fill two waves and each split keeps >= 256 of K
+  const int64_t tiles = (int64_t)grid.x * grid.y * nbatch, want = 2 * (int64_t)ctx->num_sms;
+  int64_t nsplit = 1;
+  if (tiles < want && K >= 512) {
+    nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 256, 16});
+    if (nsplit < 1) nsplit = 1;
+  }
+  int64_t kchunk = K;
+  if (nsplit > 1) {
+    kchunk = ((K + nsplit - 1) / nsplit + BK - 1) / BK * BK;
+    nsplit = (K + kchunk - 1) / kchunk;
+  }
+  T* part = nullptr;
+  const int64_t per = nbatch * M * N;
+  if (nsplit > 1) TCI_TRY(tci_dev_alloc(ctx, sizeof(T) * nsplit * per, (void**)&part));
+  T* cout = nsplit > 1 ? part : (T*)C;
+  const int64_t ocb = nsplit > 1 ? M * N : scb, ocm = nsplit > 1 ? N : scm, ocn = nsplit > 1 ? 1 : scn;
+  const int64_t bmax = 65535 / nsplit;
+  tci_status st = TCI_OK;
+  for (int64_t b0 = 0; b0 < nbatch && st == TCI_OK; b0 += bmax) {
+    const int64_t nb = nbatch - b0 < bmax ? nbatch - b0 : bmax;
+    grid.z = (unsigned)(nb * nsplit);
     const T* a = (const T*)A + b0 * sab;
     const T* b = (const T*)B + b0 * sbb;
-    T* c = (T*)C + b0 * scb;
+    T* c = cout + b0 * ocb;
+    const int ns = (int)nsplit;
     if (ac == 0 && bc == 0)
-      k_gemm_strided<T, 0, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+      k_gemm_strided<T, 0, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
+                                                            ocb, ns, kchunk, per);
     else if (ac == 0 && bc == 1)
-      k_gemm_strided<T, 0, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+      k_gemm_strided<T, 0, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
+                                                            ocb, ns, kchunk, per);
     else if (ac == 1 && bc == 0)
-      k_gemm_strided<T, 1, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
+      k_gemm_strided<T, 1, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
+                                                            ocb, ns, kchunk, per);
     else
-      k_gemm_strided<T, 1, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, scm, scn, sab, sbb, scb);
-    TCI_CUDA(ctx, cudaGetLastError());
+      k_gemm_strided<T, 1, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
+                                                            ocb, ns, kchunk, per);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) st = tci_cuda_fail(ctx, e, "gemm launch");
   }
-  return TCI_OK;
+  if (nsplit > 1) {
+    if (st == TCI_OK) {
+      const int64_t blocks = std::min<int64_t>((per + 255) / 256, (int64_t)ctx->num_sms * 16);
+      k_split_sum<T><<<(unsigned)std::max<int64_t>(1, blocks), 256, 0, ctx->stream>>>(part, (int)nsplit, nbatch, M, N,
+                                                                                       (T*)C, scb, scm, scn);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) st = tci_cuda_fail(ctx, e, "gemm split sum");
+    }
+    tci_dev_free(part);
+  }
+  return st;
 }
 
 }  // namespace

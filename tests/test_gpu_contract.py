@@ -213,3 +213,18 @@ def test_contract_one_tensor_as_both_operands(ctx, tci, la, lb, lc, shape):
     t = ctx.wrap(to_dev(A))
     out = tci.contract_into(ctx, t, la, t, lb, None, lc).to_numpy()
     np.testing.assert_allclose(out, o_contract(A, la, A, lb, lc), atol=1e-12)
+
+
+@pytest.mark.parametrize("la,lb,lc,dims", [("zsab", "zsAb", "zaA", {"z": 3, "s": 2, "a": 20, "A": 20, "b": 3000}),
+                                           ("ik", "jk", "ij", {"i": 33, "j": 70, "k": 20000}),
+                                           ("kij", "kjl", "il", {"k": 7, "i": 5, "j": 2048, "l": 9})])
+@pytest.mark.parametrize("dtype", [np.float64, np.complex128, np.float32])
+def test_contract_split_k_matches_oracle(ctx, tci, la, lb, lc, dims, dtype):
+    """Few output tiles and a long summed bond: the native GEMM splits K and adds the partials in order."""
+    A = random_tensor([dims[c] for c in la], 5, dtype)
+    B = random_tensor([dims[c] for c in lb], 6, dtype)
+    wide = np.complex128 if np.iscomplexobj(A) else np.float64
+    ref = o_contract(A.astype(wide), la, B.astype(wide), lb, lc)
+    out = tci.contract(ctx, to_dev(A), la, to_dev(B), lb, lc).cpu().numpy()
+    tol = 1e-13 if dtype in (np.float64, np.complex128) else 2e-6
+    assert rel_frob_err(out, ref) < tol
