@@ -47,7 +47,8 @@ constexpr int GMAX = 20;         // basis vectors per fused pass
 constexpr int OFF_ALPHA = 0;
 constexpr int OFF_BETA = MAXM;
 constexpr int OFF_H = 2 * MAXM;          // MAXM + 1 entries: pass-1 coefficients
-constexpr int OFF_CTRL = 3 * MAXM + 8;   // [0] stop flag, [1] steps done, [2] theta, [3] sum of squares
+constexpr int OFF_CTRL = 3 * MAXM + 8;   // [0] stop flag, [1] steps done, [2] theta, [3] sum of squares,
+                                         // [4] pass-1 sum of squares, [5] [6] pass gates, [7] second passes
 constexpr int OFF_Y = 3 * MAXM + 16;     // Ritz coefficients
 constexpr int OFF_H2 = 4 * MAXM + 32;    // MAXM + 1 entries: pass-2 coefficients
 constexpr int NSCAL = 5 * MAXM + 64;
@@ -175,15 +176,17 @@ __device__ __forceinline__ void block_partials(const typename A::Acc (&a)[G], in
   }
 }
 
-// partials of <V_{v0+g}, w>, g < nv <= G, into part rows v0 + g
-template <class A, int G>
+// partials of <V_{v0+g}, w>, g < nv <= G, into part rows v0 + g; with SQ
+// also the partials of ||w||^2 into part_sq
+template <class A, int G, bool SQ>
 __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                              const typename A::V* __restrict__ w, int64_t n, double* __restrict__ part,
-                                             const double* __restrict__ ctrl) {
+                                             double* __restrict__ part_sq, const double* __restrict__ ctrl) {
   if (ctrl[0] != 0.0) return;
   typename A::Acc a[G];
 #pragma unroll
   for (int g = 0; g < G; ++g) a[g] = A::zero();
+  typename A::Acc q = A::zero();
   using Vt = typename A::V;
   const Vt* Vb = V + (int64_t)v0 * ldv;
   for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
@@ -191,8 +194,13 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
 #pragma unroll
     for (int g = 0; g < G; ++g)
       if (g < nv) A::acc(a[g], Vb[(int64_t)g * ldv + i], x);
+    if (SQ) A::acc(q, x, x);
   }
   block_partials<A, G>(a, nv, part + (int64_t)v0 * NBMAX);
+  if (SQ) {
+    const typename A::Acc qa[1] = {q};
+    block_partials<A, 1>(qa, 1, part_sq);
+  }
 }
 
 // w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
@@ -378,10 +386,30 @@ __global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int6
 
 // alpha_j = <v_j, H v_j> (the pass-1 coefficient of v_j); without
 // re-orthogonalisation the pass-3 coefficients are (beta_{j-1}, alpha_j).
-__global__ void k_post_pass1(double* scal, int j, int reorth) {
-  if (scal[OFF_CTRL] != 0.0) return;
+// With dgks, the second Gram-Schmidt pass is kept only where the first one
+// cancelled: ||w'||^2 = ||w||^2 - sum_i h_i^2 (V orthonormal) below
+// ||w||^2 / 2, i.e. ||w'|| < ||w|| / sqrt(2) (Daniel, Gragg, Kaufman & Stewart,
+// Math. Comp. 30, 1976).  Gates read by the passes that follow (a pass runs
+// while its gate is 0): ctrl[5] = 1 when the second pass is skipped (or the
+// iteration stopped), ctrl[6] = 1 when it is taken (or stopped).
+__global__ void k_post_pass1(double* scal, int j, int reorth, int dgks) {
+  double* ctrl = scal + OFF_CTRL;
+  if (ctrl[0] != 0.0) {
+    ctrl[5] = 1.0;
+    ctrl[6] = 1.0;
+    return;
+  }
   scal[OFF_ALPHA + j] = scal[OFF_H + j];
   if (!reorth && j > 0) scal[OFF_H + j - 1] = scal[OFF_BETA + j - 1];
+  bool second = true;
+  if (reorth && dgks) {
+    double h2 = 0.0;
+    for (int i = 0; i <= j; ++i) h2 += scal[OFF_H + i] * scal[OFF_H + i];
+    second = ctrl[4] - h2 < 0.5 * ctrl[4];
+  }
+  ctrl[5] = second ? 0.0 : 1.0;
+  ctrl[6] = second ? 1.0 : 0.0;
+  if (reorth && second) ctrl[7] += 1.0;   // second passes taken (reported with TCI_VERBOSE)
 }
 
 // beta_j = ||w||, stop test, step counter.
@@ -553,30 +581,34 @@ int wave_grid(tci_context ctx, const void* kernel) {
   return g;
 }
 
-template <class A, int G>
+template <class A, int G, bool SQ>
 int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                  int64_t n, double* part, const double* ctrl) {
-  const int grid = wave_grid(ctx, (const void*)k_dots<A, G>);
-  k_dots<A, G><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, ctrl);
+                  int64_t n, double* part, double* part_sq, const double* ctrl) {
+  const int grid = wave_grid(ctx, (const void*)k_dots<A, G, SQ>);
+  k_dots<A, G, SQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, part_sq, ctrl);
   return grid;
 }
 
-template <class A>
+template <class A, bool SQ>
 int dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                int64_t n, double* part, const double* ctrl) {
-  if (nv <= 8) return dots_launch_g<A, 8>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
-  if (nv <= 16) return dots_launch_g<A, 16>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
-  return dots_launch_g<A, GMAX>(ctx, V, ldv, v0, nv, w, n, part, ctrl);
+                int64_t n, double* part, double* part_sq, const double* ctrl) {
+  if (nv <= 8) return dots_launch_g<A, 8, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  if (nv <= 16) return dots_launch_g<A, 16, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
 }
 
-// out[0..nv) = <V_{v0+v}, w>
+// out[0..nv) = <V_{v0+v}, w>; *sumsq_out = ||w||^2 when sumsq_out
 template <class A>
 tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                    int64_t n, double* part, double* out, const double* ctrl) {
+                    int64_t n, double* part, double* out, const double* ctrl, double* sumsq_out = nullptr) {
+  double* part_sq = part + (int64_t)MAXM * NBMAX;
   for (int g0 = 0; g0 < nv; g0 += GMAX) {
     const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
-    const int grid = dots_launch<A>(ctx, V, ldv, v0 + g0, g, w, n, part, ctrl);
+    const bool sq = sumsq_out && g0 == 0;
+    const int grid = sq ? dots_launch<A, true>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl)
+                        : dots_launch<A, false>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl);
     k_reduce_parts<<<g, 256, 0, ctx->stream>>>(part + (int64_t)(v0 + g0) * NBMAX, g, grid, out + g0, ctrl);
+    if (sq) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, grid, sumsq_out, ctrl);
   }
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
@@ -687,13 +719,19 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       k_from_f64<A><<<NBMAX, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
     }
     if (reorth) {
-      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl));
-      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1);
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, nullptr, ctrl));
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, ctrl));
+      // classical Gram-Schmidt against the whole basis, repeated where the first
+      // pass cancelled (DGKS); both continuations are launched, each gated
+      const int dgks = j + 1 <= GMAX ? 1 : 0;
+      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, dgks ? ctrl + 4 : nullptr));
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks);
+      // second pass taken: w -= V h with the new dots, then w -= V h2 with ||w||^2
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, nullptr, ctrl + 5));
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, ctrl + 5));
+      // second pass skipped: w -= V h with ||w||^2
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6));
     } else {
       TCI_TRY(run_dots<A>(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl));
-      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0);
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0, 0);
       const int v0 = j > 0 ? j - 1 : 0;
       TCI_TRY(run_update<A>(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl));
     }
@@ -755,12 +793,13 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     if (split) TCI_TRY((lanczos_run<ArithF64, kInPieces>(p, psi, nsteps, reorth, xd, tol)));
     else TCI_TRY((lanczos_run<ArithF64, kInNone>(p, psi, nsteps, reorth, xd, tol)));
   }
-  TCI_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctrl, 4 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TCI_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctrl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   std::vector<double> ab(2 * MAXM);
   TCI_CUDA(ctx, cudaMemcpyAsync(ab.data(), S, 2 * MAXM * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
   TCI_TRY(tci_synchronize(ctx));
   const int k = (int)ctx->h_scalars[1];
   *ritz = ctx->h_scalars[2];
+  if (ctx->verbose > 0 && reorth) vs.info += " second_gs_passes=" + std::to_string((int)ctx->h_scalars[7]);
   if (steps_done) *steps_done = k;
   for (int i = 0; i < nsteps; ++i) {
     if (alpha) alpha[i] = i < k ? ab[OFF_ALPHA + i] : 0.0;
