@@ -352,6 +352,17 @@ def run_gpu(args):
     torch.cuda.synchronize()
     lanczos_df_ms = e0.elapsed_time(e1)
     plan.set_lanczos_arith("f64")
+    # ---- the same solve with the second Gram-Schmidt pass in every step (CGS2)
+    plan.set_gram_schmidt("twice")
+    plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res_cgs2 = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lanczos_cgs2_ms = e0.elapsed_time(e1)
+    plan.set_gram_schmidt("dgks")
 
     # ---- per-stage events of single matvecs (roofline of the GEMM kernel)
     stages = []
@@ -458,6 +469,9 @@ def run_gpu(args):
             "clocks": clocks, "ritz_value": res["theta"] if res else None,
             "autotune": {"chunk_k": tuned[0], "xchunk_k": tuned[1], "raster": tuned[2], "max_chunk_k": 256,
                          "ww_a_per_thread": plan.get_config()[3]},
+            "lanczos_cgs2_every_step": {"ms_per_step": lanczos_cgs2_ms, "ritz_value": res_cgs2["theta"],
+                                        "ritz_rel_diff_vs_dgks": abs(res_cgs2["theta"] - res["theta"]) / abs(res["theta"])
+                                        if res else None},
             "lanczos_double_float_vectors": {"ms_per_step": lanczos_df_ms, "ritz_value": res_df["theta"],
                                              "ritz_rel_diff_vs_fp64": abs(res_df["theta"] - res["theta"]) / abs(res["theta"])
                                              if res else None},

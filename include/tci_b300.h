@@ -423,9 +423,22 @@ typedef enum {
  * Errors: INVALID_ARG (invalid plan or value), INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_arith(tci_heff_plan plan, tci_lanczos_arith arith);
 
+/* Re-orthogonalisation of tci_lanczos (extension).  Every step projects
+ * H v_j against the whole basis by classical Gram-Schmidt.
+ * TCI_GS_DGKS (default): the projection is repeated only where the first
+ * one cancelled, ||w'|| < ||w|| / sqrt(2) (Daniel, Gragg, Kaufman & Stewart,
+ * Math. Comp. 30, 1976); where it is not repeated the second projection
+ * would change w only at rounding level.  TCI_GS_TWICE: always twice (CGS2).
+ * Errors: INVALID_ARG (invalid plan or value), INVALID_CONTEXT. */
+typedef enum {
+  TCI_GS_DGKS = 0,
+  TCI_GS_TWICE = 1
+} tci_gram_schmidt;
+tci_status tci_heff_set_gram_schmidt(tci_heff_plan plan, tci_gram_schmidt mode);
+
 /* Lanczos ground state of H_eff (textbook; Golub & Van Loan Sec. 10.1 with
- * classical Gram-Schmidt applied twice when reorth != 0; Ritz value by Sturm
- * bisection, Sec. 8.4).  All vector work runs on the device, in the
+ * full classical Gram-Schmidt re-orthogonalisation when reorth != 0, see
+ * tci_heff_set_gram_schmidt; Ritz value by Sturm bisection, Sec. 8.4).  All vector work runs on the device, in the
  * arithmetic chosen by tci_heff_set_lanczos_arith (FP64 by default);
  * scalars (alpha, beta, Gram-Schmidt coefficients, the tridiagonal
  * eigenpair) are FP64.

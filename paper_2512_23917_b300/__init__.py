@@ -100,6 +100,7 @@ SIGNATURES = [
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
+    ("tci_heff_set_gram_schmidt", C.c_int, [_p, C.c_int]),
     ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
     ("tci_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
     ("tci_trunc_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), _dp, C.c_int64,
@@ -553,6 +554,12 @@ class HeffPlan:
     def set_lanczos_arith(self, arith: str):
         """Vector arithmetic of lanczos(): "auto", "f64" or "df32" (double-float FP32 pairs)."""
         _check(lib.tci_heff_set_lanczos_arith(self.handle, self.LANCZOS_ARITH[arith]), self.ctx.handle)
+
+    GRAM_SCHMIDT = {"dgks": 0, "twice": 1}
+
+    def set_gram_schmidt(self, mode: str):
+        """Re-orthogonalisation of lanczos(): "dgks" (second pass where the first cancelled) or "twice"."""
+        _check(lib.tci_heff_set_gram_schmidt(self.handle, self.GRAM_SCHMIDT[mode]), self.ctx.handle)
 
     def lanczos(self, psi0, nsteps: int, reorth: bool = True, x=None):
         ritz = C.c_double()

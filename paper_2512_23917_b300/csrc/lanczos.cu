@@ -721,7 +721,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     if (reorth) {
       // classical Gram-Schmidt against the whole basis, repeated where the first
       // pass cancelled (DGKS); both continuations are launched, each gated
-      const int dgks = j + 1 <= GMAX ? 1 : 0;
+      const int dgks = (p->gs_mode == TCI_GS_DGKS && j + 1 <= GMAX) ? 1 : 0;
       TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, dgks ? ctrl + 4 : nullptr));
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks);
       // second pass taken: w -= V h with the new dots, then w -= V h2 with ||w||^2
@@ -814,5 +814,14 @@ extern "C" tci_status tci_heff_set_lanczos_arith(tci_heff_plan p, tci_lanczos_ar
   if (arith != TCI_LANCZOS_AUTO && arith != TCI_LANCZOS_F64 && arith != TCI_LANCZOS_DF32)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_lanczos_arith: unknown arithmetic %d", (int)arith);
   p->vec_arith = (int)arith;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_gram_schmidt(tci_heff_plan p, tci_gram_schmidt mode) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_gram_schmidt: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (mode != TCI_GS_DGKS && mode != TCI_GS_TWICE)
+    return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_gram_schmidt: unknown mode %d", (int)mode);
+  p->gs_mode = (int)mode;
   return TCI_OK;
 }

@@ -54,6 +54,7 @@ def test_null_arguments_are_rejected_without_a_device():
     assert tci.lib.tci_heff_set_config(None, cfg) == 1
     assert tci.lib.tci_heff_get_config(None, cfg) == 1
     assert tci.lib.tci_heff_set_lanczos_arith(None, 2) == 1
+    assert tci.lib.tci_heff_set_gram_schmidt(None, 1) == 1
 
 
 @pytest.mark.skipif(os.path.exists("/dev/nvidia0"), reason="only meaningful without a GPU")

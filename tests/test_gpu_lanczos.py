@@ -13,10 +13,11 @@ pytestmark = pytest.mark.gpu
 ARITH = ["f64", "df32"]
 
 
-def gpu_lanczos(tci, ctx, L, W, R, psi0, m, precision="native", arith="auto", reorth=True):
+def gpu_lanczos(tci, ctx, L, W, R, psi0, m, precision="native", arith="auto", reorth=True, gs="dgks"):
     import torch
     plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision=precision)
     plan.set_lanczos_arith(arith)
+    plan.set_gram_schmidt(gs)
     x = torch.empty(psi0.shape, dtype=torch.float64, device="cuda")
     res = plan.lanczos(to_dev(psi0), m, reorth, x)
     res["x"] = x.cpu().numpy()
@@ -44,10 +45,11 @@ def test_ed_through_gpu_lanczos(ctx, tci, nl, nr, arith):
     assert abs(r["theta"] - e0) < 1e-10
 
 
+@pytest.mark.parametrize("gs", ["dgks", "twice"])
 @pytest.mark.parametrize("arith", ARITH)
-def test_lanczos_chi32_matches_oracle(ctx, tci, arith):
+def test_lanczos_chi32_matches_oracle(ctx, tci, arith, gs):
     psi, L, R, W = dense_heff_inputs(32, seed=20251223)
-    r = gpu_lanczos(tci, ctx, L, W, R, psi, 20, arith=arith)
+    r = gpu_lanczos(tci, ctx, L, W, R, psi, 20, arith=arith, gs=gs)
     mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
     o = o_lanczos.lanczos(mv, psi, 20)
     assert r["steps"] == o["steps"] == 20
