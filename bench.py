@@ -596,6 +596,30 @@ def run_itebd(args):
     ctx.close()
 
 
+def run_profile_bs(args):
+    """The U(1) block-sparse matvec (total chi 2048, 31 sectors) applied warmup + steps times, for ncu captures."""
+    import torch
+    import paper_2512_23917_b300 as tci
+    from tci_synth import MPO_CHANNEL_CHARGE, PHYS_CHARGE, blocksparse_inputs, blocksparse_structure
+    inp = blocksparse_inputs(total=2048, seed=SEED)
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    ctx = tci.Context(0, precision="split_bf16")
+    plan = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                          t(tci.pack_blocks(inp["L"], st["L"])), t(tci.pack_blocks(inp["R"], st["R"])), t(inp["W"]))
+    psi = t(tci.pack_blocks(inp["psi"], st["psi"]))
+    out = torch.empty_like(psi)
+    tuned = plan.autotune(psi, max_chunk_k=256)
+    for _ in range(args.warmup + args.steps):
+        plan.apply(psi, out)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": "U(1) block-sparse H_eff, total chi 2048, 31 sectors", "config": list(tuned),
+                      "matvecs": args.warmup + args.steps, "launches_per_matvec": 4}))
+    plan.close()
+    ctx.close()
+
+
 def run_profile_tebd(args):
     """The batched TEBD theta workload (256 bonds) applied warmup + steps times, for ncu captures."""
     import torch
@@ -656,6 +680,7 @@ def main():
     ap.add_argument("--profile-lanczos", action="store_true",
                     help="with --profile-chi: run 20-step Lanczos solves instead of single matvecs")
     ap.add_argument("--profile-tebd", action="store_true", help="run only the batched TEBD workload (for ncu)")
+    ap.add_argument("--profile-bs", action="store_true", help="run only the block-sparse matvec workload (for ncu)")
     ap.add_argument("--dmrg", action="store_true", help="time two-site DMRG sweeps (device vs oracle) instead")
     ap.add_argument("--dmrg-sites", type=int, default=32)
     ap.add_argument("--dmrg-chi", type=int, default=64)
@@ -684,6 +709,8 @@ def main():
         run_bp(args)
     elif args.profile_tebd:
         run_profile_tebd(args)
+    elif args.profile_bs:
+        run_profile_bs(args)
     elif args.profile_chi:
         run_profile_case(args)
     elif args.impl == "reference":
