@@ -344,6 +344,88 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       const int64_t PM = pr->M, PN = pr->N, scm = pr->scm, scn = pr->scn;
       void* const PC = pr->C;
       const int out_mode = pr->out_mode;
+      if (nkb > 0 && nkb <= p.kb_d1 && nkb <= p.kb_x) {
+        // One accumulation unit of each kind (short K, e.g. small sector blocks):
+        // fold hi*hi and the cross products while storing, without the running
+        // double-float sum.  FP64 output is the exact D1 + X, FP32 output its
+        // single rounding, the pair output the error-free TwoSum pair.
+        bool got = ptx::mbar_wait_bounded(ptx::smem_u32(&d1f[u1 & 1]), (u1 >> 1) & 1, abort_flag, p.wait_ns);
+        if (got) got = ptx::mbar_wait_bounded(ptx::smem_u32(&xf[ux & 1]), (ux >> 1) & 1, abort_flag, p.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        const uint32_t td = tmem + lane_base + (u1 & 1) * TBN + c0;
+        const uint32_t tx = tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0;
+        const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
+        const int64_t n0 = (int64_t)nb * TBN + c0;
+#pragma unroll
+        for (int g = 0; g < COLS_PER_WARP / 16; ++g) {
+          uint32_t vd[16], vx[16];
+          ptx::tmem_ld_32x32b_x16(td + g * 16, vd);
+          ptx::tmem_ld_32x32b_x16(tx + g * 16, vx);
+          ptx::tmem_ld_wait();
+          if (row >= PM) continue;
+          const int64_t ng = n0 + g * 16;
+          if (out_mode == 1) {
+            float* crow = (float*)PC + row * scm;
+            const bool vec = scn == 1 && ((((uintptr_t)(crow + ng)) & 15) == 0) && ng + 16 <= PN;
+#pragma unroll
+            for (int j = 0; j < 16; j += 4) {
+              const float4 o = make_float4(__uint_as_float(vd[j]) + __uint_as_float(vx[j]),
+                                           __uint_as_float(vd[j + 1]) + __uint_as_float(vx[j + 1]),
+                                           __uint_as_float(vd[j + 2]) + __uint_as_float(vx[j + 2]),
+                                           __uint_as_float(vd[j + 3]) + __uint_as_float(vx[j + 3]));
+              if (vec) {
+                *(float4*)(crow + ng + j) = o;
+              } else {
+                if (ng + j < PN) crow[(ng + j) * scn] = o.x;
+                if (ng + j + 1 < PN) crow[(ng + j + 1) * scn] = o.y;
+                if (ng + j + 2 < PN) crow[(ng + j + 2) * scn] = o.z;
+                if (ng + j + 3 < PN) crow[(ng + j + 3) * scn] = o.w;
+              }
+            }
+          } else if (out_mode == 2) {
+            float2* crow = (float2*)PC + row * scm;
+            const bool vec = scn == 1 && ((((uintptr_t)(crow + ng)) & 15) == 0) && ng + 16 <= PN;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              float4 o;
+              two_sum(__uint_as_float(vd[j]), __uint_as_float(vx[j]), o.x, o.y);
+              two_sum(__uint_as_float(vd[j + 1]), __uint_as_float(vx[j + 1]), o.z, o.w);
+              if (vec) {
+                *(float4*)(crow + ng + j) = o;
+              } else {
+                if (ng + j < PN) crow[(ng + j) * scn] = make_float2(o.x, o.y);
+                if (ng + j + 1 < PN) crow[(ng + j + 1) * scn] = make_float2(o.z, o.w);
+              }
+            }
+          } else {
+            double* crow = (double*)PC + row * scm;
+            const bool vec = scn == 1 && ((((uintptr_t)(crow + ng)) & 15) == 0) && ng + 16 <= PN;
+#pragma unroll
+            for (int j = 0; j < 16; j += 2) {
+              const double2 o = make_double2((double)__uint_as_float(vd[j]) + (double)__uint_as_float(vx[j]),
+                                             (double)__uint_as_float(vd[j + 1]) + (double)__uint_as_float(vx[j + 1]));
+              if (vec) {
+                *(double2*)(crow + ng + j) = o;
+              } else {
+                if (ng + j < PN) crow[(ng + j) * scn] = o.x;
+                if (ng + j + 1 < PN) crow[(ng + j + 1) * scn] = o.y;
+              }
+            }
+          }
+        }
+        ptx::tc_fence_before();
+        if (lane == 0) {
+          ptx::mbar_arrive(ptx::smem_u32(&d1e[u1 & 1]));
+          ptx::mbar_arrive(ptx::smem_u32(&xe[ux & 1]));
+        }
+        ++u1;
+        ++ux;
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < COLS_PER_WARP; ++j) rh[j] = 0.f;
 #pragma unroll
