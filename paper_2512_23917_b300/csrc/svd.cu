@@ -46,44 +46,37 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// One block per pair (p, q): rows p and q of W (length m) and of Q (length nq).
-// A pair is rotated when |g| > tol ||x|| ||y|| (relative) and |g| > abs_tol
-// (the rotation would move the matrix by more than rounding noise of its
-// Frobenius norm); without the absolute test, vectors of negligible norm are
-// re-rotated forever by the rounding noise of the large ones.
-__global__ void __launch_bounds__(kSvdT) k_jacobi_round(double* __restrict__ W, int64_t m, double* __restrict__ Q,
-                                                        int64_t nq, const int2* __restrict__ pairs, double tol,
-                                                        double abs_tol, int* __restrict__ rotated) {
+// One block of kRotT threads per pair (p, q): rows p and q of W (length m)
+// and of Q (length nq).  The squared row norms are tracked in nrm2 (exact at
+// the start of every sweep) and updated by Rutishauser's formulas
+// ||x'||^2 = ||x||^2 - t g, ||y'||^2 = ||y||^2 + t g, so a pair costs one dot
+// product instead of three: FP64 issue slots, not bytes, bound a round on
+// B300.  A pair is rotated when |g| > tol ||x|| ||y|| (relative) and
+// |g| > abs_tol (the rotation would move the matrix by more than rounding
+// noise of its Frobenius norm); without the absolute test, vectors of
+// negligible norm are re-rotated forever by the rounding noise of the large
+// ones.  A sweep without rotations decides convergence on exact norms.
+constexpr int kRotT = 128;
+
+__global__ void __launch_bounds__(kRotT) k_jacobi_round(double* __restrict__ W, int64_t m, double* __restrict__ Q,
+                                                        int64_t nq, const int2* __restrict__ pairs,
+                                                        double* __restrict__ nrm2, double tol, double abs_tol,
+                                                        int* __restrict__ rotated) {
   const int2 pq = pairs[blockIdx.x];
   double* wp = W + (int64_t)pq.x * m;
   double* wq = W + (int64_t)pq.y * m;
-  double a = 0.0, b = 0.0, g = 0.0;
-  for (int64_t i = threadIdx.x; i < m; i += kSvdT) {
-    const double x = wp[i], y = wq[i];
-    a = fma(x, x, a);
-    b = fma(y, y, b);
-    g = fma(x, y, g);
-  }
-  __shared__ double red[3][kSvdT / 32];
+  double g = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += kRotT) g = fma(wp[i], wq[i], g);
+  __shared__ double red[kRotT / 32];
   __shared__ double cs[2];
   __shared__ int rot;
-  a = warp_sum_d(a);
-  b = warp_sum_d(b);
   g = warp_sum_d(g);
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    red[0][wid] = a;
-    red[1][wid] = b;
-    red[2][wid] = g;
-  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double A = 0.0, B = 0.0, G = 0.0;
-    for (int k = 0; k < kSvdT / 32; ++k) {
-      A += red[0][k];
-      B += red[1][k];
-      G += red[2][k];
-    }
+    double G = 0.0;
+    for (int k = 0; k < kRotT / 32; ++k) G += red[k];
+    const double A = nrm2[pq.x], B = nrm2[pq.y];
     rot = 0;
     if (fabs(G) > abs_tol && fabs(G) > tol * sqrt(A * B)) {
       const double zeta = (B - A) / (2.0 * G);
@@ -91,6 +84,8 @@ __global__ void __launch_bounds__(kSvdT) k_jacobi_round(double* __restrict__ W, 
       const double c = 1.0 / sqrt(1.0 + t * t);
       cs[0] = c;
       cs[1] = c * t;
+      nrm2[pq.x] = fmax(A - t * G, 0.0);
+      nrm2[pq.y] = B + t * G;
       rot = 1;
       atomicExch(rotated, 1);
     }
@@ -98,17 +93,33 @@ __global__ void __launch_bounds__(kSvdT) k_jacobi_round(double* __restrict__ W, 
   __syncthreads();
   if (!rot) return;
   const double c = cs[0], s = cs[1];
-  for (int64_t i = threadIdx.x; i < m; i += kSvdT) {
+  for (int64_t i = threadIdx.x; i < m; i += kRotT) {
     const double x = wp[i], y = wq[i];
     wp[i] = c * x - s * y;
     wq[i] = s * x + c * y;
   }
   double* qp = Q + (int64_t)pq.x * nq;
   double* qq = Q + (int64_t)pq.y * nq;
-  for (int64_t i = threadIdx.x; i < nq; i += kSvdT) {
+  for (int64_t i = threadIdx.x; i < nq; i += kRotT) {
     const double x = qp[i], y = qq[i];
     qp[i] = c * x - s * y;
     qq[i] = s * x + c * y;
+  }
+}
+
+// sq[r] = ||W_r||^2 (one block per row)
+__global__ void __launch_bounds__(kSvdT) k_row_sumsq(const double* __restrict__ W, int64_t m, double* __restrict__ sq) {
+  const double* w = W + (int64_t)blockIdx.x * m;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += kSvdT) a = fma(w[i], w[i], a);
+  __shared__ double red[kSvdT / 32];
+  a = warp_sum_d(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kSvdT / 32; ++k) s += red[k];
+    sq[blockIdx.x] = s;
   }
 }
 
@@ -393,8 +404,9 @@ struct SvdWork {
   double* Vn = nullptr;     // n x n length-n singular vectors
   double* Uc = nullptr;     // chi x m length-m singular vectors (sorted)
   int* iota = nullptr;      // chi
+  double* rn2 = nullptr;    // n tracked squared norms of the Jacobi rows
   void free_all() {
-    void* ps[] = {W, Q, norms, pairs, flag, perm, R, tau, nrm2, qperm, Vn, Uc, iota};
+    void* ps[] = {W, Q, norms, pairs, flag, perm, R, tau, nrm2, qperm, Vn, Uc, iota, rn2};
     for (void* p : ps) tci_dev_free(p);
   }
 };
@@ -495,12 +507,15 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
   }
   const double tol = sqrt((double)mj) * 2.220446049250313e-16;
   int sweeps = 0;
+  if (!w.rn2 && (st = tci_dev_alloc(ctx, sizeof(double) * n, (void**)&w.rn2)) != TCI_OK) return fail(st);
   for (; sweeps < kMaxSweeps && !pairs.empty(); ++sweeps) {
     cudaMemsetAsync(w.flag, 0, sizeof(int), ctx->stream);
+    k_row_sumsq<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.rn2);   // exact norms each sweep
     for (size_t r = 0; r + 1 < start.size(); ++r) {
       const int np = start[r + 1] - start[r];
       if (np > 0)
-        k_jacobi_round<<<np, kSvdT, 0, ctx->stream>>>(Wj, mj, w.Q, n, w.pairs + start[r], tol, abs_tol, w.flag);
+        k_jacobi_round<<<np, kRotT, 0, ctx->stream>>>(Wj, mj, w.Q, n, w.pairs + start[r], w.rn2, tol, abs_tol,
+                                                        w.flag);
     }
     int rotated = 0;
     e = cudaMemcpyAsync(&rotated, w.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
