@@ -107,6 +107,77 @@ __global__ void __launch_bounds__(kRotT) k_jacobi_round(double* __restrict__ W, 
   }
 }
 
+// The same round with both row pairs (W and Q) held in registers, E elements
+// per thread (m, nq <= kRotT * E): every row is loaded once, before the
+// reduction, and the squared norms are fetched at the same time, so a round
+// costs one memory round trip instead of four.
+template <int E>
+__global__ void __launch_bounds__(kRotT) k_jacobi_round_reg(double* __restrict__ W, int64_t m,
+                                                            double* __restrict__ Q, int64_t nq,
+                                                            const int2* __restrict__ pairs,
+                                                            double* __restrict__ nrm2, double tol, double abs_tol,
+                                                            int* __restrict__ rotated) {
+  const int2 pq = pairs[blockIdx.x];
+  double* wp = W + (int64_t)pq.x * m;
+  double* wq = W + (int64_t)pq.y * m;
+  double* qp = Q + (int64_t)pq.x * nq;
+  double* qq = Q + (int64_t)pq.y * nq;
+  double A = 0.0, B = 0.0;
+  if (threadIdx.x == 0) {
+    A = nrm2[pq.x];
+    B = nrm2[pq.y];
+  }
+  double x[E], y[E], u[E], v[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t i = threadIdx.x + (int64_t)e * kRotT;
+    x[e] = i < m ? wp[i] : 0.0;
+    y[e] = i < m ? wq[i] : 0.0;
+    u[e] = i < nq ? qp[i] : 0.0;
+    v[e] = i < nq ? qq[i] : 0.0;
+  }
+  double g = 0.0;
+#pragma unroll
+  for (int e = 0; e < E; ++e) g = fma(x[e], y[e], g);
+  __shared__ double red[kRotT / 32];
+  __shared__ double cs[2];
+  __shared__ int rot;
+  g = warp_sum_d(g);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double G = 0.0;
+    for (int k = 0; k < kRotT / 32; ++k) G += red[k];
+    rot = 0;
+    if (fabs(G) > abs_tol && fabs(G) > tol * sqrt(A * B)) {
+      const double zeta = (B - A) / (2.0 * G);
+      const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+      const double c = 1.0 / sqrt(1.0 + t * t);
+      cs[0] = c;
+      cs[1] = c * t;
+      nrm2[pq.x] = fmax(A - t * G, 0.0);
+      nrm2[pq.y] = B + t * G;
+      rot = 1;
+      atomicExch(rotated, 1);
+    }
+  }
+  __syncthreads();
+  if (!rot) return;
+  const double c = cs[0], s = cs[1];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t i = threadIdx.x + (int64_t)e * kRotT;
+    if (i < m) {
+      wp[i] = c * x[e] - s * y[e];
+      wq[i] = s * x[e] + c * y[e];
+    }
+    if (i < nq) {
+      qp[i] = c * u[e] - s * v[e];
+      qq[i] = s * u[e] + c * v[e];
+    }
+  }
+}
+
 // sq[r] = ||W_r||^2 (one block per row)
 __global__ void __launch_bounds__(kSvdT) k_row_sumsq(const double* __restrict__ W, int64_t m, double* __restrict__ sq) {
   const double* w = W + (int64_t)blockIdx.x * m;
@@ -359,6 +430,21 @@ __global__ void k_iota(int* __restrict__ p, int64_t n) {
     p[i] = (int)i;
 }
 
+void launch_round(tci_context ctx, int np, double* W, int64_t m, double* Q, int64_t nq, const int2* pairs,
+                  double* nrm2, double tol, double abs_tol, int* rotated) {
+  const int64_t len = m > nq ? m : nq;
+  if (len <= kRotT)
+    k_jacobi_round_reg<1><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+  else if (len <= 2 * kRotT)
+    k_jacobi_round_reg<2><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+  else if (len <= 4 * kRotT)
+    k_jacobi_round_reg<4><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+  else if (len <= 8 * kRotT)
+    k_jacobi_round_reg<8><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+  else   // longer rows: the register copies would cost occupancy (measured slower at 2048)
+    k_jacobi_round<<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+}
+
 int grid_of(tci_context ctx, int64_t n) {
   int64_t b = (n + 255) / 256;
   const int64_t cap = (int64_t)ctx->num_sms * 16;
@@ -514,8 +600,7 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
     for (size_t r = 0; r + 1 < start.size(); ++r) {
       const int np = start[r + 1] - start[r];
       if (np > 0)
-        k_jacobi_round<<<np, kRotT, 0, ctx->stream>>>(Wj, mj, w.Q, n, w.pairs + start[r], w.rn2, tol, abs_tol,
-                                                        w.flag);
+        launch_round(ctx, np, Wj, mj, w.Q, n, w.pairs + start[r], w.rn2, tol, abs_tol, w.flag);
     }
     int rotated = 0;
     e = cudaMemcpyAsync(&rotated, w.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
