@@ -58,53 +58,125 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // ones.  A sweep without rotations decides convergence on exact norms.
 constexpr int kRotT = 128;
 
+// Long rows (the generic round): plane rotations in scaled form.  A row is
+// kept as d_i times its stored values (W and Q rows share d_i, which is 1 at
+// the start of every sweep); rotating actual rows x = d_p x~, y = d_q y~ by
+// (c, s = c t) gives x' = c d_p (x~ - t (d_q / d_p) y~) and
+// y' = c d_q (y~ + t (d_p / d_q) x~), so the stored rows take one FMA per
+// element each and the scales are multiplied by c (the fast Givens idea of
+// Gentleman, 1973; the rounding error per element is the same as that of
+// the explicit rotation).  A scale that would fall below 2^-400 is folded
+// into its row by an explicit rotation instead.
 __global__ void __launch_bounds__(kRotT) k_jacobi_round(double* __restrict__ W, int64_t m, double* __restrict__ Q,
                                                         int64_t nq, const int2* __restrict__ pairs,
-                                                        double* __restrict__ nrm2, double tol, double abs_tol,
-                                                        int* __restrict__ rotated) {
+                                                        double* __restrict__ nrm2, double* __restrict__ dsc,
+                                                        double tol, double abs_tol, int* __restrict__ rotated) {
   const int2 pq = pairs[blockIdx.x];
   double* wp = W + (int64_t)pq.x * m;
   double* wq = W + (int64_t)pq.y * m;
   double g = 0.0;
   for (int64_t i = threadIdx.x; i < m; i += kRotT) g = fma(wp[i], wq[i], g);
   __shared__ double red[kRotT / 32];
-  __shared__ double cs[2];
+  __shared__ double cf[4];
   __shared__ int rot;
   g = warp_sum_d(g);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = g;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double G = 0.0;
-    for (int k = 0; k < kRotT / 32; ++k) G += red[k];
+    double Gs = 0.0;
+    for (int k = 0; k < kRotT / 32; ++k) Gs += red[k];
+    const double dp = dsc[pq.x], dq = dsc[pq.y];
+    const double G = dp * dq * Gs;
     const double A = nrm2[pq.x], B = nrm2[pq.y];
     rot = 0;
     if (fabs(G) > abs_tol && fabs(G) > tol * sqrt(A * B)) {
       const double zeta = (B - A) / (2.0 * G);
       const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
       const double c = 1.0 / sqrt(1.0 + t * t);
-      cs[0] = c;
-      cs[1] = c * t;
       nrm2[pq.x] = fmax(A - t * G, 0.0);
       nrm2[pq.y] = B + t * G;
-      rot = 1;
+      const double np_ = c * dp, nq_ = c * dq;
+      if (np_ > 0x1p-400 && nq_ > 0x1p-400) {
+        cf[0] = -t * (dq / dp);   // x~' = x~ + cf0 y~
+        cf[1] = t * (dp / dq);    // y~' = y~ + cf1 x~
+        dsc[pq.x] = np_;
+        dsc[pq.y] = nq_;
+        rot = 1;
+      } else {                    // explicit rotation of the actual rows, scales back to 1
+        const double s = c * t;
+        cf[0] = c * dp;
+        cf[1] = -s * dq;
+        cf[2] = s * dp;
+        cf[3] = c * dq;
+        dsc[pq.x] = 1.0;
+        dsc[pq.y] = 1.0;
+        rot = 2;
+      }
       atomicExch(rotated, 1);
     }
   }
   __syncthreads();
   if (!rot) return;
-  const double c = cs[0], s = cs[1];
-  for (int64_t i = threadIdx.x; i < m; i += kRotT) {
-    const double x = wp[i], y = wq[i];
-    wp[i] = c * x - s * y;
-    wq[i] = s * x + c * y;
-  }
   double* qp = Q + (int64_t)pq.x * nq;
   double* qq = Q + (int64_t)pq.y * nq;
-  for (int64_t i = threadIdx.x; i < nq; i += kRotT) {
-    const double x = qp[i], y = qq[i];
-    qp[i] = c * x - s * y;
-    qq[i] = s * x + c * y;
+  if (rot == 1) {
+    const double f0 = cf[0], f1 = cf[1];
+    for (int64_t i = threadIdx.x; i < m; i += kRotT) {
+      const double x = wp[i], y = wq[i];
+      wp[i] = fma(f0, y, x);
+      wq[i] = fma(f1, x, y);
+    }
+    for (int64_t i = threadIdx.x; i < nq; i += kRotT) {
+      const double x = qp[i], y = qq[i];
+      qp[i] = fma(f0, y, x);
+      qq[i] = fma(f1, x, y);
+    }
+  } else {
+    const double a11 = cf[0], a12 = cf[1], a21 = cf[2], a22 = cf[3];
+    for (int64_t i = threadIdx.x; i < m; i += kRotT) {
+      const double x = wp[i], y = wq[i];
+      wp[i] = fma(a11, x, a12 * y);
+      wq[i] = fma(a21, x, a22 * y);
+    }
+    for (int64_t i = threadIdx.x; i < nq; i += kRotT) {
+      const double x = qp[i], y = qq[i];
+      qp[i] = fma(a11, x, a12 * y);
+      qq[i] = fma(a21, x, a22 * y);
+    }
   }
+}
+
+// Fold the scales into the rows (W and Q), reset them to 1 and take the exact
+// squared norms of the W rows (one block per row).
+__global__ void __launch_bounds__(kSvdT) k_fold_scales(double* __restrict__ W, int64_t m, double* __restrict__ Q,
+                                                       int64_t nq, double* __restrict__ dsc,
+                                                       double* __restrict__ sq) {
+  const int64_t r = blockIdx.x;
+  const double d = dsc[r];
+  double* w = W + r * m;
+  double* q = Q + r * nq;
+  double a = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += kSvdT) {
+    const double x = d * w[i];
+    if (d != 1.0) w[i] = x;
+    a = fma(x, x, a);
+  }
+  if (d != 1.0)
+    for (int64_t i = threadIdx.x; i < nq; i += kSvdT) q[i] *= d;
+  __shared__ double red[kSvdT / 32];
+  a = warp_sum_d(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < kSvdT / 32; ++k) s += red[k];
+    sq[r] = s;
+    dsc[r] = 1.0;
+  }
+}
+
+__global__ void k_fill(double* __restrict__ p, int64_t n, double v) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
 }
 
 // The same round with both row pairs (W and Q) held in registers, E elements
@@ -431,7 +503,7 @@ __global__ void k_iota(int* __restrict__ p, int64_t n) {
 }
 
 void launch_round(tci_context ctx, int np, double* W, int64_t m, double* Q, int64_t nq, const int2* pairs,
-                  double* nrm2, double tol, double abs_tol, int* rotated) {
+                  double* nrm2, double* dsc, double tol, double abs_tol, int* rotated) {
   const int64_t len = m > nq ? m : nq;
   if (len <= kRotT)
     k_jacobi_round_reg<1><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
@@ -442,8 +514,10 @@ void launch_round(tci_context ctx, int np, double* W, int64_t m, double* Q, int6
   else if (len <= 8 * kRotT)
     k_jacobi_round_reg<8><<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
   else   // longer rows: the register copies would cost occupancy (measured slower at 2048)
-    k_jacobi_round<<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, tol, abs_tol, rotated);
+    k_jacobi_round<<<np, kRotT, 0, ctx->stream>>>(W, m, Q, nq, pairs, nrm2, dsc, tol, abs_tol, rotated);
 }
+
+bool round_uses_registers(int64_t m, int64_t nq) { return (m > nq ? m : nq) <= 8 * kRotT; }
 
 int grid_of(tci_context ctx, int64_t n) {
   int64_t b = (n + 255) / 256;
@@ -491,8 +565,9 @@ struct SvdWork {
   double* Uc = nullptr;     // chi x m length-m singular vectors (sorted)
   int* iota = nullptr;      // chi
   double* rn2 = nullptr;    // n tracked squared norms of the Jacobi rows
+  double* dsc = nullptr;    // n row scales of the scaled rotations
   void free_all() {
-    void* ps[] = {W, Q, norms, pairs, flag, perm, R, tau, nrm2, qperm, Vn, Uc, iota, rn2};
+    void* ps[] = {W, Q, norms, pairs, flag, perm, R, tau, nrm2, qperm, Vn, Uc, iota, rn2, dsc};
     for (void* p : ps) tci_dev_free(p);
   }
 };
@@ -594,13 +669,22 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
   const double tol = sqrt((double)mj) * 2.220446049250313e-16;
   int sweeps = 0;
   if (!w.rn2 && (st = tci_dev_alloc(ctx, sizeof(double) * n, (void**)&w.rn2)) != TCI_OK) return fail(st);
+  const bool scaled = !round_uses_registers(mj, n);   // scaled rotations in the generic round
+  if (scaled) {
+    if ((st = tci_dev_alloc(ctx, sizeof(double) * n, (void**)&w.dsc)) != TCI_OK) return fail(st);
+    k_fill<<<grid_of(ctx, n), 256, 0, ctx->stream>>>(w.dsc, n, 1.0);
+  }
   for (; sweeps < kMaxSweeps && !pairs.empty(); ++sweeps) {
     cudaMemsetAsync(w.flag, 0, sizeof(int), ctx->stream);
-    k_row_sumsq<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.rn2);   // exact norms each sweep
+    // exact norms each sweep (scales folded into the rows first)
+    if (scaled)
+      k_fold_scales<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.Q, n, w.dsc, w.rn2);
+    else
+      k_row_sumsq<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.rn2);
     for (size_t r = 0; r + 1 < start.size(); ++r) {
       const int np = start[r + 1] - start[r];
       if (np > 0)
-        launch_round(ctx, np, Wj, mj, w.Q, n, w.pairs + start[r], w.rn2, tol, abs_tol, w.flag);
+        launch_round(ctx, np, Wj, mj, w.Q, n, w.pairs + start[r], w.rn2, w.dsc, tol, abs_tol, w.flag);
     }
     int rotated = 0;
     e = cudaMemcpyAsync(&rotated, w.flag, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream);
@@ -609,6 +693,7 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
     if (!rotated) break;
   }
   if (sweeps == kMaxSweeps) return fail(tci_fail(ctx, TCI_ERR_TIMEOUT, "svd: Jacobi sweeps did not converge"));
+  if (scaled) k_fold_scales<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.Q, n, w.dsc, w.rn2);
   t_last_sweeps = sweeps;
   // singular values, sorted
   k_row_norms<<<(unsigned)n, kSvdT, 0, ctx->stream>>>(Wj, mj, w.norms);

@@ -110,3 +110,14 @@ def test_dmrg_split_precision_close_to_ed(ctx, tci):
         ctx.set_precision("native")
     e0 = ed_ground(10)
     assert abs(e[-1] - e0) < 1e-6 * abs(e0)
+
+
+@pytest.mark.parametrize("shape,k", [((1100, 1100), 1), ((5000, 20), 1), ((12, 3000), 1)])
+def test_svd_long_rows_match_oracle(ctx, tci, shape, k):
+    """Rows longer than 1024 take the scaled-rotation round (with and without QR preconditioning)."""
+    a = random_tensor(shape, 31)
+    u, s, vt = tci.svd(ctx, _tensor(tci, ctx, a), k)
+    u, s, vt = u.to_numpy(), s.to_numpy(), vt.to_numpy()
+    rs = o_linalg.svd(a, k)[1]
+    np.testing.assert_allclose(s, rs, rtol=1e-12, atol=1e-12 * rs.max())
+    _check_svd(a, k, u, s, vt, 1e-12)
