@@ -178,12 +178,12 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU path
 def lanczos_launches(m: int) -> int:
-    """Kernel launches of one m-step Lanczos solve on a split-BF16 plan with CGS2 (basis <= 24 vectors)."""
+    """Kernel launches of one m-step Lanczos solve on a split-BF16 plan (basis <= 20 vectors, DGKS)."""
     n = 4                                           # init scalars, psi0 sum of squares + reduce, start vector
     for j in range(m):
         n += 3                                      # GEMM1, W.W, GEMM2 (the split is fused into the next-vector kernel)
-        n += 2 + 1                                  # pass-1 dots + reduce, alpha
-        n += 2 + 2                                  # pass-2 update+dots + reduce, pass-3 update+norm + reduce
+        n += 3 + 1                                  # pass-1 dots + reduce + sum-of-squares reduce, alpha / DGKS test
+        n += 2 + 2 + 2                              # gated: update+dots, update+norm (second pass); update+norm
         n += 1                                      # beta / stop test
         if j + 1 < m:
             n += 1                                  # v_{j+1} = w / beta and its bfloat16 pieces

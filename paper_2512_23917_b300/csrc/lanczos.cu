@@ -581,10 +581,20 @@ int wave_grid(tci_context ctx, const void* kernel) {
   return g;
 }
 
+// Grid of a vector pass over n elements: one wave, but no more blocks than
+// give each thread 8 elements (short vectors, e.g. DMRG bonds of small chi,
+// would otherwise spend the pass on empty blocks and a long partial-sum
+// reduction).  Fixed per (kernel, device, n), so reductions stay deterministic.
+int pass_grid(tci_context ctx, const void* kernel, int64_t n) {
+  const int g = wave_grid(ctx, kernel);
+  const int64_t cap = (n + (int64_t)NT * 8 - 1) / ((int64_t)NT * 8);
+  return cap < g ? (int)(cap < 1 ? 1 : cap) : g;
+}
+
 template <class A, int G, bool SQ>
 int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
                   int64_t n, double* part, double* part_sq, const double* ctrl) {
-  const int grid = wave_grid(ctx, (const void*)k_dots<A, G, SQ>);
+  const int grid = pass_grid(ctx, (const void*)k_dots<A, G, SQ>, n);
   k_dots<A, G, SQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, part_sq, ctrl);
   return grid;
 }
@@ -617,7 +627,7 @@ tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
 template <class A, int G, bool DOTS, bool SUMSQ>
 int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                     typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
-  const int grid = wave_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ>);
+  const int grid = pass_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ>, n);
   k_update<A, G, DOTS, SUMSQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
   return grid;
 }
