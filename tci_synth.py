@@ -257,3 +257,12 @@ def bp_tns_inputs(n: int, edges, chi: int, seed: int = DEFAULT_SEED, d: int = 2)
     V = [rng.standard_normal((d,) + (chi,) * deg[i]) for i in range(n)]
     M = [np.eye(chi) / np.sqrt(chi) for _ in range(2 * len(edges))]
     return V, M
+
+
+def complex_heff_inputs(chi: int, seed: int = DEFAULT_SEED, chi_r: int | None = None, Dw: int = 3, d: int = 2):
+    """Complex H_eff inputs: psi[chi,d,d,chi_r], L[chi,Dw,chi], R[chi_r,Dw,chi_r], W[Dw,Dw,d,d],
+    complex128 with N(0,1) real and imaginary parts (numpy PCG64 from ``seed``)."""
+    chi_r = chi if chi_r is None else chi_r
+    rng = np.random.default_rng(seed)
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    return c(chi, d, d, chi_r), c(chi, Dw, chi), c(chi_r, Dw, chi_r), c(Dw, Dw, d, d)

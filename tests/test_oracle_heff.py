@@ -144,3 +144,14 @@ def test_flop_count_formula():
     chi = 2048
     assert heff.heff_flops(chi) == 4 * chi ** 3 * 4 * 5 + 2 * chi ** 2 * 16 * 25
     assert abs(heff.heff_flops(2048) - 6.905e11) / 6.905e11 < 1e-3
+
+
+@pytest.mark.parametrize("chi,chi_r,Dw,d", [(2, 3, 2, 2), (3, 2, 3, 3)])
+def test_complex_heff_matches_explicit_matrix(chi, chi_r, Dw, d):
+    """Complex L, W, R, psi: both contraction orders equal the loop-built dense matrix (no conjugation)."""
+    from tci_synth import complex_heff_inputs
+    psi, L, R, W = complex_heff_inputs(chi, 7, chi_r, Dw, d)
+    H = heff.heff_matrix_loops(L, W, R)
+    ref = (H @ psi.ravel()).reshape(psi.shape)
+    for order in ("L", "R"):
+        np.testing.assert_allclose(heff.heff_apply(L, W, R, psi, order), ref, atol=1e-12)
