@@ -289,7 +289,13 @@ tci_status tci_close(tci_context ctx, tci_tensor a, tci_tensor b, double eps, in
  * in the plan's arithmetic, W W pre-contracted), so the caller may free L,
  * W, R after creation.  Arithmetic: the context precision at creation
  * (NATIVE = FP64 everywhere; SPLIT_BF16[_3] = tensor-core contraction,
- * output FP64).  Errors: SHAPE, DTYPE, ALLOC, CUDA. */
+ * output FP64).
+ * Complex plans: L, W, R all C128 (any Dw >= 1, d >= 1; psi and out C128
+ * [chiL, d, d, chiR]).  Such a plan applies H_eff as four tci_contract calls
+ * in native complex FP64 arithmetic, (psi R) W W L, on copies it owns;
+ * tci_heff_apply and tci_heff_flops (8 real flops per complex multiply-add)
+ * accept it, every other plan call returns UNSUPPORTED.
+ * Errors: SHAPE, DTYPE, ALLOC, CUDA. */
 tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
                                 tci_heff_plan* plan);
 tci_status tci_heff_plan_destroy(tci_heff_plan* plan);

@@ -162,6 +162,7 @@ tci_status heff_run_cfg(void* a, const tci_gemm_cfg& cfg) {
 
 extern "C" tci_status tci_heff_autotune(tci_heff_plan p, tci_tensor psi, tci_tensor out, int max_chunk_k, int* chosen) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_autotune: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "heff_autotune: complex plans support tci_heff_apply only");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "heff_autotune");
@@ -195,6 +196,7 @@ extern "C" tci_status tci_heff_autotune(tci_heff_plan p, tci_tensor psi, tci_ten
 
 extern "C" tci_status tci_heff_get_config(tci_heff_plan p, int* cfg) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_get_config: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "heff_get_config: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (!cfg) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_get_config: NULL cfg");
   const bool split = p->prec != TCI_PREC_NATIVE;
@@ -207,6 +209,7 @@ extern "C" tci_status tci_heff_get_config(tci_heff_plan p, int* cfg) {
 
 extern "C" tci_status tci_heff_set_config(tci_heff_plan p, const int* cfg) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_set_config: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "heff_set_config: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (!cfg) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_set_config: NULL cfg");
   if (p->prec == TCI_PREC_NATIVE) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "heff_set_config: FP64 plan has no configuration");

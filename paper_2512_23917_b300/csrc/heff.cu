@@ -272,6 +272,63 @@ int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 
 }  // namespace
 
+// ------------------------------------------------------------------ complex plans
+// H_eff on C128 tensors through the library's own contraction (native
+// complex FP64), in the order (psi R) W W L:
+//   U0[x,i,j,b,r] = sum_y psi[x,i,j,y] R[b,r,y]
+//   U1[x,i,b,m,u] = sum_{r,j} U0[x,i,j,b,r] W[m,r,u,j]
+//   U2[x,b,u,s,w] = sum_{m,i} U1[x,i,b,m,u] W[w,m,s,i]
+//   out[a,s,u,b]  = sum_{w,x} L[a,w,x] U2[x,b,u,s,w]
+static tci_status complex_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R, tci_heff_plan* out) {
+  if (L->dtype != TCI_C128 || W->dtype != TCI_C128 || R->dtype != TCI_C128)
+    return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_create: a complex plan needs L, W, R all C128");
+  if (L->order != 3 || R->order != 3 || W->order != 4)
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L[chi,Dw,chi], W[Dw,Dw,d,d], R[chi,Dw,chi]");
+  const int64_t Dw = W->shape[0], d = W->shape[2], chiL = L->shape[0], chiR = R->shape[0];
+  if (Dw < 1 || d < 1 || W->shape[1] != Dw || W->shape[3] != d || L->shape[1] != Dw || L->shape[2] != chiL ||
+      R->shape[1] != Dw || R->shape[2] != chiR || chiL < 1 || chiR < 1)
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: inconsistent complex L/W/R shapes");
+  tci_heff_plan p = new tci_heff_plan_s();
+  p->magic = kPlanMagic;
+  p->ctx = ctx;
+  p->chiL = chiL;
+  p->chiR = chiR;
+  p->prec = TCI_PREC_NATIVE;
+  p->cplx = true;
+  p->cd = d;
+  p->cDw = Dw;
+  tci_status s = tci_copy(ctx, L, &p->cL);
+  if (s == TCI_OK) s = tci_copy(ctx, W, &p->cW);
+  if (s == TCI_OK) s = tci_copy(ctx, R, &p->cR);
+  if (s != TCI_OK) {
+    tci_heff_plan_destroy(&p);
+    return s;
+  }
+  *out = p;
+  return TCI_OK;
+}
+
+static tci_status complex_apply(tci_heff_plan p, tci_tensor psi, tci_tensor out) {
+  tci_context ctx = p->ctx;
+  for (tci_tensor t : {psi, out}) {
+    if (!tci_ten_ok(t)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_apply: invalid tensor");
+    if (t->dtype != TCI_C128) return tci_fail(ctx, TCI_ERR_DTYPE, "heff_apply: a complex plan takes C128 psi and out");
+    if (t->order != 4 || t->shape[0] != p->chiL || t->shape[1] != p->cd || t->shape[2] != p->cd || t->shape[3] != p->chiR)
+      return tci_fail(ctx, TCI_ERR_SHAPE, "heff_apply: psi and out must be [%lld,%lld,%lld,%lld]", (long long)p->chiL,
+                      (long long)p->cd, (long long)p->cd, (long long)p->chiR);
+  }
+  if (psi->data == out->data) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_apply: psi and out overlap");
+  TCI_TRY(tci_contract(ctx, psi, "xijy", p->cR, "bry", &p->cU[0], "xijbr"));
+  TCI_TRY(tci_contract(ctx, p->cU[0], "xijbr", p->cW, "mruj", &p->cU[1], "xibmu"));
+  TCI_TRY(tci_contract(ctx, p->cU[1], "xibmu", p->cW, "wmsi", &p->cU[2], "xbusw"));
+  tci_tensor o = out;
+  return tci_contract(ctx, p->cL, "awx", p->cU[2], "xbusw", &o, "asub");
+}
+
+static tci_status complex_unsupported(tci_heff_plan p, const char* what) {
+  return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "%s: complex plans support tci_heff_apply only", what);
+}
+
 // ------------------------------------------------------------------ plan
 extern "C" tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
                                            tci_heff_plan* out) {
@@ -280,6 +337,7 @@ extern "C" tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_te
   if (!out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: NULL output");
   *out = nullptr;
   if (!tci_ten_ok(L) || !tci_ten_ok(W) || !tci_ten_ok(R)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: invalid tensor");
+  if (L->dtype == TCI_C128 || W->dtype == TCI_C128 || R->dtype == TCI_C128) return complex_plan_create(ctx, L, W, R, out);
   if (L->dtype != TCI_F64 || W->dtype != TCI_F64 || R->dtype != TCI_F64)
     return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_create: L, W, R must be F64");
   if (L->order != 3 || R->order != 3 || W->order != 4) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L[chi,Dw,chi], W[Dw,Dw,d,d], R[chi,Dw,chi]");
@@ -359,6 +417,8 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
                   p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
   for (void* b : bufs) tci_dev_free(b);
+  for (tci_tensor* t : {&p->cL, &p->cW, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2]})
+    if (*t) tci_tensor_free(t);
   for (int i = 0; i < 8; ++i) {
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);
     if (p->ev_out[i]) cudaEventDestroy(p->ev_out[i]);
@@ -373,6 +433,10 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
 
 extern "C" double tci_heff_flops(tci_heff_plan p) {
   if (!p || p->magic != kPlanMagic) return 0.0;
+  if (p->cplx) {   // complex multiply-adds of the four contractions, 8 real flops each
+    const double chiL = (double)p->chiL, chiR = (double)p->chiR, d = (double)p->cd, Dw = (double)p->cDw;
+    return 8.0 * (chiL * d * d * chiR * Dw * (chiL + chiR) + 2.0 * chiL * chiR * d * d * d * Dw * Dw);
+  }
   const double chiL = (double)p->chiL, chiR = (double)p->chiR, d = 2.0, Dw = HEFF_DW;
   return 2.0 * chiL * d * d * chiR * Dw * (chiL + chiR) + 2.0 * chiL * chiR * d * d * d * d * Dw * Dw;
 }
@@ -442,6 +506,7 @@ static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, f
 
 extern "C" tci_status tci_heff_apply_timed(tci_heff_plan p, tci_tensor psi, tci_tensor out, float* stage_ms) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply_timed: invalid plan");
+  if (p->cplx) return complex_unsupported(p, "heff_apply_timed");
   TCI_CHECK_CTX(p->ctx);
   if (!stage_ms) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_apply_timed: NULL stage_ms");
   TCI_TRY(check_vec(p, psi, "heff_apply_timed psi"));
@@ -463,6 +528,7 @@ extern "C" tci_status tci_heff_apply(tci_heff_plan p, tci_tensor psi, tci_tensor
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply: invalid plan");
   TCI_CHECK_CTX(p->ctx);
   TciVerboseScope vs(p->ctx, "heff_apply");
+  if (p->cplx) return complex_apply(p, psi, out);
   TCI_TRY(check_vec(p, psi, "heff_apply psi"));
   TCI_TRY(check_vec(p, out, "heff_apply out"));
   if (psi->data == out->data) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "heff_apply: psi and out overlap");
@@ -533,6 +599,7 @@ static tci_status apply_host_pipelined(tci_heff_plan p, const double* psi_host, 
 
 extern "C" tci_status tci_heff_apply_host(tci_heff_plan p, const double* psi_host, double* out_host) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_apply_host: invalid plan");
+  if (p->cplx) return complex_unsupported(p, "heff_apply_host");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "heff_apply_host");

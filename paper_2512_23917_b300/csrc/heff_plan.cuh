@@ -20,6 +20,10 @@ struct tci_heff_plan_s {
   int ww_na = 4;      // split W.W kernel: a' per thread (2 or 4, autotuned)
   int vec_arith = 0;  // Lanczos vector arithmetic: 0 auto, 1 FP64, 2 double-float (FP32 pairs)
   int gs_mode = 0;    // Lanczos re-orthogonalisation: 0 DGKS second pass, 1 always twice
+  // complex (C128) plan: owned copies of L, W, R and the contraction intermediates
+  bool cplx = false;
+  int64_t cd = 0, cDw = 0;
+  tci_tensor cL = nullptr, cW = nullptr, cR = nullptr, cU[3] = {nullptr, nullptr, nullptr};
   double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
   // intermediates
   void* U = nullptr;       // FP64 [(a',t1,t2), (b,wr)] (native) or FP32 U^T [(b,wr), (a',t1,t2)] (split)

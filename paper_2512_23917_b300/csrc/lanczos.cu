@@ -760,6 +760,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
 extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, int reorth, double* ritz, double* alpha,
                                   double* beta, int* steps_done, tci_tensor x) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "lanczos: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "lanczos: complex plans support tci_heff_apply only");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "lanczos");
@@ -820,6 +821,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
 
 extern "C" tci_status tci_heff_set_lanczos_arith(tci_heff_plan p, tci_lanczos_arith arith) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_arith: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "set_lanczos_arith: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (arith != TCI_LANCZOS_AUTO && arith != TCI_LANCZOS_F64 && arith != TCI_LANCZOS_DF32)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_lanczos_arith: unknown arithmetic %d", (int)arith);
@@ -829,6 +831,7 @@ extern "C" tci_status tci_heff_set_lanczos_arith(tci_heff_plan p, tci_lanczos_ar
 
 extern "C" tci_status tci_heff_set_gram_schmidt(tci_heff_plan p, tci_gram_schmidt mode) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_gram_schmidt: invalid plan");
+  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "set_gram_schmidt: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (mode != TCI_GS_DGKS && mode != TCI_GS_TWICE)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_gram_schmidt: unknown mode %d", (int)mode);

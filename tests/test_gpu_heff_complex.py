@@ -1,0 +1,55 @@
+"""Complex (C128) H_eff plans: four native complex contractions vs the oracle."""
+import numpy as np
+import pytest
+
+from oracle import heff as o_heff
+from oracle.contract import rel_frob_err
+from tci_synth import complex_heff_inputs, heisenberg_mpo
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("chi,chi_r,Dw,d", [(7, 13, 3, 2), (33, 17, 5, 2), (64, 64, 5, 2), (5, 9, 4, 3)])
+def test_complex_heff_matches_oracle(ctx, tci, chi, chi_r, Dw, d):
+    import torch
+    psi, L, R, W = complex_heff_inputs(chi, 11, chi_r, Dw, d)
+    plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native")
+    out = torch.full(psi.shape, complex("nan"), dtype=torch.complex128, device="cuda")
+    plan.apply(_dev(psi), out)
+    torch.cuda.synchronize()
+    ref = o_heff.heff_apply(L, W, R, psi)
+    assert rel_frob_err(out.cpu().numpy(), ref) < 1e-13
+    assert plan.flops == 8.0 * (chi * d * d * chi_r * Dw * (chi + chi_r) + 2.0 * chi * chi_r * d ** 3 * Dw ** 2)
+
+
+def test_complex_heff_with_a_real_mpo_equals_two_real_matvecs(ctx, tci):
+    """H_eff is linear: with real L, W, R the complex matvec acts on Re psi and Im psi separately."""
+    import torch
+    from tci_synth import dense_heff_inputs
+    psi_r, L, R, W = dense_heff_inputs(24, seed=3)
+    psi_i = dense_heff_inputs(24, seed=4)[0]
+    c = lambda a: _dev(a.astype(np.complex128))
+    plan = tci.HeffPlan(ctx, c(L), c(W), c(R), precision="native")
+    out = torch.empty(psi_r.shape, dtype=torch.complex128, device="cuda")
+    plan.apply(_dev(psi_r + 1j * psi_i), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert rel_frob_err(got.real, o_heff.heff_apply(L, W, R, psi_r)) < 1e-13
+    assert rel_frob_err(got.imag, o_heff.heff_apply(L, W, R, psi_i)) < 1e-13
+
+
+def test_complex_plan_rejects_other_calls(ctx, tci):
+    import torch
+    psi, L, R, W = complex_heff_inputs(8, 2, 8, 5, 2)
+    plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native")
+    with pytest.raises(RuntimeError):
+        plan.lanczos(_dev(psi.real.copy()), 4)
+    with pytest.raises(RuntimeError):
+        plan.apply(_dev(psi.real.copy()), torch.empty(psi.shape, dtype=torch.float64, device="cuda"))
+    with pytest.raises(RuntimeError):
+        tci.HeffPlan(ctx, _dev(L), _dev(W.real.copy()), _dev(R), precision="native")
