@@ -1,21 +1,25 @@
 // Lanczos ground-state solve of H_eff on the device (textbook: Golub &
-// Van Loan Sec. 10.1; classical Gram-Schmidt applied twice for full
-// re-orthogonalisation; Sturm-sequence bisection, Sec. 8.4, and inverse
-// iteration for the tridiagonal eigenpair).
+// Van Loan Sec. 10.1; full re-orthogonalisation by classical Gram-Schmidt,
+// repeated where the first projection cancelled (Daniel, Gragg, Kaufman &
+// Stewart 1976) or in every step on request; Sturm-sequence bisection,
+// Sec. 8.4, and inverse iteration for the tridiagonal eigenpair).
 //
 // One step j, with the basis V = [v_0 .. v_j] resident in HBM:
 //   w = H v_j                                   (the matvec; its input was
 //                                                prepared with v_j)
-//   pass 1: h = V^T w;  alpha_j = h_j            (one read of V and w)
-//   pass 2: w -= V h, then h' = V^T w            (fused: V read once, w r/w)
-//   pass 3: w -= V h', then ||w||^2              (fused)
+//   pass 1: h = V^T w, ||w||^2;  alpha_j = h_j   (one read of V and w)
+//   DGKS test: ||w - V h||^2 = ||w||^2 - |h|^2 < ||w||^2 / 2 ?
+//   taken:   pass 2: w -= V h, then h' = V^T w   (fused: V read once, w r/w)
+//            pass 3: w -= V h', then ||w||^2     (fused)
+//   skipped: pass 2': w -= V h, then ||w||^2     (fused)
+//   (all three passes are launched; device gates make the unused ones exit)
 //   beta_j = ||w||;  v_{j+1} = w / beta_j, written with the next matvec's
 //   input (its bfloat16 pieces on a split-BF16 plan) in the same pass.
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
-// = beta_{j-1} up to rounding), so passes 1-3 equal the three-term step
-// followed by two classical Gram-Schmidt passes.  Without re-orthogonal-
-// isation: pass 1 takes only alpha_j and pass 3 subtracts alpha_j v_j +
-// beta_{j-1} v_{j-1}.
+// = beta_{j-1} up to rounding), so the step equals the three-term step
+// followed by one or two classical Gram-Schmidt passes.  Without
+// re-orthogonalisation: pass 1 takes only alpha_j and the last pass
+// subtracts alpha_j v_j + beta_{j-1} v_{j-1}.
 //
 // Vector arithmetic (a policy template over the same kernels):
 //   FP64          every product and sum in FP64 (the default);
