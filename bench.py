@@ -428,8 +428,17 @@ def run_gpu(args):
         torch.cuda.synchronize()
         s64 = plan64.apply_timed(dpsi, out64)
         fp64_ms = float(sum(s64))
+        # FP64 roof: no measured FP64 peak exists; derived as 148 SMs x 2 FP64 FMA lanes per clock
+        # x 2 flops x the maximum SM clock (ncu shows the FP64 GEMM's pipe 99 % busy at that rate)
+        fp64_peak = 148 * 2 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        g64 = float(sum(s64[1:4:2]))
+        fp64_gemm_tf = (F - 2.0 * CHI * CHI * 16 * 25) / (g64 * 1e-3) / 1e12
         extra["fp64_path"] = {"gflops": F / (fp64_ms * 1e-3) / 1e9, "ms_per_matvec": fp64_ms,
-                              "stage_ms": [float(v) for v in s64]}
+                              "stage_ms": [float(v) for v in s64],
+                              "roofline": {"bound": "fp64", "kernel": "k_gemm_strided<double>",
+                                           "achieved": fp64_gemm_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                                           "frac": fp64_gemm_tf / fp64_peak,
+                                           "peak_source": "derived: 148 SMs x 2 FP64 FMA/clk x 2 x max SM clock"}}
         extra["split_vs_fp64_speedup"] = fp64_ms / mv_ms
         # error of the split matvec against the CPU oracle on sampled rows
         from oracle.contract import rel_frob_err
