@@ -18,21 +18,23 @@ import numpy as np
 from .contract import contract
 
 
-def heff_apply(L, W, R, psi, order: str = "R"):
+def heff_apply(L, W, R, psi, order: str = "R", W2=None):
     """H_eff . psi in float64 as four pairwise contractions.
 
-    order="L": (L psi) W W R;  order="R": (psi R) W W L.
+    W acts on the left site, W2 (default: W) on the right one.
+    order="L": (L psi) W W2 R;  order="R": (psi R) W2 W L.
     Labels: a/x = bra/ket left bond, b/y = bra/ket right bond, w/m/r = MPO
     bonds (left, middle, right), s/u = bra physical, i/j = ket physical.
     """
+    W2 = W if W2 is None else W2
     if order == "L":
         T = contract(L, "awx", psi, "xijy", "awijy")
         T = contract(T, "awijy", W, "wmsi", "amsjy")
-        T = contract(T, "amsjy", W, "mruj", "asury")
+        T = contract(T, "amsjy", W2, "mruj", "asury")
         return contract(T, "asury", R, "bry", "asub")
     if order == "R":
         U = contract(psi, "xijy", R, "bry", "xijbr")
-        U = contract(U, "xijbr", W, "mruj", "xibmu")
+        U = contract(U, "xijbr", W2, "mruj", "xibmu")
         U = contract(U, "xibmu", W, "wmsi", "xbusw")
         return contract(L, "awx", U, "xbusw", "asub")
     raise ValueError(order)
@@ -48,13 +50,14 @@ def heff_rows(L, W, R, psi, rows):
     return heff_apply(L[rows], W, R, psi, order="L")
 
 
-def heff_matrix_loops(L, W, R):
-    """Dense H_eff[(a,s1,s2,b), (a',t1,t2,b')] by explicit loops (chi <= 3)."""
+def heff_matrix_loops(L, W, R, W2=None):
+    """Dense H_eff[(a,s1,s2,b), (a',t1,t2,b')] by explicit loops (chi <= 3); W2 (default W) on the right site."""
+    W2 = W if W2 is None else W2
     chi_l, Dw, _ = L.shape
     chi_r = R.shape[0]
     d = W.shape[2]
     n = chi_l * d * d * chi_r
-    H = np.zeros((n, n), dtype=np.result_type(L, W, R))
+    H = np.zeros((n, n), dtype=np.result_type(L, W, W2, R))
 
     def idx(a, s1, s2, b):
         return ((a * d + s1) * d + s2) * chi_r + b
@@ -72,7 +75,7 @@ def heff_matrix_loops(L, W, R):
                                         for wm in range(Dw):
                                             for wr in range(Dw):
                                                 acc += (L[a, wl, ap] * W[wl, wm, s1, t1]
-                                                        * W[wm, wr, s2, t2] * R[b, wr, bp])
+                                                        * W2[wm, wr, s2, t2] * R[b, wr, bp])
                                     H[idx(a, s1, s2, b), idx(ap, t1, t2, bp)] = acc
     return H
 

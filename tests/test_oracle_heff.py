@@ -155,3 +155,15 @@ def test_complex_heff_matches_explicit_matrix(chi, chi_r, Dw, d):
     ref = (H @ psi.ravel()).reshape(psi.shape)
     for order in ("L", "R"):
         np.testing.assert_allclose(heff.heff_apply(L, W, R, psi, order), ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("order", ["L", "R"])
+def test_two_different_site_mpos_match_explicit_matrix(order):
+    """W on the left site and W2 on the right one (a non-uniform MPO): both orders equal the loops."""
+    rng = np.random.default_rng(12)
+    L, R = rng.standard_normal((3, 5, 3)), rng.standard_normal((2, 5, 2))
+    W, W2 = rng.standard_normal((5, 5, 2, 2)), rng.standard_normal((5, 5, 2, 2))
+    psi = rng.standard_normal((3, 2, 2, 2))
+    ref = (heff.heff_matrix_loops(L, W, R, W2) @ psi.ravel()).reshape(psi.shape)
+    np.testing.assert_allclose(heff.heff_apply(L, W, R, psi, order, W2=W2), ref, atol=1e-12)
+    assert np.abs(heff.heff_apply(L, W, R, psi, order) - ref).max() > 1e-3     # W2 matters
