@@ -298,6 +298,12 @@ tci_status tci_close(tci_context ctx, tci_tensor a, tci_tensor b, double eps, in
  * Errors: SHAPE, DTYPE, ALLOC, CUDA. */
 tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
                                 tci_heff_plan* plan);
+/* Same with a different MPO tensor on each site: W acts on the left site
+ * (s1, t1), W2 on the right one (s2, t2), i.e. W W2 in the formula above
+ * (non-uniform MPOs).  W2 has W's dtype and shape.  tci_heff_plan_create is
+ * this call with W2 = W.  Errors: as tci_heff_plan_create. */
+tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
+                                 tci_heff_plan* plan);
 tci_status tci_heff_plan_destroy(tci_heff_plan* plan);
 /* out = H_eff psi (async).  psi and out must not overlap. */
 tci_status tci_heff_apply(tci_heff_plan plan, tci_tensor psi, tci_tensor out);

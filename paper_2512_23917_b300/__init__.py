@@ -100,6 +100,7 @@ SIGNATURES = [
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
+    ("tci_heff_plan_create2", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(_p)]),
     ("tci_heff_set_gram_schmidt", C.c_int, [_p, C.c_int]),
     ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
     ("tci_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
@@ -498,15 +499,21 @@ def close(ctx: Context, a, b, eps: float) -> bool:
 class HeffPlan:
     """Two-site H_eff plan (see include/tci_b300.h, tci_heff_plan_create)."""
 
-    def __init__(self, ctx: Context, L, W, R, precision=None):
+    def __init__(self, ctx: Context, L, W, R, precision=None, W2=None):
+        """``W2`` (optional): a different MPO tensor for the right site (tci_heff_plan_create2)."""
         if precision is not None:
             ctx.set_precision(precision)
         self.ctx = ctx
         self.handle = _p()
         self.chiL, self.chiR = L.shape[0], R.shape[0]
         tl, tw, tr = ctx.wrap(L), ctx.wrap(W), ctx.wrap(R)
-        _check(lib.tci_heff_plan_create(ctx.handle, tl.handle, tw.handle, tr.handle, C.byref(self.handle)),
-               ctx.handle)
+        if W2 is None:
+            _check(lib.tci_heff_plan_create(ctx.handle, tl.handle, tw.handle, tr.handle, C.byref(self.handle)),
+                   ctx.handle)
+        else:
+            tw2 = ctx.wrap(W2)
+            _check(lib.tci_heff_plan_create2(ctx.handle, tl.handle, tw.handle, tw2.handle, tr.handle,
+                                             C.byref(self.handle)), ctx.handle)
         self._psi_wrap = {}
 
     @property

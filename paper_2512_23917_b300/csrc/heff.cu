@@ -21,7 +21,9 @@ __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 
 }
 
 // ------------------------------------------------------------------ WW = W.W
-__global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, double* __restrict__ WW) {
+// WW = sum_wm W1[wl,wm,s1,t1] W2[wm,wr,s2,t2]  (W1 on the left site, W2 on the right)
+__global__ void k_ww_precompute(const double* __restrict__ W, const double* __restrict__ W2, int Dw, int d,
+                                double* __restrict__ WW) {
   // WW index ((((wl*d + s1)*d + s2)*Dw + wr)*d + t1)*d + t2
   const int n = Dw * d * d * Dw * d * d;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -34,7 +36,7 @@ __global__ void k_ww_precompute(const double* __restrict__ W, int Dw, int d, dou
     const int wl = r;
     double acc = 0.0;
     for (int wm = 0; wm < Dw; ++wm)
-      acc += W[((wl * Dw + wm) * d + s1) * d + t1] * W[((wm * Dw + wr) * d + s2) * d + t2];
+      acc += W[((wl * Dw + wm) * d + s1) * d + t1] * W2[((wm * Dw + wr) * d + s2) * d + t2];
     WW[i] = acc;
   }
 }
@@ -276,11 +278,12 @@ int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
 // H_eff on C128 tensors through the library's own contraction (native
 // complex FP64), in the order (psi R) W W L:
 //   U0[x,i,j,b,r] = sum_y psi[x,i,j,y] R[b,r,y]
-//   U1[x,i,b,m,u] = sum_{r,j} U0[x,i,j,b,r] W[m,r,u,j]
-//   U2[x,b,u,s,w] = sum_{m,i} U1[x,i,b,m,u] W[w,m,s,i]
+//   U1[x,i,b,m,u] = sum_{r,j} U0[x,i,j,b,r] W2[m,r,u,j]   (right site)
+//   U2[x,b,u,s,w] = sum_{m,i} U1[x,i,b,m,u] W[w,m,s,i]    (left site)
 //   out[a,s,u,b]  = sum_{w,x} L[a,w,x] U2[x,b,u,s,w]
-static tci_status complex_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R, tci_heff_plan* out) {
-  if (L->dtype != TCI_C128 || W->dtype != TCI_C128 || R->dtype != TCI_C128)
+static tci_status complex_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
+                                      tci_heff_plan* out) {
+  if (L->dtype != TCI_C128 || W->dtype != TCI_C128 || W2->dtype != TCI_C128 || R->dtype != TCI_C128)
     return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_create: a complex plan needs L, W, R all C128");
   if (L->order != 3 || R->order != 3 || W->order != 4)
     return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L[chi,Dw,chi], W[Dw,Dw,d,d], R[chi,Dw,chi]");
@@ -299,6 +302,7 @@ static tci_status complex_plan_create(tci_context ctx, tci_tensor L, tci_tensor 
   p->cDw = Dw;
   tci_status s = tci_copy(ctx, L, &p->cL);
   if (s == TCI_OK) s = tci_copy(ctx, W, &p->cW);
+  if (s == TCI_OK) s = tci_copy(ctx, W2, &p->cW2);
   if (s == TCI_OK) s = tci_copy(ctx, R, &p->cR);
   if (s != TCI_OK) {
     tci_heff_plan_destroy(&p);
@@ -319,7 +323,7 @@ static tci_status complex_apply(tci_heff_plan p, tci_tensor psi, tci_tensor out)
   }
   if (psi->data == out->data) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_apply: psi and out overlap");
   TCI_TRY(tci_contract(ctx, psi, "xijy", p->cR, "bry", &p->cU[0], "xijbr"));
-  TCI_TRY(tci_contract(ctx, p->cU[0], "xijbr", p->cW, "mruj", &p->cU[1], "xibmu"));
+  TCI_TRY(tci_contract(ctx, p->cU[0], "xijbr", p->cW2, "mruj", &p->cU[1], "xibmu"));
   TCI_TRY(tci_contract(ctx, p->cU[1], "xibmu", p->cW, "wmsi", &p->cU[2], "xbusw"));
   tci_tensor o = out;
   return tci_contract(ctx, p->cL, "awx", p->cU[2], "xbusw", &o, "asub");
@@ -332,12 +336,23 @@ static tci_status complex_unsupported(tci_heff_plan p, const char* what) {
 // ------------------------------------------------------------------ plan
 extern "C" tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
                                            tci_heff_plan* out) {
+  return tci_heff_plan_create2(ctx, L, W, W, R, out);
+}
+
+extern "C" tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
+                                            tci_heff_plan* out) {
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "heff_plan_create");
   if (!out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: NULL output");
   *out = nullptr;
-  if (!tci_ten_ok(L) || !tci_ten_ok(W) || !tci_ten_ok(R)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: invalid tensor");
-  if (L->dtype == TCI_C128 || W->dtype == TCI_C128 || R->dtype == TCI_C128) return complex_plan_create(ctx, L, W, R, out);
+  if (!tci_ten_ok(L) || !tci_ten_ok(W) || !tci_ten_ok(W2) || !tci_ten_ok(R))
+    return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_create: invalid tensor");
+  if (W2->dtype != W->dtype || W2->order != W->order || !tci_is_rowmajor(W2))
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: W2 must be a row-major tensor of W's dtype and shape");
+  for (int i = 0; i < W->order; ++i)
+    if (W2->shape[i] != W->shape[i]) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: W2 must have W's shape");
+  if (L->dtype == TCI_C128 || W->dtype == TCI_C128 || R->dtype == TCI_C128)
+    return complex_plan_create(ctx, L, W, W2, R, out);
   if (L->dtype != TCI_F64 || W->dtype != TCI_F64 || R->dtype != TCI_F64)
     return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_create: L, W, R must be F64");
   if (L->order != 3 || R->order != 3 || W->order != 4) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_create: L[chi,Dw,chi], W[Dw,Dw,d,d], R[chi,Dw,chi]");
@@ -371,7 +386,7 @@ extern "C" tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_te
   // WW (FP64) on the device, then a host copy for the kernel arguments
   double* dWW = nullptr;
   if ((s = tci_dev_alloc(ctx, sizeof(double) * HEFF_NWW, (void**)&dWW)) != TCI_OK) return fail(s);
-  k_ww_precompute<<<1, 256, 0, ctx->stream>>>((const double*)W->data, (int)Dw, (int)d, dWW);
+  k_ww_precompute<<<1, 256, 0, ctx->stream>>>((const double*)W->data, (const double*)W2->data, (int)Dw, (int)d, dWW);
   cudaError_t e = cudaMemcpyAsync(p->ww, dWW, sizeof(double) * HEFF_NWW, cudaMemcpyDeviceToHost, ctx->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   tci_dev_free(dWW);
@@ -417,7 +432,7 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
                   p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
   for (void* b : bufs) tci_dev_free(b);
-  for (tci_tensor* t : {&p->cL, &p->cW, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2]})
+  for (tci_tensor* t : {&p->cL, &p->cW, &p->cW2, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2]})
     if (*t) tci_tensor_free(t);
   for (int i = 0; i < 8; ++i) {
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);

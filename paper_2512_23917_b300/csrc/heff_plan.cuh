@@ -23,7 +23,7 @@ struct tci_heff_plan_s {
   // complex (C128) plan: owned copies of L, W, R and the contraction intermediates
   bool cplx = false;
   int64_t cd = 0, cDw = 0;
-  tci_tensor cL = nullptr, cW = nullptr, cR = nullptr, cU[3] = {nullptr, nullptr, nullptr};
+  tci_tensor cL = nullptr, cW = nullptr, cW2 = nullptr, cR = nullptr, cU[3] = {nullptr, nullptr, nullptr};
   double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
   // intermediates
   void* U = nullptr;       // FP64 [(a',t1,t2), (b,wr)] (native) or FP32 U^T [(b,wr), (a',t1,t2)] (split)

@@ -110,3 +110,16 @@ def test_heff_split_ww_variants(ctx, tci, chi, chi_r, ww_na):
     plan.apply(dpsi, out)
     torch.cuda.synchronize()
     assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi)) < 1e-6
+
+
+@pytest.mark.parametrize("prec,tol", [("native", 1e-12), ("split_bf16", 1e-6)])
+def test_two_site_mpos_match_oracle(ctx, tci, prec, tol):
+    """Different MPO tensors on the two sites (tci_heff_plan_create2) against the oracle."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(40, seed=5, chi_r=33)
+    W2 = random_tensor([5, 5, 2, 2], 6)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision=prec, W2=to_dev(W2))
+    out = torch.full(psi.shape, float("nan"), dtype=torch.float64, device="cuda")
+    plan.apply(to_dev(psi), out)
+    torch.cuda.synchronize()
+    assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi, W2=W2)) < tol

@@ -53,3 +53,14 @@ def test_complex_plan_rejects_other_calls(ctx, tci):
         plan.apply(_dev(psi.real.copy()), torch.empty(psi.shape, dtype=torch.float64, device="cuda"))
     with pytest.raises(RuntimeError):
         tci.HeffPlan(ctx, _dev(L), _dev(W.real.copy()), _dev(R), precision="native")
+
+
+def test_complex_two_site_mpos(ctx, tci):
+    import torch
+    psi, L, R, W = complex_heff_inputs(9, 5, 12, 4, 2)
+    W2 = complex_heff_inputs(2, 6, 2, 4, 2)[3]
+    plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native", W2=_dev(W2))
+    out = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    plan.apply(_dev(psi), out)
+    torch.cuda.synchronize()
+    assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi, W2=W2)) < 1e-13
