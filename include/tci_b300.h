@@ -526,6 +526,15 @@ tci_status tci_tebd_plan_destroy(tci_tebd_plan* plan);
 tci_status tci_tebd_apply(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta);
 /* Algorithmic flops: sum_i 8 chi_i^3 d^2 + 8 chi_i^2 d^4 (8 real flops per complex multiply-add). */
 double tci_tebd_flops(tci_tebd_plan plan);
+/* The same batch on tensor handles (one call, no plan kept): A[i], B[i]
+ * C64 row-major [chi_i, 2, chi_i], G[i] C64 [2, 2, 2, 2]; theta[i] C64
+ * [chi_i, 2, 2, chi_i] (written), or NULL handles, which receive new owned
+ * tensors.  Builds a plan for these chi_i, packs the operands with device
+ * copies, applies it and unpacks theta; synchronises.  Arithmetic as
+ * tci_tebd_plan_create (the context precision; NATIVE is UNSUPPORTED).
+ * Errors: INVALID_ARG, DTYPE, SHAPE, UNSUPPORTED, ALLOC, CUDA. */
+tci_status tci_tebd_theta_batched(tci_context ctx, int n, const tci_tensor* A, const tci_tensor* B,
+                                  const tci_tensor* G, tci_tensor* theta);
 /* Profiling form of tci_tebd_apply: stage_ms[0..2] (host) receive the device
  * times of the split, the grouped GEMM and the gate kernel.  Synchronises. */
 tci_status tci_tebd_apply_timed(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,

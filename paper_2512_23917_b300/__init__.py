@@ -101,6 +101,7 @@ SIGNATURES = [
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_create2", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(_p)]),
+    ("tci_tebd_theta_batched", C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
     ("tci_heff_set_gram_schmidt", C.c_int, [_p, C.c_int]),
     ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
     ("tci_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
@@ -422,6 +423,20 @@ def bp(ctx: Context, n: int, edges, sites, messages, niters: int, tol: float = 0
     _check(lib.tci_bp(ctx.handle, int(n), len(edges), ed, sh, mh, int(niters), float(tol), C.byref(done), res),
            ctx.handle)
     return [t.to_numpy() for t in mt], list(res[:done.value])
+
+
+def tebd_theta_batched(ctx: Context, A, B, G):
+    """Batched TEBD theta on lists of CUDA complex64 torch tensors; returns new TCI Tensors theta_i."""
+    ta = [ctx.wrap(a) for a in A]
+    tb = [ctx.wrap(b) for b in B]
+    tg = [ctx.wrap(g) for g in G]
+    n = len(ta)
+    ha = (_p * max(1, n))(*[t.handle for t in ta])
+    hb = (_p * max(1, n))(*[t.handle for t in tb])
+    hg = (_p * max(1, n))(*[t.handle for t in tg])
+    ht = (_p * max(1, n))()
+    _check(lib.tci_tebd_theta_batched(ctx.handle, n, ha, hb, hg, ht), ctx.handle)
+    return [Tensor(ctx, ht[i]) for i in range(n)]
 
 
 def eye(ctx: Context, n: int, dtype: int = F64) -> Tensor:

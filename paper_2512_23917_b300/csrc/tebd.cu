@@ -330,3 +330,74 @@ extern "C" tci_status tci_tebd_autotune(tci_tebd_plan p, const void* A, const vo
   }
   return tci_synchronize(ctx);
 }
+
+// ------------------------------------------------------------------ handle form
+extern "C" tci_status tci_tebd_theta_batched(tci_context ctx, int n, const tci_tensor* A, const tci_tensor* B,
+                                             const tci_tensor* G, tci_tensor* theta) {
+  TCI_CHECK_CTX(ctx);
+  TciVerboseScope vs(ctx, "tebd_theta_batched");
+  if (n < 0 || (n > 0 && (!A || !B || !G || !theta)))
+    return tci_fail(ctx, TCI_ERR_INVALID_ARG, "tebd_theta_batched: invalid arrays");
+  if (n == 0) return TCI_OK;
+  std::vector<int64_t> chi(n);
+  for (int i = 0; i < n; ++i) {
+    const tci_tensor a = A[i], b = B[i], g = G[i];
+    if (!tci_ten_ok(a) || !tci_ten_ok(b) || !tci_ten_ok(g))
+      return tci_fail(ctx, TCI_ERR_INVALID_ARG, "tebd_theta_batched: invalid tensor of bond %d", i);
+    if (a->dtype != TCI_C64 || b->dtype != TCI_C64 || g->dtype != TCI_C64)
+      return tci_fail(ctx, TCI_ERR_DTYPE, "tebd_theta_batched: A, B, G must be C64 (bond %d)", i);
+    const int64_t c = a->order == 3 ? a->shape[0] : -1;
+    if (c < 1 || a->shape[1] != 2 || a->shape[2] != c || b->order != 3 || b->shape[0] != c || b->shape[1] != 2 ||
+        b->shape[2] != c || g->order != 4 || g->shape[0] != 2 || g->shape[1] != 2 || g->shape[2] != 2 ||
+        g->shape[3] != 2 || !tci_is_rowmajor(a) || !tci_is_rowmajor(b) || !tci_is_rowmajor(g))
+      return tci_fail(ctx, TCI_ERR_SHAPE, "tebd_theta_batched: bond %d needs row-major A, B [chi,2,chi], G [2,2,2,2]", i);
+    if (theta[i]) {
+      const tci_tensor t = theta[i];
+      if (!tci_ten_ok(t) || t->dtype != TCI_C64 || t->order != 4 || t->shape[0] != c || t->shape[1] != 2 ||
+          t->shape[2] != 2 || t->shape[3] != c || !tci_is_rowmajor(t))
+        return tci_fail(ctx, TCI_ERR_SHAPE, "tebd_theta_batched: theta of bond %d must be C64 [chi,2,2,chi]", i);
+    }
+    chi[i] = c;
+  }
+  tci_tebd_plan plan = nullptr;
+  TCI_TRY(tci_tebd_plan_create(ctx, n, chi.data(), &plan));
+  int64_t na = 0, nt = 0;
+  for (int64_t c : chi) {
+    na += 2 * c * c;
+    nt += 4 * c * c;
+  }
+  const size_t eb = 2 * sizeof(float);
+  void *pa = nullptr, *pb = nullptr, *pg = nullptr, *pt = nullptr;
+  tci_status st = tci_dev_alloc(ctx, eb * na, &pa);
+  if (st == TCI_OK) st = tci_dev_alloc(ctx, eb * na, &pb);
+  if (st == TCI_OK) st = tci_dev_alloc(ctx, eb * 16 * n, &pg);
+  if (st == TCI_OK) st = tci_dev_alloc(ctx, eb * nt, &pt);
+  cudaError_t e = cudaSuccess;
+  int64_t oa = 0, ot = 0;
+  for (int i = 0; i < n && st == TCI_OK && e == cudaSuccess; ++i) {
+    const int64_t c = chi[i];
+    e = cudaMemcpyAsync((char*)pa + eb * oa, A[i]->data, eb * 2 * c * c, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char*)pb + eb * oa, B[i]->data, eb * 2 * c * c, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char*)pg + eb * 16 * i, G[i]->data, eb * 16, cudaMemcpyDeviceToDevice, ctx->stream);
+    oa += 2 * c * c;
+  }
+  if (st == TCI_OK && e != cudaSuccess) st = tci_cuda_fail(ctx, e, "tebd_theta_batched: pack");
+  if (st == TCI_OK) st = tci_tebd_apply(plan, pa, pb, pg, pt);
+  for (int i = 0; i < n && st == TCI_OK; ++i) {
+    const int64_t c = chi[i];
+    if (!theta[i]) {
+      const int64_t shp[4] = {c, 2, 2, c};
+      st = tci_allocate(ctx, TCI_C64, 4, shp, &theta[i]);
+      if (st != TCI_OK) break;
+    }
+    e = cudaMemcpyAsync(theta[i]->data, (char*)pt + eb * ot, eb * 4 * c * c, cudaMemcpyDeviceToDevice, ctx->stream);
+    if (e != cudaSuccess) st = tci_cuda_fail(ctx, e, "tebd_theta_batched: unpack");
+    ot += 4 * c * c;
+  }
+  if (st == TCI_OK) st = tci_synchronize(ctx);
+  for (void* q : {pa, pb, pg, pt}) tci_dev_free(q);
+  tci_tebd_plan_destroy(&plan);
+  return st;
+}

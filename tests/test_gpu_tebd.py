@@ -82,3 +82,17 @@ def test_tebd_graph_replay_with_new_buffers(ctx, tci):
         for c, a, b, g in zip(chis, A, B, G):
             assert rel_frob_err(th[off:off + 4 * c * c].reshape(c, 2, 2, c), o_tebd.theta(a, b, g)) < 1e-5, call
             off += 4 * c * c
+
+
+def test_tebd_theta_batched_on_handles(ctx, tci):
+    """The handle form (tci_tebd_theta_batched) equals the oracle bond by bond."""
+    chis, A, B, G = tebd_inputs(7, seed=8, chi_lo=3, chi_hi=70)
+    ctx.set_precision("split_bf16")
+    try:
+        out = tci.tebd_theta_batched(ctx, [to_dev(a) for a in A], [to_dev(b) for b in B], [to_dev(g) for g in G])
+    finally:
+        ctx.set_precision("native")
+    for t, a, b, g in zip(out, A, B, G):
+        got = t.to_numpy()
+        assert got.shape == (a.shape[0], 2, 2, a.shape[0])
+        assert rel_frob_err(got, o_tebd.theta(a, b, g)) < 1e-5
