@@ -123,11 +123,11 @@ tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t
   if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
   int ac = (sak == 1 || sam != 1) ? 0 : 1;
   int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
-  // split K when the tiles cannot fill two waves and each split keeps >= 256 of K
+  // split K when the tiles cannot fill two waves and each split keeps >= 64 of K
   const int64_t tiles = (int64_t)grid.x * grid.y * nbatch, want = 2 * (int64_t)ctx->num_sms;
   int64_t nsplit = 1;
-  if (tiles < want && K >= 512) {
-    nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 256, 16});
+  if (tiles < want && K >= 128) {
+    nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 64, 16});
     if (nsplit < 1) nsplit = 1;
   }
   int64_t kchunk = K;

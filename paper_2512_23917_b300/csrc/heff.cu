@@ -194,12 +194,23 @@ __global__ void __launch_bounds__(256) k_ww_split(const WWArgs<float> args, cons
   }
 }
 
+// The W.W step is FP64-pipe work (400 FMAs per (a', b) pair), so the tile
+// shrinks for small bonds until the grid covers the SMs.
 tci_status launch_ww_f64(tci_context ctx, const WWArgs<double>& args, const double* U, int64_t chiL, int64_t chiR,
                          double* V, int64_t ldv) {
-  constexpr int ATILE = 16, BT = 16;
-  dim3 grid((unsigned)((chiR + BT - 1) / BT), (unsigned)((chiL + ATILE - 1) / ATILE));
-  if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: chiL too large");
-  k_ww_apply<ATILE, BT><<<grid, ATILE * BT, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
+  const int64_t sms = ctx->num_sms;
+  auto blocks = [&](int at, int bt) { return ((chiR + bt - 1) / bt) * ((chiL + at - 1) / at); };
+  if (blocks(16, 16) >= 2 * sms) {
+    dim3 grid((unsigned)((chiR + 15) / 16), (unsigned)((chiL + 15) / 16));
+    if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: chiL too large");
+    k_ww_apply<16, 16><<<grid, 256, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
+  } else if (blocks(8, 8) >= sms) {
+    dim3 grid((unsigned)((chiR + 7) / 8), (unsigned)((chiL + 7) / 8));
+    k_ww_apply<8, 8><<<grid, 64, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
+  } else {
+    dim3 grid((unsigned)((chiR + 7) / 8), (unsigned)((chiL + 3) / 4));
+    k_ww_apply<4, 8><<<grid, 32, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
+  }
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
