@@ -67,3 +67,12 @@ def test_bp_rejects_bad_input(ctx, tci):
         tci.bp(ctx, n, edges, V, [np.eye(3)] + M[1:], 2)            # message shape
     with pytest.raises(RuntimeError):
         tci.bp(ctx, n, [(0, 9)] + edges[1:], V, M, 2)               # vertex out of range
+
+
+def test_bp_isolated_site_and_zero_iterations(ctx, tci):
+    """A vertex without bonds carries no messages; zero iterations return the start messages."""
+    n, edges = 5, [(0, 1), (1, 2), (2, 3)]          # vertex 4 is isolated
+    V, M = bp_tns_inputs(n, edges, 3, seed=9)
+    _compare(tci, ctx, n, edges, V, M, 4)
+    got, res = tci.bp(ctx, n, edges, V, M, 0)
+    assert res == [] and all(np.array_equal(g, m) for g, m in zip(got, M))

@@ -41,3 +41,13 @@ def test_itebd_rejects_bad_cell(ctx, tci):
         tci.itebd(ctx, tfim_bond_hamiltonian(), 0.01, gam, [lam[0], lam[1][:3]], 4, 5)
     with pytest.raises(RuntimeError):
         tci.itebd(ctx, tfim_bond_hamiltonian(), -0.01, gam, lam, 4, 5)
+
+
+def test_itebd_bond_dimension_one(ctx, tci):
+    """chi = 1 (product states): the device iteration equals the oracle's, energies stay above the exact one."""
+    h = tfim_bond_hamiltonian(1.0, 0.8)
+    gam, lam = itebd_initial_state(1, 4)
+    e, _, G, L = tci.itebd(ctx, h, 0.02, gam, lam, 1, 200)
+    re, _, _ = o_itebd.itebd(h, 0.02, gam, lam, 1, 200)
+    np.testing.assert_allclose(e, re, rtol=0, atol=1e-10)
+    assert L[1].shape == (1,) and abs(abs(L[1][0]) - 1.0) < 1e-12

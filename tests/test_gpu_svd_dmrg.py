@@ -121,3 +121,16 @@ def test_svd_long_rows_match_oracle(ctx, tci, shape, k):
     rs = o_linalg.svd(a, k)[1]
     np.testing.assert_allclose(s, rs, rtol=1e-12, atol=1e-12 * rs.max())
     _check_svd(a, k, u, s, vt, 1e-12)
+
+
+def test_svd_rank_deficient_with_qr_preconditioning(ctx, tci):
+    """Rank 5 of 60 columns (QR-preconditioned path): zero pivots in R, tiny singular values."""
+    rng = np.random.default_rng(15)
+    a = rng.standard_normal((80, 5)) @ rng.standard_normal((5, 60))
+    u, s, vt = tci.svd(ctx, _tensor(tci, ctx, a), 1)
+    s = s.to_numpy()
+    np.testing.assert_allclose(s[:5], np.linalg.svd(a, compute_uv=False)[:5], rtol=1e-12)
+    assert np.all(s[5:] < 1e-12 * s[0])
+    _check_svd(a, 1, u.to_numpy(), s, vt.to_numpy(), 1e-12)
+    ut, st, vtt, err = tci.trunc_svd(ctx, _tensor(tci, ctx, a), 1, 1, 60, 0.0, 1e-10)
+    assert st.to_numpy().shape == (5,) and err < 1e-24                   # rule (a) drops the zero values
