@@ -394,12 +394,12 @@ def run_gpu(args):
     psi_h = torch.from_numpy(np.ascontiguousarray(psi)).pin_memory()
     x_h = torch.empty(psi.shape, dtype=torch.float64).pin_memory()
     dpsi_e = torch.empty_like(dpsi)
+    t_psi, t_x = ctx.wrap(dpsi_e), ctx.wrap(x)
 
     def e2e_step():
-        dpsi_e.copy_(psi_h, non_blocking=True)
+        t_psi.copy_from_host(psi_h.data_ptr())          # tci_from_host
         r = plan.lanczos(dpsi_e, LANCZOS_STEPS, True, x)
-        x_h.copy_(x, non_blocking=True)
-        torch.cuda.synchronize()
+        t_x.copy_to_host(x_h.data_ptr())               # tci_to_host
         return r
 
     e2e_step()
@@ -409,7 +409,8 @@ def run_gpu(args):
     e2e_s = (time.perf_counter() - t0) / args.steps
     e2e = {"value": LANCZOS_STEPS * F / e2e_s / 1e9, "unit": "GFLOP/s", "h2d_bytes_per_step": int(psi.nbytes),
            "d2h_bytes_per_step": int(psi.nbytes) + 8, "ms_per_step": 1e3 * e2e_s,
-           "step": "psi host->device, 20-step Lanczos solve, Ritz vector device->host (pinned buffers)"}
+           "step": "psi host->device (tci_from_host), 20-step Lanczos solve (tci_lanczos), Ritz vector "
+                   "device->host (tci_to_host); pinned host buffers"}
     # one matvec through the C ABI with host buffers (copies overlapped with compute in chunks)
     out_h = torch.empty(psi.shape, dtype=torch.float64).pin_memory().numpy()
     psi_hn = psi_h.numpy()

@@ -268,6 +268,14 @@ class Tensor:
         arr = np.ascontiguousarray(arr)
         _check(lib.tci_from_host(self.ctx.handle, self.handle, _p(arr.ctypes.data)), self.ctx.handle)
 
+    def copy_from_host(self, address: int):
+        """tci_from_host from a host buffer at ``address`` (e.g. pinned memory) holding size() elements."""
+        _check(lib.tci_from_host(self.ctx.handle, self.handle, _p(int(address))), self.ctx.handle)
+
+    def copy_to_host(self, address: int):
+        """tci_to_host into a host buffer at ``address`` of size_bytes() bytes."""
+        _check(lib.tci_to_host(self.ctx.handle, self.handle, _p(int(address))), self.ctx.handle)
+
     def reshape_(self, shape):
         _check(lib.tci_reshape(self.ctx.handle, self.handle, len(shape), _arr64(shape)), self.ctx.handle)
         return self
