@@ -122,3 +122,25 @@ def lanczos(matvec, v0, m: int, reorth: bool = True, tol: float = 1e-12):
     for yj, vj in zip(y, V[:k]):
         x = x + yj * vj
     return {"theta": theta, "x": x, "alpha": np.array(alpha), "beta": np.array(beta), "steps": k, "y": y}
+
+
+def lanczos_real_form(matvec, v0, m: int, reorth: bool = True, tol: float = 1e-12):
+    """Lanczos for a Hermitian operator on complex vectors, run on its real form.
+
+    A Hermitian H = A + iB acting on v = x + iy is the real symmetric operator
+    [[A, -B], [B, A]] on (x, y); with v stored as interleaved (re, im) pairs
+    that operator acts on the float64 view of v, its spectrum is H's with every
+    eigenvalue twice, so its lowest Ritz value converges to H's ground energy.
+    ``lanczos`` above runs on that view unchanged; the Ritz vector is returned
+    as complex128.
+    """
+    v0 = np.ascontiguousarray(v0, dtype=np.complex128)
+    shape = v0.shape
+
+    def mv(u):
+        z = np.ascontiguousarray(u).view(np.complex128).reshape(shape)
+        return np.ascontiguousarray(matvec(z), dtype=np.complex128).ravel().view(np.float64)
+
+    r = lanczos(mv, v0.ravel().view(np.float64), m, reorth, tol)
+    r["x"] = np.ascontiguousarray(r["x"]).view(np.complex128)
+    return r

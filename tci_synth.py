@@ -266,3 +266,15 @@ def complex_heff_inputs(chi: int, seed: int = DEFAULT_SEED, chi_r: int | None = 
     rng = np.random.default_rng(seed)
     c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
     return c(chi, d, d, chi_r), c(chi, Dw, chi), c(chi_r, Dw, chi_r), c(Dw, Dw, d, d)
+
+
+def hermitian_heff_inputs(chi: int, seed: int = DEFAULT_SEED, chi_r: int | None = None):
+    """Complex environments that make the Heisenberg H_eff Hermitian: L, R complex128 with
+    L_w <- (L_w + conj(L_{sigma(w)})^T)/2 (the complex form of the channel-wise symmetrisation),
+    W the real Heisenberg MPO as complex128, psi complex128; all parts N(0,1)."""
+    chi_r = chi if chi_r is None else chi_r
+    rng = np.random.default_rng(seed)
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    herm = lambda E: 0.5 * (E + np.conj(np.transpose(E, (2, 1, 0))[:, MPO_SIGMA, :]))
+    psi, L, R = c(chi, 2, 2, chi_r), herm(c(chi, 5, chi)), herm(c(chi_r, 5, chi_r))
+    return psi, L, R, heisenberg_mpo().astype(np.complex128)

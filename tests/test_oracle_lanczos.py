@@ -100,3 +100,22 @@ def test_sturm_count_with_an_exact_zero_pivot():
     alpha, beta = [-0.25, -0.25], [0.5]
     assert sturm_count(alpha, beta, -0.25) == 1
     assert abs(lowest_eigenvalue_bisect(alpha, beta) + 0.75) < 1e-15
+
+
+def test_real_form_lanczos_finds_hermitian_ground_energy():
+    rng = np.random.default_rng(3)
+    a = rng.standard_normal((40, 40)) + 1j * rng.standard_normal((40, 40))
+    H = 0.5 * (a + a.conj().T)
+    r = lanczos.lanczos_real_form(lambda v: H @ v, rng.standard_normal(40) + 0j, 80)
+    assert abs(r["theta"] - np.linalg.eigvalsh(H)[0]) < 1e-10
+    x = r["x"]
+    assert np.linalg.norm(H @ x - r["theta"] * x) < 1e-8 and abs(np.linalg.norm(x) - 1.0) < 1e-12
+
+
+def test_hermitian_heff_and_its_ground_energy():
+    from tci_synth import hermitian_heff_inputs
+    psi, L, R, W = hermitian_heff_inputs(3, 4, 2)
+    H = heff.heff_matrix_loops(L, W, R)
+    np.testing.assert_allclose(H, H.conj().T, atol=1e-12)                  # the symmetrisation works
+    r = lanczos.lanczos_real_form(lambda v: heff.heff_apply(L, W, R, v), psi, 2 * H.shape[0])
+    assert abs(r["theta"] - np.linalg.eigvalsh(H)[0]) < 1e-9
