@@ -292,9 +292,13 @@ tci_status tci_close(tci_context ctx, tci_tensor a, tci_tensor b, double eps, in
  * output FP64).
  * Complex plans: L, W, R all C128 (any Dw >= 1, d >= 1; psi and out C128
  * [chiL, d, d, chiR]).  Such a plan applies H_eff as four tci_contract calls
- * in native complex FP64 arithmetic, (psi R) W W L, on copies it owns;
- * tci_heff_apply and tci_heff_flops (8 real flops per complex multiply-add)
- * accept it, every other plan call returns UNSUPPORTED.
+ * in native complex FP64 arithmetic, (psi R) W W L, on copies it owns.
+ * tci_heff_apply, tci_heff_flops (8 real flops per complex multiply-add) and
+ * tci_lanczos (FP64 vectors; for a Hermitian H_eff, run on its real form:
+ * C128 vectors as interleaved FP64 pairs, the real symmetric operator
+ * [[Re H, -Im H], [Im H, Re H]] whose spectrum is H's with each eigenvalue
+ * twice) accept it; the host-buffer, timed, autotune and config calls return
+ * UNSUPPORTED.
  * Errors: SHAPE, DTYPE, ALLOC, CUDA. */
 tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor R,
                                 tci_heff_plan* plan);

@@ -340,6 +340,19 @@ static tci_status complex_apply(tci_heff_plan p, tci_tensor psi, tci_tensor out)
   return tci_contract(ctx, p->cL, "awx", p->cU[2], "xbusw", &o, "asub");
 }
 
+// Matvec on raw device pointers of a complex plan (the Lanczos basis stores
+// C128 vectors as interleaved FP64 pairs): borrowed C128 views kept in the
+// plan, repointed at every call.
+tci_status tci_heff_apply_complex_raw(tci_heff_plan p, const double* psi, double* out) {
+  tci_context ctx = p->ctx;
+  const int64_t shp[4] = {p->chiL, p->cd, p->cd, p->chiR};
+  if (!p->cVin) TCI_TRY(tci_tensor_wrap(ctx, TCI_C128, 4, shp, nullptr, (void*)psi, &p->cVin));
+  if (!p->cVout) TCI_TRY(tci_tensor_wrap(ctx, TCI_C128, 4, shp, nullptr, out, &p->cVout));
+  p->cVin->data = (void*)psi;
+  p->cVout->data = out;
+  return complex_apply(p, p->cVin, p->cVout);
+}
+
 static tci_status complex_unsupported(tci_heff_plan p, const char* what) {
   return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "%s: complex plans support tci_heff_apply only", what);
 }
@@ -443,7 +456,7 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
                   p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
   for (void* b : bufs) tci_dev_free(b);
-  for (tci_tensor* t : {&p->cL, &p->cW, &p->cW2, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2]})
+  for (tci_tensor* t : {&p->cL, &p->cW, &p->cW2, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2], &p->cVin, &p->cVout})
     if (*t) tci_tensor_free(t);
   for (int i = 0; i < 8; ++i) {
     if (p->ev_in[i]) cudaEventDestroy(p->ev_in[i]);

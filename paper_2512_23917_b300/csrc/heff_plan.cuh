@@ -24,6 +24,7 @@ struct tci_heff_plan_s {
   bool cplx = false;
   int64_t cd = 0, cDw = 0;
   tci_tensor cL = nullptr, cW = nullptr, cW2 = nullptr, cR = nullptr, cU[3] = {nullptr, nullptr, nullptr};
+  tci_tensor cVin = nullptr, cVout = nullptr;   // borrowed views for the Lanczos matvec
   double ww[HEFF_NWW];   // WW[wl][s1 s2][wr][t1 t2]
   // intermediates
   void* U = nullptr;       // FP64 [(a',t1,t2), (b,wr)] (native) or FP32 U^T [(b,wr), (a',t1,t2)] (split)
@@ -58,4 +59,5 @@ struct tci_heff_plan_s {
 // Time the split W.W kernel variants on the plan's current intermediates and
 // keep the faster (p->ww_na); *ms_out (may be NULL) receives its duration.
 tci_status tci_heff_tune_ww(tci_heff_plan p, float* ms_out);
+tci_status tci_heff_apply_complex_raw(tci_heff_plan p, const double* psi, double* out);
 tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, bool psi_presplit, int out_mode = 0);

@@ -700,9 +700,10 @@ template <class A, int MODE>
 tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol) {
   using Vt = typename A::V;
   tci_context ctx = p->ctx;
-  const int64_t n = p->chiL * 4 * p->chiR;
+  // a complex plan runs on the real form: C128 vectors as interleaved FP64 pairs
+  const int64_t rows = p->cplx ? 2 * p->chiL * p->cd * p->cd : p->chiL * 4, cols = p->chiR;
+  const int64_t n = rows * cols;
   const int64_t ldv = (n + 31) / 32 * 32;
-  const int64_t rows = p->chiL * 4, cols = p->chiR;
   constexpr bool kDF = std::is_same<Vt, float2>::value;
   if (MODE == kInF64) {
     if (!p->lz_x64) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_x64));
@@ -727,7 +728,10 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     if (MODE == kInPieces) {
       TCI_TRY(tci_heff_apply_raw(p, nullptr, w, true, kDF ? 2 : 0));
     } else if (MODE == kInNone) {
-      TCI_TRY(tci_heff_apply_raw(p, (const double*)vj, w, false, 0));
+      if (p->cplx)
+        TCI_TRY(tci_heff_apply_complex_raw(p, (const double*)vj, (double*)w));
+      else
+        TCI_TRY(tci_heff_apply_raw(p, (const double*)vj, w, false, 0));
     } else {
       TCI_TRY(tci_heff_apply_raw(p, p->lz_x64, p->lz_o64, false, 0));
       k_from_f64<A><<<NBMAX, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
@@ -764,23 +768,26 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
 extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, int reorth, double* ritz, double* alpha,
                                   double* beta, int* steps_done, tci_tensor x) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "lanczos: invalid plan");
-  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "lanczos: complex plans support tci_heff_apply only");
   tci_context ctx = p->ctx;
   TCI_CHECK_CTX(ctx);
   TciVerboseScope vs(ctx, "lanczos");
   if (nsteps < 1 || nsteps > MAXM) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: nsteps must be in 1..%d", MAXM);
   if (!ritz) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: NULL ritz output");
+  const tci_dtype vdt = p->cplx ? TCI_C128 : TCI_F64;
+  const int64_t d = p->cplx ? p->cd : 2;
   auto check = [&](tci_tensor t, const char* what) -> tci_status {
     if (!tci_ten_ok(t)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: invalid %s", what);
-    if (t->dtype != TCI_F64) return tci_fail(ctx, TCI_ERR_DTYPE, "lanczos: %s must be F64", what);
-    if (t->order != 4 || t->shape[0] != p->chiL || t->shape[1] != 2 || t->shape[2] != 2 || t->shape[3] != p->chiR ||
+    if (t->dtype != vdt) return tci_fail(ctx, TCI_ERR_DTYPE, "lanczos: %s must be %s", what, p->cplx ? "C128" : "F64");
+    if (t->order != 4 || t->shape[0] != p->chiL || t->shape[1] != d || t->shape[2] != d || t->shape[3] != p->chiR ||
         !tci_is_rowmajor(t))
-      return tci_fail(ctx, TCI_ERR_SHAPE, "lanczos: %s must be row-major [chiL,2,2,chiR]", what);
+      return tci_fail(ctx, TCI_ERR_SHAPE, "lanczos: %s must be row-major [chiL,d,d,chiR]", what);
     return TCI_OK;
   };
   TCI_TRY(check(psi0, "psi0"));
   if (x) TCI_TRY(check(x, "x"));
-  const int64_t n = p->chiL * 4 * p->chiR;
+  if (p->cplx && p->vec_arith == TCI_LANCZOS_DF32)
+    return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "lanczos: complex plans run FP64 vectors only");
+  const int64_t n = p->cplx ? 2 * p->chiL * d * d * p->chiR : p->chiL * 4 * p->chiR;
   const int64_t ldv = (n + 31) / 32 * 32;
   if (p->lz_cap < nsteps + 1) {
     cudaStreamSynchronize(ctx->stream);
@@ -825,7 +832,6 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
 
 extern "C" tci_status tci_heff_set_lanczos_arith(tci_heff_plan p, tci_lanczos_arith arith) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_arith: invalid plan");
-  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "set_lanczos_arith: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (arith != TCI_LANCZOS_AUTO && arith != TCI_LANCZOS_F64 && arith != TCI_LANCZOS_DF32)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_lanczos_arith: unknown arithmetic %d", (int)arith);
@@ -835,7 +841,6 @@ extern "C" tci_status tci_heff_set_lanczos_arith(tci_heff_plan p, tci_lanczos_ar
 
 extern "C" tci_status tci_heff_set_gram_schmidt(tci_heff_plan p, tci_gram_schmidt mode) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_gram_schmidt: invalid plan");
-  if (p->cplx) return tci_fail(p->ctx, TCI_ERR_UNSUPPORTED, "set_gram_schmidt: complex plans support tci_heff_apply only");
   TCI_CHECK_CTX(p->ctx);
   if (mode != TCI_GS_DGKS && mode != TCI_GS_TWICE)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_gram_schmidt: unknown mode %d", (int)mode);

@@ -48,7 +48,7 @@ def test_complex_plan_rejects_other_calls(ctx, tci):
     psi, L, R, W = complex_heff_inputs(8, 2, 8, 5, 2)
     plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native")
     with pytest.raises(RuntimeError):
-        plan.lanczos(_dev(psi.real.copy()), 4)
+        plan.lanczos(_dev(psi.real.copy()), 4)            # F64 start vector on a complex plan
     with pytest.raises(RuntimeError):
         plan.apply(_dev(psi.real.copy()), torch.empty(psi.shape, dtype=torch.float64, device="cuda"))
     with pytest.raises(RuntimeError):
@@ -64,3 +64,46 @@ def test_complex_two_site_mpos(ctx, tci):
     plan.apply(_dev(psi), out)
     torch.cuda.synchronize()
     assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi, W2=W2)) < 1e-13
+
+
+def _lanczos(tci, ctx, L, W, R, psi, m, gs="dgks"):
+    import torch
+    plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native")
+    plan.set_gram_schmidt(gs)
+    x = torch.empty(psi.shape, dtype=torch.complex128, device="cuda")
+    res = plan.lanczos(_dev(psi), m, True, x)
+    res["x"] = x.cpu().numpy()
+    return res
+
+
+@pytest.mark.parametrize("gs", ["dgks", "twice"])
+def test_complex_lanczos_matches_real_form_oracle(ctx, tci, gs):
+    from oracle import lanczos as o_lanczos
+    from tci_synth import hermitian_heff_inputs
+    psi, L, R, W = hermitian_heff_inputs(8, 3, 6)
+    r = _lanczos(tci, ctx, L, W, R, psi, 20, gs)
+    o = o_lanczos.lanczos_real_form(lambda v: o_heff.heff_apply(L, W, R, v), psi, 20)
+    assert r["steps"] == o["steps"] == 20
+    np.testing.assert_allclose(r["alpha"], o["alpha"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(r["beta"], o["beta"], rtol=1e-10, atol=1e-10)
+    assert abs(r["theta"] - o["theta"]) < 1e-10 * abs(o["theta"])
+    assert np.linalg.norm(r["x"].ravel() - o["x"]) < 1e-8
+
+
+def test_complex_lanczos_reaches_the_hermitian_ground_energy(ctx, tci):
+    from tci_synth import hermitian_heff_inputs
+    psi, L, R, W = hermitian_heff_inputs(3, 5, 2)
+    H = o_heff.heff_matrix_loops(L, W, R)
+    r = _lanczos(tci, ctx, L, W, R, psi, 2 * H.shape[0])
+    assert abs(r["theta"] - np.linalg.eigvalsh(H)[0]) < 1e-9
+    x = r["x"].ravel()
+    assert np.linalg.norm(H @ x - r["theta"] * x) < 1e-7
+
+
+def test_complex_lanczos_rejects_double_float_vectors(ctx, tci):
+    from tci_synth import hermitian_heff_inputs
+    psi, L, R, W = hermitian_heff_inputs(4, 3, 4)
+    plan = tci.HeffPlan(ctx, _dev(L), _dev(W), _dev(R), precision="native")
+    plan.set_lanczos_arith("df32")
+    with pytest.raises(RuntimeError):
+        plan.lanczos(_dev(psi), 4)
