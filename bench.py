@@ -549,7 +549,7 @@ def run_bp(args):
     n, edges = heavy_hex_graph(6, 11)
     chi, iters = args.bp_chi, args.bp_iters
     V, M = bp_tns_inputs(n, edges, chi, SEED)
-    ctx = tci.Context(0)
+    ctx = tci.Context(0, precision=args.bp_precision)
     tci.bp(ctx, n, edges, V, M, 2)                       # warm-up (allocator, kernels)
     t0 = time.perf_counter()
     got, res = tci.bp(ctx, n, edges, V, M, iters)
@@ -558,14 +558,19 @@ def run_bp(args):
     t0 = time.perf_counter()
     ref, rres = o_bp.bp(n, edges, V, M, n_cpu)
     cpu_s = time.perf_counter() - t0
+    got_s, _ = tci.bp(ctx, n, edges, V, M, n_cpu)           # the sampled iterations on the device
+    msg_diff = max(float(np.abs(g - r).max()) for g, r in zip(got_s, ref))
     fl = bp_flops(n, edges, V)
     line = {"metric": "BP iteration time, heavy-hex TNS", "value": 1e3 * gpu_s / iters, "unit": "ms per iteration",
-            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "dtype": "f64" if args.bp_precision == "native" else "bf16x3 pieces, f32 accumulation, f64 storage",
             "config": {"workload": f"BP message iteration on a {n}-qubit heavy-hex patch ({len(edges)} bonds, "
-                                   f"{2 * len(edges)} messages), random real TNS, d=2, chi {chi}, {iters} iterations",
+                                   f"{2 * len(edges)} messages), random real TNS, d=2, chi {chi}, {iters} iterations, "
+                                   f"{args.bp_precision} contractions",
                        "sites": n, "bonds": len(edges), "chi": chi, "iterations": iters},
             "gflops_per_s": fl / (gpu_s / iters) / 1e9, "flops_per_iteration": fl,
             "residual_last": res[-1], "oracle_residual_at_sample_end": rres[-1],
+            "max_message_diff_vs_oracle_at_sample_end": msg_diff,
             "device_residual_at_sample_end": res[n_cpu - 1],
             "cpu_baseline": {"value": 1e3 * cpu_s / n_cpu, "unit": "ms per iteration",
                              "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
@@ -705,6 +710,7 @@ def main():
     ap.add_argument("--bp-chi", type=int, default=32)
     ap.add_argument("--bp-iters", type=int, default=20)
     ap.add_argument("--bp-oracle-iters", type=int, default=3)
+    ap.add_argument("--bp-precision", default="native", choices=["native", "split_bf16"])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)

@@ -253,7 +253,9 @@ tci_status tci_transpose_to(tci_context ctx, tci_tensor in, const int* new_order
  * Both operands must have the same dtype.  Real F64/F32 contractions use the
  * context precision; complex ones use native arithmetic.
  * A label in a, b and c at once is a batch bond: every slice of it is
- * contracted on its own (C_IJB = sum_S A_ISB B_SJB), in native arithmetic.
+ * contracted on its own (C_IJB = sum_S A_ISB B_SJB), all slices in one
+ * launch (real operands under a split precision: one grouped tensor-core
+ * launch; otherwise native arithmetic).
  * Errors: LABEL (repeated label in one operand, count mismatch, dimension
  * mismatch), UNSUPPORTED (a free label missing from c), DTYPE, ALLOC, CUDA. */
 tci_status tci_contract(tci_context ctx, tci_tensor a, const char* labels_a, tci_tensor b,

@@ -166,8 +166,10 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
   if (!gb.modes.empty()) {
     // ----- batch bonds (labels in a, b and c): one product per batch slice.
     // Operands are packed to [batch][M][K] and [batch][N][K], the slices run
-    // as one batched launch of the native-arithmetic GEMM (any precision
-    // setting), and the [batch][M][N] result is scattered into c.
+    // as one launch -- the native-arithmetic batched GEMM, or for real
+    // operands under a split precision one grouped split-BF16 tensor-core
+    // launch with a problem per slice -- and the [batch][M][N] result is
+    // scattered into c.
     if (NB * M * N > 0) {
       auto pack3 = [&](tci_tensor t, bool is_a, const Group& g1, void** out) -> tci_status {
         int ord = 0;
@@ -197,8 +199,48 @@ static tci_status contract_impl(tci_context ctx, tci_tensor a, const int32_t* la
       if (s == TCI_OK) s = tci_dev_alloc(ctx, (size_t)(NB * M * N) * eb, &Ck);
       if (s != TCI_OK) return cleanup(s);
       scratch.push_back(Ck);
-      if (K == 0) cudaMemsetAsync(Ck, 0, (size_t)(NB * M * N) * eb, ctx->stream);
-      else s = tci_gemm_native_batched(ctx, dt, NB, M, N, K, Apk, M * K, K, 1, Bpk, N * K, K, 1, Ck, M * N, N, 1);
+      const bool split = ctx->precision != TCI_PREC_NATIVE && (dt == TCI_F64 || dt == TCI_F32);
+      if (K == 0) {
+        cudaMemsetAsync(Ck, 0, (size_t)(NB * M * N) * eb, ctx->stream);
+      } else if (split) {
+        // pieces of all slices in one plane set each: [3][NB*M][Kp] and [3][NB*N][Kp]
+        const int64_t Kp = (K + 7) / 8 * 8;
+        void *Ap3 = nullptr, *Bp3 = nullptr;
+        s = tci_dev_alloc(ctx, (size_t)(3 * NB * M * Kp) * 2, &Ap3);
+        if (s == TCI_OK) {
+          scratch.push_back(Ap3);
+          s = tci_dev_alloc(ctx, (size_t)(3 * NB * N * Kp) * 2, &Bp3);
+        }
+        if (s == TCI_OK) {
+          scratch.push_back(Bp3);
+          s = tci_launch_split3(ctx, dt, Apk, NB * M, K, K, 1, Ap3, Kp);
+        }
+        if (s == TCI_OK) s = tci_launch_split3(ctx, dt, Bpk, NB * N, K, K, 1, Bp3, Kp);
+        std::vector<tci_split_problem> probs;
+        for (int64_t bi = 0; bi < NB && s == TCI_OK; ++bi) {
+          tci_split_problem q;
+          q.Ap = (const char*)Ap3 + (size_t)(bi * M * Kp) * 2;
+          q.Bp = (const char*)Bp3 + (size_t)(bi * N * Kp) * 2;
+          q.M = M;
+          q.N = N;
+          q.Kp = Kp;
+          q.C = (char*)Ck + (size_t)(bi * M * N) * eb;
+          q.out_mode = dt == TCI_F64 ? 0 : 1;
+          q.scm = N;
+          q.scn = 1;
+          q.a_plane_rows = NB * M;
+          q.b_plane_rows = NB * N;
+          probs.push_back(q);
+        }
+        tci_split_group* grp = nullptr;
+        if (s == TCI_OK) s = tci_split_group_create(ctx, (int)probs.size(), probs.data(), &grp);
+        if (s == TCI_OK)
+          s = tci_split_group_launch(ctx, grp, ctx->precision == TCI_PREC_SPLIT_BF16_3 ? 3 : 6, ctx->split_chunk_k,
+                                     ctx->split_xchunk_k, 0);
+        if (grp) tci_split_group_destroy(grp);
+      } else {
+        s = tci_gemm_native_batched(ctx, dt, NB, M, N, K, Apk, M * K, K, 1, Bpk, N * K, K, 1, Ck, M * N, N, 1);
+      }
       if (s != TCI_OK) return cleanup(s);
       int ord = 0;
       int64_t shp[3 * TCI_MAX_ORDER], sst[3 * TCI_MAX_ORDER], dst[3 * TCI_MAX_ORDER];

@@ -641,7 +641,8 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
   for (int i : order) {
     const tci_split_problem& q = probs[i];
     GemmProblem pr;
-    TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_mode, q.scm, q.scn));
+    TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_mode, q.scm, q.scn, q.a_plane_rows,
+                         q.b_plane_rows));
     pr.tile_begin = tiles;
     tiles += pr.num_m * pr.num_n;
     host.push_back(pr);

@@ -178,6 +178,7 @@ struct tci_split_problem {
   void* C;          // element (m, n) at C[m*scm + n*scn]
   int out_mode;
   int64_t scm, scn;
+  int64_t a_plane_rows = 0, b_plane_rows = 0;   // piece-plane stride in rows (0: M, N)
 };
 struct tci_split_group;
 tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out);

@@ -76,3 +76,19 @@ def test_bp_isolated_site_and_zero_iterations(ctx, tci):
     _compare(tci, ctx, n, edges, V, M, 4)
     got, res = tci.bp(ctx, n, edges, V, M, 0)
     assert res == [] and all(np.array_equal(g, m) for g, m in zip(got, M))
+
+
+@pytest.mark.parametrize("chi", [4, 16])
+def test_bp_split_precision_close_to_oracle(ctx, tci, chi):
+    """Under the split-BF16 context precision the batched contractions run on the tensor cores."""
+    n, edges = heavy_hex_graph(3, 5)
+    V, M = bp_tns_inputs(n, edges, chi, seed=13)
+    ctx.set_precision("split_bf16")
+    try:
+        got, res = tci.bp(ctx, n, edges, V, M, 5)
+    finally:
+        ctx.set_precision("native")
+    ref, rres = o_bp.bp(n, edges, V, M, 5)
+    np.testing.assert_allclose(res, rres, rtol=1e-4, atol=1e-6)
+    for g, r in zip(got, ref):
+        assert np.linalg.norm(g - r) < 1e-5

@@ -200,7 +200,10 @@ def test_contract_batch_bonds_match_oracle(ctx, tci, la, lb, lc, dims, dtype, pr
     if ref.size == 0 or not np.any(ref):
         assert np.all(out == 0)
         return
-    tol = 1e-13 if dtype in (np.float64, np.complex128) else 2e-6
+    if prec == "split_bf16" and dtype != np.complex128:
+        tol = 3e-6                          # real slices run on the split-BF16 tensor cores
+    else:
+        tol = 1e-13 if dtype in (np.float64, np.complex128) else 2e-6
     assert rel_frob_err(out, ref) < tol
 
 
