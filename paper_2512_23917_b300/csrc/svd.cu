@@ -6,17 +6,20 @@
 // the kappa = min(I, J) vectors along the longer dimension (columns of A'
 // when J <= I, rows otherwise) are orthogonalised pairwise by plane rotations
 // that are also applied to Q (initially the identity).  Each round of a sweep
-// rotates kappa/2 disjoint pairs in parallel (round-robin order, one block per
-// pair); sweeps repeat until no pair needs a rotation.  Then the norms of the
-// vectors are the singular values, the normalised vectors one set of singular
-// vectors and Q the other.  Arithmetic is FP64 for F64 and F32 tensors.
+// rotates kappa/2 disjoint pairs in parallel (round-robin order, one block of
+// 128 threads per pair, row norms tracked so a pair needs one dot product;
+// rows up to 1024 long are rotated from registers, longer ones in scaled
+// form); sweeps repeat until no pair needs a rotation.  Then the norms of
+// the vectors are the singular values, the normalised vectors one set of
+// singular vectors and Q the other.  Arithmetic is FP64 for F64 and F32
+// tensors.
 //
 // From kappa = 32 up, the Jacobi iteration is preconditioned as Drmac &
 // Veselic (SIAM J. Matrix Anal. Appl. 29, 2008) do: a Householder QR with
 // column pivoting of the m x n matrix whose columns are the n vectors,
 // X P = H R, then one-sided Jacobi on the rows of R (R^T's columns).  On the
 // graded matrices of truncation workloads the sweep count drops severalfold
-// (about 30 to about 8 for an iTEBD two-site tensor).  With the converged
+// (about 30 to about 10 for an iTEBD two-site tensor).  With the converged
 // rows sigma_i x_i^T = (Q' R)_i: X = sum_i (H [q'_i; 0]) sigma_i (P x_i)^T,
 // so the length-m singular vectors are H applied to rows of Q' and the
 // length-n ones are the permuted rows x_i.
