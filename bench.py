@@ -191,6 +191,17 @@ def lanczos_launches(m: int) -> int:
     return n
 
 
+def lanczos_vector_roofline(ms_step: float, mv_ms: float, n: int, peaks) -> dict:
+    """The Lanczos vector work of one solve (step time minus its matvecs) against HBM: algorithmic
+    bytes 8 n (2j + 3) per step j (the basis read for the dots and for the update, w read and
+    written, the next vector written).  The passes are FP64-pipe bound on B300 (see DESIGN)."""
+    ms = ms_step - LANCZOS_STEPS * mv_ms
+    nbytes = sum(8.0 * n * (2 * j + 3) for j in range(LANCZOS_STEPS))
+    gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None
+    return {"ms_per_solve": ms, "algorithmic_bytes": nbytes, "achieved_gbs": gbs,
+            "peak_gbs": peaks["hbm_gbs"], "frac_hbm": gbs / peaks["hbm_gbs"] if gbs else None}
+
+
 def measure_blocksparse(tci, ctx, dev, peaks, with_oracle: bool):
     """U(1) block-sparse matvec, total chi = 2048, 31 sectors (one grouped launch per GEMM stage)."""
     import torch
@@ -485,6 +496,7 @@ def run_gpu(args):
             "lanczos_double_float_vectors": {"ms_per_step": lanczos_df_ms, "ritz_value": res_df["theta"],
                                              "ritz_rel_diff_vs_fp64": abs(res_df["theta"] - res["theta"]) / abs(res["theta"])
                                              if res else None},
+            "lanczos_vectors": lanczos_vector_roofline(ms_step, mv_only_ms, psi.size, peaks),
             "matvec": {"gflops": F / (mv_only_ms * 1e-3) / 1e9, "ms": mv_only_ms,
                        "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),
                                     "gemm2": float(st[3])},
