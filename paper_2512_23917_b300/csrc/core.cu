@@ -828,10 +828,7 @@ __global__ void k_sum_partials(const double* __restrict__ part, int np, double* 
   if (threadIdx.x == 0) *out = s;
 }
 
-static double* g_partials_unused = nullptr;
-
 tci_status tci_launch_sumsq(tci_context ctx, tci_dtype dt, const void* x, int64_t n, double* d_out) {
-  // partials live after the first 8 scalars of the context scratch when they fit
   static_assert(kRedBlocks <= 4096, "partials");
   double* part = nullptr;
   TCI_TRY(tci_dev_alloc(ctx, kRedBlocks * sizeof(double), (void**)&part));
@@ -843,9 +840,8 @@ tci_status tci_launch_sumsq(tci_context ctx, tci_dtype dt, const void* x, int64_
   }
   k_sum_partials<<<1, 1024, 0, ctx->stream>>>(part, kRedBlocks, d_out);
   cudaError_t e = cudaGetLastError();
-  cudaFreeAsync(part, ctx->stream);
+  tci_dev_free(part);   // stream-ordered, after the two kernels
   if (e != cudaSuccess) return tci_cuda_fail(ctx, e, "sumsq kernels");
-  (void)g_partials_unused;
   return TCI_OK;
 }
 

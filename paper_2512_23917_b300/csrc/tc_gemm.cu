@@ -64,7 +64,7 @@ constexpr int COLS_PER_WARP = TBN / (NEPI / 4);  // columns drained by one epilo
 // One GEMM of a (possibly grouped) launch.  In a grouped launch the table
 // lives in device memory, sorted by decreasing K so the longest tiles are
 // scheduled first; tiles of problem i are [tile_begin, tile_begin + num_m*num_n).
-struct alignas(64) GemmProblem {
+struct GemmProblem {   // aligned as its tensor maps (TMA descriptors in global memory)
   CUtensorMap tmA;   // bf16 pieces [3][M][Kp], box {32, 128, 3}
   CUtensorMap tmB;   // bf16 pieces [3][N][Kp], box {32, 128, 3}
   void* C;
@@ -72,6 +72,7 @@ struct alignas(64) GemmProblem {
   int num_m, num_n, num_kb, tile_begin;
   int out_mode, pad0, pad1, pad2;
 };
+static_assert(alignof(GemmProblem) >= 64 && sizeof(GemmProblem) % 64 == 0, "tensor maps need 64-byte alignment");
 
 struct GemmParams {
   const GemmProblem* table;   // grouped launches only
