@@ -178,15 +178,17 @@ def run_reference(args):
 
 # ---------------------------------------------------------------------------- GPU path
 def lanczos_launches(m: int) -> int:
-    """Kernel launches of one m-step Lanczos solve on a split-BF16 plan (basis <= 20 vectors, DGKS)."""
+    """Kernel launches of one m-step Lanczos solve on a split-BF16 plan (basis <= 20 vectors, DGKS);
+    with graph replay the host enqueues them as one graph launch."""
     n = 4                                           # init scalars, psi0 sum of squares + reduce, start vector
     for j in range(m):
         n += 3                                      # GEMM1, W.W, GEMM2 (the split is fused into the next-vector kernel)
-        n += 3 + 1                                  # pass-1 dots + reduce + sum-of-squares reduce, alpha / DGKS test
-        n += 2 + 2 + 2                              # gated: update+dots, update+norm (second pass); update+norm
+        n += 3 + 1                                  # pass-1 dots + reduces (dots, sum of squares), alpha / DGKS test
+        n += 3 + 1                                  # gated: update + dots + norm and reduces, pass-3 choice
+        n += 2 + 2                                  # gated: FP64 pass 3 + reduce; skipped branch update + reduce
         n += 1                                      # beta / stop test
         if j + 1 < m:
-            n += 1                                  # v_{j+1} = w / beta and its bfloat16 pieces
+            n += 2                                  # v_{j+1} (gated: plain, or with the FP32 pass-3 terms)
     n += 2                                          # tridiagonal eigensolve, Ritz vector
     return n
 

@@ -424,7 +424,10 @@ tci_status tci_bp(tci_context ctx, int nsites, int nedges, const int64_t* edges,
                   tci_tensor* messages, int niters, double tol, int* iters_done, double* residuals);
 
 /* Vector arithmetic of tci_lanczos (extension; the paper has no Lanczos
- * API).  TCI_LANCZOS_F64: every dot product and vector update in FP64.
+ * API).  TCI_LANCZOS_F64: vectors in FP64, every dot product and every
+ * update term that is not at rounding level in FP64 (rounding-level
+ * Gram-Schmidt terms are summed in FP32 under an error bound below FP64
+ * rounding, see tci_heff_lanczos_stats).
  * TCI_LANCZOS_DF32: vectors held as pairs of FP32 numbers hi + lo
  * (double-float, Dekker 1971; ~48 significant bits) with error-free
  * transformations, so the vector passes run on the FP32 pipes (B300 issues
@@ -468,6 +471,29 @@ tci_status tci_heff_set_gram_schmidt(tci_heff_plan plan, tci_gram_schmidt mode);
  * Synchronises.  Errors: INVALID_ARG, SHAPE, ALLOC, CUDA. */
 tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reorth, double* ritz,
                        double* alpha, double* beta, int* steps_done, tci_tensor x);
+
+/* Counters of the last tci_lanczos on `plan` (extension), into stats[4]
+ * (host): [0] steps done; [1] steps whose Gram-Schmidt projection was
+ * repeated (DGKS) or, with TCI_GS_TWICE, every re-orthogonalised step;
+ * [2] update passes whose rounding-level terms (coefficients of v_0 ..
+ * v_{j-2}, 1-norm at most 2^-32 ||w|| / (k + 8) for k such terms) were
+ * summed in FP32 and subtracted with one FP64 FMA, adding an error below
+ * 2^-56 ||w||; [3] steps whose second projection was applied that way,
+ * folded into the next-vector pass with beta_j^2 = ||w'||^2 - |h'|^2.  [2]
+ * and [3] stay 0 for double-float vectors and without re-orthogonalisation.
+ * All zero before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
+tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
+
+/* CUDA-graph replay of tci_lanczos on split-precision real plans
+ * (extension; on by default).  A solve launches a sequence fixed by its
+ * arguments (psi0 and x addresses, nsteps, reorth, the vector arithmetic,
+ * the Gram-Schmidt mode and the plan's GEMM configuration), every branch
+ * being decided on the device; the first call with a given sequence runs
+ * eagerly, the second captures it into a graph and later calls replay the
+ * graph, so the host enqueues one launch per solve.  enable = 0 runs every
+ * solve eagerly and releases the graph.  Results are identical either way.
+ * Errors: INVALID_ARG, INVALID_CONTEXT. */
+tci_status tci_heff_set_lanczos_graphs(tci_heff_plan plan, int enable);
 
 /* ------------------------------------------- U(1) block-sparse H_eff
  * Charge-conserving (U(1)) block-sparse tensors are listed as future work of

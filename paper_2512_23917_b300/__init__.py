@@ -99,6 +99,8 @@ SIGNATURES = [
     ("tci_bs_autotune", C.c_int, [_p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_tebd_autotune", C.c_int, [_p, _p, _p, _p, _p, C.c_int, C.POINTER(C.c_int)]),
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
+    ("tci_heff_lanczos_stats", C.c_int, [_p, C.POINTER(C.c_int)]),
+    ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_create2", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(_p)]),
     ("tci_tebd_theta_batched", C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
@@ -602,6 +604,17 @@ class HeffPlan:
                                C.byref(k), tx.handle if tx is not None else None), self.ctx.handle)
         return {"theta": ritz.value, "alpha": np.array(alpha[:k.value]), "beta": np.array(beta[:k.value]),
                 "steps": k.value}
+
+    def set_lanczos_graphs(self, enable: bool):
+        """Replay repeated lanczos() calls from a captured CUDA graph (default on, split plans)."""
+        _check(lib.tci_heff_set_lanczos_graphs(self.handle, int(bool(enable))), self.ctx.handle)
+
+    def lanczos_stats(self):
+        """Counters of the last lanczos(): steps, repeated projections, FP32-term update passes,
+        second projections folded into the next-vector pass."""
+        st = (C.c_int * 4)()
+        _check(lib.tci_heff_lanczos_stats(self.handle, st), self.ctx.handle)
+        return {"steps": st[0], "second_passes": st[1], "f32_term_passes": st[2], "fused_pass3": st[3]}
 
     def close(self):
         if self.handle:

@@ -464,6 +464,7 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   }
   if (p->s_h2d) cudaStreamDestroy(p->s_h2d);
   if (p->s_d2h) cudaStreamDestroy(p->s_d2h);
+  tci_graph_destroy(&p->lz_graph);
   p->magic = 0;
   delete p;
   *pp = nullptr;

@@ -9,12 +9,28 @@
 //                                                prepared with v_j)
 //   pass 1: h = V^T w, ||w||^2;  alpha_j = h_j   (one read of V and w)
 //   DGKS test: ||w - V h||^2 = ||w||^2 - |h|^2 < ||w||^2 / 2 ?
-//   taken:   pass 2: w -= V h, then h' = V^T w   (fused: V read once, w r/w)
-//            pass 3: w -= V h', then ||w||^2     (fused)
-//   skipped: pass 2': w -= V h, then ||w||^2     (fused)
-//   (all three passes are launched; device gates make the unused ones exit)
+//   taken:   pass 2: w -= V h, then h' = V^T w and ||w||^2  (fused: V read
+//                    once, w read and written)
+//            pass 3: w -= V h', then ||w||^2                (fused)
+//   skipped: pass 2': w -= V h, then ||w||^2                (fused)
+//   (all passes are launched; device gates make the unused ones exit)
 //   beta_j = ||w||;  v_{j+1} = w / beta_j, written with the next matvec's
 //   input (its bfloat16 pieces on a split-BF16 plan) in the same pass.
+//
+// Rounding-level terms in FP32 (FP64 vectors only).  In a Lanczos step the
+// pass-1 coefficients h_0 .. h_{j-2} and all second-pass coefficients h' are
+// of the order of the rounding error of w (the recurrence leaves only
+// alpha_j and beta_{j-1}).  Where a device test bounds their 1-norm by
+// 2^-32 ||w|| / (k + 8), k the number of such terms, these are summed in
+// FP32 from the basis
+// truncated to 24 significant bits (f32_trunc) and subtracted from w with
+// one FP64 FMA; the error this adds is below 2^-56 ||w||, under the FP64
+// rounding of the update itself.  Pass 3 is then folded into the
+// next-vector kernel, with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h'
+// is orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  Every
+// product and sum that decides alpha, beta or a coefficient stays FP64;
+// the FP32 terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64
+// of its FP32 rate).  Where the test fails the FP64 passes run instead.
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
 // followed by one or two classical Gram-Schmidt passes.  Without
@@ -55,11 +71,36 @@ constexpr int OFF_CTRL = 3 * MAXM + 8;   // [0] stop flag, [1] steps done, [2] t
                                          // [4] pass-1 sum of squares, [5] [6] pass gates, [7] second passes
 constexpr int OFF_Y = 3 * MAXM + 16;     // Ritz coefficients
 constexpr int OFF_H2 = 4 * MAXM + 32;    // MAXM + 1 entries: pass-2 coefficients
+constexpr int OFF_LO = 5 * MAXM + 40;    // FP32 rounding-level terms (LO_* below)
 constexpr int NSCAL = 5 * MAXM + 64;
+// OFF_LO + : pass-2 / 2' FP32 terms (count, scale, inverse scale), pass-2
+// ||w'||^2, pass-3 FP32 scale and inverse, gates (run while 0) of the FP32
+// next-vector kernel, the FP64 pass 3 and the plain next-vector kernel,
+// counters of FP32-term passes and fused pass-3 corrections.
+constexpr int LO_NS1 = 0, LO_SC1 = 1, LO_ISC1 = 2, LO_WN2 = 3, LO_SC3 = 4, LO_ISC3 = 5;
+constexpr int LO_GFAST = 6, LO_GSLOW = 7, LO_GNEXT = 8, LO_N1 = 9, LO_N3 = 10;
+static_assert(OFF_LO + LO_N3 < NSCAL, "scalar layout");
+// FP32 terms are taken where their coefficients' 1-norm times (nv + 8) is
+// at most 2^-32 times the norm of the vector they update.
+constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   return v;
+}
+
+// x truncated to an FP32 number with 24 significant bits, from the IEEE-754
+// bit fields on the integer pipes (no FP64 instruction): the exponent is
+// re-biased (1023 -> 127) and the top 23 fraction bits kept.  Exponents are
+// clamped to FP32's normal range, so |x| < 2^-126 becomes a number of that
+// size with x's sign (an absolute error below 2^-125) and |x| >= 2^128 the
+// largest binade; NaN and infinity are not preserved (only basis vectors,
+// |x| <= 1, come here).
+__device__ __forceinline__ float f32_trunc(double x) {
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  unsigned a = min(max(hi & 0x7fffffffu, 0x38100000u), 0x47efffffu);   // exponent in [897, 1150]
+  a -= 0x38000000u;                                                      // 1023 - 127 = 896
+  return __uint_as_float(__funnelshift_l(lo, a, 3) | (hi & 0x80000000u));
 }
 
 // ---------------------------------------------------------------- double-float
@@ -162,10 +203,13 @@ struct ArithDF {
 // ---------------------------------------------------------------- vector kernels
 // Per-block partial sums of G accumulators (fixed order): part[g*NBMAX +
 // blockIdx.x] for g < nv.
+// Called by every thread of the block; two calls with the same G in one
+// kernel share `sh`, hence the barrier before it is written.
 template <class A, int G>
 __device__ __forceinline__ void block_partials(const typename A::Acc (&a)[G], int nv, double* part) {
   __shared__ double sh[NT / 32][G];
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
 #pragma unroll
   for (int g = 0; g < G; ++g)
     if (g < nv) {
@@ -208,16 +252,27 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
 }
 
 // w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
-// into part rows v0 + g, or (SUMSQ) partials of ||w||^2 into part_sq.
+// into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  With
+// lo (FP64 vectors only; v0 = 0) the first lo[LO_NS1] terms are summed in
+// FP32 with coefficients scaled by lo[LO_SC1] and subtracted with one FP64
+// FMA (see the header).
 template <class A, int G, bool DOTS, bool SUMSQ>
 __global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                                const double* __restrict__ coef, typename A::V* __restrict__ w,
                                                int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
-                                               const double* __restrict__ ctrl) {
+                                               const double* __restrict__ ctrl, const double* __restrict__ lo) {
   using Vt = typename A::V;
+  constexpr bool kF64 = std::is_same<Vt, double>::value;
   if (ctrl[0] != 0.0) return;
   __shared__ typename A::Coef cs[G];
-  if (threadIdx.x < G) cs[threadIdx.x] = A::coef(threadIdx.x < nv ? coef[v0 + threadIdx.x] : 0.0);
+  __shared__ float csf[G];
+  const int ns = (kF64 && lo) ? (int)lo[LO_NS1] : 0;
+  if (threadIdx.x < G) {
+    const double c = threadIdx.x < nv ? coef[v0 + threadIdx.x] : 0.0;
+    cs[threadIdx.x] = A::coef(c);
+    csf[threadIdx.x] = ns > 0 ? (float)(c * lo[LO_SC1]) : 0.f;
+  }
+  const double isc = ns > 0 ? lo[LO_ISC1] : 0.0;
   __syncthreads();
   constexpr int GD = DOTS ? G : 1;
   typename A::Acc d[GD];
@@ -248,10 +303,23 @@ __global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__
         if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i + stride];
     }
     typename A::Sub t = A::sub_begin(x);
+    Vt y;
+    if constexpr (kF64) {
+      float sf = 0.f;
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) A::sub(t, cs[g], v[g]);
-    const Vt y = A::sub_end(t);
+      for (int g = 0; g < G; ++g)
+        if (g < nv) {
+          if (g < ns) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
+          else A::sub(t, cs[g], v[g]);
+        }
+      y = A::sub_end(t);
+      if (ns > 0) y = fma(-(double)sf, isc, y);
+    } else {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < nv) A::sub(t, cs[g], v[g]);
+      y = A::sub_end(t);
+    }
     w[i] = y;
     if (DOTS) {
 #pragma unroll
@@ -290,13 +358,13 @@ __device__ __forceinline__ void emit(typename A::V y, int64_t i, int64_t r, int6
   if (MODE == kInF64) x64[i] = A::to_double(y);
 }
 
-// v_{j+1} = w / beta_j (unless stopped); element (r, k) of [rows][cols].
+// v_{j+1} = w / beta_j (unless stopped or gated off); element (r, k) of [rows][cols].
 template <class A, int MODE>
 __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w, typename A::V* __restrict__ vn,
                                              int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
-                                             int j) {
-  if (scal[OFF_CTRL] != 0.0) return;
+                                             int j, const double* __restrict__ gate) {
+  if (scal[OFF_CTRL] != 0.0 || gate[0] != 0.0) return;
   const typename A::Coef c = A::coef(1.0 / scal[OFF_BETA + j]);
   const int64_t plane = rows * Kp;
   const int64_t kend = MODE == kInPieces ? Kp : cols;
@@ -305,6 +373,38 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
       if (k < cols) {
         const int64_t i = r * cols + k;
         emit<A, MODE>(A::mul(w[i], c), i, r, k, vn, pieces, Kp, plane, x64);
+      } else {
+        split3_store(pieces + r * Kp + k, plane, 0.f);
+      }
+    }
+}
+
+// Pass 3 folded into the next vector (FP64 vectors): v_{j+1} = (w - V h') /
+// beta_j with the rounding-level terms h'_g v_g summed in FP32 (header);
+// runs where k_post_pass2 chose it.
+template <int MODE>
+__global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, int64_t ldv, int nv,
+                                                  const double* __restrict__ w, double* __restrict__ vn, int64_t rows,
+                                                  int64_t cols, __nv_bfloat16* __restrict__ pieces, int64_t Kp,
+                                                  const double* __restrict__ scal, int j) {
+  if (scal[OFF_CTRL] != 0.0 || scal[OFF_LO + LO_GFAST] != 0.0) return;
+  __shared__ float cf[MAXM];
+  const double sc = scal[OFF_LO + LO_SC3];
+  for (int g = threadIdx.x; g < nv; g += NT) cf[g] = (float)(scal[OFF_H2 + g] * sc);
+  __syncthreads();
+  const double isc = scal[OFF_LO + LO_ISC3];
+  const double binv = 1.0 / scal[OFF_BETA + j];
+  const int64_t plane = rows * Kp;
+  const int64_t kend = MODE == kInPieces ? Kp : cols;
+  for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+    for (int64_t k = threadIdx.x; k < kend; k += NT) {
+      if (k < cols) {
+        const int64_t i = r * cols + k;
+        float sf = 0.f;
+#pragma unroll 8
+        for (int g = 0; g < nv; ++g) sf = __fmaf_rn(cf[g], f32_trunc(V[(int64_t)g * ldv + i]), sf);
+        const double y = fma(-(double)sf, isc, w[i]) * binv;
+        emit<ArithF64, MODE>(y, i, r, k, vn, pieces, Kp, plane, nullptr);
       } else {
         split3_store(pieces + r * Kp + k, plane, 0.f);
       }
@@ -396,8 +496,14 @@ __global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int6
 // Math. Comp. 30, 1976).  Gates read by the passes that follow (a pass runs
 // while its gate is 0): ctrl[5] = 1 when the second pass is skipped (or the
 // iteration stopped), ctrl[6] = 1 when it is taken (or stopped).
-__global__ void k_post_pass1(double* scal, int j, int reorth, int dgks) {
+//
+// With f32 (FP64 vectors, re-orthogonalisation) the terms of h_0 .. h_{j-2}
+// in passes 2 and 2' are summed in FP32 where sum |h_i| (j + 7) <= 2^-32 ||w||
+// (header); the FP32 scale puts the largest of them in [1, 2).
+__global__ void k_post_pass1(double* scal, int j, int reorth, int dgks, int f32) {
   double* ctrl = scal + OFF_CTRL;
+  double* lo = scal + OFF_LO;
+  lo[LO_NS1] = 0.0;
   if (ctrl[0] != 0.0) {
     ctrl[5] = 1.0;
     ctrl[6] = 1.0;
@@ -414,6 +520,56 @@ __global__ void k_post_pass1(double* scal, int j, int reorth, int dgks) {
   ctrl[5] = second ? 0.0 : 1.0;
   ctrl[6] = second ? 1.0 : 0.0;
   if (reorth && second) ctrl[7] += 1.0;   // second passes taken (reported with TCI_VERBOSE)
+  if (reorth && f32 && j >= 2) {
+    double l1 = 0.0, mx = 0.0;
+    for (int i = 0; i + 1 < j; ++i) {
+      const double a = fabs(scal[OFF_H + i]);
+      l1 += a;
+      mx = fmax(mx, a);
+    }
+    if (l1 * (double)(j + 7) <= kF32Bound * sqrt(ctrl[4])) {
+      const int e = mx > 0.0 ? ilogb(mx) : 0;
+      lo[LO_NS1] = (double)(j - 1);
+      lo[LO_SC1] = ldexp(1.0, -e);
+      lo[LO_ISC1] = ldexp(1.0, e);
+      lo[LO_N1] += 1.0;
+    }
+  }
+}
+
+// After pass 2 (second Gram-Schmidt pass taken and not stopped): fold pass 3
+// into the next-vector kernel where f32 and sum |h'_i| (j + 9) <= 2^-32 ||w'||,
+// setting ||w||^2 = ||w'||^2 - |h'|^2 for beta_j; else run pass 3 in FP64.
+// Gates (run while 0): LO_GFAST fused kernel, LO_GSLOW FP64 pass 3,
+// LO_GNEXT plain next-vector kernel.
+__global__ void k_post_pass2(double* scal, int j, int f32) {
+  double* ctrl = scal + OFF_CTRL;
+  double* lo = scal + OFF_LO;
+  if (ctrl[0] != 0.0 || ctrl[5] != 0.0) {   // stopped, or the second pass was skipped
+    lo[LO_GFAST] = 1.0;
+    lo[LO_GSLOW] = 1.0;
+    lo[LO_GNEXT] = 0.0;
+    return;
+  }
+  double l1 = 0.0, l2 = 0.0, mx = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    const double a = fabs(scal[OFF_H2 + i]);
+    l1 += a;
+    l2 += a * a;
+    mx = fmax(mx, a);
+  }
+  const double wn2 = lo[LO_WN2];
+  const bool fast = f32 && wn2 > 0.0 && l1 * (double)(j + 9) <= kF32Bound * sqrt(wn2);
+  lo[LO_GFAST] = fast ? 0.0 : 1.0;
+  lo[LO_GSLOW] = fast ? 1.0 : 0.0;
+  lo[LO_GNEXT] = fast ? 1.0 : 0.0;
+  if (fast) {
+    const int e = mx > 0.0 ? ilogb(mx) : 0;
+    lo[LO_SC3] = ldexp(1.0, -e);
+    lo[LO_ISC3] = ldexp(1.0, e);
+    ctrl[3] = wn2 - l2;
+    lo[LO_N3] += 1.0;
+  }
 }
 
 // beta_j = ||w||, stop test, step counter.
@@ -603,12 +759,31 @@ int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, 
   return grid;
 }
 
+// FP64 passes are instantiated for every basis size G = nv: the compiler
+// evaluates the FMAs of an unrolled `if (g < nv)` loop unconditionally and
+// selects the result, and on B300 each needless DFMA costs as much as a
+// needed one.  Double-float passes (FP32 pipes) use G in {8, 16, GMAX}.
+template <class A, bool SQ, int G = 1>
+int dots_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
+               int64_t n, double* part, double* part_sq, const double* ctrl) {
+  if constexpr (G == GMAX) {
+    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  } else {
+    if (nv <= G) return dots_launch_g<A, G, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    return dots_exact<A, SQ, G + 1>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  }
+}
+
 template <class A, bool SQ>
 int dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
                 int64_t n, double* part, double* part_sq, const double* ctrl) {
-  if (nv <= 8) return dots_launch_g<A, 8, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
-  if (nv <= 16) return dots_launch_g<A, 16, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
-  return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  if constexpr (std::is_same<A, ArithF64>::value) {
+    return dots_exact<A, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  } else {
+    if (nv <= 8) return dots_launch_g<A, 8, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    if (nv <= 16) return dots_launch_g<A, 16, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  }
 }
 
 // out[0..nv) = <V_{v0+v}, w>; *sumsq_out = ||w||^2 when sumsq_out
@@ -630,49 +805,72 @@ tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
 
 template <class A, int G, bool DOTS, bool SUMSQ>
 int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
-                    typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
+                    typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl,
+                    const double* lo) {
   const int grid = pass_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ>, n);
-  k_update<A, G, DOTS, SUMSQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+  k_update<A, G, DOTS, SUMSQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
   return grid;
+}
+
+template <class A, bool DOTS, bool SUMSQ, int G = 1>
+int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
+                 typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+  if constexpr (G == GMAX) {
+    return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  } else {
+    if (nv <= G) return update_launch_g<A, G, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_exact<A, DOTS, SUMSQ, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  }
 }
 
 template <class A, bool DOTS, bool SUMSQ>
 int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
-                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl) {
-  if (nv <= 8) return update_launch_g<A, 8, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-  if (nv <= 16) return update_launch_g<A, 16, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-  return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
+                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+  if constexpr (std::is_same<A, ArithF64>::value) {
+    return update_exact<A, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  } else {
+    if (nv <= 8) return update_launch_g<A, 8, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (nv <= 16)
+      return update_launch_g<A, 16, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  }
 }
 
 // w -= sum_{v0 <= v < v0+nv} coef[v] V_v; then dots_out[0..nv) = <V_v, w>
-// (when dots_out) or *sumsq_out = ||w||^2 (when sumsq_out).  One fused pass
-// for nv <= GMAX; a larger basis is updated group by group and its dots
-// taken in a separate pass.
+// (when dots_out) and *sumsq_out = ||w||^2 (when sumsq_out).  One fused pass
+// for nv <= GMAX (with lo: FP32 rounding-level terms, v0 = 0); a larger
+// basis is updated group by group in FP64 and its dots taken in a separate pass.
 template <class A>
 tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                       typename A::V* w, int64_t n, double* part, double* dots_out, double* sumsq_out,
-                      const double* ctrl) {
+                      const double* ctrl, const double* lo = nullptr) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
-  if (dots_out && sumsq_out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (dots and sumsq in one pass)");
+  if (lo && v0 != 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (FP32 terms need v0 = 0)");
   int sq_grid = 0;
   if (nv <= GMAX) {
-    if (dots_out) {
-      const int grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-      k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
-    } else if (sumsq_out) {
-      sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    } else {
-      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl);
-    }
+    int grid = 0;
+    if (dots_out && sumsq_out)
+      grid = update_launch<A, true, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    else if (dots_out)
+      grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    else if (sumsq_out)
+      grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    else
+      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
+    sq_grid = grid;
   } else {
     for (int g0 = 0; g0 < nv; g0 += GMAX) {
       const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
-      if (g0 + g == nv && sumsq_out)
-        sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+      if (g0 + g == nv && sumsq_out && !dots_out)
+        sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr);
       else
-        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl);
+        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr);
     }
-    if (dots_out) TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl));
+    if (dots_out) {
+      TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl, sumsq_out));
+      sumsq_out = nullptr;   // reduced by run_dots
+    }
   }
   if (sumsq_out) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, sq_grid, sumsq_out, ctrl);
   TCI_CUDA(ctx, cudaGetLastError());
@@ -688,9 +886,16 @@ void launch_start(tci_context ctx, const double* psi0, typename A::V* v0, int64_
 
 template <class A, int MODE>
 void launch_next(tci_context ctx, const typename A::V* w, typename A::V* vn, int64_t rows, int64_t cols,
-                 __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j) {
+                 __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j, const double* gate) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
-  k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j);
+  k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j, gate);
+}
+
+template <int MODE>
+void launch_next_corr(tci_context ctx, const double* V, int64_t ldv, int nv, const double* w, double* vn,
+                      int64_t rows, int64_t cols, __nv_bfloat16* pieces, int64_t Kp, const double* S, int j) {
+  const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
+  k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j);
 }
 
 // The Lanczos iteration in arithmetic A with matvec input mode MODE
@@ -705,6 +910,9 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   const int64_t n = rows * cols;
   const int64_t ldv = (n + 31) / 32 * 32;
   constexpr bool kDF = std::is_same<Vt, float2>::value;
+  // FP32 rounding-level terms: FP64 vectors whose next vector is written by
+  // k_next / k_next_corr (every mode but the double-float one)
+  constexpr bool kF32Terms = !kDF && MODE != kInF64;
   if (MODE == kInF64) {
     if (!p->lz_x64) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_x64));
     if (!p->lz_o64) TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * n, (void**)&p->lz_o64));
@@ -740,21 +948,31 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // classical Gram-Schmidt against the whole basis, repeated where the first
       // pass cancelled (DGKS); both continuations are launched, each gated
       const int dgks = (p->gs_mode == TCI_GS_DGKS && j + 1 <= GMAX) ? 1 : 0;
-      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, dgks ? ctrl + 4 : nullptr));
-      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks);
-      // second pass taken: w -= V h with the new dots, then w -= V h2 with ||w||^2
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, nullptr, ctrl + 5));
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, ctrl + 5));
+      const double* lo1 = (kF32Terms && j + 1 <= GMAX) ? S + OFF_LO : nullptr;
+      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, (kF32Terms && j + 1 <= GMAX) ? 1 : 0);
+      // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
+      // with ||w||^2 in FP64, or folded into the next-vector kernel
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,
+                            lo1));
+      k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, kF32Terms ? 1 : 0);
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW));
       // second pass skipped: w -= V h with ||w||^2
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6));
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6, lo1));
     } else {
       TCI_TRY(run_dots<A>(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl));
-      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0, 0);
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0, 0, 0);
       const int v0 = j > 0 ? j - 1 : 0;
       TCI_TRY(run_update<A>(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl));
     }
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
-    if (j + 1 < nsteps) launch_next<A, MODE>(ctx, w, V + (int64_t)(j + 1) * ldv, rows, cols, pieces, Kp, p->lz_x64, S, j);
+    if (j + 1 < nsteps) {
+      Vt* vn = V + (int64_t)(j + 1) * ldv;
+      launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl);
+      if constexpr (kF32Terms) {
+        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j);
+      }
+    }
     TCI_CUDA(ctx, cudaGetLastError());
   }
   k_tridiag_lowest<<<1, NT, 0, ctx->stream>>>(S);
@@ -763,6 +981,29 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   return TCI_OK;
 }
 
+}  // namespace
+
+namespace {
+struct SolveArgs {
+  tci_heff_plan p;
+  const double* psi;
+  int nsteps, reorth;
+  double* x;
+  double tol;
+  int arith;
+  bool split;
+};
+
+// One solve's launches on p->ctx->stream (the body a graph captures).
+tci_status solve_body(void* a) {
+  const SolveArgs& s = *(const SolveArgs*)a;
+  if (s.arith == TCI_LANCZOS_DF32) {
+    if (s.split) return lanczos_run<ArithDF, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+    return lanczos_run<ArithDF, kInF64>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+  }
+  if (s.split) return lanczos_run<ArithF64, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+  return lanczos_run<ArithF64, kInNone>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+}
 }  // namespace
 
 extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, int reorth, double* ritz, double* alpha,
@@ -808,20 +1049,47 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   vs.info = arith == TCI_LANCZOS_DF32 ? "double-float vectors" : "FP64 vectors";
   const double* psi = (const double*)psi0->data;
   double* xd = x ? (double*)x->data : nullptr;
-  if (arith == TCI_LANCZOS_DF32) {
-    if (split) TCI_TRY((lanczos_run<ArithDF, kInPieces>(p, psi, nsteps, reorth, xd, tol)));
-    else TCI_TRY((lanczos_run<ArithDF, kInF64>(p, psi, nsteps, reorth, xd, tol)));
-  } else {
-    if (split) TCI_TRY((lanczos_run<ArithF64, kInPieces>(p, psi, nsteps, reorth, xd, tol)));
-    else TCI_TRY((lanczos_run<ArithF64, kInNone>(p, psi, nsteps, reorth, xd, tol)));
+  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split};
+  bool done = false;
+  if (split && !p->cplx && p->lz_graphs) {
+    // eager on the first call with a key, captured on the second, replayed after
+    const std::vector<int64_t> key = {(int64_t)(uintptr_t)psi, (int64_t)(uintptr_t)xd, nsteps, reorth, arith,
+                                      p->gs_mode, p->products, p->chunk_k, p->xchunk_k, p->raster, p->ww_na,
+                                      (int64_t)(uintptr_t)p->lz_V, (int64_t)ctx->wait_limit_ns};
+    if (!(p->lz_graph.exec && key == p->lz_graph_key) && key == p->lz_last_key) {
+      tci_graph_destroy(&p->lz_graph);
+      p->lz_graph_key.clear();
+      if (tci_graph_capture(ctx, &p->lz_graph, solve_body, &sa, {}) == TCI_OK) {
+        p->lz_graph_key = key;
+      } else {   // run eagerly from now on
+        tci_graph_destroy(&p->lz_graph);
+        cudaGetLastError();
+        p->lz_graphs = 0;
+      }
+    }
+    if (p->lz_graph.exec && key == p->lz_graph_key) {
+      TCI_CUDA(ctx, cudaGraphLaunch(p->lz_graph.exec, ctx->stream));
+      done = true;
+    }
+    p->lz_last_key = key;
   }
+  if (!done) TCI_TRY(solve_body(&sa));
   TCI_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctrl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  std::vector<double> ab(2 * MAXM);
+  std::vector<double> ab(2 * MAXM), cnt(2);
   TCI_CUDA(ctx, cudaMemcpyAsync(ab.data(), S, 2 * MAXM * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+  TCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), S + OFF_LO + LO_N1, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  static_assert(LO_N3 == LO_N1 + 1, "counter layout");
   TCI_TRY(tci_synchronize(ctx));
   const int k = (int)ctx->h_scalars[1];
   *ritz = ctx->h_scalars[2];
-  if (ctx->verbose > 0 && reorth) vs.info += " second_gs_passes=" + std::to_string((int)ctx->h_scalars[7]);
+  p->lz_stats[0] = k;
+  p->lz_stats[1] = reorth ? (int)ctx->h_scalars[7] : 0;
+  p->lz_stats[2] = (int)cnt[0];
+  p->lz_stats[3] = (int)cnt[1];
+  if (ctx->verbose > 0 && reorth)
+    vs.info += " second_gs_passes=" + std::to_string(p->lz_stats[1]) + " f32_term_passes=" +
+               std::to_string(p->lz_stats[2]) + " fused_pass3=" + std::to_string(p->lz_stats[3]);
   if (steps_done) *steps_done = k;
   for (int i = 0; i < nsteps; ++i) {
     if (alpha) alpha[i] = i < k ? ab[OFF_ALPHA + i] : 0.0;
@@ -845,5 +1113,26 @@ extern "C" tci_status tci_heff_set_gram_schmidt(tci_heff_plan p, tci_gram_schmid
   if (mode != TCI_GS_DGKS && mode != TCI_GS_TWICE)
     return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "set_gram_schmidt: unknown mode %d", (int)mode);
   p->gs_mode = (int)mode;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_lanczos_stats(tci_heff_plan p, int* stats) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "lanczos_stats: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (!stats) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "lanczos_stats: NULL stats");
+  for (int i = 0; i < 4; ++i) stats[i] = p->lz_stats[i];
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_lanczos_graphs(tci_heff_plan p, int enable) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_graphs: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  p->lz_graphs = enable ? 1 : 0;
+  if (!enable) {
+    cudaStreamSynchronize(p->ctx->stream);
+    tci_graph_destroy(&p->lz_graph);
+    p->lz_graph_key.clear();
+    p->lz_last_key.clear();
+  }
   return TCI_OK;
 }

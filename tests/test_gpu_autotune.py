@@ -47,3 +47,23 @@ def test_tebd_autotune_parity(ctx, tci):
     for c, a, b, g in zip(chis, A, B, G):
         assert rel_frob_err(got[off:off + 4 * c * c].reshape(c, 2, 2, c), o_tebd.theta(a, b, g)) < 1e-5
         off += 4 * c * c
+
+
+def test_heff_every_tuning_candidate_chi2048(ctx, tci):
+    """At chi = 2048 every configuration the tuner may pick keeps the 1e-6 matvec bound."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(2048, seed=20251223)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    ref = o_heff.heff_apply(L, W, R, psi)
+    dpsi = to_dev(psi)
+    out = torch.empty_like(dpsi)
+    for chunk in (128, 256):
+        for xchunk in (1024, 4096):
+            for raster in (0, 8, 16):
+                for ww_na in (2, 4):
+                    plan.set_config(chunk, xchunk, raster, ww_na)
+                    out.fill_(float("nan"))
+                    plan.apply(dpsi, out)
+                    torch.cuda.synchronize()
+                    err = rel_frob_err(out.cpu().numpy(), ref)
+                    assert err < 1e-6, (chunk, xchunk, raster, ww_na, err)

@@ -97,3 +97,85 @@ def test_lanczos_split_bf16_df_vs_f64_vectors(ctx, tci):
         r = gpu_lanczos(tci, ctx, L, W, R, psi, 20, precision="split_bf16", arith=arith)
         assert abs(r["theta"] - o["theta"]) < 1e-6 * abs(o["theta"]), arith
         assert np.linalg.norm(np.abs(r["x"].ravel()) - np.abs(o["x"])) < 1e-4, arith
+
+
+def test_lanczos_chi2048_timed_configuration(ctx, tci):
+    """The timed solve itself: autotuned split-BF16 plan, 20 DGKS steps at chi = 2048.
+
+    The oracle's own 20-step solve is too slow here, so the result is checked through
+    properties that hold at any size, each against FP64 arithmetic outside the GPU path:
+      - x is a unit vector;
+      - theta is the lowest eigenvalue of the returned tridiagonal T (Sturm bisection) and
+        lies below every alpha_j (each alpha_j is a Rayleigh quotient in the Krylov space);
+      - theta equals the FP64 Rayleigh quotient <x, H x>, H x taken by one oracle matvec;
+      - ||H x - theta x|| equals the Lanczos residual beta_m |y_m| (H V = V T + beta_m v e_m^T).
+    The split-BF16 matvec error bound (1e-6 relative) sets both tolerances.
+    """
+    import torch
+    psi, L, R, W = dense_heff_inputs(2048, seed=20251223)
+    dpsi = to_dev(psi)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    out = torch.empty_like(dpsi)
+    plan.autotune(dpsi, out, max_chunk_k=256)
+    x = torch.empty_like(dpsi)
+    r = plan.lanczos(dpsi, 20, True, x)
+    x = x.cpu().numpy().ravel()
+    a, b, theta = r["alpha"], r["beta"], r["theta"]
+    assert r["steps"] == 20
+    assert abs(np.linalg.norm(x) - 1.0) < 1e-12
+    assert abs(theta - o_lanczos.lowest_eigenvalue_bisect(a, b[:-1])) < 1e-12 * abs(theta)
+    assert theta <= a.min()
+    hx = o_heff.heff_apply(L, W, R, x.reshape(psi.shape)).ravel()
+    rq = float(x @ hx)
+    assert abs(rq - theta) < 1e-6 * abs(theta), (rq, theta)
+    y = o_lanczos.tridiag_eigvec(a, b[:-1], theta)
+    res_true = np.linalg.norm(hx - theta * x)
+    res_lanczos = abs(b[-1] * y[-1]) / np.linalg.norm(y)
+    assert abs(res_true - res_lanczos) < 1e-6 * abs(theta), (res_true, res_lanczos)
+    st = plan.lanczos_stats()
+    assert st["steps"] == 20 and 1 <= st["fused_pass3"] <= st["second_passes"], st
+
+
+def test_lanczos_rounding_level_terms_counted(ctx, tci):
+    """FP64 plan, FP64 vectors: from step 2 on the rounding-level update terms take the FP32
+    path, and every repeated projection is folded into the next-vector pass; double-float
+    vectors never take either."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(32, seed=20251223)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="native")
+    plan.set_gram_schmidt("twice")
+    x = torch.empty(psi.shape, dtype=torch.float64, device="cuda")
+    plan.lanczos(to_dev(psi), 20, True, x)
+    st = plan.lanczos_stats()
+    assert st == {"steps": 20, "second_passes": 20, "f32_term_passes": 18, "fused_pass3": 20}, st
+    plan.set_lanczos_arith("df32")
+    plan.lanczos(to_dev(psi), 20, True, x)
+    st = plan.lanczos_stats()
+    assert st["steps"] == 20 and st["f32_term_passes"] == 0 and st["fused_pass3"] == 0, st
+
+
+@pytest.mark.parametrize("chi,chi_r,arith", [(64, 64, "f64"), (75, 61, "f64"), (64, 40, "df32")])
+def test_lanczos_graph_replay_identical(ctx, tci, chi, chi_r, arith):
+    """Split-BF16 plan: eager, captured and replayed solves give bit-identical results, also
+    when the start-vector buffer alternates (a new key runs eagerly first)."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(chi, seed=13, chi_r=chi_r)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    plan.set_lanczos_arith(arith)
+    d1, d2 = to_dev(psi), to_dev(psi)
+    x = torch.empty_like(d1)
+
+    def solve(dpsi):
+        x.fill_(float("nan"))
+        r = plan.lanczos(dpsi, 20, True, x)
+        return r, x.cpu().numpy()
+
+    plan.set_lanczos_graphs(False)
+    ref, xref = solve(d1)
+    plan.set_lanczos_graphs(True)
+    for dpsi in (d1, d1, d1, d1, d2, d2, d2, d1, d1):
+        r, xr = solve(dpsi)
+        assert r["theta"] == ref["theta"] and r["steps"] == ref["steps"]
+        np.testing.assert_array_equal(r["alpha"], ref["alpha"])
+        np.testing.assert_array_equal(r["beta"], ref["beta"])
+        np.testing.assert_array_equal(xr, xref)
