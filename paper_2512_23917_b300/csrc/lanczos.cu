@@ -31,6 +31,9 @@
 // product and sum that decides alpha, beta or a coefficient stays FP64;
 // the FP32 terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64
 // of its FP32 rate).  Where the test fails the FP64 passes run instead.
+// (With a split-BF16 matvec h_0 .. h_{j-2} are of the order of the matvec
+// error, ~1e-7 ||w||, and pass 2 stays FP64: a double-float evaluation of
+// those terms measured no faster than their FP64 FMAs.)
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
 // followed by one or two classical Gram-Schmidt passes.  Without
@@ -80,8 +83,9 @@ constexpr int NSCAL = 5 * MAXM + 64;
 constexpr int LO_NS1 = 0, LO_SC1 = 1, LO_ISC1 = 2, LO_WN2 = 3, LO_SC3 = 4, LO_ISC3 = 5;
 constexpr int LO_GFAST = 6, LO_GSLOW = 7, LO_GNEXT = 8, LO_N1 = 9, LO_N3 = 10;
 static_assert(OFF_LO + LO_N3 < NSCAL, "scalar layout");
-// FP32 terms are taken where their coefficients' 1-norm times (nv + 8) is
-// at most 2^-32 times the norm of the vector they update.
+// Terms are summed in FP32 where their coefficients' 1-norm times (k + 8),
+// k the number of such terms, is at most 2^-32 times the norm of the vector
+// they update.
 constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
 // FP32 with coefficients scaled by lo[LO_SC1] and subtracted with one FP64
 // FMA (see the header).
 template <class A, int G, bool DOTS, bool SUMSQ>
-__global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
+__global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::value ? 2 : 1)) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                                const double* __restrict__ coef, typename A::V* __restrict__ w,
                                                int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
                                                const double* __restrict__ ctrl, const double* __restrict__ lo) {
@@ -266,13 +270,15 @@ __global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__
   if (ctrl[0] != 0.0) return;
   __shared__ typename A::Coef cs[G];
   __shared__ float csf[G];
+  // FP32 terms: the first nv - 2 (lo[LO_NS1], set for exact-size FP64 passes)
   const int ns = (kF64 && lo) ? (int)lo[LO_NS1] : 0;
+  const bool f32 = ns > 0 && ns == nv - 2 && nv == G;
   if (threadIdx.x < G) {
     const double c = threadIdx.x < nv ? coef[v0 + threadIdx.x] : 0.0;
     cs[threadIdx.x] = A::coef(c);
-    csf[threadIdx.x] = ns > 0 ? (float)(c * lo[LO_SC1]) : 0.f;
+    csf[threadIdx.x] = f32 ? (float)(c * lo[LO_SC1]) : 0.f;
   }
-  const double isc = ns > 0 ? lo[LO_ISC1] : 0.0;
+  const double isc = f32 ? lo[LO_ISC1] : 0.0;
   __syncthreads();
   constexpr int GD = DOTS ? G : 1;
   typename A::Acc d[GD];
@@ -282,38 +288,58 @@ __global__ void __launch_bounds__(NT) k_update(const typename A::V* __restrict__
   const Vt* Vb = V + (int64_t)v0 * ldv;
   const int64_t stride = (int64_t)gridDim.x * NT;
   int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x;
-  // software pipeline: the next element's loads are issued before this
-  // element's arithmetic, overlapping their latency within each thread
-  Vt vn[G], xn = Vt();
-  if (i < n) {
-    xn = w[i];
+  // double-float vectors: software pipeline (the next element's loads are
+  // issued before this element's arithmetic); FP64 vectors: a plain loop,
+  // whose lower register count keeps more blocks resident to hide latency
+  constexpr bool kPipe = !kF64;
+  Vt vn[kPipe ? G : 1], xn = Vt();
+  if constexpr (kPipe) {
+    if (i < n) {
+      xn = w[i];
 #pragma unroll
-    for (int g = 0; g < G; ++g)
-      if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i];
+      for (int g = 0; g < G; ++g)
+        if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i];
+    }
   }
   for (; i < n; i += stride) {
     Vt v[G];
+    Vt x;
+    if constexpr (kPipe) {
 #pragma unroll
-    for (int g = 0; g < G; ++g) v[g] = vn[g];
-    const Vt x = xn;
-    if (i + stride < n) {
-      xn = w[i + stride];
+      for (int g = 0; g < G; ++g) v[g] = vn[g];
+      x = xn;
+      if (i + stride < n) {
+        xn = w[i + stride];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i + stride];
+      }
+    } else {
 #pragma unroll
       for (int g = 0; g < G; ++g)
-        if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i + stride];
+        if (g < nv) v[g] = Vb[(int64_t)g * ldv + i];
+      x = w[i];
     }
     typename A::Sub t = A::sub_begin(x);
     Vt y;
     if constexpr (kF64) {
-      float sf = 0.f;
+      // the split point is fixed at compile time (terms 0 .. G-3 in FP32, the
+      // last two FP64): with a run-time bound the compiler would evaluate both
+      // arithmetics for every term and select
+      if (f32) {
+        float sf = 0.f;
 #pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (g < nv) {
-          if (g < ns) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
-          else A::sub(t, cs[g], v[g]);
-        }
-      y = A::sub_end(t);
-      if (ns > 0) y = fma(-(double)sf, isc, y);
+        for (int g = 0; g < G - 2; ++g) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
+#pragma unroll
+        for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
+        y = A::sub_end(t);
+        y = fma(-(double)sf, isc, y);
+      } else {
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+          if (g < nv) A::sub(t, cs[g], v[g]);
+        y = A::sub_end(t);
+      }
     } else {
 #pragma unroll
       for (int g = 0; g < G; ++g)

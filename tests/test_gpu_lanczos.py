@@ -151,7 +151,7 @@ def test_lanczos_rounding_level_terms_counted(ctx, tci):
     plan.set_lanczos_arith("df32")
     plan.lanczos(to_dev(psi), 20, True, x)
     st = plan.lanczos_stats()
-    assert st["steps"] == 20 and st["f32_term_passes"] == 0 and st["fused_pass3"] == 0, st
+    assert st["steps"] == 20 and st["f32_term_passes"] + st["fused_pass3"] == 0, st
 
 
 @pytest.mark.parametrize("chi,chi_r,arith", [(64, 64, "f64"), (75, 61, "f64"), (64, 40, "df32")])
