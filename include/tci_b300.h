@@ -472,16 +472,19 @@ tci_status tci_heff_set_gram_schmidt(tci_heff_plan plan, tci_gram_schmidt mode);
 tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reorth, double* ritz,
                        double* alpha, double* beta, int* steps_done, tci_tensor x);
 
-/* Counters of the last tci_lanczos on `plan` (extension), into stats[4]
+/* Counters of the last tci_lanczos on `plan` (extension), into stats[5]
  * (host): [0] steps done; [1] steps whose Gram-Schmidt projection was
  * repeated (DGKS) or, with TCI_GS_TWICE, every re-orthogonalised step;
  * [2] update passes whose rounding-level terms (coefficients of v_0 ..
  * v_{j-2}, 1-norm at most 2^-32 ||w|| / (k + 8) for k such terms) were
- * summed in FP32 and subtracted with one FP64 FMA, adding an error below
- * 2^-56 ||w||; [3] steps whose second projection was applied that way,
- * folded into the next-vector pass with beta_j^2 = ||w'||^2 - |h'|^2.  [2]
- * and [3] stay 0 for double-float vectors and without re-orthogonalisation.
- * All zero before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
+ * summed in FP32 and subtracted in FP64, adding an error below 2^-56 ||w||;
+ * [3] update passes whose small terms (1-norm at most 2^-10 ||w|| / (k + 8),
+ * k >= 6; e.g. the matvec-error-level terms of a split-precision plan) were
+ * summed in double-float arithmetic under the same error bound; [4] steps
+ * whose second projection was applied in FP32 and folded into the
+ * next-vector pass with beta_j^2 = ||w'||^2 - |h'|^2.  [2] to [4] stay 0
+ * for double-float vectors and without re-orthogonalisation.  All zero
+ * before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
 
 /* CUDA-graph replay of tci_lanczos on split-precision real plans

@@ -610,11 +610,12 @@ class HeffPlan:
         _check(lib.tci_heff_set_lanczos_graphs(self.handle, int(bool(enable))), self.ctx.handle)
 
     def lanczos_stats(self):
-        """Counters of the last lanczos(): steps, repeated projections, FP32-term update passes,
-        second projections folded into the next-vector pass."""
-        st = (C.c_int * 4)()
+        """Counters of the last lanczos(): steps, repeated projections, update passes with FP32 /
+        double-float small terms, second projections folded into the next-vector pass."""
+        st = (C.c_int * 5)()
         _check(lib.tci_heff_lanczos_stats(self.handle, st), self.ctx.handle)
-        return {"steps": st[0], "second_passes": st[1], "f32_term_passes": st[2], "fused_pass3": st[3]}
+        return {"steps": st[0], "second_passes": st[1], "f32_term_passes": st[2], "df_term_passes": st[3],
+                "fused_pass3": st[4]}
 
     def close(self):
         if self.handle:

@@ -51,7 +51,8 @@ struct tci_heff_plan_s {
   double* lz_part = nullptr;  // reduction partials
   double* lz_x64 = nullptr;   // double-float Lanczos with the FP64 matvec: matvec input / output
   double* lz_o64 = nullptr;
-  int lz_stats[4] = {0, 0, 0, 0};   // last tci_lanczos: steps, second GS passes, FP32-term passes, fused pass 3
+  int lz_stats[5] = {0, 0, 0, 0, 0};   // last tci_lanczos: steps, second GS passes, FP32-term passes,
+                                       // double-float-term passes, fused pass 3
   // Lanczos solves replayed from a CUDA graph (split-BF16 real plans): the
   // launch sequence of a solve is fixed by its arguments (every branch is a
   // device gate), so a repeated call with the same key replays a captured graph.

@@ -27,13 +27,17 @@
 // one FP64 FMA; the error this adds is below 2^-56 ||w||, under the FP64
 // rounding of the update itself.  Pass 3 is then folded into the
 // next-vector kernel, with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h'
-// is orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  Every
+// is orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  With a
+// reduced-precision matvec (split BF16) the pass-1 coefficients h_0 ..
+// h_{j-2} are of the order of the matvec error instead (~1e-7 ||w||); where
+// their 1-norm is at most 2^-10 ||w|| / (k + 8) (and k >= 6, below which the
+// FP64 FMAs are cheaper) their terms are summed in double-float arithmetic
+// (basis and coefficients split into FP32 pairs, products made exact with
+// FMA, Dekker / Knuth sums), again adding less than 2^-56 ||w||.  Every
 // product and sum that decides alpha, beta or a coefficient stays FP64;
-// the FP32 terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64
-// of its FP32 rate).  Where the test fails the FP64 passes run instead.
-// (With a split-BF16 matvec h_0 .. h_{j-2} are of the order of the matvec
-// error, ~1e-7 ||w||, and pass 2 stays FP64: a double-float evaluation of
-// those terms measured no faster than their FP64 FMAs.)
+// these terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64 of
+// its FP32 rate).  The update kernel is compiled once per term arithmetic;
+// all variants are launched and the one the device chose runs.
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
 // followed by one or two classical Gram-Schmidt passes.  Without
@@ -81,12 +85,14 @@ constexpr int NSCAL = 5 * MAXM + 64;
 // next-vector kernel, the FP64 pass 3 and the plain next-vector kernel,
 // counters of FP32-term passes and fused pass-3 corrections.
 constexpr int LO_NS1 = 0, LO_SC1 = 1, LO_ISC1 = 2, LO_WN2 = 3, LO_SC3 = 4, LO_ISC3 = 5;
-constexpr int LO_GFAST = 6, LO_GSLOW = 7, LO_GNEXT = 8, LO_N1 = 9, LO_N3 = 10;
-static_assert(OFF_LO + LO_N3 < NSCAL, "scalar layout");
+constexpr int LO_GFAST = 6, LO_GSLOW = 7, LO_GNEXT = 8, LO_N1 = 9, LO_N3 = 10, LO_MODE1 = 11, LO_N2 = 12;
+static_assert(OFF_LO + LO_N2 < NSCAL, "scalar layout");
 // Terms are summed in FP32 where their coefficients' 1-norm times (k + 8),
 // k the number of such terms, is at most 2^-32 times the norm of the vector
-// they update.
+// they update, and in double-float where it is at most 2^-10 times it.
 constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
+constexpr double kDFBound = 9.765625e-4;                // 2^-10
+constexpr int kTermsF64 = 0, kTermsF32 = 1, kTermsDF = 2;
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -105,6 +111,19 @@ __device__ __forceinline__ float f32_trunc(double x) {
   unsigned a = min(max(hi & 0x7fffffffu, 0x38100000u), 0x47efffffu);   // exponent in [897, 1150]
   a -= 0x38000000u;                                                      // 1023 - 127 = 896
   return __uint_as_float(__funnelshift_l(lo, a, 3) | (hi & 0x80000000u));
+}
+
+// x = h + l to ~2^-47 |x| for 2^-126 <= |x| < 2^128: h = f32_trunc(x), l the
+// 29 fraction bits below h's (their value m 2^(e - 1075), e the biased FP64
+// exponent) rounded to FP32, with x's sign; l is 0 where that value is
+// below FP32's normal range.
+__device__ __forceinline__ void f32_split2(double x, float& h, float& l) {
+  h = f32_trunc(x);
+  const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+  const int se = (int)((hi >> 20) & 0x7ffu) - 948;   // FP32 biased exponent of 2^(e - 1075)
+  const float scale = se > 0 ? __uint_as_float((unsigned)se << 23) : 0.f;
+  const float mag = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), scale);
+  l = __uint_as_float(__float_as_uint(mag) | (hi & 0x80000000u));
 }
 
 // ---------------------------------------------------------------- double-float
@@ -256,29 +275,44 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
 }
 
 // w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
-// into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  With
-// lo (FP64 vectors only; v0 = 0) the first lo[LO_NS1] terms are summed in
-// FP32 with coefficients scaled by lo[LO_SC1] and subtracted with one FP64
-// FMA (see the header).
-template <class A, int G, bool DOTS, bool SUMSQ>
+// into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  TERMS
+// (FP64 vectors; v0 = 0, nv = G): the arithmetic of the first nv - 2 terms,
+// kTermsF64, kTermsF32 or kTermsDF with coefficients scaled by lo[LO_SC1]
+// (see the header); with lo the kernel runs only when it is the variant the
+// device chose (lo[LO_MODE1] where lo[LO_NS1] = nv - 2, else kTermsF64).
+template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
 __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::value ? 2 : 1)) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                                const double* __restrict__ coef, typename A::V* __restrict__ w,
                                                int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
                                                const double* __restrict__ ctrl, const double* __restrict__ lo) {
   using Vt = typename A::V;
   constexpr bool kF64 = std::is_same<Vt, double>::value;
+  static_assert(kF64 || TERMS == kTermsF64, "reduced-precision terms need FP64 vectors");
   if (ctrl[0] != 0.0) return;
+  if (kF64 && nv != G) {   // FP64 passes are dispatched with G == nv; anything else poisons w
+    for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT)
+      w[i] = A::from_double(__longlong_as_double(0x7ff8000000000000ll));
+    return;
+  }
+  if constexpr (kF64) {
+    int mode = kTermsF64;
+    if (lo && nv == G && nv > 2 && (int)lo[LO_NS1] == nv - 2) mode = (int)lo[LO_MODE1];
+    if (mode != TERMS) return;
+  }
   __shared__ typename A::Coef cs[G];
-  __shared__ float csf[G];
-  // FP32 terms: the first nv - 2 (lo[LO_NS1], set for exact-size FP64 passes)
-  const int ns = (kF64 && lo) ? (int)lo[LO_NS1] : 0;
-  const bool f32 = ns > 0 && ns == nv - 2 && nv == G;
+  __shared__ float csf[G], csl[G];
   if (threadIdx.x < G) {
     const double c = threadIdx.x < nv ? coef[v0 + threadIdx.x] : 0.0;
     cs[threadIdx.x] = A::coef(c);
-    csf[threadIdx.x] = f32 ? (float)(c * lo[LO_SC1]) : 0.f;
+    if constexpr (TERMS != kTermsF64) {
+      const double cc = c * lo[LO_SC1];   // exact: a power-of-two scale
+      const float ch = (float)cc;
+      csf[threadIdx.x] = ch;
+      csl[threadIdx.x] = (float)(cc - (double)ch);
+    }
   }
-  const double isc = f32 ? lo[LO_ISC1] : 0.0;
+  double isc = 0.0;
+  if constexpr (TERMS != kTermsF64) isc = lo[LO_ISC1];
   __syncthreads();
   constexpr int GD = DOTS ? G : 1;
   typename A::Acc d[GD];
@@ -315,31 +349,47 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
           if (g < nv) vn[g] = Vb[(int64_t)g * ldv + i + stride];
       }
     } else {
+      // FP64 passes are launched with G == nv (exact-size instantiations)
 #pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (g < nv) v[g] = Vb[(int64_t)g * ldv + i];
+      for (int g = 0; g < G; ++g) v[g] = Vb[(int64_t)g * ldv + i];
       x = w[i];
     }
     typename A::Sub t = A::sub_begin(x);
     Vt y;
-    if constexpr (kF64) {
-      // the split point is fixed at compile time (terms 0 .. G-3 in FP32, the
-      // last two FP64): with a run-time bound the compiler would evaluate both
-      // arithmetics for every term and select
-      if (f32) {
-        float sf = 0.f;
+    // the split point is fixed at compile time (terms 0 .. G-3 reduced, the
+    // last two FP64): with a run-time bound the compiler would evaluate both
+    // arithmetics for every term and select
+    if constexpr (TERMS == kTermsDF) {
+      // double-float sum (sh + sl): c v = ch vh + (ch vl + cl vh) with ch vh
+      // split exactly by FMA, the leading parts added by TwoSum
+      float sh = 0.f, sl = 0.f;
 #pragma unroll
-        for (int g = 0; g < G - 2; ++g) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
-#pragma unroll
-        for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
-        y = A::sub_end(t);
-        y = fma(-(double)sf, isc, y);
-      } else {
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-          if (g < nv) A::sub(t, cs[g], v[g]);
-        y = A::sub_end(t);
+      for (int g = 0; g < G - 2; ++g) {
+        float vh, vl;
+        f32_split2(v[g], vh, vl);
+        const float p = __fmul_rn(csf[g], vh);
+        const float q = __fmaf_rn(csf[g], vl, __fmaf_rn(csl[g], vh, __fmaf_rn(csf[g], vh, -p)));
+        float s2, e2;
+        df_two_sum(sh, p, s2, e2);
+        sh = s2;
+        sl = __fadd_rn(sl, __fadd_rn(e2, q));
       }
+#pragma unroll
+      for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
+      y = A::sub_end(t);
+      y = fma(-((double)sh + (double)sl), isc, y);
+    } else if constexpr (TERMS == kTermsF32) {
+      float sf = 0.f;
+#pragma unroll
+      for (int g = 0; g < G - 2; ++g) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
+#pragma unroll
+      for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
+      y = A::sub_end(t);
+      y = fma(-(double)sf, isc, y);
+    } else if constexpr (kF64) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) A::sub(t, cs[g], v[g]);
+      y = A::sub_end(t);
     } else {
 #pragma unroll
       for (int g = 0; g < G; ++g)
@@ -350,7 +400,7 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
     if (DOTS) {
 #pragma unroll
       for (int g = 0; g < GD; ++g)
-        if (g < nv) A::acc(d[g], v[g], y);
+        if (kF64 || g < nv) A::acc(d[g], v[g], y);
     }
     if (SUMSQ) A::acc(q, y, y);
   }
@@ -524,8 +574,9 @@ __global__ void __launch_bounds__(NT) k_sumsq(const double* __restrict__ w, int6
 // iteration stopped), ctrl[6] = 1 when it is taken (or stopped).
 //
 // With f32 (FP64 vectors, re-orthogonalisation) the terms of h_0 .. h_{j-2}
-// in passes 2 and 2' are summed in FP32 where sum |h_i| (j + 7) <= 2^-32 ||w||
-// (header); the FP32 scale puts the largest of them in [1, 2).
+// in passes 2 and 2' are summed in FP32 where sum |h_i| (j + 7) <= 2^-32 ||w||,
+// else in double-float where it is <= 2^-10 ||w|| and j >= 7 (header); the
+// scale puts the largest of them in [1, 2).
 __global__ void k_post_pass1(double* scal, int j, int reorth, int dgks, int f32) {
   double* ctrl = scal + OFF_CTRL;
   double* lo = scal + OFF_LO;
@@ -553,12 +604,16 @@ __global__ void k_post_pass1(double* scal, int j, int reorth, int dgks, int f32)
       l1 += a;
       mx = fmax(mx, a);
     }
-    if (l1 * (double)(j + 7) <= kF32Bound * sqrt(ctrl[4])) {
+    const double wn = sqrt(ctrl[4]), k8 = (double)(j + 7);
+    // double-float terms only from six terms on (fewer cost more than their FP64 FMAs)
+    const int mode = l1 * k8 <= kF32Bound * wn ? kTermsF32 : (j >= 7 && l1 * k8 <= kDFBound * wn) ? kTermsDF : kTermsF64;
+    if (mode != kTermsF64) {
       const int e = mx > 0.0 ? ilogb(mx) : 0;
       lo[LO_NS1] = (double)(j - 1);
+      lo[LO_MODE1] = (double)mode;
       lo[LO_SC1] = ldexp(1.0, -e);
       lo[LO_ISC1] = ldexp(1.0, e);
-      lo[LO_N1] += 1.0;
+      lo[mode == kTermsF32 ? LO_N1 : LO_N2] += 1.0;
     }
   }
 }
@@ -829,36 +884,48 @@ tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
   return TCI_OK;
 }
 
-template <class A, int G, bool DOTS, bool SUMSQ>
+// Every variant of one pass uses the grid of its FP64 variant, so the partial
+// sums of whichever variant ran are reduced over the same block count.
+template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
 int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                     typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl,
                     const double* lo) {
-  const int grid = pass_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ>, n);
-  k_update<A, G, DOTS, SUMSQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  const int grid = pass_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ, kTermsF64>, n);
+  k_update<A, G, DOTS, SUMSQ, TERMS><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl,
+                                                                  lo);
   return grid;
 }
 
-template <class A, bool DOTS, bool SUMSQ, int G = 1>
+template <class A, bool DOTS, bool SUMSQ, int TERMS, int G = 1>
 int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
   if constexpr (G == GMAX) {
-    return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_launch_g<A, GMAX, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
   } else {
-    if (nv <= G) return update_launch_g<A, G, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-    return update_exact<A, DOTS, SUMSQ, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (nv <= G)
+      return update_launch_g<A, G, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_exact<A, DOTS, SUMSQ, TERMS, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
   }
 }
 
+// One update pass; with lo (FP64 vectors) all three term arithmetics are
+// launched and the one the device chose runs (the others exit at once).
 template <class A, bool DOTS, bool SUMSQ>
 int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                   typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
   if constexpr (std::is_same<A, ArithF64>::value) {
-    return update_exact<A, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    const int grid = update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (lo && nv > 2) {
+      update_exact<A, DOTS, SUMSQ, kTermsF32>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      update_exact<A, DOTS, SUMSQ, kTermsDF>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    }
+    return grid;
   } else {
-    if (nv <= 8) return update_launch_g<A, 8, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (nv <= 8)
+      return update_launch_g<A, 8, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
     if (nv <= 16)
-      return update_launch_g<A, 16, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-    return update_launch_g<A, GMAX, DOTS, SUMSQ>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      return update_launch_g<A, 16, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_launch_g<A, GMAX, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
   }
 }
 
@@ -1101,21 +1168,23 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   }
   if (!done) TCI_TRY(solve_body(&sa));
   TCI_CUDA(ctx, cudaMemcpyAsync(ctx->h_scalars, ctrl, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  std::vector<double> ab(2 * MAXM), cnt(2);
+  std::vector<double> ab(2 * MAXM), cnt(4);
   TCI_CUDA(ctx, cudaMemcpyAsync(ab.data(), S, 2 * MAXM * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-  TCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), S + OFF_LO + LO_N1, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+  TCI_CUDA(ctx, cudaMemcpyAsync(cnt.data(), S + OFF_LO + LO_N1, 4 * sizeof(double), cudaMemcpyDeviceToHost,
                                 ctx->stream));
-  static_assert(LO_N3 == LO_N1 + 1, "counter layout");
+  static_assert(LO_N3 == LO_N1 + 1 && LO_N2 == LO_N1 + 3, "counter layout");
   TCI_TRY(tci_synchronize(ctx));
   const int k = (int)ctx->h_scalars[1];
   *ritz = ctx->h_scalars[2];
   p->lz_stats[0] = k;
   p->lz_stats[1] = reorth ? (int)ctx->h_scalars[7] : 0;
   p->lz_stats[2] = (int)cnt[0];
-  p->lz_stats[3] = (int)cnt[1];
+  p->lz_stats[3] = (int)cnt[3];
+  p->lz_stats[4] = (int)cnt[1];
   if (ctx->verbose > 0 && reorth)
     vs.info += " second_gs_passes=" + std::to_string(p->lz_stats[1]) + " f32_term_passes=" +
-               std::to_string(p->lz_stats[2]) + " fused_pass3=" + std::to_string(p->lz_stats[3]);
+               std::to_string(p->lz_stats[2]) + " df_term_passes=" + std::to_string(p->lz_stats[3]) +
+               " fused_pass3=" + std::to_string(p->lz_stats[4]);
   if (steps_done) *steps_done = k;
   for (int i = 0; i < nsteps; ++i) {
     if (alpha) alpha[i] = i < k ? ab[OFF_ALPHA + i] : 0.0;
@@ -1146,7 +1215,7 @@ extern "C" tci_status tci_heff_lanczos_stats(tci_heff_plan p, int* stats) {
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "lanczos_stats: invalid plan");
   TCI_CHECK_CTX(p->ctx);
   if (!stats) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "lanczos_stats: NULL stats");
-  for (int i = 0; i < 4; ++i) stats[i] = p->lz_stats[i];
+  for (int i = 0; i < 5; ++i) stats[i] = p->lz_stats[i];
   return TCI_OK;
 }
 
