@@ -421,6 +421,19 @@ __device__ __forceinline__ void split3_store(__nv_bfloat16* o, int64_t plane, fl
   o[2 * plane] = l;
 }
 
+// Two consecutive elements (o 4-byte aligned): one bfloat16x2 store per plane.
+__device__ __forceinline__ void split3_store2(__nv_bfloat16* o, int64_t plane, float x0, float x1) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const float2 hf = __bfloat1622float2(h);
+  const float r0 = __fsub_rn(x0, hf.x), r1 = __fsub_rn(x1, hf.y);
+  const __nv_bfloat162 m = __floats2bfloat162_rn(r0, r1);
+  const float2 mf = __bfloat1622float2(m);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(__fsub_rn(r0, mf.x), __fsub_rn(r1, mf.y));
+  *reinterpret_cast<__nv_bfloat162*>(o) = h;
+  *reinterpret_cast<__nv_bfloat162*>(o + plane) = m;
+  *reinterpret_cast<__nv_bfloat162*>(o + 2 * plane) = l;
+}
+
 // Matvec input written next to a new basis vector.
 constexpr int kInNone = 0;     // the matvec reads the FP64 basis vector itself
 constexpr int kInPieces = 1;   // bfloat16 pieces of fl32(v), K-major [3][rows][Kp], zero in k >= cols
@@ -444,6 +457,23 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
   const typename A::Coef c = A::coef(1.0 / scal[OFF_BETA + j]);
   const int64_t plane = rows * Kp;
   const int64_t kend = MODE == kInPieces ? Kp : cols;
+  if constexpr (std::is_same<typename A::V, double>::value && MODE != kInF64) {
+    if ((cols & 1) == 0) {   // element pairs: 16-byte loads and stores, bfloat16x2 pieces
+      for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+        for (int64_t k = 2 * (int64_t)threadIdx.x; k < kend; k += 2 * NT) {
+          if (k < cols) {
+            const int64_t i = r * cols + k;
+            const double2 x = *reinterpret_cast<const double2*>(w + i);
+            const double y0 = A::mul(x.x, c), y1 = A::mul(x.y, c);
+            *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
+            if (MODE == kInPieces) split3_store2(pieces + r * Kp + k, plane, A::f32(y0), A::f32(y1));
+          } else {
+            split3_store2(pieces + r * Kp + k, plane, 0.f, 0.f);
+          }
+        }
+      return;
+    }
+  }
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
     for (int64_t k = threadIdx.x; k < kend; k += NT) {
       if (k < cols) {
@@ -472,6 +502,29 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
   const double binv = 1.0 / scal[OFF_BETA + j];
   const int64_t plane = rows * Kp;
   const int64_t kend = MODE == kInPieces ? Kp : cols;
+  if ((cols & 1) == 0) {   // element pairs: 16-byte loads and stores, bfloat16x2 pieces
+    for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
+      for (int64_t k = 2 * (int64_t)threadIdx.x; k < kend; k += 2 * NT) {
+        if (k < cols) {
+          const int64_t i = r * cols + k;
+          float s0 = 0.f, s1 = 0.f;
+#pragma unroll 8
+          for (int g = 0; g < nv; ++g) {
+            const double2 v = *reinterpret_cast<const double2*>(V + (int64_t)g * ldv + i);
+            s0 = __fmaf_rn(cf[g], f32_trunc(v.x), s0);
+            s1 = __fmaf_rn(cf[g], f32_trunc(v.y), s1);
+          }
+          const double2 x = *reinterpret_cast<const double2*>(w + i);
+          const double y0 = fma(-(double)s0, isc, x.x) * binv, y1 = fma(-(double)s1, isc, x.y) * binv;
+          *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
+          if (MODE == kInPieces)
+            split3_store2(pieces + r * Kp + k, plane, __double2float_rn(y0), __double2float_rn(y1));
+        } else {
+          split3_store2(pieces + r * Kp + k, plane, 0.f, 0.f);
+        }
+      }
+    return;
+  }
   for (int64_t r = blockIdx.x; r < rows; r += gridDim.x)
     for (int64_t k = threadIdx.x; k < kend; k += NT) {
       if (k < cols) {
