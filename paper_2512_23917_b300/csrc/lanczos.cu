@@ -17,27 +17,30 @@
 //   beta_j = ||w||;  v_{j+1} = w / beta_j, written with the next matvec's
 //   input (its bfloat16 pieces on a split-BF16 plan) in the same pass.
 //
-// Rounding-level terms in FP32 (FP64 vectors only).  In a Lanczos step the
-// pass-1 coefficients h_0 .. h_{j-2} and all second-pass coefficients h' are
-// of the order of the rounding error of w (the recurrence leaves only
-// alpha_j and beta_{j-1}).  Where a device test bounds their 1-norm by
-// 2^-32 ||w|| / (k + 8), k the number of such terms, these are summed in
-// FP32 from the basis
-// truncated to 24 significant bits (f32_trunc) and subtracted from w with
-// one FP64 FMA; the error this adds is below 2^-56 ||w||, under the FP64
-// rounding of the update itself.  Pass 3 is then folded into the
-// next-vector kernel, with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h'
-// is orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  With a
-// reduced-precision matvec (split BF16) the pass-1 coefficients h_0 ..
-// h_{j-2} are of the order of the matvec error instead (~1e-7 ||w||); where
-// their 1-norm is at most 2^-10 ||w|| / (k + 8) (and k >= 6, below which the
-// FP64 FMAs are cheaper) their terms are summed in double-float arithmetic
-// (basis and coefficients split into FP32 pairs, products made exact with
-// FMA, Dekker / Knuth sums), again adding less than 2^-56 ||w||.  Every
-// product and sum that decides alpha, beta or a coefficient stays FP64;
-// these terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64 of
-// its FP32 rate).  The update kernel is compiled once per term arithmetic;
-// all variants are launched and the one the device chose runs.
+// Reduced-precision update terms (FP64 vectors only).  In a Lanczos step
+// the pass-1 coefficients h_0 .. h_{j-2} and all second-pass coefficients h'
+// are small: the recurrence leaves only alpha_j and beta_{j-1}, so they are
+// of the order of the rounding error of w (FP64 matvec) or of the matvec
+// error (split BF16, ~1e-7 ||w||).  A device test takes the 1-norm of the k
+// coefficients of such terms:
+//   <= 2^-32 ||w|| / (k + 8): the terms are summed in FP32 from the basis
+//      truncated to 24 significant bits (f32_trunc) and subtracted from w
+//      with one FP64 FMA;
+//   <= 2^-10 ||w|| / (k + 8), k >= 6 (fewer cost more than their FP64
+//      FMAs): they are summed in double-float arithmetic (basis and
+//      coefficients split into FP32 pairs, products made exact with FMA,
+//      Dekker / Knuth sums);
+// either way the error added is below 2^-56 ||w||, under the FP64 rounding
+// of the update itself; otherwise the terms stay FP64.  The update kernel is
+// compiled once per term arithmetic; all variants are launched and the one
+// the device chose runs.  The second pass's h' are rounding-level after the
+// first projection, so pass 3 is folded into the next-vector kernel (FP32
+// terms), with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h' is
+// orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  Every dot
+// product, and so every alpha, beta and coefficient, stays FP64; the reduced
+// terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64 of its FP32
+// rate).
+//
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
 // followed by one or two classical Gram-Schmidt passes.  Without
@@ -45,7 +48,8 @@
 // subtracts alpha_j v_j + beta_{j-1} v_{j-1}.
 //
 // Vector arithmetic (a policy template over the same kernels):
-//   FP64          every product and sum in FP64 (the default);
+//   FP64          FP64 vectors, every dot product in FP64 (the default;
+//                 small update terms reduced as above);
 //   double-float  vectors held as FP32 pairs hi + lo (~48 significant bits)
 //                 with error-free transformations, so the passes run on the
 //                 FP32 pipes: B300 issues FP64 FMAs at ~1/64 of its FP32
