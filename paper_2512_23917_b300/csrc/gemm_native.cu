@@ -3,9 +3,10 @@
 // Operands are read in place through arbitrary (m,k)/(n,k) strides, so a
 // permuted operand needs no materialised transpose.  FP64 on B300 has no
 // fast tensor-core path, so a register-tiled FMA kernel is the FP64 roof.
-// When the output has too few tiles to fill the SMs and K is long (a batch
-// of small Gram-like products), K is split: each split writes a partial
-// product and a second kernel adds the partials in split order.
+// When the output has too few tiles to fill the SMs and K is long enough (a
+// batch of small Gram-like products, or a small H_eff), K is split: each
+// split writes a partial product and a second kernel adds the partials in
+// split order.
 #include <algorithm>
 
 #include "tci_internal.cuh"
@@ -32,11 +33,14 @@ template <> __device__ __forceinline__ double zero_<double>() { return 0.0; }
 template <> __device__ __forceinline__ float2 zero_<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 zero_<double2>() { return make_double2(0.0, 0.0); }
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
-constexpr int NT = (BM / TM) * (BN / TN);   // 256 threads
+// Tiles of BM x BN outputs, BK deep, TM x TN outputs per thread, 256 threads:
+// 64 x 64 by default, 32 x 32 when 64-wide tiles cannot occupy every SM (an
+// SM issues only 2 FP64 FMAs per clock, so small products must spread out).
+constexpr int BK = 16;
+constexpr int NT = 256;
 
 // ACONT: 0 = operand contiguous (or best) along k, 1 = along m/n.
-template <typename T, int ACONT, int BCONT>
+template <typename T, int ACONT, int BCONT, int BM, int BN, int TM, int TN>
 __global__ void __launch_bounds__(NT) k_gemm_strided(int64_t M, int64_t N, int64_t K, const T* __restrict__ A,
                                                      int64_t sam, int64_t sak, const T* __restrict__ B, int64_t sbn,
                                                      int64_t sbk, T* __restrict__ C, int64_t scm, int64_t scn,
@@ -115,19 +119,20 @@ __global__ void k_split_sum(const T* __restrict__ part, int nsplit, int64_t nb, 
   }
 }
 
-template <typename T>
-tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
-                  int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C, int64_t scb,
-                  int64_t scm, int64_t scn) {
+template <typename T, int BM, int BN, int TM, int TN>
+tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
+                        int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C,
+                        int64_t scb, int64_t scm, int64_t scn) {
+  static_assert((BM / TM) * (BN / TN) == NT, "tile shape");
   dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
   if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
   int ac = (sak == 1 || sam != 1) ? 0 : 1;
   int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
-  // split K when the tiles cannot fill two waves and each split keeps >= 64 of K
+  // split K when the tiles cannot fill two waves and each split keeps >= 32 of K
   const int64_t tiles = (int64_t)grid.x * grid.y * nbatch, want = 2 * (int64_t)ctx->num_sms;
   int64_t nsplit = 1;
-  if (tiles < want && K >= 128) {
-    nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 64, 16});
+  if (tiles < want && K >= 64) {
+    nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 32, 16});
     if (nsplit < 1) nsplit = 1;
   }
   int64_t kchunk = K;
@@ -150,17 +155,17 @@ tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t
     T* c = cout + b0 * ocb;
     const int ns = (int)nsplit;
     if (ac == 0 && bc == 0)
-      k_gemm_strided<T, 0, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
-                                                            ocb, ns, kchunk, per);
+      k_gemm_strided<T, 0, 0, BM, BN, TM, TN><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm,
+                                                                            ocn, sab, sbb, ocb, ns, kchunk, per);
     else if (ac == 0 && bc == 1)
-      k_gemm_strided<T, 0, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
-                                                            ocb, ns, kchunk, per);
+      k_gemm_strided<T, 0, 1, BM, BN, TM, TN><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm,
+                                                                            ocn, sab, sbb, ocb, ns, kchunk, per);
     else if (ac == 1 && bc == 0)
-      k_gemm_strided<T, 1, 0><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
-                                                            ocb, ns, kchunk, per);
+      k_gemm_strided<T, 1, 0, BM, BN, TM, TN><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm,
+                                                                            ocn, sab, sbb, ocb, ns, kchunk, per);
     else
-      k_gemm_strided<T, 1, 1><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm, ocn, sab, sbb,
-                                                            ocb, ns, kchunk, per);
+      k_gemm_strided<T, 1, 1, BM, BN, TM, TN><<<grid, NT, 0, ctx->stream>>>(M, N, K, a, sam, sak, b, sbn, sbk, c, ocm,
+                                                                            ocn, sab, sbb, ocb, ns, kchunk, per);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) st = tci_cuda_fail(ctx, e, "gemm launch");
   }
@@ -175,6 +180,16 @@ tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t
     tci_dev_free(part);
   }
   return st;
+}
+
+template <typename T>
+tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
+                  int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C, int64_t scb,
+                  int64_t scm, int64_t scn) {
+  const int64_t tiles64 = ((M + 63) / 64) * ((N + 63) / 64) * nbatch;
+  if (tiles64 < (int64_t)ctx->num_sms)
+    return launch_tiles<T, 32, 32, 2, 2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
+  return launch_tiles<T, 64, 64, 4, 4>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
 }
 
 }  // namespace

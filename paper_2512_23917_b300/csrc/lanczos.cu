@@ -97,6 +97,7 @@ static_assert(OFF_LO + LO_N2 < NSCAL, "scalar layout");
 constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
 constexpr double kDFBound = 9.765625e-4;                // 2^-10
 constexpr int kTermsF64 = 0, kTermsF32 = 1, kTermsDF = 2;
+constexpr int64_t kReducedMinN = 1 << 20;               // vector length from which reduced terms are used
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1098,9 +1099,12 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // classical Gram-Schmidt against the whole basis, repeated where the first
       // pass cancelled (DGKS); both continuations are launched, each gated
       const int dgks = (p->gs_mode == TCI_GS_DGKS && j + 1 <= GMAX) ? 1 : 0;
-      const double* lo1 = (kF32Terms && j + 1 <= GMAX) ? S + OFF_LO : nullptr;
+      // reduced-precision update terms where they pay: basis <= GMAX, long vectors
+      // (below kReducedMinN the FP64 work is smaller than the extra launches)
+      const bool reduced = kF32Terms && j + 1 <= GMAX && n >= kReducedMinN;
+      const double* lo1 = reduced ? S + OFF_LO : nullptr;
       TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
-      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, (kF32Terms && j + 1 <= GMAX) ? 1 : 0);
+      k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,

@@ -138,21 +138,33 @@ def test_lanczos_chi2048_timed_configuration(ctx, tci):
 
 
 def test_lanczos_rounding_level_terms_counted(ctx, tci):
-    """FP64 plan, FP64 vectors: from step 2 on the rounding-level update terms take the FP32
-    path, and every repeated projection is folded into the next-vector pass; double-float
-    vectors never take either."""
+    """FP64 plan, FP64 vectors, vectors of 2^20 elements (chi = 512): from step 2 on the
+    rounding-level update terms take the FP32 path and every repeated projection is folded
+    into the next-vector pass, with alpha, beta and theta still equal to the oracle's; shorter
+    vectors and double-float vectors take neither."""
     import torch
-    psi, L, R, W = dense_heff_inputs(32, seed=20251223)
+    psi, L, R, W = dense_heff_inputs(512, seed=20251223)
     plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="native")
     plan.set_gram_schmidt("twice")
     x = torch.empty(psi.shape, dtype=torch.float64, device="cuda")
-    plan.lanczos(to_dev(psi), 20, True, x)
+    r = plan.lanczos(to_dev(psi), 20, True, x)
     st = plan.lanczos_stats()
     assert st == {"steps": 20, "second_passes": 20, "f32_term_passes": 18, "df_term_passes": 0, "fused_pass3": 20}, st
+    mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
+    o = o_lanczos.lanczos(mv, psi, 20)
+    np.testing.assert_allclose(r["alpha"], o["alpha"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(r["beta"], o["beta"], rtol=1e-10, atol=1e-10)
+    assert abs(r["theta"] - o["theta"]) < 1e-12 * abs(o["theta"])
     plan.set_lanczos_arith("df32")
     plan.lanczos(to_dev(psi), 20, True, x)
     st = plan.lanczos_stats()
     assert st["steps"] == 20 and st["f32_term_passes"] + st["df_term_passes"] + st["fused_pass3"] == 0, st
+    small, Ls, Rs, Ws = dense_heff_inputs(32, seed=20251223)
+    plan_s = tci.HeffPlan(ctx, to_dev(Ls), to_dev(Ws), to_dev(Rs), precision="native")
+    xs = torch.empty(small.shape, dtype=torch.float64, device="cuda")
+    plan_s.lanczos(to_dev(small), 20, True, xs)
+    st = plan_s.lanczos_stats()
+    assert st["f32_term_passes"] + st["df_term_passes"] == 0 and st["fused_pass3"] == st["second_passes"], st
 
 
 @pytest.mark.parametrize("chi,chi_r,arith", [(64, 64, "f64"), (75, 61, "f64"), (64, 40, "df32")])
