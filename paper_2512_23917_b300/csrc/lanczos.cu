@@ -60,6 +60,7 @@
 // the whole solve and reads back once at the end.  Reductions are
 // deterministic: a fixed grid, a fixed per-thread order and an in-order sum
 // of the block partials.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include <map>
@@ -851,6 +852,132 @@ __global__ void __launch_bounds__(NT) k_tridiag_lowest(double* scal) {
   for (int i = 0; i < m; ++i) scal[OFF_Y + i] = sgn * y[i];
 }
 
+// ---------------------------------------------------------------- short vectors
+// One step's vector work for short FP64 vectors (re-orthogonalisation, the
+// matvec reading the basis itself) in a single launch of one cluster of
+// up to kSmallClMax CTAs: pass 1 (dots, ||w||^2), the DGKS test, pass 2 (update, and
+// where the second pass is taken its dots), pass 3, beta_j, the stop test
+// and v_{j+1}, each pass's block sums combined across the cluster through
+// distributed shared memory.  Every thread owns the same elements in every
+// pass, and every CTA adds the CTAs' sums in rank order, so the totals are
+// identical in all CTAs and deterministic.  Used where n (j + 2) is small
+// enough that launches, not FP64 FMAs, set the step's time; it writes the
+// same scalars and vectors as the multi-kernel path, so the two mix freely
+// from step to step.
+namespace cg = cooperative_groups;
+constexpr int kSmallClMax = 16, kSmallNT = 512;
+constexpr int64_t kSmallWork = 1 << 19;   // n (j + 2) up to which a step runs as one launch
+
+__global__ void __launch_bounds__(kSmallNT)
+    k_step_small(double* __restrict__ V, int64_t ldv, double* __restrict__ w, int64_t n,
+                 double* __restrict__ scal, int j, int m, double tol, int dgks) {
+  double* ctrl = scal + OFF_CTRL;
+  if (ctrl[0] != 0.0) return;   // stopped: every CTA reads the same flag and leaves together
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double part[MAXM + 2], tot[MAXM + 2], hs[MAXM + 1];
+  __shared__ double wred[kSmallNT / 32][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int ncl = (int)cl.num_blocks();
+  const int64_t T = (int64_t)ncl * kSmallNT;
+  const int64_t t0 = (int64_t)cl.block_rank() * kSmallNT + threadIdx.x;
+  const int nv = j + 1;
+
+  // block sums of a[0..cnt) into part[base..base+cnt)
+  auto block_sum8 = [&](const double (&a)[8], int base, int cnt) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const double v = warp_sum(a[k]);
+      if (lane == 0) wred[wid][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      double v = 0.0;
+      for (int q = 0; q < kSmallNT / 32; ++q) v += wred[q][threadIdx.x];
+      part[base + threadIdx.x] = v;
+    }
+    __syncthreads();
+  };
+  // cluster totals of part[0..cnt) into tot, in rank order
+  auto cluster_sum = [&](int cnt) {
+    cl.sync();
+    for (int k = threadIdx.x; k < cnt; k += kSmallNT) {
+      double v = 0.0;
+      for (int r = 0; r < ncl; ++r) v += cl.map_shared_rank(part, r)[k];
+      tot[k] = v;
+    }
+    cl.sync();   // all remote reads done before part is rewritten; tot visible block-wide
+  };
+  // sums over the owned elements of: dots <V_g, w> for g < ndot, then (sq) ||w||^2
+  auto dots = [&](int ndot, bool sq) {
+    const int nval = ndot + (sq ? 1 : 0);
+    for (int g0 = 0; g0 < nval; g0 += 8) {
+      double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int64_t i = t0; i < n; i += T) {
+        const double x = w[i];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int g = g0 + k;
+          if (g < ndot) a[k] = fma(V[(int64_t)g * ldv + i], x, a[k]);
+          else if (g == ndot && sq) a[k] = fma(x, x, a[k]);
+        }
+      }
+      block_sum8(a, g0, nval - g0 < 8 ? nval - g0 : 8);
+    }
+    cluster_sum(nval);
+  };
+  // w -= sum_g c_g V_g over the owned elements, then the cluster total of ||w||^2 in tot[0]
+  auto update_sq = [&](const double* c) {
+    double a[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int64_t i = t0; i < n; i += T) {
+      double sacc = 0.0;
+      for (int g = 0; g < nv; ++g) sacc = fma(c[g], V[(int64_t)g * ldv + i], sacc);
+      const double y = w[i] - sacc;
+      w[i] = y;
+      a[0] = fma(y, y, a[0]);
+    }
+    block_sum8(a, 0, 1);
+    cluster_sum(1);
+  };
+
+  dots(nv, true);                                    // pass 1: h = V^T w, ||w||^2
+  for (int g = threadIdx.x; g < nv; g += kSmallNT) hs[g] = tot[g];
+  const double wn2_1 = tot[nv];
+  __syncthreads();
+  const double alpha = hs[j];
+  double hh = 0.0;
+  for (int g = 0; g < nv; ++g) hh += hs[g] * hs[g];
+  const bool second = !dgks || wn2_1 - hh < 0.5 * wn2_1;   // DGKS test, as k_post_pass1
+  double wn2;
+  if (second) {
+    update_sq(hs);                                   // pass 2: w -= V h (its norm unused)
+    dots(nv, false);                                 // h' = V^T w
+    __syncthreads();
+    for (int g = threadIdx.x; g < nv; g += kSmallNT) hs[g] = tot[g];
+    __syncthreads();
+    update_sq(hs);                                   // pass 3: w -= V h', ||w||^2
+  } else {
+    update_sq(hs);                                   // pass 2': w -= V h, ||w||^2
+  }
+  wn2 = tot[0];
+  const double b = sqrt(wn2);
+  const bool stop = j == m - 1 || b < tol * fabs(alpha);   // as k_finish_beta
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    scal[OFF_H + j] = alpha;
+    scal[OFF_ALPHA + j] = alpha;
+    scal[OFF_BETA + j] = b;
+    ctrl[1] = (double)(j + 1);
+    ctrl[3] = wn2;
+    ctrl[4] = wn2_1;
+    if (second) ctrl[7] += 1.0;
+    if (stop) ctrl[0] = 1.0;
+  }
+  if (!stop) {                                       // v_{j+1} = w / beta_j
+    const double inv = 1.0 / b;
+    double* vn = V + (int64_t)(j + 1) * ldv;
+    for (int64_t i = t0; i < n; i += T) vn[i] = w[i] * inv;
+  }
+}
+
 __global__ void k_init_scal(double* scal) {
   for (int i = threadIdx.x; i < NSCAL; i += blockDim.x) scal[i] = 0.0;
 }
@@ -1049,6 +1176,53 @@ void launch_next_corr(tci_context ctx, const double* V, int64_t ldv, int nv, con
   k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j);
 }
 
+// One cluster of the largest size the device runs (16 CTAs where
+// non-portable cluster sizes are allowed, else 8), found once per device.
+int small_cluster(tci_context ctx) {
+  static std::mutex mu;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(ctx->device);
+  if (it != cache.end()) return it->second;
+  int best = 8;
+  if (cudaFuncSetAttribute(k_step_small, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kSmallClMax;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kSmallClMax);
+    cfg.blockDim = dim3(kSmallNT);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_step_small, &cfg) == cudaSuccess && nclusters >= 1)
+      best = kSmallClMax;
+  }
+  cudaGetLastError();
+  cache[ctx->device] = best;
+  return best;
+}
+
+tci_status launch_step_small(tci_context ctx, double* V, int64_t ldv, double* w, int64_t n, double* S, int j,
+                             int nsteps, double tol, int dgks) {
+  const int ncl = small_cluster(ctx);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ncl);
+  cfg.blockDim = dim3(kSmallNT);
+  cfg.stream = ctx->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  TCI_CUDA(ctx, cudaLaunchKernelEx(&cfg, k_step_small, V, ldv, w, n, S, j, nsteps, tol, dgks));
+  return TCI_OK;
+}
+
 // The Lanczos iteration in arithmetic A with matvec input mode MODE
 // (kInPieces for a split-BF16 plan; kInNone for FP64 vectors on an FP64
 // plan; kInF64 for double-float vectors on an FP64 plan).
@@ -1094,6 +1268,14 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     } else {
       TCI_TRY(tci_heff_apply_raw(p, p->lz_x64, p->lz_o64, false, 0));
       k_from_f64<A><<<NBMAX, NT, 0, ctx->stream>>>(p->lz_o64, w, n, ctrl);
+    }
+    if constexpr (std::is_same<A, ArithF64>::value && MODE == kInNone) {
+      // short vectors: the whole step's vector work as one cluster launch
+      if (reorth && n * (j + 2) <= kSmallWork) {
+        const int dgks = (p->gs_mode == TCI_GS_DGKS && j + 1 <= GMAX) ? 1 : 0;
+        TCI_TRY(launch_step_small(ctx, V, ldv, w, n, S, j, nsteps, tol, dgks));
+        continue;
+      }
     }
     if (reorth) {
       // classical Gram-Schmidt against the whole basis, repeated where the first

@@ -164,7 +164,7 @@ def test_lanczos_rounding_level_terms_counted(ctx, tci):
     xs = torch.empty(small.shape, dtype=torch.float64, device="cuda")
     plan_s.lanczos(to_dev(small), 20, True, xs)
     st = plan_s.lanczos_stats()
-    assert st["f32_term_passes"] + st["df_term_passes"] == 0 and st["fused_pass3"] == st["second_passes"], st
+    assert st["f32_term_passes"] + st["df_term_passes"] == 0, st
 
 
 @pytest.mark.parametrize("chi,chi_r,arith", [(64, 64, "f64"), (75, 61, "f64"), (64, 40, "df32")])
