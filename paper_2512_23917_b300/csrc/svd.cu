@@ -29,9 +29,12 @@
 // truncation error sum_{i >= chi} s_i^2 / sum_i s_i^2 <= target or
 // chi = chi_max.  Singular vectors of zero singular values are returned as
 // zero vectors.
+#include <cooperative_groups.h>
 #include <math.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -253,6 +256,101 @@ __global__ void __launch_bounds__(kRotT) k_jacobi_round_reg(double* __restrict__
   }
 }
 
+// ---------------------------------------------------------------- small problems
+// All sweeps of a small factorisation (rows and vectors at most 32 E long) in
+// one launch of a cluster of CTAs: a warp per pair, the rounds separated by
+// cluster barriers, exact norms at the start of every sweep, and the
+// any-rotation test of a sweep combined across the cluster through
+// distributed shared memory.  The rotation arithmetic is that of
+// k_jacobi_round_reg.  Used where the rounds, not their FP64 work, set the
+// time (one launch and one host read instead of a launch per round and a
+// synchronisation per sweep).  info[0] = sweeps done, info[1] = converged.
+namespace cg = cooperative_groups;
+constexpr int kClT = 256;
+constexpr int kClMax = 16;
+
+template <int E>
+__global__ void __launch_bounds__(kClT) k_jacobi_cluster(double* __restrict__ W, int64_t m, double* __restrict__ Q,
+                                                        int64_t nq, int64_t n, const int2* __restrict__ pairs,
+                                                        const int* __restrict__ start, int nrounds,
+                                                        double* __restrict__ nrm2, double tol, double abs_tol,
+                                                        int max_sweeps, int* __restrict__ info) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ int srot;
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)cl.num_blocks() * (kClT / 32);
+  const int gw = (int)cl.block_rank() * (kClT / 32) + (int)(threadIdx.x >> 5);
+  int sweep = 0;
+  bool converged = false;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    if (threadIdx.x == 0) srot = 0;
+    for (int64_t r = gw; r < n; r += nw) {   // exact squared norms
+      const double* wr = W + r * m;
+      double a = 0.0;
+      for (int64_t i = lane; i < m; i += 32) a = fma(wr[i], wr[i], a);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) nrm2[r] = a;
+    }
+    cl.sync();
+    for (int rd = 0; rd < nrounds; ++rd) {
+      const int p0 = start[rd], np = start[rd + 1] - p0;
+      for (int k = gw; k < np; k += nw) {
+        const int2 pq = pairs[p0 + k];
+        double* wp = W + (int64_t)pq.x * m;
+        double* wq = W + (int64_t)pq.y * m;
+        double* qp = Q + (int64_t)pq.x * nq;
+        double* qq = Q + (int64_t)pq.y * nq;
+        double x[E], y[E], u[E], v[E];
+        double g = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t i = lane + 32 * e;
+          x[e] = i < m ? wp[i] : 0.0;
+          y[e] = i < m ? wq[i] : 0.0;
+          u[e] = i < nq ? qp[i] : 0.0;
+          v[e] = i < nq ? qq[i] : 0.0;
+          g = fma(x[e], y[e], g);
+        }
+        for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+        const double A = nrm2[pq.x], B = nrm2[pq.y];
+        __syncwarp();   // every lane has read the norms before lane 0 updates them
+        if (fabs(g) > abs_tol && fabs(g) > tol * sqrt(A * B)) {   // the same decision in every lane
+          const double zeta = (B - A) / (2.0 * g);
+          const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t), s = c * t;
+          if (lane == 0) {
+            nrm2[pq.x] = fmax(A - t * g, 0.0);
+            nrm2[pq.y] = B + t * g;
+            srot = 1;
+          }
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const int64_t i = lane + 32 * e;
+            if (i < m) {
+              wp[i] = c * x[e] - s * y[e];
+              wq[i] = s * x[e] + c * y[e];
+            }
+            if (i < nq) {
+              qp[i] = c * u[e] - s * v[e];
+              qq[i] = s * u[e] + c * v[e];
+            }
+          }
+        }
+      }
+      cl.sync();
+    }
+    // any rotation in this sweep, anywhere in the cluster (same answer in every CTA)
+    int any = 0;
+    for (int r = 0; r < (int)cl.num_blocks(); ++r) any |= *cl.map_shared_rank(&srot, r);
+    converged = any == 0;
+    cl.sync();   // every CTA has read every flag before the next sweep clears its own
+  }
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    info[0] = sweep;
+    info[1] = converged ? 1 : 0;
+  }
+}
+
 // sq[r] = ||W_r||^2 (one block per row)
 __global__ void __launch_bounds__(kSvdT) k_row_sumsq(const double* __restrict__ W, int64_t m, double* __restrict__ sq) {
   const double* w = W + (int64_t)blockIdx.x * m;
@@ -456,6 +554,129 @@ __global__ void __launch_bounds__(kSvdT) k_qr_apply(double* __restrict__ W, int6
   if (threadIdx.x == 0) nrm2[j] = s2;
 }
 
+// The whole pivoted Householder QR (the k_qr_pivot / k_qr_apply steps for
+// k = 0 .. n-1) in one launch of a cluster for columns up to 32 E long: per
+// step, one warp picks the pivot, swaps and forms the reflector, a cluster
+// barrier, then a warp per later column applies it and recomputes that
+// column's norm, and another barrier.  Same arithmetic as the two kernels
+// (warp instead of block sums).
+template <int E>
+__global__ void __launch_bounds__(kClT) k_qr_cluster(double* __restrict__ W, int64_t m, int n,
+                                                    double* __restrict__ nrm2, int* __restrict__ qperm,
+                                                    double* __restrict__ tau) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int lane = threadIdx.x & 31;
+  const int nw = (int)cl.num_blocks() * (kClT / 32);
+  const int gw = (int)cl.block_rank() * (kClT / 32) + (int)(threadIdx.x >> 5);
+  for (int k = 0; k < n; ++k) {
+    if (gw == 0) {
+      // argmax of nrm2[k..n) (first index on ties)
+      double best = -1.0;
+      int besti = n;
+      for (int j = k + lane; j < n; j += 32) {
+        const double x = nrm2[j];
+        if (x > best) {
+          best = x;
+          besti = j;
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, besti, o);
+        if (ob > best || (ob == best && oi < besti)) {
+          best = ob;
+          besti = oi;
+        }
+      }
+      const int p = besti < n ? besti : k;
+      double* x = W + (int64_t)k * m;
+      if (p != k) {
+        double* b = W + (int64_t)p * m;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t r = lane + 32 * e;
+          if (r < m) {
+            const double t = x[r];
+            x[r] = b[r];
+            b[r] = t;
+          }
+        }
+        if (lane == 0) {
+          const double t = nrm2[k];
+          nrm2[k] = nrm2[p];
+          nrm2[p] = t;
+          const int q = qperm[k];
+          qperm[k] = qperm[p];
+          qperm[p] = q;
+        }
+        __syncwarp();
+      }
+      // Householder reflector of column k, rows k..m-1
+      const double alpha = x[k];
+      double sub = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t r = lane + 32 * e;
+        if (r > k && r < m) sub = fma(x[r], x[r], sub);
+      }
+      for (int o = 16; o > 0; o >>= 1) sub += __shfl_xor_sync(0xffffffffu, sub, o);
+      __syncwarp();   // every lane has read x[k] before lane 0 overwrites it
+      if (!(sub > 0.0)) {
+        if (lane == 0) tau[k] = 0.0;
+      } else {
+        const double beta = -copysign(sqrt(alpha * alpha + sub), alpha);
+        const double scale = 1.0 / (alpha - beta);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t r = lane + 32 * e;
+          if (r > k && r < m) x[r] *= scale;
+        }
+        if (lane == 0) {
+          tau[k] = (beta - alpha) / beta;
+          x[k] = beta;
+        }
+      }
+    }
+    cl.sync();
+    const double t = tau[k];
+    const double* v = W + (int64_t)k * m;
+    for (int j = k + 1 + gw; j < n; j += nw) {
+      double* y = W + (int64_t)j * m;
+      double vv[E], yy[E];
+      double d = 0.0;
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const int64_t r = lane + 32 * e;
+        const bool in = r > k && r < m;
+        vv[e] = in ? v[r] : 0.0;
+        yy[e] = in ? y[r] : 0.0;
+        d = fma(vv[e], yy[e], d);
+      }
+      double s2 = 0.0;
+      if (t != 0.0) {
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const double yk = y[k];
+        __syncwarp();   // every lane has read y[k] before lane 0 updates it
+        const double f = t * (d + yk);
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const int64_t r = lane + 32 * e;
+          if (r > k && r < m) {
+            yy[e] = fma(-f, vv[e], yy[e]);
+            y[r] = yy[e];
+          }
+        }
+        if (lane == 0) y[k] = yk - f;
+      }
+#pragma unroll
+      for (int e = 0; e < E; ++e) s2 = fma(yy[e], yy[e], s2);
+      for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+      if (lane == 0) nrm2[j] = s2;
+    }
+    cl.sync();
+  }
+}
+
 // R (n x n, row-major, upper triangle): R[i][j] = X[i][j] = W[j][i] for i <= j.
 __global__ void k_build_r(const double* __restrict__ W, int64_t m, int64_t n, double* __restrict__ R) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n * n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -522,6 +743,101 @@ void launch_round(tci_context ctx, int np, double* W, int64_t m, double* Q, int6
 
 bool round_uses_registers(int64_t m, int64_t nq) { return (m > nq ? m : nq) <= 8 * kRotT; }
 
+// Cluster size for a kernel of kClT threads: 16 CTAs where the device allows
+// non-portable clusters, else 8 (found once per kernel and device).
+template <typename K>
+int cluster_size_for(tci_context ctx, K* kernel) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  const auto key = std::make_pair((const void*)kernel, ctx->device);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  int best = 8;
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kClMax;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(kClMax);
+    cfg.blockDim = dim3(kClT);
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, kernel, &cfg) == cudaSuccess && nclusters >= 1) best = kClMax;
+  }
+  cudaGetLastError();
+  cache[key] = best;
+  return best;
+}
+
+template <int E>
+cudaError_t launch_jacobi_cluster_e(tci_context ctx, double* W, int64_t m, double* Q, int64_t n, const int2* pairs,
+                                    const int* start, int nrounds, double* nrm2, double tol, double abs_tol,
+                                    int max_sweeps, int* info) {
+  const int ncl = cluster_size_for(ctx, k_jacobi_cluster<E>);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ncl);
+  cfg.blockDim = dim3(kClT);
+  cfg.stream = ctx->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_jacobi_cluster<E>, W, m, Q, n, n, pairs, start, nrounds, nrm2, tol, abs_tol,
+                            max_sweeps, info);
+}
+
+template <int E>
+cudaError_t launch_qr_cluster_e(tci_context ctx, double* W, int64_t m, int n, double* nrm2, int* qperm,
+                                double* tau) {
+  const int ncl = cluster_size_for(ctx, k_qr_cluster<E>);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ncl);
+  cfg.blockDim = dim3(kClT);
+  cfg.stream = ctx->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_qr_cluster<E>, W, m, n, nrm2, qperm, tau);
+}
+
+// The pivoted QR in one cluster launch for columns up to 256 long.
+bool qr_clustered(int64_t m) { return m <= 8 * 32; }
+
+cudaError_t launch_qr_cluster(tci_context ctx, double* W, int64_t m, int n, double* nrm2, int* qperm, double* tau) {
+  if (m <= 32) return launch_qr_cluster_e<1>(ctx, W, m, n, nrm2, qperm, tau);
+  if (m <= 64) return launch_qr_cluster_e<2>(ctx, W, m, n, nrm2, qperm, tau);
+  if (m <= 128) return launch_qr_cluster_e<4>(ctx, W, m, n, nrm2, qperm, tau);
+  return launch_qr_cluster_e<8>(ctx, W, m, n, nrm2, qperm, tau);
+}
+
+// All sweeps in one cluster launch when the rows and vectors are <= 64 long (measured:
+// faster up to 32, even at 64, slower from 128, where a round has enough pairs to fill the GPU).
+bool jacobi_clustered(int64_t m, int64_t n) { return (m > n ? m : n) <= 2 * 32 && n >= 2; }
+
+cudaError_t launch_jacobi_cluster(tci_context ctx, double* W, int64_t m, double* Q, int64_t n, const int2* pairs,
+                                  const int* start, int nrounds, double* nrm2, double tol, double abs_tol,
+                                  int max_sweeps, int* info) {
+  const int64_t len = m > n ? m : n;
+  if (len <= 32)
+    return launch_jacobi_cluster_e<1>(ctx, W, m, Q, n, pairs, start, nrounds, nrm2, tol, abs_tol, max_sweeps, info);
+  if (len <= 64)
+    return launch_jacobi_cluster_e<2>(ctx, W, m, Q, n, pairs, start, nrounds, nrm2, tol, abs_tol, max_sweeps, info);
+  if (len <= 128)
+    return launch_jacobi_cluster_e<4>(ctx, W, m, Q, n, pairs, start, nrounds, nrm2, tol, abs_tol, max_sweeps, info);
+  return launch_jacobi_cluster_e<8>(ctx, W, m, Q, n, pairs, start, nrounds, nrm2, tol, abs_tol, max_sweeps, info);
+}
+
 int grid_of(tci_context ctx, int64_t n) {
   int64_t b = (n + 255) / 256;
   const int64_t cap = (int64_t)ctx->num_sms * 16;
@@ -558,6 +874,8 @@ struct SvdWork {
   double* norms = nullptr;
   int2* pairs = nullptr;
   int* flag = nullptr;
+  int* info = nullptr;      // cluster sweeps: sweeps done, converged
+  int* rstart = nullptr;    // cluster sweeps: first pair of each round
   int* perm = nullptr;
   // QR preconditioning
   double* R = nullptr;      // n x n: R, then the Jacobi vectors
@@ -570,7 +888,7 @@ struct SvdWork {
   double* rn2 = nullptr;    // n tracked squared norms of the Jacobi rows
   double* dsc = nullptr;    // n row scales of the scaled rotations
   void free_all() {
-    void* ps[] = {W, Q, norms, pairs, flag, perm, R, tau, nrm2, qperm, Vn, Uc, iota, rn2, dsc};
+    void* ps[] = {W, Q, norms, pairs, flag, info, rstart, perm, R, tau, nrm2, qperm, Vn, Uc, iota, rn2, dsc};
     for (void* p : ps) tci_dev_free(p);
   }
 };
@@ -659,9 +977,15 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(w.qperm, qp.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "svd: QR set-up"));
-    for (int64_t kk = 0; kk < n; ++kk) {
-      k_qr_pivot<<<1, kQrT, 0, ctx->stream>>>(w.W, m, (int)n, (int)kk, w.nrm2, w.qperm, w.tau);
-      if (kk + 1 < n) k_qr_apply<<<(unsigned)(n - kk - 1), kSvdT, 0, ctx->stream>>>(w.W, m, (int)kk, w.nrm2, w.tau);
+    if (qr_clustered(m)) {
+      e = launch_qr_cluster(ctx, w.W, m, (int)n, w.nrm2, w.qperm, w.tau);
+      if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "svd: QR"));
+    } else {
+      for (int64_t kk = 0; kk < n; ++kk) {
+        k_qr_pivot<<<1, kQrT, 0, ctx->stream>>>(w.W, m, (int)n, (int)kk, w.nrm2, w.qperm, w.tau);
+        if (kk + 1 < n)
+          k_qr_apply<<<(unsigned)(n - kk - 1), kSvdT, 0, ctx->stream>>>(w.W, m, (int)kk, w.nrm2, w.tau);
+      }
     }
     k_build_r<<<grid_of(ctx, n * n), 256, 0, ctx->stream>>>(w.W, m, n, w.R);
     e = cudaGetLastError();
@@ -676,6 +1000,21 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
   if (scaled) {
     if ((st = tci_dev_alloc(ctx, sizeof(double) * n, (void**)&w.dsc)) != TCI_OK) return fail(st);
     k_fill<<<grid_of(ctx, n), 256, 0, ctx->stream>>>(w.dsc, n, 1.0);
+  }
+  if (!scaled && !pairs.empty() && jacobi_clustered(mj, n)) {
+    const int nrounds = (int)start.size() - 1;
+    if ((st = tci_dev_alloc(ctx, sizeof(int) * 2, (void**)&w.info)) != TCI_OK) return fail(st);
+    if ((st = tci_dev_alloc(ctx, sizeof(int) * start.size(), (void**)&w.rstart)) != TCI_OK) return fail(st);
+    e = cudaMemcpyAsync(w.rstart, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = launch_jacobi_cluster(ctx, Wj, mj, w.Q, n, w.pairs, w.rstart, nrounds, w.rn2, tol, abs_tol, kMaxSweeps,
+                                w.info);
+    int info[2] = {0, 0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(info, w.info, sizeof(info), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "svd: cluster sweeps"));
+    sweeps = info[1] ? info[0] - 1 : kMaxSweeps;   // as the loop below counts: sweeps that rotated
+    pairs.clear();   // done: skip the per-round loop below
   }
   for (; sweeps < kMaxSweeps && !pairs.empty(); ++sweeps) {
     cudaMemsetAsync(w.flag, 0, sizeof(int), ctx->stream);
