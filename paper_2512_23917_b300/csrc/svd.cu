@@ -9,7 +9,9 @@
 // rotates kappa/2 disjoint pairs in parallel (round-robin order, one block of
 // 128 threads per pair, row norms tracked so a pair needs one dot product;
 // rows up to 1024 long are rotated from registers, longer ones in scaled
-// form); sweeps repeat until no pair needs a rotation.  Then the norms of
+// form); sweeps repeat until no pair needs a rotation.  Small factorisations
+// (vectors up to 64 long) run all their sweeps in one launch of a CTA cluster
+// (a warp per pair, cluster barriers between rounds).  Then the norms of
 // the vectors are the singular values, the normalised vectors one set of
 // singular vectors and Q the other.  Arithmetic is FP64 for F64 and F32
 // tensors.
@@ -22,7 +24,8 @@
 // (about 30 to about 10 for an iTEBD two-site tensor).  With the converged
 // rows sigma_i x_i^T = (Q' R)_i: X = sum_i (H [q'_i; 0]) sigma_i (P x_i)^T,
 // so the length-m singular vectors are H applied to rows of Q' and the
-// length-n ones are the permuted rows x_i.
+// length-n ones are the permuted rows x_i.  For columns up to 256 long the
+// whole QR runs in one cluster launch (a warp per column update).
 //
 // trunc_svd keeps chi values by the paper's rules: (a) drop s_i < s_min;
 // (b) keep at least chi_min (or all that remain after (a)); (c) grow until the
