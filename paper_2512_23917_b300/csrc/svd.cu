@@ -303,6 +303,7 @@ __global__ void __launch_bounds__(kClT) k_jacobi_cluster(double* __restrict__ W,
         double* wq = W + (int64_t)pq.y * m;
         double* qp = Q + (int64_t)pq.x * nq;
         double* qq = Q + (int64_t)pq.y * nq;
+        const double A = nrm2[pq.x], B = nrm2[pq.y];   // issued with the row loads
         double x[E], y[E], u[E], v[E];
         double g = 0.0;
 #pragma unroll
@@ -315,7 +316,6 @@ __global__ void __launch_bounds__(kClT) k_jacobi_cluster(double* __restrict__ W,
           g = fma(x[e], y[e], g);
         }
         for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
-        const double A = nrm2[pq.x], B = nrm2[pq.y];
         __syncwarp();   // every lane has read the norms before lane 0 updates them
         if (fabs(g) > abs_tol && fabs(g) > tol * sqrt(A * B)) {   // the same decision in every lane
           const double zeta = (B - A) / (2.0 * g);
@@ -724,6 +724,56 @@ __global__ void __launch_bounds__(kSvdT) k_apply_h(const double* __restrict__ W,
   if (threadIdx.x == 0) y[k] -= f;
 }
 
+// All reflectors, last to first, for rows up to 32 E long: a warp per row c of
+// Uc holds the row in registers and applies H_{n-1} .. H_0 in turn (rows are
+// independent, so one launch replaces n); the arithmetic of k_apply_h.
+template <int E>
+__global__ void __launch_bounds__(kSvdT) k_apply_h_all(const double* __restrict__ W, int64_t m, int n,
+                                                       const double* __restrict__ tau, double* __restrict__ Uc,
+                                                       int64_t chi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t c = (int64_t)blockIdx.x * (kSvdT / 32) + (threadIdx.x >> 5);
+  if (c >= chi) return;
+  double* yrow = Uc + c * m;
+  double y[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t r = lane + 32 * e;
+    y[e] = r < m ? yrow[r] : 0.0;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    const double t = tau[k];
+    if (t == 0.0) continue;
+    const double* v = W + (int64_t)k * m;
+    double vv[E];
+    double d = 0.0;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t r = lane + 32 * e;
+      vv[e] = (r > k && r < m) ? v[r] : 0.0;
+      d = fma(vv[e], y[e], d);
+    }
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+    double yk = 0.0;   // y[k], held by lane k % 32 in element k / 32
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+      if (e == k / 32) yk = y[e];
+    yk = __shfl_sync(0xffffffffu, yk, k & 31);
+    const double f = t * (d + yk);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t r = lane + 32 * e;
+      if (r > k && r < m) y[e] = fma(-f, vv[e], y[e]);
+      else if (r == k) y[e] -= f;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t r = lane + 32 * e;
+    if (r < m) yrow[r] = y[e];
+  }
+}
+
 __global__ void k_iota(int* __restrict__ p, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     p[i] = (int)i;
@@ -1112,8 +1162,18 @@ tci_status svd_impl(tci_context ctx, tci_tensor a, int k, tci_tensor* u, tci_ten
       if ((st = tci_dev_alloc(ctx, sizeof(int) * chi, (void**)&w.iota)) != TCI_OK) return fail(st);
       k_init_u<<<grid_of(ctx, chi * m), 256, 0, ctx->stream>>>(w.Q, n, w.perm, w.norms, chi, m, w.Uc);
       k_iota<<<grid_of(ctx, chi), 256, 0, ctx->stream>>>(w.iota, chi);
-      for (int64_t kk = n - 1; kk >= 0; --kk)
-        k_apply_h<<<(unsigned)chi, kSvdT, 0, ctx->stream>>>(w.W, m, (int)kk, w.tau, w.Uc);
+      const unsigned hb = (unsigned)((chi + kSvdT / 32 - 1) / (kSvdT / 32));
+      if (m <= 32)
+        k_apply_h_all<1><<<hb, kSvdT, 0, ctx->stream>>>(w.W, m, (int)n, w.tau, w.Uc, chi);
+      else if (m <= 64)
+        k_apply_h_all<2><<<hb, kSvdT, 0, ctx->stream>>>(w.W, m, (int)n, w.tau, w.Uc, chi);
+      else if (m <= 128)
+        k_apply_h_all<4><<<hb, kSvdT, 0, ctx->stream>>>(w.W, m, (int)n, w.tau, w.Uc, chi);
+      else if (m <= 256)
+        k_apply_h_all<8><<<hb, kSvdT, 0, ctx->stream>>>(w.W, m, (int)n, w.tau, w.Uc, chi);
+      else
+        for (int64_t kk = n - 1; kk >= 0; --kk)
+          k_apply_h<<<(unsigned)chi, kSvdT, 0, ctx->stream>>>(w.W, m, (int)kk, w.tau, w.Uc);
       LM = w.Uc;
       permLM = w.iota;
       normLM = 0;
