@@ -97,6 +97,41 @@ __global__ void __launch_bounds__(ATILE * BT, 4) k_ww_apply(const WWArgs<double>
   }
 }
 
+// FP64 path for small bond dimensions: one thread per output (a', b, s, wl)
+// instead of per pair, so a chi = 64 bond spreads over ~80k threads rather
+// than 4k.  A block covers 8 a' x 2 b: their 8 x 4 x 2 x 5 = 320 inputs are
+// staged in shared memory (one per thread) with the 400 W.W coefficients;
+// a' runs fastest, so stores of one (s, wl) are contiguous along GEMM2's K.
+constexpr int kWWsA = 8, kWWsB = 2, kWWsT = kWWsA * kWWsB * 20;   // 320 threads
+__global__ void __launch_bounds__(kWWsT) k_ww_apply_small(const WWArgs<double> args, const double* __restrict__ U,
+                                                          int64_t chiL, int64_t chiR, double* __restrict__ V,
+                                                          int64_t ldv) {
+  constexpr int Dw = HEFF_DW, D2 = 4;
+  __shared__ double Us[kWWsA][D2][kWWsB][Dw];
+  __shared__ double ww[Dw * D2 * Dw * D2];
+  const int64_t a0 = (int64_t)blockIdx.y * kWWsA, b0 = (int64_t)blockIdx.x * kWWsB;
+  const int64_t ldu = chiR * Dw;
+  for (int i = threadIdx.x; i < Dw * D2 * Dw * D2; i += kWWsT) ww[i] = args.ww[i];
+  {
+    // staging: thread -> (wr, b, t, a') with wr fastest (contiguous (b, wr) runs of U rows)
+    const int wr = threadIdx.x % Dw, bl = (threadIdx.x / Dw) % kWWsB, t = (threadIdx.x / (Dw * kWWsB)) % D2,
+              al = threadIdx.x / (Dw * kWWsB * D2);
+    const int64_t ap = a0 + al, b = b0 + bl;
+    Us[al][t][bl][wr] = (ap < chiL && b < chiR) ? U[(ap * D2 + t) * ldu + b * Dw + wr] : 0.0;
+  }
+  __syncthreads();
+  const int al = threadIdx.x % kWWsA, o = (threadIdx.x / kWWsA) % 20, bl = threadIdx.x / (kWWsA * 20);
+  const int64_t ap = a0 + al, b = b0 + bl;
+  if (ap >= chiL || b >= chiR) return;
+  const int s = o % D2, wl = o / D2;
+  double acc = 0.0;
+#pragma unroll
+  for (int wr = 0; wr < Dw; ++wr)
+#pragma unroll
+    for (int t = 0; t < D2; ++t) acc += ww[((wl * D2 + s) * Dw + wr) * D2 + t] * Us[al][t][bl][wr];
+  V[b * ldv + ap + s * (chiR * ldv) + wl * chiL] = acc;
+}
+
 // Split path.  GEMM1 stores U transposed, U^T [(b,wr), (a',t)] (row length
 // 4 chiL), so that one thread reads the NA*4 values (a', t), a' in
 // [a0, a0+NA), of each of its five rows (b, wr) as contiguous float4s and a
@@ -207,9 +242,10 @@ tci_status launch_ww_f64(tci_context ctx, const WWArgs<double>& args, const doub
   } else if (blocks(8, 8) >= sms) {
     dim3 grid((unsigned)((chiR + 7) / 8), (unsigned)((chiL + 7) / 8));
     k_ww_apply<8, 8><<<grid, 64, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
-  } else {
-    dim3 grid((unsigned)((chiR + 7) / 8), (unsigned)((chiL + 3) / 4));
-    k_ww_apply<4, 8><<<grid, 32, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
+  } else {   // few pairs: a thread per output
+    dim3 grid((unsigned)((chiR + kWWsB - 1) / kWWsB), (unsigned)((chiL + kWWsA - 1) / kWWsA));
+    if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "W.W step: chiL too large");
+    k_ww_apply_small<<<grid, kWWsT, 0, ctx->stream>>>(args, U, chiL, chiR, V, ldv);
   }
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
