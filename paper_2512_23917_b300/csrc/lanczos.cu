@@ -736,17 +736,21 @@ __device__ int sturm_count(const double* a, const double* b, int m, double x) {
   return cnt;
 }
 
-// K7: lowest eigenpair of T_k = tridiag(beta, alpha, beta) in one CTA:
-// multisection on the Sturm count (each of NT threads tests one point per
+// K7: lowest eigenpair of T_k = tridiag(beta, alpha, beta) in one warp:
+// multisection on the Sturm count (each of kTriP threads tests one point per
 // round), then inverse iteration with Gaussian elimination with partial
-// pivoting on T - sigma I.
-__global__ void __launch_bounds__(NT) k_tridiag_lowest(double* scal) {
+// pivoting on T - sigma I.  One warp, not a block: every Sturm count costs m
+// FP64 divisions, which B300's FP64 pipe makes the expensive part (256 points
+// per round took ~76 us per solve; 32 points need ~2x the rounds at 1/8 the
+// divisions each).
+constexpr int kTriP = 32;
+__global__ void __launch_bounds__(kTriP) k_tridiag_lowest(double* scal) {
   __shared__ double a[MAXM], b[MAXM];
   __shared__ double lo, hi;
   __shared__ int first;
   const int m = (int)scal[OFF_CTRL + 1];
   if (m <= 0) return;
-  for (int i = threadIdx.x; i < m; i += NT) {
+  for (int i = threadIdx.x; i < m; i += kTriP) {
     a[i] = scal[OFF_ALPHA + i];
     b[i] = i < m - 1 ? scal[OFF_BETA + i] : 0.0;
   }
@@ -762,10 +766,10 @@ __global__ void __launch_bounds__(NT) k_tridiag_lowest(double* scal) {
     hi = h;
   }
   __syncthreads();
-  for (int round = 0; round < 64; ++round) {
+  for (int round = 0; round < 256; ++round) {   // ends at an ulp long before (33x per round)
     const double l = lo, h = hi;
-    const double x = l + (h - l) * (double)(threadIdx.x + 1) / (double)(NT + 1);
-    if (threadIdx.x == 0) first = NT;
+    const double x = l + (h - l) * (double)(threadIdx.x + 1) / (double)(kTriP + 1);
+    if (threadIdx.x == 0) first = kTriP;
     __syncthreads();
     const bool hit = x > l && x < h && sturm_count(a, b, m, x) >= 1;
     if (hit) atomicMin(&first, (int)threadIdx.x);
@@ -773,11 +777,11 @@ __global__ void __launch_bounds__(NT) k_tridiag_lowest(double* scal) {
     if (threadIdx.x == 0) {
       const int f = first;
       double nl = l, nh = h;
-      if (f < NT) {
-        nh = l + (h - l) * (double)(f + 1) / (double)(NT + 1);
-        if (f > 0) nl = l + (h - l) * (double)f / (double)(NT + 1);
+      if (f < kTriP) {
+        nh = l + (h - l) * (double)(f + 1) / (double)(kTriP + 1);
+        if (f > 0) nl = l + (h - l) * (double)f / (double)(kTriP + 1);
       } else {
-        nl = l + (h - l) * (double)NT / (double)(NT + 1);
+        nl = l + (h - l) * (double)kTriP / (double)(kTriP + 1);
       }
       if (!(nl > l) && !(nh < h)) {   // no progress: converged to an ulp
         nl = l;
@@ -1311,7 +1315,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     }
     TCI_CUDA(ctx, cudaGetLastError());
   }
-  k_tridiag_lowest<<<1, NT, 0, ctx->stream>>>(S);
+  k_tridiag_lowest<<<1, kTriP, 0, ctx->stream>>>(S);
   if (x) k_ritz<A><<<NBMAX, NT, 0, ctx->stream>>>(V, ldv, S, x, n);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
