@@ -31,7 +31,11 @@ def _check_svd(a, k, u, s, vt, tol):
 
 
 @pytest.mark.parametrize("shape,k", [((3, 4, 12), 2), ((40, 7), 1), ((7, 40), 1), ((33, 2, 2, 17), 2),
-                                     ((1, 5), 1), ((64, 2, 2, 64), 2), ((5, 1), 1)])
+                                     ((1, 5), 1), ((64, 2, 2, 64), 2), ((5, 1), 1),
+                                     # around the single-launch limits: Jacobi sweeps for vectors <= 64
+                                     # long, the pivoted QR for columns <= 256 long
+                                     ((64, 64), 1), ((65, 65), 1), ((257, 40), 1), ((40, 257), 1),
+                                     ((256, 33), 1)])
 def test_svd_matches_oracle(ctx, tci, shape, k):
     a = random_tensor(shape, 21)
     u, s, vt = tci.svd(ctx, _tensor(tci, ctx, a), k)
