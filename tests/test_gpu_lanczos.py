@@ -192,3 +192,18 @@ def test_lanczos_graph_replay_identical(ctx, tci, chi, chi_r, arith):
         np.testing.assert_array_equal(r["alpha"], ref["alpha"])
         np.testing.assert_array_equal(r["beta"], ref["beta"])
         np.testing.assert_array_equal(xr, xref)
+
+
+@pytest.mark.parametrize("gs", ["dgks", "twice"])
+def test_lanczos_short_and_long_step_paths_mix(ctx, tci, gs):
+    """chi = 128 (n = 2^16): the first steps run as one cluster launch each (n (j + 2) <= 2^19),
+    the later ones as the multi-kernel passes; alpha, beta, theta equal the oracle's."""
+    psi, L, R, W = dense_heff_inputs(128, seed=9)
+    r = gpu_lanczos(tci, ctx, L, W, R, psi, 20, gs=gs)
+    mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
+    o = o_lanczos.lanczos(mv, psi, 20)
+    assert r["steps"] == o["steps"] == 20
+    np.testing.assert_allclose(r["alpha"], o["alpha"], rtol=1e-10, atol=1e-10)
+    np.testing.assert_allclose(r["beta"], o["beta"], rtol=1e-10, atol=1e-10)
+    assert abs(r["theta"] - o["theta"]) < 1e-12 * abs(o["theta"])
+    assert abs(np.linalg.norm(r["x"]) - 1.0) < 1e-12
