@@ -489,12 +489,13 @@ tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
 
 /* CUDA-graph replay of tci_lanczos on split-precision real plans
  * (extension; on by default).  A solve launches a sequence fixed by its
- * arguments (psi0 and x addresses, nsteps, reorth, the vector arithmetic,
+ * arguments (whether x is given, nsteps, reorth, the vector arithmetic,
  * the Gram-Schmidt mode and the plan's GEMM configuration), every branch
  * being decided on the device; the first call with a given sequence runs
  * eagerly, the second captures it into a graph and later calls replay the
- * graph, so the host enqueues one launch per solve.  enable = 0 runs every
- * solve eagerly and releases the graph.  Results are identical either way.
+ * graph (with the call's psi0 and x addresses), so the host enqueues one
+ * launch per solve.  enable = 0 runs every solve eagerly and releases the
+ * graph.  Results are identical either way.
  * Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_graphs(tci_heff_plan plan, int enable);
 

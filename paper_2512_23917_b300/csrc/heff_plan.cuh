@@ -55,7 +55,8 @@ struct tci_heff_plan_s {
                                        // double-float-term passes, fused pass 3
   // Lanczos solves replayed from a CUDA graph (split-BF16 real plans): the
   // launch sequence of a solve is fixed by its arguments (every branch is a
-  // device gate), so a repeated call with the same key replays a captured graph.
+  // device gate), so a repeated call with the same key replays a captured
+  // graph, its psi0 / x kernel arguments set for the call.
   int lz_graphs = 1;
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;

@@ -1324,6 +1324,23 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
 }  // namespace
 
 namespace {
+// Point argument `idx` (a pointer; the kernel takes `nargs` arguments) of the
+// graph's kernel node `node` at `value` in the instantiated graph; the other
+// arguments keep their captured values.
+tci_status graph_set_ptr_arg(tci_context ctx, tci_graph& g, int node, int nargs, int idx, const void* value) {
+  cudaKernelNodeParams kp;
+  TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(g.nodes[node], &kp));
+  if (!kp.kernelParams) return tci_fail(ctx, TCI_ERR_CUDA, "lanczos graph: kernel node without parameters");
+  void* args[16];
+  for (int i = 0; i < nargs; ++i) args[i] = kp.kernelParams[i];
+  const void* v = value;
+  args[idx] = (void*)&v;
+  kp.kernelParams = args;
+  kp.extra = nullptr;
+  TCI_CUDA(ctx, cudaGraphExecKernelNodeSetParams(g.exec, g.nodes[node], &kp));
+  return TCI_OK;
+}
+
 struct SolveArgs {
   tci_heff_plan p;
   const double* psi;
@@ -1392,14 +1409,20 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split};
   bool done = false;
   if (split && !p->cplx && p->lz_graphs) {
-    // eager on the first call with a key, captured on the second, replayed after
-    const std::vector<int64_t> key = {(int64_t)(uintptr_t)psi, (int64_t)(uintptr_t)xd, nsteps, reorth, arith,
-                                      p->gs_mode, p->products, p->chunk_k, p->xchunk_k, p->raster, p->ww_na,
-                                      (int64_t)(uintptr_t)p->lz_V, (int64_t)ctx->wait_limit_ns};
+    // eager on the first call with a key, captured on the second, replayed after;
+    // psi0 and x are not part of the key: the three kernel nodes that read psi0
+    // or write x get the call's pointers before every replay
+    const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->products, p->chunk_k,
+                                      p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
+                                      (int64_t)ctx->wait_limit_ns};
+    const bool df = arith == TCI_LANCZOS_DF32;
+    std::vector<const void*> io = {(const void*)k_sumsq,
+                                   df ? (const void*)k_start<ArithDF, kInPieces> : (const void*)k_start<ArithF64, kInPieces>};
+    if (xd) io.push_back(df ? (const void*)k_ritz<ArithDF> : (const void*)k_ritz<ArithF64>);
     if (!(p->lz_graph.exec && key == p->lz_graph_key) && key == p->lz_last_key) {
       tci_graph_destroy(&p->lz_graph);
       p->lz_graph_key.clear();
-      if (tci_graph_capture(ctx, &p->lz_graph, solve_body, &sa, {}) == TCI_OK) {
+      if (tci_graph_capture(ctx, &p->lz_graph, solve_body, &sa, io) == TCI_OK) {
         p->lz_graph_key = key;
       } else {   // run eagerly from now on
         tci_graph_destroy(&p->lz_graph);
@@ -1408,6 +1431,10 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
       }
     }
     if (p->lz_graph.exec && key == p->lz_graph_key) {
+      // k_sumsq(psi0, n, part), k_start(psi0, ...), k_ritz(V, ldv, S, x, n)
+      TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 0, 3, 0, psi));
+      TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 1, 8, 0, psi));
+      if (xd) TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 2, 5, 3, xd));
       TCI_CUDA(ctx, cudaGraphLaunch(p->lz_graph.exec, ctx->stream));
       done = true;
     }
