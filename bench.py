@@ -197,7 +197,8 @@ def lanczos_launches(m: int) -> int:
 def lanczos_vector_roofline(ms_step: float, mv_ms: float, n: int, peaks) -> dict:
     """The Lanczos vector work of one solve (step time minus its matvecs) against HBM: algorithmic
     bytes 8 n (2j + 3) per step j (the basis read for the dots and for the update, w read and
-    written, the next vector written).  The passes are FP64-pipe bound on B300 (see DESIGN)."""
+    written, the next vector written).  The FP64 passes are bound by the FP64 pipe on B300 (2 FP64
+    FMAs per clock per SM), not by these bytes."""
     ms = ms_step - LANCZOS_STEPS * mv_ms
     nbytes = sum(8.0 * n * (2 * j + 3) for j in range(LANCZOS_STEPS))
     gbs = nbytes / (ms * 1e-3) / 1e9 if ms > 0 else None
