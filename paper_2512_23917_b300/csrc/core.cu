@@ -144,7 +144,7 @@ std::string tci_shape_str(const tci_tensor_s* t) {
 // with cudaFreeAsync on the stream they were allocated on, so the temporaries
 // of a call never synchronise the device the way cudaMalloc / cudaFree do.
 // The pool keeps up to kPoolKeepBytes of freed memory for reuse; more is
-// released to the driver at the next synchronisation.  Memory allocated while
+// returned to the CUDA driver at the next synchronisation.  Memory allocated while
 // the context's stream is being captured into a graph, or without a context,
 // comes from plain cudaMalloc.
 namespace {
