@@ -487,6 +487,14 @@ tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reor
  * before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
 
+/* Reduced-precision small update terms of tci_lanczos with FP64 vectors
+ * (extension; on by default): the FP32 and double-float evaluations of
+ * rounding-level and matvec-error-level Gram-Schmidt terms counted by
+ * tci_heff_lanczos_stats [2] to [4], each under an added error below
+ * 2^-56 ||w||.  enable = 0 keeps every update term in FP64 (slower on B300,
+ * equal to rounding).  Errors: INVALID_ARG, INVALID_CONTEXT. */
+tci_status tci_heff_set_lanczos_reduced_terms(tci_heff_plan plan, int enable);
+
 /* CUDA-graph replay of tci_lanczos on split-precision real plans
  * (extension; on by default).  A solve launches a sequence fixed by its
  * arguments (whether x is given, nsteps, reorth, the vector arithmetic,

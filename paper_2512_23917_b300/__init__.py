@@ -101,6 +101,7 @@ SIGNATURES = [
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_lanczos_stats", C.c_int, [_p, C.POINTER(C.c_int)]),
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
+    ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_create2", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(_p)]),
     ("tci_tebd_theta_batched", C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
@@ -608,6 +609,10 @@ class HeffPlan:
     def set_lanczos_graphs(self, enable: bool):
         """Replay repeated lanczos() calls from a captured CUDA graph (default on, split plans)."""
         _check(lib.tci_heff_set_lanczos_graphs(self.handle, int(bool(enable))), self.ctx.handle)
+
+    def set_lanczos_reduced_terms(self, enable: bool):
+        """Allow (default) or forbid the FP32 / double-float evaluation of small update terms."""
+        _check(lib.tci_heff_set_lanczos_reduced_terms(self.handle, int(bool(enable))), self.ctx.handle)
 
     def lanczos_stats(self):
         """Counters of the last lanczos(): steps, repeated projections, update passes with FP32 /

@@ -58,6 +58,7 @@ struct tci_heff_plan_s {
   // device gate), so a repeated call with the same key replays a captured
   // graph, its psi0 / x kernel arguments set for the call.
   int lz_graphs = 1;
+  int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;
 };

@@ -1287,7 +1287,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       const int dgks = (p->gs_mode == TCI_GS_DGKS && j + 1 <= GMAX) ? 1 : 0;
       // reduced-precision update terms where they pay: basis <= GMAX, long vectors
       // (below kReducedMinN the FP64 work is smaller than the extra launches)
-      const bool reduced = kF32Terms && j + 1 <= GMAX && n >= kReducedMinN;
+      const bool reduced = kF32Terms && p->lz_reduced && j + 1 <= GMAX && n >= kReducedMinN;
       const double* lo1 = reduced ? S + OFF_LO : nullptr;
       TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
@@ -1295,7 +1295,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // with ||w||^2 in FP64, or folded into the next-vector kernel
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,
                             lo1));
-      k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, kF32Terms ? 1 : 0);
+      k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, (kF32Terms && p->lz_reduced) ? 1 : 0);
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW));
       // second pass skipped: w -= V h with ||w||^2
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6, lo1));
@@ -1412,7 +1412,8 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     // eager on the first call with a key, captured on the second, replayed after;
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
     // or write x get the call's pointers before every replay
-    const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->products, p->chunk_k,
+    const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->lz_reduced, p->products,
+                                      p->chunk_k,
                                       p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
                                       (int64_t)ctx->wait_limit_ns};
     const bool df = arith == TCI_LANCZOS_DF32;
@@ -1503,5 +1504,12 @@ extern "C" tci_status tci_heff_set_lanczos_graphs(tci_heff_plan p, int enable) {
     p->lz_graph_key.clear();
     p->lz_last_key.clear();
   }
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_lanczos_reduced_terms(tci_heff_plan p, int enable) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_reduced_terms: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  p->lz_reduced = enable ? 1 : 0;
   return TCI_OK;
 }

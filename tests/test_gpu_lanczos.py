@@ -207,3 +207,27 @@ def test_lanczos_short_and_long_step_paths_mix(ctx, tci, gs):
     np.testing.assert_allclose(r["beta"], o["beta"], rtol=1e-10, atol=1e-10)
     assert abs(r["theta"] - o["theta"]) < 1e-12 * abs(o["theta"])
     assert abs(np.linalg.norm(r["x"]) - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("precision,chi", [("split_bf16", 512), ("native", 512)])
+def test_lanczos_reduced_terms_equal_fp64_terms(ctx, tci, precision, chi):
+    """Vectors of 2^20 elements: the FP32 / double-float small update terms change alpha, beta
+    and theta only at rounding level against every update term in FP64 (the same plan)."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(chi, seed=17)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision=precision)
+    plan.set_gram_schmidt("twice")
+    dpsi = to_dev(psi)
+    x = torch.empty_like(dpsi)
+    r1 = plan.lanczos(dpsi, 20, True, x)
+    st = plan.lanczos_stats()
+    assert st["f32_term_passes"] + st["df_term_passes"] >= 12 and st["fused_pass3"] == 20, st
+    x1 = x.cpu().numpy()
+    plan.set_lanczos_reduced_terms(False)
+    r0 = plan.lanczos(dpsi, 20, True, x)
+    st = plan.lanczos_stats()
+    assert st["f32_term_passes"] + st["df_term_passes"] + st["fused_pass3"] == 0, st
+    np.testing.assert_allclose(r1["alpha"], r0["alpha"], rtol=1e-11, atol=1e-11 * np.abs(r0["alpha"]).max())
+    np.testing.assert_allclose(r1["beta"], r0["beta"], rtol=1e-11)
+    assert abs(r1["theta"] - r0["theta"]) < 1e-12 * abs(r0["theta"])
+    assert np.linalg.norm(x1 - x.cpu().numpy()) < 1e-9
