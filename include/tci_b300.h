@@ -310,6 +310,17 @@ tci_status tci_heff_plan_create(tci_context ctx, tci_tensor L, tci_tensor W, tci
  * this call with W2 = W.  Errors: as tci_heff_plan_create. */
 tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
                                  tci_heff_plan* plan);
+
+/* Replace a real plan's environments (and MPO tensors) by new ones of the
+ * same shapes (extension; the paper has no plan object): L [chiL, Dw, chiL],
+ * W and W2 [Dw, Dw, 2, 2] (W2 may be NULL: W on both sites), R
+ * [chiR, Dw, chiR], row-major F64 device tensors, copied (FP64 plan) or
+ * split into bfloat16 pieces (split plans) into the plan's own buffers on the
+ * context's stream; the plan's configuration, workspaces and Lanczos graph
+ * are kept (the graph is dropped when W.W changes).  A sweep that meets the
+ * same bond dimensions again reuses one plan this way.  Errors: INVALID_ARG,
+ * SHAPE (shapes differ from the plan's), UNSUPPORTED (complex plans), CUDA. */
+tci_status tci_heff_plan_reload(tci_heff_plan plan, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R);
 tci_status tci_heff_plan_destroy(tci_heff_plan* plan);
 /* out = H_eff psi (async).  psi and out must not overlap. */
 tci_status tci_heff_apply(tci_heff_plan plan, tci_tensor psi, tci_tensor out);
@@ -495,8 +506,8 @@ tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
  * equal to rounding).  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_reduced_terms(tci_heff_plan plan, int enable);
 
-/* CUDA-graph replay of tci_lanczos on split-precision real plans
- * (extension; on by default).  A solve launches a sequence fixed by its
+/* CUDA-graph replay of tci_lanczos on real plans (extension; on by
+ * default).  A solve launches a sequence fixed by its
  * arguments (whether x is given, nsteps, reorth, the vector arithmetic,
  * the Gram-Schmidt mode and the plan's GEMM configuration), every branch
  * being decided on the device; the first call with a given sequence runs

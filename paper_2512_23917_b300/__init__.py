@@ -102,6 +102,7 @@ SIGNATURES = [
     ("tci_heff_lanczos_stats", C.c_int, [_p, C.POINTER(C.c_int)]),
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
     ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
+    ("tci_heff_plan_reload", C.c_int, [_p, _p, _p, _p, _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_create2", C.c_int, [_p, _p, _p, _p, _p, C.POINTER(_p)]),
     ("tci_tebd_theta_batched", C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
@@ -609,6 +610,14 @@ class HeffPlan:
     def set_lanczos_graphs(self, enable: bool):
         """Replay repeated lanczos() calls from a captured CUDA graph (default on, split plans)."""
         _check(lib.tci_heff_set_lanczos_graphs(self.handle, int(bool(enable))), self.ctx.handle)
+
+    def reload(self, L, W, R, W2=None):
+        """New environments / MPO tensors of the same shapes (torch CUDA tensors) for this plan."""
+        tl, tw, tr = self.ctx.wrap(L), self.ctx.wrap(W), self.ctx.wrap(R)
+        tw2 = self.ctx.wrap(W2) if W2 is not None else None
+        _check(lib.tci_heff_plan_reload(self.handle, tl.handle, tw.handle, tw2.handle if tw2 is not None else None,
+                                        tr.handle), self.ctx.handle)
+        self._keep = (L, W, R, W2)
 
     def set_lanczos_reduced_terms(self, enable: bool):
         """Allow (default) or forbid the FP32 / double-float evaluation of small update terms."""

@@ -14,9 +14,10 @@
 //   a sweep runs k = 0..N-2 then N-2..0; its energy is the last Ritz value.
 #include <string.h>
 
+#include <map>
 #include <vector>
 
-#include "tci_internal.cuh"
+#include "heff_plan.cuh"
 
 namespace {
 
@@ -73,16 +74,31 @@ extern "C" tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_
   TCI_TRY(unit_tensor(ctx, env_shape, 0, &R[N].t));
   for (int k = N - 1; k >= 1; --k) TCI_TRY(update_right(ctx, R[k + 1].t, A[k].t, W, &R[k].t));
 
+  // one H_eff plan per bond shape (chiL, chiR), reloaded with each bond's
+  // environments: the MPO is the same everywhere, so W.W is computed once per
+  // plan, and the plan's Lanczos graph is replayed from its third solve on
+  std::map<std::pair<int64_t, int64_t>, tci_heff_plan> plans;
+  struct PlanCache {
+    std::map<std::pair<int64_t, int64_t>, tci_heff_plan>& m;
+    ~PlanCache() {
+      for (auto& kv : m) tci_heff_plan_destroy(&kv.second);
+    }
+  } plan_cache{plans};
   auto solve = [&](int k, tci_tensor* ground, double* theta) -> tci_status {
     TciOwned psi, x;
-    tci_heff_plan plan = nullptr;
     TCI_TRY(contract3(ctx, A[k].t, "abc", A[k + 1].t, "cde", "abde", &psi.t));
     TCI_TRY(tci_allocate(ctx, TCI_F64, 4, psi.t->shape, &x.t));
-    TCI_TRY(tci_heff_plan_create(ctx, L[k].t, W, R[k + 2].t, &plan));
+    const auto key = std::make_pair(L[k].t->shape[0], R[k + 2].t->shape[0]);
+    auto it = plans.find(key);
+    if (it == plans.end()) {
+      tci_heff_plan plan = nullptr;
+      TCI_TRY(tci_heff_plan_create(ctx, L[k].t, W, R[k + 2].t, &plan));
+      it = plans.emplace(key, plan).first;
+    } else {
+      TCI_TRY(tci_heff_plan_reload_impl(it->second, L[k].t, W, W, R[k + 2].t, true));
+    }
     int done = 0;
-    tci_status st = tci_lanczos(plan, psi.t, lanczos_steps, 1, theta, nullptr, nullptr, &done, x.t);
-    tci_heff_plan_destroy(&plan);
-    TCI_TRY(st);
+    TCI_TRY(tci_lanczos(it->second, psi.t, lanczos_steps, 1, theta, nullptr, nullptr, &done, x.t));
     *ground = x.release();
     return TCI_OK;
   };

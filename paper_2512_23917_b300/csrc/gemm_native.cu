@@ -119,17 +119,11 @@ __global__ void k_split_sum(const T* __restrict__ part, int nsplit, int64_t nb, 
   }
 }
 
-template <typename T, int BM, int BN, int TM, int TN>
-tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
-                        int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C,
-                        int64_t scb, int64_t scm, int64_t scn) {
-  static_assert((BM / TM) * (BN / TN) == NT, "tile shape");
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
-  if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
-  int ac = (sak == 1 || sam != 1) ? 0 : 1;
-  int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
+// K split of a launch: split count and depth per split (nsplit = 1: no split).
+void split_of(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, int BM, int BN, int64_t* nsplit_out,
+              int64_t* kchunk_out) {
+  const int64_t tiles = ((N + BN - 1) / BN) * ((M + BM - 1) / BM) * nbatch, want = 2 * (int64_t)ctx->num_sms;
   // split K when the tiles cannot fill two waves and each split keeps >= 32 of K
-  const int64_t tiles = (int64_t)grid.x * grid.y * nbatch, want = 2 * (int64_t)ctx->num_sms;
   int64_t nsplit = 1;
   if (tiles < want && K >= 64) {
     nsplit = std::min<int64_t>({(want + tiles - 1) / tiles, K / 32, 16});
@@ -140,9 +134,33 @@ tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, i
     kchunk = ((K + nsplit - 1) / nsplit + BK - 1) / BK * BK;
     nsplit = (K + kchunk - 1) / kchunk;
   }
+  *nsplit_out = nsplit;
+  *kchunk_out = kchunk;
+}
+
+// 64 x 64 tiles unless they cannot occupy every SM
+bool small_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N) {
+  return ((M + 63) / 64) * ((N + 63) / 64) * nbatch < (int64_t)ctx->num_sms;
+}
+
+template <typename T, int BM, int BN, int TM, int TN>
+tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
+                        int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C,
+                        int64_t scb, int64_t scm, int64_t scn, void* ws, size_t ws_bytes) {
+  static_assert((BM / TM) * (BN / TN) == NT, "tile shape");
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  if (grid.y > 65535u) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "gemm: M too large for the native kernel");
+  int ac = (sak == 1 || sam != 1) ? 0 : 1;
+  int bc = (sbk == 1 || sbn != 1) ? 0 : 1;
+  int64_t nsplit, kchunk;
+  split_of(ctx, nbatch, M, N, K, BM, BN, &nsplit, &kchunk);
   T* part = nullptr;
   const int64_t per = nbatch * M * N;
-  if (nsplit > 1) TCI_TRY(tci_dev_alloc(ctx, sizeof(T) * nsplit * per, (void**)&part));
+  const bool own = nsplit > 1 && !(ws && ws_bytes >= sizeof(T) * nsplit * per);   // else the caller's workspace
+  if (nsplit > 1) {
+    if (own) TCI_TRY(tci_dev_alloc(ctx, sizeof(T) * nsplit * per, (void**)&part));
+    else part = (T*)ws;
+  }
   T* cout = nsplit > 1 ? part : (T*)C;
   const int64_t ocb = nsplit > 1 ? M * N : scb, ocm = nsplit > 1 ? N : scm, ocn = nsplit > 1 ? 1 : scn;
   const int64_t bmax = 65535 / nsplit;
@@ -177,7 +195,7 @@ tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, i
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) st = tci_cuda_fail(ctx, e, "gemm split sum");
     }
-    tci_dev_free(part);
+    if (own) tci_dev_free(part);
   }
   return st;
 }
@@ -185,26 +203,47 @@ tci_status launch_tiles(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, i
 template <typename T>
 tci_status launch(tci_context ctx, int64_t nbatch, int64_t M, int64_t N, int64_t K, const void* A, int64_t sab,
                   int64_t sam, int64_t sak, const void* B, int64_t sbb, int64_t sbn, int64_t sbk, void* C, int64_t scb,
-                  int64_t scm, int64_t scn) {
-  const int64_t tiles64 = ((M + 63) / 64) * ((N + 63) / 64) * nbatch;
-  if (tiles64 < (int64_t)ctx->num_sms)
-    return launch_tiles<T, 32, 32, 2, 2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
-  return launch_tiles<T, 64, 64, 4, 4>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
+                  int64_t scm, int64_t scn, void* ws, size_t ws_bytes) {
+  if (small_tiles(ctx, nbatch, M, N))
+    return launch_tiles<T, 32, 32, 2, 2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn,
+                                         ws, ws_bytes);
+  return launch_tiles<T, 64, 64, 4, 4>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn, ws,
+                                       ws_bytes);
 }
 
 }  // namespace
 
+tci_status tci_gemm_native_batched_ws(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
+                                      const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
+                                      int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn, void* ws,
+                                      size_t ws_bytes) {
+  if (nbatch <= 0 || M == 0 || N == 0) return TCI_OK;
+  switch (dt) {
+    case TCI_F32:
+      return launch<float>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn, ws, ws_bytes);
+    case TCI_F64:
+      return launch<double>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn, ws, ws_bytes);
+    case TCI_C64:
+      return launch<float2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn, ws, ws_bytes);
+    case TCI_C128:
+      return launch<double2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn, ws, ws_bytes);
+  }
+  return tci_fail(ctx, TCI_ERR_DTYPE, "gemm: bad dtype");
+}
+
+size_t tci_gemm_native_workspace(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K) {
+  if (nbatch <= 0 || M == 0 || N == 0) return 0;
+  const bool st = small_tiles(ctx, nbatch, M, N);
+  int64_t nsplit, kchunk;
+  split_of(ctx, nbatch, M, N, K, st ? 32 : 64, st ? 32 : 64, &nsplit, &kchunk);
+  return nsplit > 1 ? tci_elem_bytes(dt) * (size_t)(nsplit * nbatch * M * N) : 0;
+}
+
 tci_status tci_gemm_native_batched(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
                                    const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
                                    int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn) {
-  if (nbatch <= 0 || M == 0 || N == 0) return TCI_OK;
-  switch (dt) {
-    case TCI_F32: return launch<float>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
-    case TCI_F64: return launch<double>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
-    case TCI_C64: return launch<float2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
-    case TCI_C128: return launch<double2>(ctx, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn);
-  }
-  return tci_fail(ctx, TCI_ERR_DTYPE, "gemm: bad dtype");
+  return tci_gemm_native_batched_ws(ctx, dt, nbatch, M, N, K, A, sab, sam, sak, B, sbb, sbn, sbk, C, scb, scm, scn,
+                                    nullptr, 0);
 }
 
 tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, int64_t K, const void* A, int64_t sam,

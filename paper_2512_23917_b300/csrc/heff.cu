@@ -12,6 +12,10 @@
 // pieces), so no transpose is ever materialised for the GEMMs.
 #include <cuda_bf16.h>
 
+#include <string.h>
+
+#include <algorithm>
+
 #include "heff_plan.cuh"
 
 namespace {
@@ -462,6 +466,10 @@ extern "C" tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_t
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->R64, R->data, sizeof(double) * chiR * Dw * chiR, cudaMemcpyDeviceToDevice, ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "heff_plan_create: copy L/R"));
+    // split-K partials of the two GEMMs, owned by the plan (no allocation per matvec)
+    p->ws_bytes = std::max(tci_gemm_native_workspace(ctx, TCI_F64, 1, chiL * 4, chiR * Dw, chiR),
+                           tci_gemm_native_workspace(ctx, TCI_F64, 1, chiL, 4 * chiR, Dw * chiL));
+    if (p->ws_bytes && (s = tci_dev_alloc(ctx, p->ws_bytes, &p->ws)) != TCI_OK) return fail(s);
   } else {
     p->Kp1 = pad8(chiR);
     p->Kp2 = pad8(Dw * chiL);
@@ -485,12 +493,66 @@ extern "C" tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_t
   return TCI_OK;
 }
 
+// New environments (and MPO tensors) of the same shapes for an existing real
+// plan: L and R copied (FP64 plan) or re-split (split plan) into the plan's
+// own buffers, stream-ordered; W.W recomputed unless same_mpo.  A changed W.W
+// drops the plan's Lanczos graph (its kernels take W.W by value).
+tci_status tci_heff_plan_reload_impl(tci_heff_plan p, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
+                                     bool same_mpo) {
+  tci_context ctx = p->ctx;
+  if (p->cplx) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_plan_reload: real plans only");
+  if (!W2) W2 = W;
+  const int64_t Dw = HEFF_DW, chiL = p->chiL, chiR = p->chiR;
+  for (tci_tensor t : {L, W, W2, R})
+    if (!tci_ten_ok(t) || t->dtype != TCI_F64 || !tci_is_rowmajor(t))
+      return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_reload: L, W, W2, R must be row-major F64");
+  if (L->order != 3 || R->order != 3 || W->order != 4 || W2->order != 4 || L->shape[0] != chiL || L->shape[1] != Dw ||
+      L->shape[2] != chiL || R->shape[0] != chiR || R->shape[1] != Dw || R->shape[2] != chiR || W->shape[0] != Dw ||
+      W->shape[1] != Dw || W->shape[2] != 2 || W->shape[3] != 2)
+    return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_reload: shapes differ from the plan's");
+  for (int i = 0; i < 4; ++i)
+    if (W2->shape[i] != W->shape[i]) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_reload: W2 must have W's shape");
+  if (!same_mpo) {
+    double* dWW = nullptr;
+    TCI_TRY(tci_dev_alloc(ctx, sizeof(double) * HEFF_NWW, (void**)&dWW));
+    k_ww_precompute<<<1, 256, 0, ctx->stream>>>((const double*)W->data, (const double*)W2->data, (int)Dw, 2, dWW);
+    double ww[HEFF_NWW];
+    cudaError_t e = cudaMemcpyAsync(ww, dWW, sizeof(ww), cudaMemcpyDeviceToHost, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    tci_dev_free(dWW);
+    if (e != cudaSuccess) return tci_cuda_fail(ctx, e, "heff_plan_reload: WW");
+    if (memcmp(ww, p->ww, sizeof(ww)) != 0) {
+      memcpy(p->ww, ww, sizeof(ww));
+      tci_graph_destroy(&p->lz_graph);
+      p->lz_graph_key.clear();
+      p->lz_last_key.clear();
+    }
+  }
+  if (p->prec == TCI_PREC_NATIVE) {
+    TCI_CUDA(ctx, cudaMemcpyAsync(p->L64, L->data, sizeof(double) * chiL * Dw * chiL, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+    TCI_CUDA(ctx, cudaMemcpyAsync(p->R64, R->data, sizeof(double) * chiR * Dw * chiR, cudaMemcpyDeviceToDevice,
+                                  ctx->stream));
+  } else {
+    TCI_TRY(tci_launch_split3(ctx, TCI_F64, L->data, chiL, Dw * chiL, Dw * chiL, 1, p->Lp, p->Kp2));
+    TCI_TRY(tci_launch_split3(ctx, TCI_F64, R->data, chiR * Dw, chiR, chiR, 1, p->Rp, p->Kp1));
+  }
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_plan_reload(tci_heff_plan p, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_plan_reload: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  TciVerboseScope vs(p->ctx, "heff_plan_reload");
+  return tci_heff_plan_reload_impl(p, L, W, W2, R, false);
+}
+
 extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   if (!pp || !*pp || (*pp)->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "heff_plan_destroy: invalid plan");
   tci_heff_plan p = *pp;
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
-                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64};
+                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64, p->ws};
   for (void* b : bufs) tci_dev_free(b);
   for (tci_tensor* t : {&p->cL, &p->cW, &p->cW2, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2], &p->cVin, &p->cVout})
     if (*t) tci_tensor_free(t);
@@ -526,10 +588,11 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, boo
     if (out_mode != 0 || psi_presplit) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_apply: FP64 plan writes FP64");
     WWArgs<double> args;
     for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = p->ww[i];
-    TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL * 4, chiR * Dw, chiR, psi, chiR, 1, p->R64, chiR, 1, p->U, chiR * Dw, 1));
+    TCI_TRY(tci_gemm_native_batched_ws(ctx, TCI_F64, 1, chiL * 4, chiR * Dw, chiR, psi, 0, chiR, 1, p->R64, 0, chiR, 1,
+                                       p->U, 0, chiR * Dw, 1, p->ws, p->ws_bytes));
     TCI_TRY(launch_ww_f64(ctx, args, (const double*)p->U, chiL, chiR, p->V64, Dw * chiL));
-    TCI_TRY(tci_gemm_native(ctx, TCI_F64, chiL, 4 * chiR, Dw * chiL, p->L64, Dw * chiL, 1, p->V64, Dw * chiL, 1, out,
-                            4 * chiR, 1));
+    TCI_TRY(tci_gemm_native_batched_ws(ctx, TCI_F64, 1, chiL, 4 * chiR, Dw * chiL, p->L64, 0, Dw * chiL, 1, p->V64, 0,
+                                       Dw * chiL, 1, out, 0, 4 * chiR, 1, p->ws, p->ws_bytes));
     return TCI_OK;
   }
   WWArgs<float> args;

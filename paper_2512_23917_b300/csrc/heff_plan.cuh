@@ -57,6 +57,8 @@ struct tci_heff_plan_s {
   // launch sequence of a solve is fixed by its arguments (every branch is a
   // device gate), so a repeated call with the same key replays a captured
   // graph, its psi0 / x kernel arguments set for the call.
+  void* ws = nullptr;          // FP64 plan: split-K partials of the matvec GEMMs
+  size_t ws_bytes = 0;
   int lz_graphs = 1;
   int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
   tci_graph lz_graph;
@@ -71,3 +73,8 @@ struct tci_heff_plan_s {
 tci_status tci_heff_tune_ww(tci_heff_plan p, float* ms_out);
 tci_status tci_heff_apply_complex_raw(tci_heff_plan p, const double* psi, double* out);
 tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, bool psi_presplit, int out_mode = 0);
+
+// Reload environments of the same shapes into a real plan (see tci_heff_plan_reload);
+// same_mpo skips recomputing W.W (the caller guarantees W and W2 are unchanged).
+tci_status tci_heff_plan_reload_impl(tci_heff_plan p, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R,
+                                     bool same_mpo);

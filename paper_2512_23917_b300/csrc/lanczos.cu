@@ -1408,7 +1408,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   double* xd = x ? (double*)x->data : nullptr;
   SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split};
   bool done = false;
-  if (split && !p->cplx && p->lz_graphs) {
+  if (!p->cplx && p->lz_graphs) {
     // eager on the first call with a key, captured on the second, replayed after;
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
     // or write x get the call's pointers before every replay
@@ -1417,8 +1417,9 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
                                       p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
                                       (int64_t)ctx->wait_limit_ns};
     const bool df = arith == TCI_LANCZOS_DF32;
-    std::vector<const void*> io = {(const void*)k_sumsq,
-                                   df ? (const void*)k_start<ArithDF, kInPieces> : (const void*)k_start<ArithF64, kInPieces>};
+    const void* start_fn = split ? (df ? (const void*)k_start<ArithDF, kInPieces> : (const void*)k_start<ArithF64, kInPieces>)
+                                 : (df ? (const void*)k_start<ArithDF, kInF64> : (const void*)k_start<ArithF64, kInNone>);
+    std::vector<const void*> io = {(const void*)k_sumsq, start_fn};
     if (xd) io.push_back(df ? (const void*)k_ritz<ArithDF> : (const void*)k_ritz<ArithF64>);
     if (!(p->lz_graph.exec && key == p->lz_graph_key) && key == p->lz_last_key) {
       tci_graph_destroy(&p->lz_graph);

@@ -134,6 +134,14 @@ tci_status tci_gemm_native(tci_context ctx, tci_dtype dt, int64_t M, int64_t N, 
 tci_status tci_gemm_native_batched(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
                                    const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
                                    int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn);
+// The same with a caller-owned split-K workspace (used when ws_bytes covers
+// tci_gemm_native_workspace; then nothing is allocated, e.g. inside a graph capture).
+tci_status tci_gemm_native_batched_ws(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K,
+                                      const void* A, int64_t sab, int64_t sam, int64_t sak, const void* B, int64_t sbb,
+                                      int64_t sbn, int64_t sbk, void* C, int64_t scb, int64_t scm, int64_t scn, void* ws,
+                                      size_t ws_bytes);
+// Bytes of split-K partial products the native GEMM of this shape needs (0: no split).
+size_t tci_gemm_native_workspace(tci_context ctx, tci_dtype dt, int64_t nbatch, int64_t M, int64_t N, int64_t K);
 
 // Split-BF16 tensor-core GEMM (tcgen05).  Operands are given as three
 // bfloat16 piece planes each: A pieces [3][M][Kp] and B pieces [3][N][Kp]

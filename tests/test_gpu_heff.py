@@ -123,3 +123,33 @@ def test_two_site_mpos_match_oracle(ctx, tci, prec, tol):
     plan.apply(to_dev(psi), out)
     torch.cuda.synchronize()
     assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi, W2=W2)) < tol
+
+
+@pytest.mark.parametrize("prec", ["native", "split_bf16"])
+def test_plan_reload_equals_new_plan(ctx, tci, prec):
+    """tci_heff_plan_reload: new environments (and a new MPO) in an existing plan give the same
+    matvec and Lanczos results as a plan created from them, also after graph replays."""
+    import torch
+    psi, L1, R1, W = dense_heff_inputs(40, seed=3, chi_r=33)
+    _, L2, R2, _ = dense_heff_inputs(40, seed=4, chi_r=33)
+    W2 = random_tensor([5, 5, 2, 2], 8)
+    plan = tci.HeffPlan(ctx, to_dev(L1), to_dev(W), to_dev(R1), precision=prec)
+    dpsi = to_dev(psi)
+    x = torch.empty_like(dpsi)
+    for _ in range(3):                      # eager, captured, replayed
+        plan.lanczos(dpsi, 12, True, x)
+    for (L, R, Wn) in ((L2, R2, W), (L1, R1, W2)):
+        plan.reload(to_dev(L), to_dev(Wn), to_dev(R))
+        ref = tci.HeffPlan(ctx, to_dev(L), to_dev(Wn), to_dev(R), precision=prec)
+        out, out_ref = torch.empty_like(dpsi), torch.empty_like(dpsi)
+        plan.apply(dpsi, out)
+        ref.apply(dpsi, out_ref)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(out.cpu().numpy(), out_ref.cpu().numpy())
+        tol = 1e-12 if prec == "native" else 1e-6
+        assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, Wn, R, psi)) < tol
+        for _ in range(3):
+            r = plan.lanczos(dpsi, 12, True, x)
+            r_ref = ref.lanczos(dpsi, 12, True, torch.empty_like(dpsi))
+            assert r["theta"] == r_ref["theta"]
+            np.testing.assert_array_equal(r["alpha"], r_ref["alpha"])
