@@ -494,7 +494,10 @@ tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reor
  * summed in double-float arithmetic under the same error bound; [4] steps
  * whose second projection was applied in FP32 and folded into the
  * next-vector pass with beta_j^2 = ||w'||^2 - |h'|^2.  [2] to [4] stay 0
- * for double-float vectors and without re-orthogonalisation.  All zero
+ * for double-float vectors, without re-orthogonalisation, with reduced terms
+ * switched off (tci_heff_set_lanczos_reduced_terms) and on steps whose vector
+ * work runs as one cluster launch (n (j + 2) <= 2^19); [2] and [3] also for
+ * vectors shorter than 2^20 elements and bases beyond 20 vectors.  All zero
  * before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
 
