@@ -35,7 +35,7 @@ def test_blocksparse_equals_dense_and_respects_charge():
     for (ia, s1, s2, ib) in blocksparse_structure(dims, inp["qmax"])["psi"]:
         mask[off[ia]:off[ia] + dims[ia], s1, s2, off[ib]:off[ib] + dims[ib]] = True
     assert np.max(np.abs(dense[~mask])) < 1e-12 * np.max(np.abs(dense))
-    # block-by-block recomputation with only the allowed blocks, by brute-force sums
+    # the other contraction order (L first) on the same zero-filled tensors
     psiD = blocksparse.densify_psi({k: v.astype(float) for k, v in inp["psi"].items()}, dims)
     LD = blocksparse.densify_env({k: v.astype(float) for k, v in inp["L"].items()}, dims)
     RD = blocksparse.densify_env({k: v.astype(float) for k, v in inp["R"].items()}, dims)
@@ -43,6 +43,94 @@ def test_blocksparse_equals_dense_and_respects_charge():
     assert rel_frob_err(dense, ref) < 1e-13
     flops = blocksparse.bs_flops(inp)
     assert 0 < flops < heff.heff_flops(64)
+
+
+def _brute_force_bs_heff(inp):
+    """out and the multiply-add count of the block-sparse H_eff, by explicit loops.
+
+    Works on the zero-filled (densified) tensors and reads the block structure
+    from their nonzero pattern only (no block lists): stage 1 takes one
+    multiply-add per pair psi[a',t1,t2,b'] != 0, R[b,wr,b'] != 0; stage 2 applies
+    the 20 x 20 W.W matrix on every (a', b) pair where some U[a',:,:,b,:] != 0;
+    stage 3 takes one multiply-add per L[a,wl,a'] != 0 and (a', b) pair carrying
+    U, for every output element whose block is allowed (psi's pattern).
+    """
+    dims = inp["dims"]
+    P = blocksparse.densify_psi({k: v.astype(float) for k, v in inp["psi"].items()}, dims)
+    L = blocksparse.densify_env({k: v.astype(float) for k, v in inp["L"].items()}, dims)
+    R = blocksparse.densify_env({k: v.astype(float) for k, v in inp["R"].items()}, dims)
+    W = inp["W"]
+    n, Dw, d = L.shape[0], W.shape[0], W.shape[2]
+    U = np.zeros((n, d, d, n, Dw))
+    mac1 = 0
+    for ap, t1, t2, bp in zip(*np.nonzero(P)):
+        for b in range(n):
+            for wr in range(Dw):
+                if R[b, wr, bp] != 0.0:
+                    U[ap, t1, t2, b, wr] += P[ap, t1, t2, bp] * R[b, wr, bp]
+                    mac1 += 1
+    V = np.zeros((d, d, n, Dw, n))
+    carries = np.zeros((n, n), dtype=bool)
+    mac2 = 0
+    for ap in range(n):
+        for b in range(n):
+            if not np.any(U[ap, :, :, b, :] != 0.0):
+                continue
+            carries[ap, b] = True
+            for wl in range(Dw):
+                for s1 in range(d):
+                    for s2 in range(d):
+                        acc = 0.0
+                        for wr in range(Dw):
+                            for t1 in range(d):
+                                for t2 in range(d):
+                                    ww = 0.0
+                                    for wm in range(Dw):
+                                        ww += W[wl, wm, s1, t1] * W[wm, wr, s2, t2]
+                                    acc += ww * U[ap, t1, t2, b, wr]
+                                    mac2 += 1
+                        V[s1, s2, b, wl, ap] = acc
+    out = np.zeros((n, d, d, n))
+    mac3 = 0
+    for a, s1, s2, b in zip(*np.nonzero(P)):
+        acc = 0.0
+        for wl in range(Dw):
+            for ap in range(n):
+                if L[a, wl, ap] != 0.0 and carries[ap, b]:
+                    acc += L[a, wl, ap] * V[s1, s2, b, wl, ap]
+                    mac3 += 1
+        out[a, s1, s2, b] = acc
+    return out, mac1, mac2, mac3
+
+
+def _asymmetric_bs_inputs(dims, seed):
+    """Block-sparse inputs with the given (not mirror-symmetric) sector dims, q = -qmax..qmax."""
+    dims = np.asarray(dims, dtype=np.int64)
+    qmax = (len(dims) - 1) // 2
+    st = blocksparse_structure(dims, qmax)
+    rng = np.random.default_rng(seed)
+    draw = lambda k, j: rng.standard_normal((dims[k[0]], dims[k[j]])).astype(np.float32)
+    return {"dims": dims, "qmax": qmax, "psi": {k: draw(k, 3) for k in st["psi"]},
+            "L": {k: draw(k, 2) for k in st["L"]}, "R": {k: draw(k, 2) for k in st["R"]},
+            "W": heisenberg_mpo(1.0)}
+
+
+@pytest.mark.parametrize("case", ["gaussian", "asymmetric"])
+def test_blocksparse_brute_force_sum_and_flop_count(case):
+    if case == "gaussian":
+        # 5 sectors (dims 1, 3, 4, 3, 1): the edge sectors leave some (a', b) pairs without U
+        inp = blocksparse_inputs(total=12, seed=11, qmax=2, sigma=1.0)
+        assert list(inp["dims"]) == [1, 3, 4, 3, 1]
+    else:
+        # no mirror symmetry, so a swapped operand dimension changes the count
+        inp = _asymmetric_bs_inputs([2, 1, 4, 3, 1, 2, 1], seed=12)
+    out_bf, mac1, mac2, mac3 = _brute_force_bs_heff(inp)
+    _, dense = blocksparse.bs_heff_apply(inp)
+    assert rel_frob_err(dense, out_bf) < 1e-13
+    n = int(np.sum(inp["dims"]))
+    assert mac1 > 0 and mac2 > 0 and mac3 > 0
+    assert mac2 % 400 == 0 and mac2 // 400 < n * n        # not every (a', b) pair carries U
+    assert blocksparse.bs_flops(inp) == 2.0 * (mac1 + mac2 + mac3)
 
 
 def test_blocksparse_flop_count_config():
