@@ -318,8 +318,10 @@ tci_status tci_heff_plan_create2(tci_context ctx, tci_tensor L, tci_tensor W, tc
  * split into bfloat16 pieces (split plans) into the plan's own buffers on the
  * context's stream; the plan's configuration, workspaces and Lanczos graph
  * are kept (the graph is dropped when W.W changes).  A sweep that meets the
- * same bond dimensions again reuses one plan this way.  Errors: INVALID_ARG,
- * SHAPE (shapes differ from the plan's), UNSUPPORTED (complex plans), CUDA. */
+ * same bond dimensions again reuses one plan this way.  Errors: INVALID_ARG
+ * (invalid plan or tensor handle), DTYPE (a tensor is not F64), SHAPE (not
+ * row-major, or shapes differ from the plan's), UNSUPPORTED (complex plans),
+ * CUDA. */
 tci_status tci_heff_plan_reload(tci_heff_plan plan, tci_tensor L, tci_tensor W, tci_tensor W2, tci_tensor R);
 tci_status tci_heff_plan_destroy(tci_heff_plan* plan);
 /* out = H_eff psi (async).  psi and out must not overlap. */
@@ -520,6 +522,13 @@ tci_status tci_heff_set_lanczos_reduced_terms(tci_heff_plan plan, int enable);
  * graph.  Results are identical either way.
  * Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_graphs(tci_heff_plan plan, int enable);
+
+/* Graph replay state of `plan` (extension): info[0] = 1 while replay is
+ * enabled (a failed capture turns it off and later solves run eagerly),
+ * info[1] = 1 when the last tci_lanczos ran as one graph launch and 0 when it
+ * ran eagerly, info[2] = graph launches of this plan so far.  info holds 3
+ * int64_t.  Errors: INVALID_ARG (invalid plan, NULL info), INVALID_CONTEXT. */
+tci_status tci_heff_lanczos_graph_info(tci_heff_plan plan, int64_t* info);
 
 /* ------------------------------------------- U(1) block-sparse H_eff
  * Charge-conserving (U(1)) block-sparse tensors are listed as future work of

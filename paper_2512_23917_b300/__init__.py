@@ -101,6 +101,7 @@ SIGNATURES = [
     ("tci_lanczos", C.c_int, [_p, _p, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(C.c_int), _p]),
     ("tci_heff_lanczos_stats", C.c_int, [_p, C.POINTER(C.c_int)]),
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
+    ("tci_heff_lanczos_graph_info", C.c_int, [_p, _i64p]),
     ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_reload", C.c_int, [_p, _p, _p, _p, _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
@@ -608,7 +609,8 @@ class HeffPlan:
                 "steps": k.value}
 
     def set_lanczos_graphs(self, enable: bool):
-        """Replay repeated lanczos() calls from a captured CUDA graph (default on, split plans)."""
+        """Replay repeated lanczos() calls from a captured CUDA graph (default on, real plans;
+        complex plans run eagerly)."""
         _check(lib.tci_heff_set_lanczos_graphs(self.handle, int(bool(enable))), self.ctx.handle)
 
     def reload(self, L, W, R, W2=None):
@@ -630,6 +632,13 @@ class HeffPlan:
         _check(lib.tci_heff_lanczos_stats(self.handle, st), self.ctx.handle)
         return {"steps": st[0], "second_passes": st[1], "f32_term_passes": st[2], "df_term_passes": st[3],
                 "fused_pass3": st[4]}
+
+    def lanczos_graph_info(self):
+        """Graph replay state: enabled (False after a capture failed), whether the last lanczos()
+        ran as one graph launch, and the number of graph launches of this plan."""
+        info = (C.c_int64 * 3)()
+        _check(lib.tci_heff_lanczos_graph_info(self.handle, info), self.ctx.handle)
+        return {"enabled": bool(info[0]), "last_from_graph": bool(info[1]), "graph_launches": int(info[2])}
 
     def close(self):
         if self.handle:

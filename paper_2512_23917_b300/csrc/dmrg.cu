@@ -95,6 +95,8 @@ extern "C" tci_status tci_dmrg(tci_context ctx, tci_tensor W, int nsites, int64_
       TCI_TRY(tci_heff_plan_create(ctx, L[k].t, W, R[k + 2].t, &plan));
       it = plans.emplace(key, plan).first;
     } else {
+      // same_mpo = true skips the W.W recompute: valid because this driver applies
+      // one MPO tensor W on every site (a per-site MPO would need false here)
       TCI_TRY(tci_heff_plan_reload_impl(it->second, L[k].t, W, W, R[k + 2].t, true));
     }
     int done = 0;

@@ -503,9 +503,11 @@ tci_status tci_heff_plan_reload_impl(tci_heff_plan p, tci_tensor L, tci_tensor W
   if (p->cplx) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_plan_reload: real plans only");
   if (!W2) W2 = W;
   const int64_t Dw = HEFF_DW, chiL = p->chiL, chiR = p->chiR;
-  for (tci_tensor t : {L, W, W2, R})
-    if (!tci_ten_ok(t) || t->dtype != TCI_F64 || !tci_is_rowmajor(t))
-      return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_reload: L, W, W2, R must be row-major F64");
+  for (tci_tensor t : {L, W, W2, R}) {
+    if (!tci_ten_ok(t)) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "heff_plan_reload: invalid L, W, W2 or R");
+    if (t->dtype != TCI_F64) return tci_fail(ctx, TCI_ERR_DTYPE, "heff_plan_reload: L, W, W2, R must be F64");
+    if (!tci_is_rowmajor(t)) return tci_fail(ctx, TCI_ERR_SHAPE, "heff_plan_reload: L, W, W2, R must be row-major");
+  }
   if (L->order != 3 || R->order != 3 || W->order != 4 || W2->order != 4 || L->shape[0] != chiL || L->shape[1] != Dw ||
       L->shape[2] != chiL || R->shape[0] != chiR || R->shape[1] != Dw || R->shape[2] != chiR || W->shape[0] != Dw ||
       W->shape[1] != Dw || W->shape[2] != 2 || W->shape[3] != 2)

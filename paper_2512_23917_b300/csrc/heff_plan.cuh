@@ -53,13 +53,15 @@ struct tci_heff_plan_s {
   double* lz_o64 = nullptr;
   int lz_stats[5] = {0, 0, 0, 0, 0};   // last tci_lanczos: steps, second GS passes, FP32-term passes,
                                        // double-float-term passes, fused pass 3
-  // Lanczos solves replayed from a CUDA graph (split-BF16 real plans): the
+  // Lanczos solves replayed from a CUDA graph (real plans): the
   // launch sequence of a solve is fixed by its arguments (every branch is a
   // device gate), so a repeated call with the same key replays a captured
   // graph, its psi0 / x kernel arguments set for the call.
   void* ws = nullptr;          // FP64 plan: split-K partials of the matvec GEMMs
   size_t ws_bytes = 0;
   int lz_graphs = 1;
+  int lz_last_graph = 0;       // the last solve ran as a graph launch (1) or eagerly (0)
+  int64_t lz_graph_launches = 0;
   int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;

@@ -1408,6 +1408,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   double* xd = x ? (double*)x->data : nullptr;
   SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split};
   bool done = false;
+  p->lz_last_graph = 0;
   if (!p->cplx && p->lz_graphs) {
     // eager on the first call with a key, captured on the second, replayed after;
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
@@ -1439,6 +1440,8 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
       if (xd) TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 2, 5, 3, xd));
       TCI_CUDA(ctx, cudaGraphLaunch(p->lz_graph.exec, ctx->stream));
       done = true;
+      p->lz_last_graph = 1;
+      ++p->lz_graph_launches;
     }
     p->lz_last_key = key;
   }
@@ -1492,6 +1495,16 @@ extern "C" tci_status tci_heff_lanczos_stats(tci_heff_plan p, int* stats) {
   TCI_CHECK_CTX(p->ctx);
   if (!stats) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "lanczos_stats: NULL stats");
   for (int i = 0; i < 5; ++i) stats[i] = p->lz_stats[i];
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_lanczos_graph_info(tci_heff_plan p, int64_t* info) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "lanczos_graph_info: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (!info) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "lanczos_graph_info: NULL info");
+  info[0] = p->lz_graphs;
+  info[1] = p->lz_last_graph;
+  info[2] = p->lz_graph_launches;
   return TCI_OK;
 }
 

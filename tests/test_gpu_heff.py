@@ -153,3 +153,28 @@ def test_plan_reload_equals_new_plan(ctx, tci, prec):
             r_ref = ref.lanczos(dpsi, 12, True, torch.empty_like(dpsi))
             assert r["theta"] == r_ref["theta"]
             np.testing.assert_array_equal(r["alpha"], r_ref["alpha"])
+
+
+def test_plan_reload_error_codes(ctx, tci):
+    """tci_heff_plan_reload: a non-F64 tensor is DTYPE, a non-row-major one or another shape is
+    SHAPE, and an invalid tensor handle is INVALID_ARG."""
+    import ctypes
+    import torch
+    psi, L, R, W = dense_heff_inputs(16, seed=3)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="native")
+    dL, dW, dR = to_dev(L), to_dev(W), to_dev(R)
+    with pytest.raises(tci.TciError) as e:
+        plan.reload(dL.float(), dW, dR)
+    assert e.value.status_name == "TCI_ERR_DTYPE"
+    with pytest.raises(tci.TciError) as e:
+        plan.reload(dL.transpose(0, 2), dW, dR)
+    assert e.value.status_name == "TCI_ERR_SHAPE"
+    with pytest.raises(tci.TciError) as e:
+        plan.reload(to_dev(dense_heff_inputs(17, seed=3)[1]), dW, dR)
+    assert e.value.status_name == "TCI_ERR_SHAPE"
+    tw, tr = ctx.wrap(dW), ctx.wrap(dR)
+    junk = ctypes.create_string_buffer(4096)             # zero bytes: no tensor handle's magic
+    bogus = ctypes.c_void_p(ctypes.addressof(junk))
+    st = tci.lib.tci_heff_plan_reload(plan.handle, bogus, tw.handle, None, tr.handle)
+    assert tci.STATUS[st] == "TCI_ERR_INVALID_ARG"
+    torch.cuda.synchronize()

@@ -167,31 +167,40 @@ def test_lanczos_rounding_level_terms_counted(ctx, tci):
     assert st["f32_term_passes"] + st["df_term_passes"] == 0, st
 
 
-@pytest.mark.parametrize("chi,chi_r,arith", [(64, 64, "f64"), (75, 61, "f64"), (64, 40, "df32")])
-def test_lanczos_graph_replay_identical(ctx, tci, chi, chi_r, arith):
-    """Split-BF16 plan: eager, captured and replayed solves give bit-identical results, also
-    when the start-vector buffer alternates (a new key runs eagerly first)."""
+@pytest.mark.parametrize("precision,chi,chi_r,arith", [
+    ("split_bf16", 64, 64, "f64"), ("split_bf16", 75, 61, "f64"), ("split_bf16", 64, 40, "df32"),
+    ("native", 64, 64, "f64"), ("native", 75, 61, "f64"), ("native", 64, 40, "df32")])
+def test_lanczos_graph_replay_identical(ctx, tci, precision, chi, chi_r, arith):
+    """Eager, captured and replayed solves give bit-identical results on split-BF16 and FP64
+    plans, with FP64 and double-float vectors, while the start-vector and Ritz-vector buffers
+    alternate (the replay patches psi0 and x into the captured kernel nodes); every solve after
+    the first eager one runs as a graph launch."""
     import torch
     psi, L, R, W = dense_heff_inputs(chi, seed=13, chi_r=chi_r)
-    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision=precision)
     plan.set_lanczos_arith(arith)
     d1, d2 = to_dev(psi), to_dev(psi)
-    x = torch.empty_like(d1)
+    x1, x2 = torch.empty_like(d1), torch.empty_like(d1)
 
-    def solve(dpsi):
+    def solve(dpsi, x):
         x.fill_(float("nan"))
         r = plan.lanczos(dpsi, 20, True, x)
         return r, x.cpu().numpy()
 
     plan.set_lanczos_graphs(False)
-    ref, xref = solve(d1)
+    ref, xref = solve(d1, x1)
+    assert not plan.lanczos_graph_info()["last_from_graph"]
     plan.set_lanczos_graphs(True)
-    for dpsi in (d1, d1, d1, d1, d2, d2, d2, d1, d1):
-        r, xr = solve(dpsi)
+    for i, (dpsi, x) in enumerate(((d1, x1), (d1, x1), (d1, x2), (d1, x1), (d2, x2), (d2, x1), (d2, x2),
+                                   (d1, x2), (d1, x1))):
+        r, xr = solve(dpsi, x)
+        info = plan.lanczos_graph_info()
+        assert info["enabled"] and info["last_from_graph"] == (i >= 1), (i, info)
         assert r["theta"] == ref["theta"] and r["steps"] == ref["steps"]
         np.testing.assert_array_equal(r["alpha"], ref["alpha"])
         np.testing.assert_array_equal(r["beta"], ref["beta"])
         np.testing.assert_array_equal(xr, xref)
+    assert plan.lanczos_graph_info()["graph_launches"] == 8
 
 
 @pytest.mark.parametrize("gs", ["dgks", "twice"])
