@@ -306,6 +306,122 @@ def measure_tebd(tci, ctx, dev, peaks, with_oracle: bool):
     return res
 
 
+def measure_fp64_peak(tci, ctx, dev):
+    """Measured FP64 ceilings of this device: cuBLAS DGEMM through torch.matmul at 8192^3 (best of 3
+    after a warm-up) and the library's DFMA-loop probe (tci_probe_fp64_rate); the larger one is the
+    FP64 roofline denominator."""
+    import torch
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(SEED)
+    a = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev, generator=g)
+    c = torch.empty_like(a)
+    torch.matmul(a, b, out=c)
+    stream = torch.cuda.current_stream(dev)
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(a, b, out=c)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    dgemm = 2.0 * n ** 3 / (best * 1e-3) / 1e9
+    del a, b, c
+    torch.cuda.empty_cache()
+    probe = ctx.probe_fp64_rate(20000)
+    return {"torch_matmul_f64_8192_gflops": dgemm, "dfma_loop_gflops": probe, "peak_gflops": max(dgemm, probe),
+            "peak_source": "measured: max(torch.matmul float64 8192^3, DFMA-loop probe)"}
+
+
+def measure_config1(tci, ctx, dev, with_oracle: bool):
+    """chi = 32 FP64 plan: the 20-step Lanczos solve (seeded, symmetrised environments) timed, and the
+    12-site ED check: exact environments of 5 + 5 sites around psi[32,2,2,32], the device Lanczos run
+    to convergence (80 steps) against exact diagonalisation of the 12-site chain."""
+    import torch
+    from tci_synth import dense_heff_inputs, heisenberg_mpo
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    psi, L, R, W = dense_heff_inputs(32, seed=SEED)
+    plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="native")
+    dpsi = t(psi)
+    x = torch.empty_like(dpsi)
+    for _ in range(3):
+        plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 20
+    e0.record(stream)
+    for _ in range(n):
+        r = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    F = plan.flops
+    res = {"workload": "20-step FP64 Lanczos, dense two-site H_eff, chi=32, d=2, Dw=5 (FP64 plan)",
+           "ms_per_solve": ms, "gflops": LANCZOS_STEPS * F / (ms * 1e-3) / 1e9, "ritz_value": r["theta"]}
+    plan.close()
+    if with_oracle:
+        from oracle import heff as o_heff
+        from oracle import lanczos as o_lanczos
+        o = o_lanczos.lanczos(lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape)), psi, LANCZOS_STEPS)
+        res["ritz_rel_err_vs_oracle"] = abs(r["theta"] - o["theta"]) / abs(o["theta"])
+        import scipy.sparse.linalg as spla
+        Wm = heisenberg_mpo()
+        Le, Re = o_heff.left_env(Wm, 5), o_heff.right_env(Wm, 5)
+        e_ed = float(spla.eigsh(o_heff.mpo_chain_matrix(Wm, 12), k=1, which="SA", tol=1e-14)[0][0])
+        pe = tci.HeffPlan(ctx, t(Le), t(Wm), t(Re), precision="native")
+        start = t(np.random.default_rng(SEED).standard_normal((32, 2, 2, 32)))
+        re = pe.lanczos(start, 80, True, torch.empty_like(start))
+        pe.close()
+        res["ed_check"] = {"sites": 12, "psi_shape": [32, 2, 2, 32], "lanczos_steps": 80,
+                           "e0_device_lanczos": re["theta"], "e0_exact_diagonalisation": e_ed,
+                           "abs_err": abs(re["theta"] - e_ed)}
+    return res
+
+
+def measure_config2(tci, ctx, dev, fp64_peak_gflops: float, with_oracle: bool):
+    """chi = 1024 FP64 plan: the 20-step Lanczos solve with FP64 re-orthogonalisation, its rate, the
+    matvec GEMMs against the measured FP64 peak, and the Ritz value against the oracle's solve."""
+    import torch
+    from tci_synth import dense_heff_inputs
+    t = lambda x: torch.from_numpy(np.ascontiguousarray(x)).to(dev)
+    psi, L, R, W = dense_heff_inputs(1024, seed=SEED)
+    plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="native")
+    dpsi = t(psi)
+    x = torch.empty_like(dpsi)
+    for _ in range(2):                                  # eager, then captured
+        plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n = 2
+    e0.record(stream)
+    for _ in range(n):
+        r = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    F = plan.flops
+    s64 = plan.apply_timed(dpsi, torch.empty_like(dpsi))
+    g64 = float(s64[1] + s64[3])
+    gemm_gf = (F - 2.0 * 1024 * 1024 * 16 * 25) / (g64 * 1e-3) / 1e9
+    res = {"workload": "20-step FP64 Lanczos (FP64 re-orthogonalisation), dense two-site H_eff, chi=1024, d=2, Dw=5, "
+                       "FP64 plan", "ms_per_solve": ms, "gflops": LANCZOS_STEPS * F / (ms * 1e-3) / 1e9,
+           "matvec_stage_ms": [float(v) for v in s64], "ritz_value": r["theta"],
+           "roofline": {"bound": "fp64", "kernel": "k_gemm_strided<double>", "achieved": gemm_gf,
+                        "peak": fp64_peak_gflops, "unit": "GFLOP/s", "frac": gemm_gf / fp64_peak_gflops,
+                        "peak_source": "measured FP64 peak of this run (fp64_peak)"}}
+    plan.close()
+    if with_oracle:
+        from oracle import heff as o_heff
+        from oracle import lanczos as o_lanczos
+        o = o_lanczos.lanczos(lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape)), psi, LANCZOS_STEPS)
+        res["ritz_rel_err_vs_oracle"] = abs(r["theta"] - o["theta"]) / abs(o["theta"])
+    return res
+
+
 def run_gpu(args):
     import torch
     rank, world, local = dist_info()
@@ -491,9 +607,9 @@ def run_gpu(args):
         torch.cuda.synchronize()
         s64 = plan64.apply_timed(dpsi, out64)
         fp64_ms = float(sum(s64))
-        # FP64 roof: no measured FP64 peak exists; derived as 148 SMs x 2 FP64 FMA lanes per clock
-        # x 2 flops x the maximum SM clock (ncu shows the FP64 GEMM's pipe 99 % busy at that rate)
-        fp64_peak = 148 * 2 * 2 * peaks.get("sm_max_mhz", 2032.0) * 1e6 / 1e12
+        fp64_peaks = measure_fp64_peak(tci, ctx, dev)
+        extra["fp64_peak"] = fp64_peaks
+        fp64_peak = fp64_peaks["peak_gflops"] / 1e3
         g64 = float(sum(s64[1:4:2]))
         fp64_gemm_tf = (F - 2.0 * CHI * CHI * 16 * 25) / (g64 * 1e-3) / 1e12
         extra["fp64_path"] = {"gflops": F / (fp64_ms * 1e-3) / 1e9, "ms_per_matvec": fp64_ms,
@@ -501,7 +617,7 @@ def run_gpu(args):
                               "roofline": {"bound": "fp64", "kernel": "k_gemm_strided<double>",
                                            "achieved": fp64_gemm_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                                            "frac": fp64_gemm_tf / fp64_peak,
-                                           "peak_source": "derived: 148 SMs x 2 FP64 FMA/clk x 2 x max SM clock"}}
+                                           "peak_source": fp64_peaks["peak_source"]}}
         extra["split_vs_fp64_speedup"] = fp64_ms / mv_ms
         # error of the split matvec against the CPU oracle on sampled rows
         from oracle.contract import rel_frob_err
@@ -525,12 +641,16 @@ def run_gpu(args):
 
     rows = {}
     if not args.skip_rows:
+        rows["config1_chi32"] = measure_config1(tci, ctx, dev, rank == 0)
+        if rank == 0:
+            rows["config2_fp64_lanczos_chi1024"] = measure_config2(tci, ctx, dev, extra["fp64_peak"]["peak_gflops"],
+                                                                   True)
         rows["a7_blocksparse"] = measure_blocksparse(tci, ctx, dev, peaks, rank == 0)
         rows["a8_tebd"] = measure_tebd(tci, ctx, dev, peaks, rank == 0)
     clocks = clk.summary()
     line = {"metric": METRIC, "value": value, "unit": "GFLOP/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "vs_baseline": None, "dtype": "split-bf16x3 (6 products) / fp64 Lanczos", "data": "synthetic",
             "config": {"workload": "20-step Lanczos on the dense two-site H_eff, Heisenberg MPO, chi=2048, d=2, Dw=5, "
                                    "split-BF16 matvec (3 pieces, 6 products, FP32 tensor-memory accumulation drained "
                                    "every chunk_k of K into a double-float sum), FP64 Lanczos (dots, CGS2, "

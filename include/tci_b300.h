@@ -97,6 +97,12 @@ const char* tci_last_error(tci_context ctx);
  * device `device` and stream `stream` (a cudaStream_t; NULL = the legacy
  * default stream).  Reads TCI_VERBOSE (App. C.3) once: 0 silent, 1 one line
  * per call on stderr, 2 adds the call's device time (this synchronises).
+ * Also reads TCI_FAULT_ALLOC (extension, for tests of the out-of-memory
+ * path): "n:k" makes the context's pooled device allocation number n
+ * (0-based, counted from creation) fail k times in a row on the host, as if
+ * the device were out of memory, before the pool is asked; k = 1 exercises
+ * the trim-and-retry path (the call succeeds), k >= 2 makes the call return
+ * TCI_ERR_ALLOC.  The device is never touched by the injection.
  * On failure *ctx is set to NULL.  Errors: INVALID_ARG, CUDA. */
 tci_status tci_create_context(tci_context* ctx, int device, void* stream);
 
@@ -132,6 +138,16 @@ tci_status tci_context_set_split_chunks(tci_context ctx, int chunk_k, int xchunk
  * force when their graph was captured.
  * Errors: INVALID_CONTEXT. */
 tci_status tci_context_set_wait_limit(tci_context ctx, uint64_t limit_ns);
+
+/* Measured FP64 FMA rate of the context's device (extension; the paper has
+ * no counterpart): one kernel of 4 blocks of 256 threads per SM, each thread
+ * running 8 independent FP64 FMA chains for `iters` iterations, timed with
+ * CUDA events on the context's stream; *gflops (host) receives the best of
+ * three launches after a warm-up, as 2 flops per FMA.  It is the FP64
+ * roofline denominator of the benchmark.  Synchronises; allocates and frees
+ * a small device buffer.  Errors: INVALID_ARG (NULL gflops, iters < 1),
+ * ALLOC, CUDA, INVALID_CONTEXT. */
+tci_status tci_probe_fp64_rate(tci_context ctx, int iters, double* gflops);
 
 /* Block the host until all work queued on the context's stream finished;
  * maps a sticky device error or a kernel timeout status to CUDA/TIMEOUT. */

@@ -109,6 +109,7 @@ SIGNATURES = [
     ("tci_tebd_theta_batched", C.c_int, [_p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
     ("tci_heff_set_gram_schmidt", C.c_int, [_p, C.c_int]),
     ("tci_context_set_wait_limit", C.c_int, [_p, C.c_uint64]),
+    ("tci_probe_fp64_rate", C.c_int, [_p, C.c_int, _dp]),
     ("tci_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p)]),
     ("tci_trunc_svd", C.c_int, [_p, _p, C.c_int, C.POINTER(_p), C.POINTER(_p), C.POINTER(_p), _dp, C.c_int64,
                                 C.c_int64, C.c_double, C.c_double]),
@@ -187,6 +188,12 @@ class Context:
     def set_wait_limit(self, limit_ns: int):
         """Limit of the bounded device waits (ns; 0 = default 2 s)."""
         _check(lib.tci_context_set_wait_limit(self.handle, int(limit_ns)), self.handle)
+
+    def probe_fp64_rate(self, iters: int = 20000) -> float:
+        """Measured FP64 FMA rate of the device in GFLOP/s (a DFMA loop on every SM)."""
+        g = C.c_double()
+        _check(lib.tci_probe_fp64_rate(self.handle, int(iters), C.byref(g)), self.handle)
+        return g.value
 
     def set_stream(self, stream: int):
         _check(lib.tci_context_set_stream(self.handle, _p(int(stream))), self.handle)

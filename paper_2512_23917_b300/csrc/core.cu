@@ -198,12 +198,17 @@ tci_status tci_dev_alloc(tci_context ctx, size_t bytes, void** p) {
     }
     cudaMemPool_t pool = cs == cudaStreamCaptureStatusNone ? pool_of(ctx->device) : nullptr;
     if (pool) {
-      e = cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
+      // injected failures (TCI_FAULT_ALLOC) stand in for the pool's answer on the host
+      int injected = ctx->pool_allocs == ctx->fault_alloc_at ? ctx->fault_alloc_times : 0;
+      ++ctx->pool_allocs;
+      e = injected-- > 0 ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
       if (e == cudaErrorMemoryAllocation) {   // give cached memory back and try once more
         cudaGetLastError();
         cudaStreamSynchronize(ctx->stream);
         cudaMemPoolTrimTo(pool, 0);
-        e = cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
+        if (ctx->verbose > 0)
+          fprintf(stderr, "[tci] pool: allocation of %zu bytes failed; pool trimmed, retrying once\n", bytes);
+        e = injected-- > 0 ? cudaErrorMemoryAllocation : cudaMallocFromPoolAsync(p, bytes, pool, ctx->stream);
       }
       if (e == cudaSuccess) {
         DevicePools& dp = device_pools();
@@ -267,6 +272,14 @@ extern "C" tci_status tci_create_context(tci_context* out, int device, void* str
   ctx->split_xchunk_k = 1024;
   const char* v = getenv("TCI_VERBOSE");
   ctx->verbose = v ? atoi(v) : 0;
+  if (const char* f = getenv("TCI_FAULT_ALLOC")) {
+    long long at = -1;
+    int times = 0;
+    if (sscanf(f, "%lld:%d", &at, &times) == 2 && at >= 0 && times > 0) {
+      ctx->fault_alloc_at = at;
+      ctx->fault_alloc_times = times;
+    }
+  }
   cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
   ctx->d_scalars = nullptr;
   ctx->d_status = nullptr;

@@ -21,6 +21,12 @@ struct tci_context_s {
   int split_chunk_k;    // K depth per hi*hi accumulation unit of the split GEMM
   int split_xchunk_k;   // K depth per cross-product accumulation unit
   uint64_t wait_limit_ns = 0;   // bounded device waits of the tensor-core kernels (0: 2 s)
+  // host-side allocation-failure injection (TCI_FAULT_ALLOC="n:k", read at context
+  // creation): pooled allocation number n of this context (0-based) fails k times
+  // in a row before the pool is asked, as if the device were out of memory
+  int64_t fault_alloc_at = -1;
+  int fault_alloc_times = 0;
+  int64_t pool_allocs = 0;   // pooled allocations requested so far
   std::string last_error;
   // device scratch for reductions and kernel status words (owned)
   double* d_scalars;   // 64 doubles

@@ -54,3 +54,62 @@ def test_expired_wait_in_heff_plan_then_recovery(ctx, tci):
     ctx.synchronize()
     assert rel_frob_err(out.cpu().numpy(), o_heff.heff_apply(L, W, R, psi)) < 1e-6
     ctx.set_precision("native")
+
+
+def test_injected_allocation_failure_trim_retry_then_alloc_error(tci, monkeypatch, capfd):
+    """TCI_FAULT_ALLOC injects out-of-memory answers on the host (the device is never touched):
+    one injected failure is absorbed by the pool's trim-and-retry path and the call succeeds;
+    two in a row make the call return TCI_ERR_ALLOC, and the context keeps working after it."""
+    import torch
+    x = to_dev(random_tensor([64, 33], 5))
+    ref = x.cpu().numpy()
+    stream = torch.cuda.current_stream().cuda_stream
+    monkeypatch.setenv("TCI_VERBOSE", "1")
+    monkeypatch.setenv("TCI_FAULT_ALLOC", "0:1")
+    c1 = tci.Context(0, stream)
+    y = c1.wrap(x).copy()                               # the context's first pooled allocation
+    c1.synchronize()
+    np.testing.assert_array_equal(y.to_numpy(), ref)
+    assert "pool trimmed, retrying once" in capfd.readouterr().err
+    y.free()
+    c1.close()
+    monkeypatch.setenv("TCI_FAULT_ALLOC", "0:2")
+    c2 = tci.Context(0, stream)
+    with pytest.raises(tci.TciError) as ei:
+        c2.wrap(x).copy()
+    assert ei.value.status_name == "TCI_ERR_ALLOC"
+    err = capfd.readouterr().err
+    assert "pool trimmed, retrying once" in err and "[tci] error 6:" in err
+    y = c2.wrap(x).copy()                               # allocation 1 is not injected
+    c2.synchronize()
+    np.testing.assert_array_equal(y.to_numpy(), ref)
+    y.free()
+    c2.close()
+
+
+@pytest.mark.parametrize("level", [0, 1, 2])
+def test_verbose_levels(tci, monkeypatch, capfd, level):
+    """TCI_VERBOSE (App. C.3): 0 prints nothing, 1 one line per call on stderr, 2 adds the
+    call's device time."""
+    import re
+    import torch
+    monkeypatch.setenv("TCI_VERBOSE", str(level))
+    monkeypatch.delenv("TCI_FAULT_ALLOC", raising=False)
+    a, b = to_dev(random_tensor([12, 2, 9], 1)), to_dev(random_tensor([9, 2, 5], 2))
+    capfd.readouterr()
+    c = tci.Context(0, torch.cuda.current_stream().cuda_stream)
+    tci.contract(c, a, "ijk", b, "klm", "ijlm")
+    c.synchronize()
+    c.close()
+    lines = [ln for ln in capfd.readouterr().err.splitlines() if ln.startswith("[tci]")]
+    if level == 0:
+        assert lines == []
+        return
+    assert lines[0].startswith("[tci] create_context device=0")
+    assert lines[-1] == "[tci] destroy_context"
+    calls = [ln for ln in lines if ln.startswith("[tci] contract ")]
+    assert len(calls) == 1 and "ijk,klm->ijlm f64{12,2,9} x f64{9,2,5}" in calls[0]
+    if level == 2:
+        assert re.search(r" time=\d+\.\d{3} ms$", calls[0]), calls[0]
+    else:
+        assert "time=" not in calls[0]

@@ -105,6 +105,20 @@ def test_truncated_dmrg_matches_oracle_sweeps(ctx, tci):
     assert max(terr) > 0.0
 
 
+def test_dmrg_long_chain_bulk_energy_density(ctx, tci):
+    """Open chains of 32 and 64 sites at chi_max 32 on the device: the bulk energy per site
+    (E_64 - E_32) / 32 is within 3e-4 of 1/4 - ln 2 (the conformal 1/N term leaves 1.0e-4 in the
+    difference, plus truncation), and each energy equals the oracle's sweeps."""
+    e_inf = 0.25 - np.log(2.0)
+    W = to_dev(heisenberg_mpo())
+    e32, _ = tci.dmrg(ctx, W, 32, 32, 4)
+    e64, _ = tci.dmrg(ctx, W, 64, 32, 4)
+    bulk = (e64[-1] - e32[-1]) / 32
+    assert 0.0 < bulk - e_inf < 3e-4, bulk
+    oe64, _ = o_dmrg.dmrg(heisenberg_mpo(), 64, 32, 4)
+    assert abs(e64[-1] - oe64[-1]) < 1e-8 * abs(oe64[-1])
+
+
 def test_dmrg_split_precision_close_to_ed(ctx, tci):
     from test_oracle_dmrg import ed_ground
     ctx.set_precision("split_bf16")

@@ -52,3 +52,20 @@ def test_environment_updates_match_exact_environments():
         Rk = o_dmrg.update_right(Rk, B, W)
     np.testing.assert_array_equal(Lk, o_heff.left_env(W, 3))
     np.testing.assert_array_equal(Rk, o_heff.right_env(W, 3))
+
+
+def test_long_chain_bulk_energy_density():
+    """Open chains of 32 and 64 sites at chi_max 32 (4 sweeps): in the bulk energy per site
+    (E_64 - E_32) / 32 the boundary energy cancels, and it approaches the infinite chain's
+    1/4 - ln 2 (Hulthen's Bethe-ansatz value).  What remains is the conformal 1/N term of the open
+    chain, -pi^2 v c / (24 N) with v = pi/2, c = 1, which leaves pi^2 / (48 * 64 * 32) = 1.0e-4 in
+    the difference, plus the truncation at chi 32: tolerance 3e-4.  The energy per site of the
+    64-site chain alone is further off (the boundary energy over 64 sites), within 1e-2."""
+    e_inf = 0.25 - np.log(2.0)
+    e32, _ = o_dmrg.dmrg(heisenberg_mpo(), 32, 32, 4)
+    e64, _ = o_dmrg.dmrg(heisenberg_mpo(), 64, 32, 4)
+    bulk = (e64[-1] - e32[-1]) / 32
+    assert abs(bulk - e_inf) < 3e-4, bulk
+    assert 0.0 < bulk - e_inf < 3e-4          # the 1/N term raises the finite-chain difference
+    assert abs(e64[-1] / 64 - e_inf) < 1e-2
+    assert e64[-1] / 64 > e_inf               # open boundaries cost energy
