@@ -44,7 +44,7 @@ SEED = 20251223
 # DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec, the mean
 # of GEMM1 (956 MB) and GEMM2 (1554 MB) from one ncu capture of this kernel build with the
 # autotuned tile order (profiles/dram_heff_chi2048.md).  Set to None whenever the kernel changes.
-GEMM_DRAM_BYTES_PER_LAUNCH = 1.264e9
+GEMM_DRAM_BYTES_PER_LAUNCH = None
 
 
 def heff_flops(chi: int) -> float:

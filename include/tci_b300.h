@@ -519,6 +519,19 @@ tci_status tci_lanczos(tci_heff_plan plan, tci_tensor psi0, int nsteps, int reor
  * before the first solve.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
 
+/* First Gram-Schmidt projection of tci_lanczos formed inside the matvec
+ * (extension; off by default): on split-BF16 plans with FP64 vectors the dot
+ * products <v_i, H v_j> (i <= j, basis up to 23 vectors) and ||H v_j||^2 are
+ * computed in FP64 by the epilogue of the matvec's second GEMM from the
+ * output tiles it stores, instead of a separate pass over the basis; per-CTA
+ * partial sums are added in a fixed order.  Results agree with the separate
+ * pass to FP64 rounding.  On B300 it is slower (measured at chi = 2048: the
+ * GEMM takes 2.0 / 2.9 / 4.5 ms with 1 / 10 / 20 basis vectors against 1.55 ms
+ * plus 0.1-0.6 ms for the separate pass), because the epilogue threads'
+ * extra state spills registers and their dot products wait on DRAM between
+ * accumulator drains.  Errors: INVALID_ARG, INVALID_CONTEXT. */
+tci_status tci_heff_set_lanczos_fused_dots(tci_heff_plan plan, int enable);
+
 /* Reduced-precision small update terms of tci_lanczos with FP64 vectors
  * (extension; on by default): the FP32 and double-float evaluations of
  * rounding-level and matvec-error-level Gram-Schmidt terms counted by

@@ -102,6 +102,7 @@ SIGNATURES = [
     ("tci_heff_lanczos_stats", C.c_int, [_p, C.POINTER(C.c_int)]),
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
     ("tci_heff_lanczos_graph_info", C.c_int, [_p, _i64p]),
+    ("tci_heff_set_lanczos_fused_dots", C.c_int, [_p, C.c_int]),
     ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_reload", C.c_int, [_p, _p, _p, _p, _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
@@ -627,6 +628,11 @@ class HeffPlan:
         _check(lib.tci_heff_plan_reload(self.handle, tl.handle, tw.handle, tw2.handle if tw2 is not None else None,
                                         tr.handle), self.ctx.handle)
         self._keep = (L, W, R, W2)
+
+    def set_lanczos_fused_dots(self, enable: bool):
+        """Form the first projection's dots in the matvec's GEMM2 epilogue (split plans; off by default:
+        slower on B300 than the separate pass)."""
+        _check(lib.tci_heff_set_lanczos_fused_dots(self.handle, int(bool(enable))), self.ctx.handle)
 
     def set_lanczos_reduced_terms(self, enable: bool):
         """Allow (default) or forbid the FP32 / double-float evaluation of small update terms."""

@@ -609,6 +609,24 @@ tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, boo
   return TCI_OK;
 }
 
+// Split plan, psi already split into p->psip, FP64 output: the matvec with
+// the dot products of its output folded into GEMM2 (see
+// tci_gemm_split_bf16_dots): part rows 0..nv-1 receive the partial sums of
+// <V_i, out>, row nv those of <out, out>, over *grid CTAs.
+tci_status tci_heff_apply_raw_dots(tci_heff_plan p, double* out, const double* V, int64_t ldv, int nv, double* part,
+                                   int part_stride, int* grid) {
+  tci_context ctx = p->ctx;
+  if (p->prec == TCI_PREC_NATIVE || p->cplx) return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "heff_apply_dots: split plans only");
+  const int64_t chiL = p->chiL, chiR = p->chiR, Dw = HEFF_DW;
+  WWArgs<float> args;
+  for (int i = 0; i < HEFF_NWW; ++i) args.ww[i] = (float)p->ww[i];
+  TCI_TRY(tci_gemm_split_bf16(ctx, chiL * 4, chiR * Dw, p->Kp1, p->psip, p->Rp, p->U, 1, 1, chiL * 4, p->products,
+                              p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(launch_ww_split(ctx, args, (const float*)p->U, chiL, chiR, p->Vp, p->Kp2, 4 * chiR * p->Kp2, p->ww_na));
+  return tci_gemm_split_bf16_dots(ctx, chiL, 4 * chiR, p->Kp2, p->Lp, p->Vp, out, p->products, p->chunk_k,
+                                  p->xchunk_k, p->raster, V, ldv, nv, part, part_stride, grid);
+}
+
 // Same as tci_heff_apply_raw with CUDA events between the stages (split,
 // GEMM1, W.W, GEMM2); ms[0..3] receive the stage durations.
 static tci_status apply_timed(tci_heff_plan p, const double* psi, double* out, float* ms) {

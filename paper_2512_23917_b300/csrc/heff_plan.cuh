@@ -63,6 +63,7 @@ struct tci_heff_plan_s {
   int lz_last_graph = 0;       // the last solve ran as a graph launch (1) or eagerly (0)
   int64_t lz_graph_launches = 0;
   int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
+  int lz_fuse = 0;      // split plans: first Gram-Schmidt projection formed in the matvec's GEMM2 (opt-in)
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;
 };
@@ -75,6 +76,11 @@ struct tci_heff_plan_s {
 tci_status tci_heff_tune_ww(tci_heff_plan p, float* ms_out);
 tci_status tci_heff_apply_complex_raw(tci_heff_plan p, const double* psi, double* out);
 tci_status tci_heff_apply_raw(tci_heff_plan p, const double* psi, void* out, bool psi_presplit, int out_mode = 0);
+// Split plan, psi pieces already in p->psip, FP64 out: the matvec with the
+// dot products <V_i, out> (i < nv) and <out, out> formed in GEMM2's epilogue;
+// part[i*part_stride + b], b < *grid, are the per-CTA partial sums.
+tci_status tci_heff_apply_raw_dots(tci_heff_plan p, double* out, const double* V, int64_t ldv, int nv, double* part,
+                                   int part_stride, int* grid);
 
 // Reload environments of the same shapes into a real plan (see tci_heff_plan_reload);
 // same_mpo skips recomputing W.W (the caller guarantees W and W2 are unchanged).

@@ -7,7 +7,12 @@
 // One step j, with the basis V = [v_0 .. v_j] resident in HBM:
 //   w = H v_j                                   (the matvec; its input was
 //                                                prepared with v_j)
-//   pass 1: h = V^T w, ||w||^2;  alpha_j = h_j   (one read of V and w)
+//   pass 1: h = V^T w, ||w||^2;  alpha_j = h_j   (one read of V and w; opt-in on
+//                                                split-BF16 plans with FP64 vectors:
+//                                                formed in the matvec's GEMM2
+//                                                epilogue from the output tiles it
+//                                                stores, per-CTA partials summed in
+//                                                order; slower on B300)
 //   DGKS test: ||w - V h||^2 = ||w||^2 - |h|^2 < ||w||^2 / 2 ?
 //   taken:   pass 2: w -= V h, then h' = V^T w and ||w||^2  (fused: V read
 //                    once, w read and written)
@@ -99,6 +104,7 @@ constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
 constexpr double kDFBound = 9.765625e-4;                // 2^-10
 constexpr int kTermsF64 = 0, kTermsF32 = 1, kTermsDF = 2;
 constexpr int64_t kReducedMinN = 1 << 20;               // vector length from which reduced terms are used
+constexpr int kFusedMax = 23;                           // basis vectors whose dots the split GEMM can fuse
 
 __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -1261,8 +1267,16 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   TCI_CUDA(ctx, cudaGetLastError());
   for (int j = 0; j < nsteps; ++j) {
     Vt* vj = V + (int64_t)j * ldv;
+    // split plan, FP64 vectors: the first projection's dots h = V^T w and ||w||^2
+    // come out of the matvec's GEMM2 epilogue (per-CTA partials, reduced in order)
+    const bool fused = MODE == kInPieces && !kDF && reorth && p->lz_fuse && j + 1 <= kFusedMax;
     // w = H v_j
-    if (MODE == kInPieces) {
+    if (fused) {
+      int grid = 0;
+      TCI_TRY(tci_heff_apply_raw_dots(p, (double*)w, (const double*)V, ldv, j + 1, part, NBMAX, &grid));
+      k_reduce_parts<<<j + 1, 256, 0, ctx->stream>>>(part, j + 1, grid, S + OFF_H, ctrl);
+      k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part + (int64_t)(j + 1) * NBMAX, 1, grid, ctrl + 4, ctrl);
+    } else if (MODE == kInPieces) {
       TCI_TRY(tci_heff_apply_raw(p, nullptr, w, true, kDF ? 2 : 0));
     } else if (MODE == kInNone) {
       if (p->cplx)
@@ -1289,7 +1303,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // (below kReducedMinN the FP64 work is smaller than the extra launches)
       const bool reduced = kF32Terms && p->lz_reduced && j + 1 <= GMAX && n >= kReducedMinN;
       const double* lo1 = reduced ? S + OFF_LO : nullptr;
-      TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
+      if (!fused) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
@@ -1413,7 +1427,8 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     // eager on the first call with a key, captured on the second, replayed after;
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
     // or write x get the call's pointers before every replay
-    const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->lz_reduced, p->products,
+    const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->lz_reduced, p->lz_fuse,
+                                      p->products,
                                       p->chunk_k,
                                       p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
                                       (int64_t)ctx->wait_limit_ns};
@@ -1518,6 +1533,13 @@ extern "C" tci_status tci_heff_set_lanczos_graphs(tci_heff_plan p, int enable) {
     p->lz_graph_key.clear();
     p->lz_last_key.clear();
   }
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_lanczos_fused_dots(tci_heff_plan p, int enable) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_fused_dots: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  p->lz_fuse = enable ? 1 : 0;
   return TCI_OK;
 }
 

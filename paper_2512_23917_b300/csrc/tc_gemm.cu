@@ -26,9 +26,27 @@
 // 32 deep (one 64-byte swizzled row per operand row and piece) through a
 // 4-stage TMA -> mbarrier -> tcgen05.mma pipeline.
 //   warp 0      : TMA producer (one lane)
-//   warp 1      : TMEM allocator + MMA issuer (one lane)
+//   warp 1      : TMEM allocator + MMA issuer (one lane issues, the warp
+//                 synchronises)
 //   warps 2..17 : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
 //                 columns 32*((w-2)/4)..+31
+//   warp 18     : watcher: performs every mbarrier wait of the MMA issuer
+//                 (stage landed, accumulator buffers drained) and hands each
+//                 k-block to warp 1 through a named barrier, one per stage.
+// The MMA issuer itself never waits on shared memory inside its loop: while
+// the tensor cores stream operands from shared memory, a shared-memory read
+// whose result the issuing thread needs stalls it for about as long as the
+// MMA queue holds work, so the tensor pipe idled ~200 clocks per k-block
+// (measured: 64 -> 80 clocks per 128x128x16 MMA with one mbarrier test per
+// 12 MMAs); a named-barrier sync costs under one clock per MMA.
+// Named-barrier use cannot deadlock or skew: the MMA warp and the watcher both
+// run the CTA's whole tile / k-block sequence (after an abort the MMA warp
+// still synchronises and commits each k-block, issuing no MMAs); the
+// watcher's arrival for a stage's use u comes after the MMA warp passed its
+// sync for use u - 1: normally because the stage is refilled only after the
+// MMAs that read it completed (full implies empty), and after an abort
+// because the watcher then waits for that commit on the stage's empty
+// barrier itself.  Every wait of the watcher is bounded.
 // Every wait is bounded (2 s, or the context's wait limit); on expiry the
 // kernel records a status word, lets its in-flight copies and MMAs land
 // (those final drains always allow 2 s), frees TMEM and returns.
@@ -56,8 +74,11 @@ constexpr int STAGE_B = 3 * PIECE_B;
 constexpr int STAGE_BYTES = STAGE_A + STAGE_B;   // 48 KB
 constexpr int TMEM_COLS = 512;                   // D1 x2, X x2 (128 columns each)
 constexpr int NEPI = 16;                         // epilogue warps (4 per TMEM lane quadrant)
-constexpr int NTHREADS = 64 + 32 * NEPI;
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256;
+constexpr int kWatchWarp = 2 + NEPI;             // waits on the MMA issuer's barriers for it
+constexpr int NTHREADS = 64 + 32 * NEPI + 32;
+constexpr int kStageBar = 1;                     // named barriers kStageBar + s hand stage s to the MMA warp
+constexpr int kMaxDots = 24;                     // fused dot products: basis vectors + 1 (sum of squares)
+constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256 + NEPI * kMaxDots * 8;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 constexpr int COLS_PER_WARP = TBN / (NEPI / 4);  // columns drained by one epilogue warp
 
@@ -76,12 +97,21 @@ static_assert(alignof(GemmProblem) >= 64 && sizeof(GemmProblem) % 64 == 0, "tens
 
 struct GemmParams {
   const GemmProblem* table;   // grouped launches only
+  const int2* tile_map;       // grouped launches: per tile {problem index, k-blocks} (one load per tile)
   int nprob, num_tiles;
   int raster;                 // 0: m-fastest tile order; G > 0: groups of G m-blocks, n-fastest inside
   int kb_d1, kb_x;            // k-blocks per D1 drain / per X drain (kb_x % kb_d1 == 0)
   int products;
   int* status;
   uint64_t wait_ns;           // limit of every wait on work in flight (the final drains keep WAIT_LIMIT_NS)
+  // fused dot products (DOTS; one FP64 problem stored row-major, C[m*N + n]): the
+  // epilogue also forms <V_i, C> (i < dot_nv, V_i = dot_V + i*dot_ldv, same flat
+  // layout as C) and <C, C> over the tiles it stores; CTA b writes its partial
+  // sums to dot_part[i*dot_stride + b] (i = dot_nv for <C, C>)
+  const double* dot_V;
+  int64_t dot_ldv;
+  int dot_nv, dot_stride;
+  double* dot_part;
 };
 
 // Local tile index -> (m-block, n-block).  With raster G > 0, consecutive
@@ -104,13 +134,14 @@ __device__ __forceinline__ void tile_coords(int lt, int num_m, int num_n, int ra
 template <bool G>
 __device__ __forceinline__ const GemmProblem* find_problem(int tile, const GemmProblem* single, const GemmParams& p) {
   if (!G) return single;
-  int lo = 0, hi = p.nprob - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (p.table[mid].tile_begin <= tile) lo = mid;
-    else hi = mid - 1;
-  }
-  return &p.table[lo];
+  return &p.table[__ldg(&p.tile_map[tile].x)];
+}
+
+// k-blocks of a tile (the MMA issuer and the watcher need nothing else)
+template <bool G>
+__device__ __forceinline__ int tile_kblocks(int tile, const GemmProblem* single, const GemmParams& p) {
+  if (!G) return single->num_kb;
+  return __ldg(&p.tile_map[tile].y);
 }
 
 // Error-free sum in FP32: s + e == a + b exactly (Knuth TwoSum).
@@ -119,6 +150,13 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   const float bp = __fsub_rn(s, a);
   const float ap = __fsub_rn(s, bp);
   e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+__device__ __forceinline__ void named_bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void named_bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
 // Wait for one accumulation unit, fold its 32-lane x COLS_PER_WARP slice into
@@ -155,9 +193,10 @@ __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, u
   return true;
 }
 
-template <bool G, int NPROD>
+template <bool G, int NPROD, bool DOTS>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_split_bf16_gemm(const __grid_constant__ GemmProblem single, const GemmParams p) {
+  static_assert(!(G && DOTS), "fused dot products are for single (non-grouped) FP64 problems");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
@@ -169,6 +208,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* done = xe + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  double* dacc = (double*)(smem + NSTAGE * STAGE_BYTES + 256);   // [NEPI][kMaxDots] per-warp dot sums
+  if (DOTS)
+    for (int i = threadIdx.x; i < NEPI * kMaxDots; i += blockDim.x) dacc[i] = 0.0;
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
@@ -240,46 +282,35 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    if (lane == 0) {
-      const uint32_t idesc = ptx::idesc_bf16_f32(TBM, TBN);
-      // descriptors are built once; a stage, a piece or a 16-deep k-step only
-      // adds a constant to the start-address field (address >> 4)
-      const uint64_t desc0 = ptx::smem_desc_kmajor(ptx::smem_u32(smem), 64);
-      constexpr uint64_t kStage = STAGE_BYTES >> 4, kB = STAGE_A >> 4, kPA = PIECE_A >> 4, kPB = PIECE_B >> 4;
-      constexpr uint64_t kKs = 32 >> 4;
-      int stage = 0;
-      uint32_t phase = 0;
-      uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
-      bool ok = true;
-      for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
-        const int nkb = find_problem<G>(tile, &single, p)->num_kb;
-        uint32_t xbuf = 0;
-        int c1 = 0, cx = 0;   // k-blocks into the current D1 / X accumulation unit
-        for (int kb = 0; kb < nkb && ok; ++kb) {
-          const bool d1_first = c1 == 0;
-          const bool x_first = cx == 0;
-          const bool d1_last = c1 + 1 == p.kb_d1 || kb + 1 == nkb;
-          const bool x_last = cx + 1 == p.kb_x || kb + 1 == nkb;
-          c1 = d1_last ? 0 : c1 + 1;
-          cx = x_last ? 0 : cx + 1;
-          const uint32_t b1 = u1 & 1;
-          if (d1_first) {
-            if (!ptx::mbar_wait_spin(ptx::smem_u32(&d1e[b1]), ((u1 >> 1) & 1) ^ 1, abort_flag, p.wait_ns)) {
-              ok = false;
-              break;
-            }
-          }
-          if (x_first) {
-            xbuf = ux & 1;
-            if (!ptx::mbar_wait_spin(ptx::smem_u32(&xe[xbuf]), ((ux >> 1) & 1) ^ 1, abort_flag, p.wait_ns)) {
-              ok = false;
-              break;
-            }
-          }
-          if (!ptx::mbar_wait_spin(ptx::smem_u32(&full[stage]), phase, abort_flag, p.wait_ns)) {
-            ok = false;
-            break;
-          }
+    const uint32_t idesc = ptx::idesc_bf16_f32(TBM, TBN);
+    // descriptors are built once; a stage, a piece or a 16-deep k-step only
+    // adds a constant to the start-address field (address >> 4)
+    const uint64_t desc0 = ptx::smem_desc_kmajor(ptx::smem_u32(smem), 64);
+    constexpr uint64_t kStage = STAGE_BYTES >> 4, kB = STAGE_A >> 4, kPA = PIECE_A >> 4, kPB = PIECE_B >> 4;
+    constexpr uint64_t kKs = 32 >> 4;
+    int stage = 0;
+    uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
+    bool live = true;          // false after an abort: keep the barrier sequence, issue nothing
+    const int kb_d1 = p.kb_d1, kb_x = p.kb_x;   // in registers: the loop reads no memory
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+      if (live && *abort_flag) live = false;   // one shared-memory read per tile
+      const int nkb = tile_kblocks<G>(tile, &single, p);
+      uint32_t xbuf = 0;
+      int c1 = 0, cx = 0;   // k-blocks into the current D1 / X accumulation unit
+      for (int kb = 0; kb < nkb; ++kb) {
+        const bool d1_first = c1 == 0;
+        const bool x_first = cx == 0;
+        const bool d1_last = c1 + 1 == kb_d1 || kb + 1 == nkb;
+        const bool x_last = cx + 1 == kb_x || kb + 1 == nkb;
+        c1 = d1_last ? 0 : c1 + 1;
+        cx = x_last ? 0 : cx + 1;
+        const uint32_t b1 = u1 & 1;
+        if (x_first) xbuf = ux & 1;
+        // the watcher saw this stage land (and, at a unit start, the buffers drained)
+        named_bar_sync(kStageBar + stage, 64);
+        if (lane == 0 && !live) {
+          ptx::mma_commit(ptx::smem_u32(&empty[stage]));   // the watcher's abort path waits on it
+        } else if (lane == 0) {
           ptx::tc_fence_after();
           const uint64_t a = desc0 + (uint64_t)stage * kStage;
           const uint64_t b = a + kB;
@@ -306,25 +337,66 @@ __global__ void __launch_bounds__(NTHREADS, 1)
             }
           }
           ptx::mma_commit(ptx::smem_u32(&empty[stage]));
-          if (++stage == NSTAGE) {
-            stage = 0;
-            phase ^= 1;
-          }
-          if (d1_last) {
-            ptx::mma_commit(ptx::smem_u32(&d1f[b1]));
-            ++u1;
-          }
-          if (x_last) {
-            ptx::mma_commit(ptx::smem_u32(&xf[xbuf]));
-            ++ux;
-          }
+          if (d1_last) ptx::mma_commit(ptx::smem_u32(&d1f[b1]));
+          if (x_last) ptx::mma_commit(ptx::smem_u32(&xf[xbuf]));
         }
+        if (d1_last) ++u1;
+        if (x_last) ++ux;
+        if (++stage == NSTAGE) stage = 0;
       }
+    }
+    if (lane == 0) {
       // all issued MMAs complete before TMEM is released
       ptx::mma_commit(ptx::smem_u32(done));
       uint64_t t0 = ptx::globaltimer();
       while (!ptx::mbar_try_wait(ptx::smem_u32(done), 0))
         if (ptx::globaltimer() - t0 > WAIT_LIMIT_NS) break;
+    }
+    __syncwarp();
+  } else if (warp == kWatchWarp) {
+    // ------------------------------------------------------------ watcher
+    // Same tile / k-block / unit sequence as the MMA warp, run to its end: lane 0
+    // waits (bounded) for each k-block's stage, and at a unit start for the
+    // accumulator buffer it reuses; then the warp arrives on the stage's barrier.
+    // After a failed wait (abort) it keeps arriving without waiting.
+    int stage = 0;
+    uint32_t phase = 0;
+    uint32_t u1 = 0, ux = 0;
+    int use = 0;   // k-blocks seen so far (use of the current stage = use / NSTAGE)
+    bool ok = true;
+    for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
+      const int nkb = tile_kblocks<G>(tile, &single, p);
+      int c1 = 0, cx = 0;
+      for (int kb = 0; kb < nkb; ++kb, ++use) {
+        const bool d1_first = c1 == 0;
+        const bool x_first = cx == 0;
+        const bool d1_last = c1 + 1 == p.kb_d1 || kb + 1 == nkb;
+        const bool x_last = cx + 1 == p.kb_x || kb + 1 == nkb;
+        c1 = d1_last ? 0 : c1 + 1;
+        cx = x_last ? 0 : cx + 1;
+        if (lane == 0) {
+          if (ok && d1_first)
+            ok = ptx::mbar_wait_spin(ptx::smem_u32(&d1e[u1 & 1]), ((u1 >> 1) & 1) ^ 1, abort_flag, p.wait_ns);
+          if (ok && x_first)
+            ok = ptx::mbar_wait_spin(ptx::smem_u32(&xe[ux & 1]), ((ux >> 1) & 1) ^ 1, abort_flag, p.wait_ns);
+          if (ok) ok = ptx::mbar_wait_spin(ptx::smem_u32(&full[stage]), phase, abort_flag, p.wait_ns);
+          if (!ok && use >= NSTAGE) {
+            // abort: arrive only once the MMA warp committed this stage's previous use
+            // (it has passed that sync; the commit lands when the tensor cores finish)
+            const uint64_t t0 = ptx::globaltimer();
+            while (!ptx::mbar_test_wait(ptx::smem_u32(&empty[stage]), phase ^ 1))
+              if (ptx::globaltimer() - t0 > WAIT_LIMIT_NS) break;
+          }
+        }
+        __syncwarp();
+        named_bar_arrive(kStageBar + stage, 64);
+        if (d1_last) ++u1;
+        if (x_last) ++ux;
+        if (++stage == NSTAGE) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
     }
   } else {
     // ------------------------------------------------------------ epilogue
@@ -336,6 +408,47 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     bool ok = true;
     float rh[COLS_PER_WARP];
     __nv_bfloat162 rl2[COLS_PER_WARP / 2];
+    // Fused dot products: the tile this warp stored last is "pending"; its work
+    // items (basis vector i, 16-column half h) run at the service points of the
+    // next tile (after each accumulator drain), so the FP64 pipe works while the
+    // tensor cores do; the last tile's items run after the loop.  Each item is
+    // one warp-wide sum added to this warp's slot: a fixed order per CTA.
+    int64_t d_off = 0;      // flat offset of this thread's 32 columns of the pending tile
+    int d_cols = 0;         // valid columns among them (0: row outside the problem)
+    int d_next = 0, d_items = 0;
+    auto d_service = [&](int upto) {
+      if (upto > d_items) upto = d_items;
+      for (; d_next < upto; ++d_next) {
+        const int i = d_next >> 1, h = d_next & 1;
+        const double* wp = (const double*)single.C + d_off + h * 16;
+        const double* vp = i < p.dot_nv ? p.dot_V + (int64_t)i * p.dot_ldv + d_off + h * 16 : wp;
+        double acc = 0.0;
+        if (d_cols >= h * 16 + 16) {
+#pragma unroll
+          for (int c = 0; c < 16; c += 2) {
+            const double2 a = *(const double2*)(wp + c), b = *(const double2*)(vp + c);
+            acc = fma(a.x, b.x, acc);
+            acc = fma(a.y, b.y, acc);
+          }
+        } else {
+          for (int c = 0; c < 16; ++c)
+            if (h * 16 + c < d_cols) acc = fma(wp[c], vp[c], acc);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) dacc[ew * kMaxDots + i] += acc;
+      }
+    };
+    // finish the pending tile, then make the tile just stored (row, first column) pending
+    auto d_push = [&](int64_t row, int64_t n0, int64_t PM, int64_t PN, int64_t scm, int nkb) {
+      d_service(d_items);
+      d_off = row * scm + n0;
+      d_cols = row < PM ? (int)max((int64_t)0, min((int64_t)COLS_PER_WARP, PN - n0)) : 0;
+      d_next = 0;
+      d_items = 2 * (p.dot_nv + 1);
+      (void)nkb;
+    };
+    int d_quota = 1;        // items per service point while the next tile drains
     for (int tile = blockIdx.x; tile < num_tiles && ok; tile += gridDim.x) {
       const GemmProblem* pr = find_problem<G>(tile, &single, p);
       const int lt = tile - pr->tile_begin;
@@ -425,6 +538,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         ++u1;
         ++ux;
+        if (DOTS) d_push(row, n0, PM, PN, scm, nkb);
         continue;
       }
 #pragma unroll
@@ -441,6 +555,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ok = drain_unit(tmem + lane_base + (u1 & 1) * TBN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
                           abort_flag, p.wait_ns, lane, rh, rl2);
           ++u1;
+          if (DOTS && ok) d_service(d_next + d_quota);
         }
         if (ok && x_last) {
           ok = drain_unit(tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0, &xf[ux & 1], &xe[ux & 1], (ux >> 1) & 1,
@@ -503,10 +618,24 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
       }
+      if (DOTS) {
+        d_push(row, n0, PM, PN, scm, nkb);
+        const int ndr = (nkb + p.kb_d1 - 1) / p.kb_d1;   // service points of the next tile (same K)
+        d_quota = (d_items + ndr - 1) / ndr;
+      }
     }
+    if (DOTS) d_service(d_items);
   }
   __syncthreads();
   if (threadIdx.x == 0 && *abort_flag) atomicExch(p.status, 1);
+  if (DOTS && warp == 2) {
+    // this CTA's partial sums, warps in order
+    for (int i = lane; i <= p.dot_nv; i += 32) {
+      double sum = 0.0;
+      for (int e = 0; e < NEPI; ++e) sum += dacc[e * kMaxDots + i];
+      p.dot_part[(int64_t)i * p.dot_stride + blockIdx.x] = sum;
+    }
+  }
   if (warp == 1) {
     __syncwarp();
     ptx::tc_fence_after();
@@ -578,10 +707,12 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
   if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
   static bool attr_set = false;
   if (!attr_set) {
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr_set = true;
   }
   gp->kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
@@ -614,16 +745,51 @@ tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_
   gp.num_tiles = pr.num_m * pr.num_n;
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
   if (products == 6)
-    k_split_bf16_gemm<false, 6><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 6, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
   else
-    k_split_bf16_gemm<false, 3><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 3, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
   TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
+// The same GEMM (one problem, FP64 output C[m*N + n]) with the fused dot
+// products of its output: part[i*part_stride + b] (b < *grid_out) receives CTA
+// b's partial sum of <V_i, C> for i < nv and of <C, C> for i = nv.
+tci_status tci_gemm_split_bf16_dots(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
+                                    double* C, int products, int chunk_k, int xchunk_k, int raster, const double* V,
+                                    int64_t ldv, int nv, double* part, int part_stride, int* grid_out) {
+  if (M <= 0 || N <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm dots: empty problem");
+  if (nv < 0 || nv + 1 > kMaxDots || !part || (nv > 0 && !V))
+    return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm dots: up to %d vectors", kMaxDots - 1);
+  if ((N & 1) || (ldv & 1) || ((uintptr_t)C & 15) || ((uintptr_t)V & 15))
+    return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm dots: 16-byte aligned rows required");
+  GemmProblem pr;
+  TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, 0, N, 1));
+  GemmParams gp;
+  memset(&gp, 0, sizeof gp);
+  TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
+  gp.nprob = 1;
+  gp.num_tiles = pr.num_m * pr.num_n;
+  gp.dot_V = V;
+  gp.dot_ldv = ldv;
+  gp.dot_nv = nv;
+  gp.dot_stride = part_stride;
+  gp.dot_part = part;
+  const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
+  if (grid > part_stride) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm dots: partial-sum rows too short");
+  if (products == 6)
+    k_split_bf16_gemm<false, 6, true><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+  else
+    k_split_bf16_gemm<false, 3, true><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+  TCI_CUDA(ctx, cudaGetLastError());
+  if (grid_out) *grid_out = grid;
   return TCI_OK;
 }
 
 // Grouped launch: build the device table once (plan time), launch many times.
 struct tci_split_group {
   GemmProblem* d_table = nullptr;
+  int2* d_tile_map = nullptr;
   int nprob = 0;
   int num_tiles = 0;
   int64_t flops_tc = 0;
@@ -652,15 +818,25 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
   g->nprob = (int)host.size();
   g->num_tiles = tiles;
   if (g->nprob > 0) {
+    std::vector<int2> map;
+    map.reserve(tiles);
+    for (int i = 0; i < g->nprob; ++i)
+      for (int t = 0; t < host[i].num_m * host[i].num_n; ++t) map.push_back(make_int2(i, host[i].num_kb));
     tci_status s = tci_dev_alloc(ctx, sizeof(GemmProblem) * host.size(), (void**)&g->d_table);
+    if (s == TCI_OK) s = tci_dev_alloc(ctx, sizeof(int2) * map.size(), (void**)&g->d_tile_map);
     if (s != TCI_OK) {
+      tci_dev_free(g->d_table);
       delete g;
       return s;
     }
     cudaError_t e = cudaMemcpyAsync(g->d_table, host.data(), sizeof(GemmProblem) * host.size(),
                                    cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(g->d_tile_map, map.data(), sizeof(int2) * map.size(), cudaMemcpyHostToDevice, ctx->stream);
+    // (copies from pageable host memory have read their source when the call returns)
     if (e != cudaSuccess) {
       tci_dev_free(g->d_table);
+      tci_dev_free(g->d_tile_map);
       delete g;
       return tci_cuda_fail(ctx, e, "split group table upload");
     }
@@ -672,6 +848,7 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
 void tci_split_group_destroy(tci_split_group* g) {
   if (!g) return;
   tci_dev_free(g->d_table);
+  tci_dev_free(g->d_tile_map);
   delete g;
 }
 
@@ -682,15 +859,16 @@ tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int
   memset(&gp, 0, sizeof gp);
   TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
   gp.table = g->d_table;
+  gp.tile_map = g->d_tile_map;
   gp.nprob = g->nprob;
   gp.num_tiles = g->num_tiles;
   GemmProblem dummy;
   memset(&dummy, 0, sizeof dummy);
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
   if (products == 6)
-    k_split_bf16_gemm<true, 6><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
+    k_split_bf16_gemm<true, 6, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
   else
-    k_split_bf16_gemm<true, 3><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
+    k_split_bf16_gemm<true, 3, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }

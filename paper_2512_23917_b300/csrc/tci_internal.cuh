@@ -169,6 +169,14 @@ tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_
                                    int out_mode, int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k,
                                    int raster);
 
+// The same on one problem with FP64 output C[m*N + n], also forming the dot
+// products of the output with nv vectors V_i = V + i*ldv (same flat layout)
+// and its sum of squares in the epilogue: part[i*part_stride + b] receives CTA
+// b's partial sum (i = nv: <C, C>); *grid_out = the CTA count (<= part_stride).
+tci_status tci_gemm_split_bf16_dots(tci_context ctx, int64_t M, int64_t N, int64_t Kp, const void* Ap, const void* Bp,
+                                    double* C, int products, int chunk_k, int xchunk_k, int raster, const double* V,
+                                    int64_t ldv, int nv, double* part, int part_stride, int* grid_out);
+
 // Configuration of the split GEMM chosen by the autotuner (or defaults).
 struct tci_gemm_cfg {
   int chunk_k = 256;

@@ -240,3 +240,31 @@ def test_lanczos_reduced_terms_equal_fp64_terms(ctx, tci, precision, chi):
     np.testing.assert_allclose(r1["beta"], r0["beta"], rtol=1e-11)
     assert abs(r1["theta"] - r0["theta"]) < 1e-12 * abs(r0["theta"])
     assert np.linalg.norm(x1 - x.cpu().numpy()) < 1e-9
+
+
+@pytest.mark.parametrize("chi,chi_r", [(64, 64), (75, 61), (200, 131)])
+def test_lanczos_fused_dots_equal_separate_pass(ctx, tci, chi, chi_r):
+    """Split-BF16 plan, FP64 vectors: the first projection's dots formed in the matvec's GEMM2
+    epilogue (opt-in) give alpha, beta, theta and the Ritz vector of the separate dot pass up to
+    FP64 summation order; ragged shapes exercise partial tiles and partial column groups."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(chi, seed=21, chi_r=chi_r)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    plan.set_lanczos_fused_dots(True)
+    dpsi = to_dev(psi)
+    x = torch.empty_like(dpsi)
+    r1 = plan.lanczos(dpsi, 20, True, x)
+    x1 = x.cpu().numpy()
+    r1b = plan.lanczos(dpsi, 20, True, x)          # captured into a graph and launched
+    assert r1b["theta"] == r1["theta"]
+    plan.set_lanczos_fused_dots(False)
+    r0 = plan.lanczos(dpsi, 20, True, x)
+    assert r0["steps"] == r1["steps"] == 20
+    np.testing.assert_allclose(r1["alpha"], r0["alpha"], rtol=1e-12, atol=1e-12 * np.abs(r0["alpha"]).max())
+    np.testing.assert_allclose(r1["beta"], r0["beta"], rtol=1e-11)
+    assert abs(r1["theta"] - r0["theta"]) < 1e-12 * abs(r0["theta"])
+    assert np.linalg.norm(x1 - x.cpu().numpy()) < 1e-9
+    # and the solve is the FP64 oracle's to the split matvec's error level
+    mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
+    o = o_lanczos.lanczos(mv, psi, 20)
+    assert abs(r1["theta"] - o["theta"]) < 1e-6 * abs(o["theta"])
