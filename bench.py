@@ -238,7 +238,7 @@ def measure_blocksparse(tci, ctx, dev, peaks, with_oracle: bool):
            "gflops": plan.flops / (ms * 1e-3) / 1e9, "ms_per_matvec": ms, "algorithmic_flops": plan.flops,
            "stage_ms": {"split": float(stg[0]), "gemm1_grouped": float(stg[1]), "ww": float(stg[2]),
                         "gemm2_grouped": float(stg[3])},
-           "launches_per_matvec": 4, "autotune": list(tuned), "cuda_graph": True,
+           "launches_per_matvec": 4, "autotune": list(tuned), "tile_n": plan.tile_n, "cuda_graph": True,
            "roofline": {"bound": "tensor", "kernel": "k_split_bf16_gemm<grouped>", "achieved": ach,
                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
                         "flops_per_launch_pair": plan.tensor_flops}}
@@ -287,7 +287,8 @@ def measure_tebd(tci, ctx, dev, peaks, with_oracle: bool):
     res = {"workload": "batched TEBD theta, 256 bonds, chi ~ U{16..512}, d=2, complex64, 3M split-BF16",
            "gflops": plan.flops / (ms * 1e-3) / 1e9, "ms_per_batch": ms, "algorithmic_flops": plan.flops,
            "stage_ms": {"split": float(stg[0]), "gemm_grouped": float(stg[1]), "gate": float(stg[2])},
-           "launches_per_batch": 3, "io_bytes": io_bytes, "autotune": list(tuned), "cuda_graph": True,
+           "launches_per_batch": 3, "io_bytes": io_bytes, "autotune": list(tuned), "tile_n": plan.tile_n,
+           "cuda_graph": True,
            "roofline": {"bound": "tensor", "kernel": "k_split_bf16_gemm<grouped>", "achieved": ach,
                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
                         "flops_per_launch": plan.tensor_flops}}

@@ -662,9 +662,22 @@ tci_status tci_heff_autotune(tci_heff_plan plan, tci_tensor psi, tci_tensor out,
  * NULL cfg, values outside the rules above), UNSUPPORTED (FP64 plan). */
 tci_status tci_heff_get_config(tci_heff_plan plan, int* cfg);
 tci_status tci_heff_set_config(tci_heff_plan plan, const int* cfg);
+/* The same for block-sparse and TEBD plans, whose grouped launches also try
+ * the tile shape: 128 x 128 or 128 x 64 output tiles (narrow tiles carry
+ * less padding and half the MMA work on problems of few columns); the
+ * chosen width is read with tci_bs_tile_n / tci_tebd_tile_n.  chosen as
+ * above (3 ints). */
 tci_status tci_bs_autotune(tci_bs_plan plan, const float* psi, int max_chunk_k, int* chosen);
 tci_status tci_tebd_autotune(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,
                              int max_chunk_k, int* chosen);
+/* Tile width (output columns per tile, 64 or 128) of a block-sparse or TEBD
+ * plan's grouped GEMMs: set it (a captured graph is dropped and re-captured
+ * by the next apply) or read it (-1 for an invalid plan).  Set errors:
+ * INVALID_ARG (invalid plan, width not 64 or 128), INVALID_CONTEXT. */
+tci_status tci_bs_set_tile_n(tci_bs_plan plan, int bn);
+int tci_bs_tile_n(tci_bs_plan plan);
+tci_status tci_tebd_set_tile_n(tci_tebd_plan plan, int bn);
+int tci_tebd_tile_n(tci_tebd_plan plan);
 
 #ifdef __cplusplus
 }

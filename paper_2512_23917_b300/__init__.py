@@ -103,6 +103,10 @@ SIGNATURES = [
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
     ("tci_heff_lanczos_graph_info", C.c_int, [_p, _i64p]),
     ("tci_heff_set_lanczos_fused_dots", C.c_int, [_p, C.c_int]),
+    ("tci_bs_set_tile_n", C.c_int, [_p, C.c_int]),
+    ("tci_bs_tile_n", C.c_int, [_p]),
+    ("tci_tebd_set_tile_n", C.c_int, [_p, C.c_int]),
+    ("tci_tebd_tile_n", C.c_int, [_p]),
     ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
     ("tci_heff_plan_reload", C.c_int, [_p, _p, _p, _p, _p]),
     ("tci_heff_set_lanczos_arith", C.c_int, [_p, C.c_int]),
@@ -700,9 +704,17 @@ class BsHeffPlan:
         return lib.tci_bs_tensor_flops(self.handle)
 
     def autotune(self, psi_packed, max_chunk_k: int = 256):
+        """Tune the grouped GEMMs; returns (chunk_k, xchunk_k, raster); the tile width is tile_n."""
         ch = (C.c_int * 3)()
         _check(lib.tci_bs_autotune(self.handle, _p(psi_packed.data_ptr()), int(max_chunk_k), ch), self.ctx.handle)
         return tuple(ch)
+
+    @property
+    def tile_n(self) -> int:
+        return lib.tci_bs_tile_n(self.handle)
+
+    def set_tile_n(self, bn: int):
+        _check(lib.tci_bs_set_tile_n(self.handle, int(bn)), self.ctx.handle)
 
     def apply_timed(self, psi_packed, out_packed):
         ms = (C.c_float * 4)()
@@ -761,6 +773,13 @@ class TebdPlan:
     @property
     def tensor_flops(self) -> float:
         return lib.tci_tebd_tensor_flops(self.handle)
+
+    @property
+    def tile_n(self) -> int:
+        return lib.tci_tebd_tile_n(self.handle)
+
+    def set_tile_n(self, bn: int):
+        _check(lib.tci_tebd_set_tile_n(self.handle, int(bn)), self.ctx.handle)
 
     def autotune(self, A_packed, B_packed, G_packed, theta_packed, max_chunk_k: int = 256):
         ch = (C.c_int * 3)()

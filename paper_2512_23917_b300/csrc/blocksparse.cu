@@ -220,8 +220,11 @@ struct tci_bs_plan_s {
   int n_tiles = 0;
   int n_psi_jobs = 0, n_tasks = 0;
   int64_t max_psi_plane = 0, max_task_elems = 0;
-  tci_split_group* g1 = nullptr;
+  tci_split_group* g1 = nullptr;     // 128-wide tiles
   tci_split_group* g2 = nullptr;
+  tci_split_group* g1n = nullptr;    // 64-wide tiles (a tile shape the autotuner may choose)
+  tci_split_group* g2n = nullptr;
+  int bn = 128;
   WWCoef coef;
   int64_t n_gemm1 = 0, n_gemm2 = 0;
   double tensor_flops = 0.0;
@@ -405,7 +408,8 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     g1.push_back({A + Ppiece[k], A + S.off, dim[B.i], S.rows, S.Kp, p->U + Uoff[k], 1, S.rows, 1});
   }
   for (auto& q : g1) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
-  if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1, 128)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1n, 64)) != TCI_OK) return fail(s);
   p->n_gemm1 = (int64_t)g1.size();
   // ---------------------------------------------------------------- W.W tasks
   std::map<long, int> task_of;   // (ja, ib) -> task
@@ -484,7 +488,8 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   e = cudaMemsetAsync(p->out_stage, 0, std::max<int64_t>(psi_elems, 1) * 4, ctx->stream);
   if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan memset"));
   for (auto& q : g2) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
-  if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2, 128)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2n, 64)) != TCI_OK) return fail(s);
   p->n_gemm2 = (int64_t)g2.size();
   // psi split jobs
   p->n_psi_jobs = (int)psi_jobs.size();
@@ -545,6 +550,8 @@ extern "C" tci_status tci_bs_plan_destroy(tci_bs_plan* pp) {
   tci_graph_destroy(&p->graph);
   tci_split_group_destroy(p->g1);
   tci_split_group_destroy(p->g2);
+  tci_split_group_destroy(p->g1n);
+  tci_split_group_destroy(p->g2n);
   void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles};
   for (void* b : bufs) tci_dev_free(b);
   p->magic = 0;
@@ -571,10 +578,10 @@ static tci_status bs_launch_all(void* arg) {
     k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, p->cap_psi, (__nv_bfloat16*)p->arena);
   }
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   return TCI_OK;
 }
 
@@ -621,11 +628,11 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
     k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
   }
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
   TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));
@@ -652,6 +659,7 @@ tci_status bs_run_cfg(void* a, const tci_gemm_cfg& cfg) {
   t->p->chunk_k = cfg.chunk_k;
   t->p->xchunk_k = cfg.xchunk_k;
   t->p->raster = cfg.raster;
+  t->p->bn = cfg.bn;
   t->p->cap_psi = t->psi;
   return bs_launch_all(t->p);
 }
@@ -668,10 +676,11 @@ extern "C" tci_status tci_bs_autotune(tci_bs_plan p, const float* psi, int max_c
                           std::to_string(p->n_gemm2) + "|p" + std::to_string(p->products);
   tci_gemm_cfg best;
   double ms = 0.0;
-  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, bs_run_cfg, &arg, &best, &ms));
+  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, bs_run_cfg, &arg, &best, &ms, true));
   p->chunk_k = best.chunk_k;
   p->xchunk_k = best.xchunk_k;
   p->raster = best.raster;
+  p->bn = best.bn;
   tci_graph_destroy(&p->graph);   // the next apply captures the tuned sequence
   if (chosen) {
     chosen[0] = best.chunk_k;
@@ -679,4 +688,21 @@ extern "C" tci_status tci_bs_autotune(tci_bs_plan p, const float* psi, int max_c
     chosen[2] = best.raster;
   }
   return tci_synchronize(ctx);
+}
+
+extern "C" tci_status tci_bs_set_tile_n(tci_bs_plan p, int bn) {
+  if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_set_tile_n: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (bn != 64 && bn != 128) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "bs_set_tile_n: tile width 64 or 128");
+  if (bn != p->bn) {
+    cudaStreamSynchronize(p->ctx->stream);
+    tci_graph_destroy(&p->graph);   // the next apply captures the new sequence
+    p->bn = bn;
+  }
+  return TCI_OK;
+}
+
+extern "C" int tci_bs_tile_n(tci_bs_plan p) {
+  if (!p || p->magic != kBsMagic) return -1;
+  return p->bn;
 }

@@ -78,9 +78,22 @@ constexpr int kWatchWarp = 2 + NEPI;             // waits on the MMA issuer's ba
 constexpr int NTHREADS = 64 + 32 * NEPI + 32;
 constexpr int kStageBar = 1;                     // named barriers kStageBar + s hand stage s to the MMA warp
 constexpr int kMaxDots = 24;                     // fused dot products: basis vectors + 1 (sum of squares)
-constexpr int SMEM_BYTES = NSTAGE * STAGE_BYTES + 1024 + 256 + NEPI * kMaxDots * 8;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 constexpr int COLS_PER_WARP = TBN / (NEPI / 4);  // columns drained by one epilogue warp
+
+// Tile width BN of a launch: 128 (every launch) or 64 (grouped launches of
+// narrow problems, a tile shape the autotuner may choose).  The accumulators
+// take 4 x BN tensor-memory columns (D1 and X, each double-buffered).
+template <int BN>
+struct TileN {
+  static_assert(BN == 64 || BN == 128, "tile width 64 or 128");
+  static constexpr int kPieceB = BN * TBK * 2;
+  static constexpr int kStageB = 3 * kPieceB;
+  static constexpr int kStageBytes = STAGE_A + kStageB;
+  static constexpr int kTmemCols = 4 * BN;
+  static constexpr int kCols = BN / (NEPI / 4);
+  static constexpr int kSmem = NSTAGE * kStageBytes + 1024 + 256 + NEPI * kMaxDots * 8;
+};
 
 // One GEMM of a (possibly grouped) launch.  In a grouped launch the table
 // lives in device memory, sorted by decreasing K so the longest tiles are
@@ -164,16 +177,17 @@ __device__ __forceinline__ void named_bar_arrive(int id, int count) {
 // compensation rl (|rl| <~ 2^-24 |rh| per drain) is kept as packed bfloat16:
 // rounding it to 8 bits costs ~2^-33 |rh| per drain, far below the target,
 // and halves its register footprint.
+template <int COLS>
 __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, uint64_t* empty_bar, uint32_t parity,
                                            volatile int* abort_flag, uint64_t wait_ns, int lane,
-                                           float (&rh)[COLS_PER_WARP], __nv_bfloat162 (&rl)[COLS_PER_WARP / 2]) {
+                                           float (&rh)[COLS], __nv_bfloat162 (&rl)[COLS / 2]) {
   // the lanes agree before the warp-collective tensor-memory loads: a wait
   // that expired in any lane aborts the whole warp
   const bool got = ptx::mbar_wait_bounded(ptx::smem_u32(full_bar), parity, abort_flag, wait_ns);
   if (!__all_sync(0xffffffffu, got)) return false;
   ptx::tc_fence_after();
 #pragma unroll
-  for (int g = 0; g < COLS_PER_WARP / 16; ++g) {
+  for (int g = 0; g < COLS / 16; ++g) {
     uint32_t v[16];
     ptx::tmem_ld_32x32b_x16(taddr + g * 16, v);
     ptx::tmem_ld_wait();
@@ -193,13 +207,15 @@ __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, u
   return true;
 }
 
-template <bool G, int NPROD, bool DOTS>
+template <bool G, int NPROD, bool DOTS, int BN>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_split_bf16_gemm(const __grid_constant__ GemmProblem single, const GemmParams p) {
+  using TN = TileN<BN>;
+  static_assert(BN == TBN || G, "narrow tiles are for grouped launches");
   static_assert(!(G && DOTS), "fused dot products are for single (non-grouped) FP64 problems");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + NSTAGE * STAGE_BYTES);
+  uint64_t* full = (uint64_t*)(smem + NSTAGE * TN::kStageBytes);
   uint64_t* empty = full + NSTAGE;
   uint64_t* d1f = empty + NSTAGE;   // D1 buffer full (MMA -> epilogue)
   uint64_t* d1e = d1f + 2;          // D1 buffer empty (epilogue -> MMA)
@@ -208,7 +224,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   uint64_t* done = xe + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  double* dacc = (double*)(smem + NSTAGE * STAGE_BYTES + 256);   // [NEPI][kMaxDots] per-warp dot sums
+  double* dacc = (double*)(smem + NSTAGE * TN::kStageBytes + 256);   // [NEPI][kMaxDots] per-warp dot sums
   if (DOTS)
     for (int i = threadIdx.x; i < NEPI * kMaxDots; i += blockDim.x) dacc[i] = 0.0;
 
@@ -235,7 +251,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     ptx::tma_prefetch_desc(&single.tmB);
   }
   if (warp == 1) {
-    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TMEM_COLS);
+    ptx::tmem_alloc(ptx::smem_u32(tmem_slot), TN::kTmemCols);
     ptx::tmem_relinquish();
   }
   ptx::tc_fence_before();
@@ -260,10 +276,10 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         for (int kb = 0; kb < nkb; ++kb) {
           if (!ptx::mbar_wait_bounded(ptx::smem_u32(&empty[stage]), phase ^ 1, abort_flag, p.wait_ns)) break;
           const uint32_t fb = ptx::smem_u32(&full[stage]);
-          ptx::mbar_arrive_expect_tx(fb, STAGE_BYTES);
-          uint8_t* sa = smem + stage * STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(fb, TN::kStageBytes);
+          uint8_t* sa = smem + stage * TN::kStageBytes;
           ptx::tma_load_3d(ptx::smem_u32(sa), &pr->tmA, fb, kb * TBK, mb * TBM, 0);
-          ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &pr->tmB, fb, kb * TBK, nb * TBN, 0);
+          ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &pr->tmB, fb, kb * TBK, nb * BN, 0);
           issued |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == NSTAGE) {
@@ -282,11 +298,11 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
   } else if (warp == 1) {
     // ------------------------------------------------------------ MMA issuer
-    const uint32_t idesc = ptx::idesc_bf16_f32(TBM, TBN);
+    const uint32_t idesc = ptx::idesc_bf16_f32(TBM, BN);
     // descriptors are built once; a stage, a piece or a 16-deep k-step only
     // adds a constant to the start-address field (address >> 4)
     const uint64_t desc0 = ptx::smem_desc_kmajor(ptx::smem_u32(smem), 64);
-    constexpr uint64_t kStage = STAGE_BYTES >> 4, kB = STAGE_A >> 4, kPA = PIECE_A >> 4, kPB = PIECE_B >> 4;
+    constexpr uint64_t kStage = TN::kStageBytes >> 4, kB = STAGE_A >> 4, kPA = PIECE_A >> 4, kPB = TN::kPieceB >> 4;
     constexpr uint64_t kKs = 32 >> 4;
     int stage = 0;
     uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
@@ -314,8 +330,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ptx::tc_fence_after();
           const uint64_t a = desc0 + (uint64_t)stage * kStage;
           const uint64_t b = a + kB;
-          const uint32_t dD1 = tmem + b1 * TBN;
-          const uint32_t dX = tmem + 2 * TBN + xbuf * TBN;
+          const uint32_t dD1 = tmem + b1 * BN;
+          const uint32_t dX = tmem + 2 * BN + xbuf * BN;
           const uint32_t acc1 = d1_first ? 0u : 1u, accx = x_first ? 0u : 1u;
           // per 16-deep k-step: hi*hi into D1, cross products (A_i, B_j) with i + j in {1, 2}
           // into X, ordered by A piece so each A piece is read from shared memory once
@@ -402,12 +418,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ epilogue
     const int ew = warp - 2;                    // 0..NEPI-1
     const int qd = warp & 3;                    // TMEM lane quadrant of this warp
-    const int c0 = (ew >> 2) * COLS_PER_WARP;   // first column of this warp
+    const int c0 = (ew >> 2) * TN::kCols;   // first column of this warp
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
     uint32_t u1 = 0, ux = 0;
     bool ok = true;
-    float rh[COLS_PER_WARP];
-    __nv_bfloat162 rl2[COLS_PER_WARP / 2];
+    float rh[TN::kCols];
+    __nv_bfloat162 rl2[TN::kCols / 2];
     // Fused dot products: the tile this warp stored last is "pending"; its work
     // items (basis vector i, 16-column half h) run at the service points of the
     // next tile (after each accumulator drain), so the FP64 pipe works while the
@@ -443,7 +459,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     auto d_push = [&](int64_t row, int64_t n0, int64_t PM, int64_t PN, int64_t scm, int nkb) {
       d_service(d_items);
       d_off = row * scm + n0;
-      d_cols = row < PM ? (int)max((int64_t)0, min((int64_t)COLS_PER_WARP, PN - n0)) : 0;
+      d_cols = row < PM ? (int)max((int64_t)0, min((int64_t)TN::kCols, PN - n0)) : 0;
       d_next = 0;
       d_items = 2 * (p.dot_nv + 1);
       (void)nkb;
@@ -470,12 +486,12 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           break;
         }
         ptx::tc_fence_after();
-        const uint32_t td = tmem + lane_base + (u1 & 1) * TBN + c0;
-        const uint32_t tx = tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0;
+        const uint32_t td = tmem + lane_base + (u1 & 1) * BN + c0;
+        const uint32_t tx = tmem + lane_base + 2 * BN + (ux & 1) * BN + c0;
         const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
-        const int64_t n0 = (int64_t)nb * TBN + c0;
+        const int64_t n0 = (int64_t)nb * BN + c0;
 #pragma unroll
-        for (int g = 0; g < COLS_PER_WARP / 16; ++g) {
+        for (int g = 0; g < TN::kCols / 16; ++g) {
           uint32_t vd[16], vx[16];
           ptx::tmem_ld_32x32b_x16(td + g * 16, vd);
           ptx::tmem_ld_32x32b_x16(tx + g * 16, vx);
@@ -542,9 +558,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         continue;
       }
 #pragma unroll
-      for (int j = 0; j < COLS_PER_WARP; ++j) rh[j] = 0.f;
+      for (int j = 0; j < TN::kCols; ++j) rh[j] = 0.f;
 #pragma unroll
-      for (int j = 0; j < COLS_PER_WARP / 2; ++j) rl2[j] = __floats2bfloat162_rn(0.f, 0.f);
+      for (int j = 0; j < TN::kCols / 2; ++j) rl2[j] = __floats2bfloat162_rn(0.f, 0.f);
       int c1 = 0, cx = 0;
       for (int kb = 0; kb < nkb; ++kb) {
         const bool d1_last = c1 + 1 == p.kb_d1 || kb + 1 == nkb;
@@ -552,13 +568,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         c1 = d1_last ? 0 : c1 + 1;
         cx = x_last ? 0 : cx + 1;
         if (d1_last) {
-          ok = drain_unit(tmem + lane_base + (u1 & 1) * TBN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
+          ok = drain_unit(tmem + lane_base + (u1 & 1) * BN + c0, &d1f[u1 & 1], &d1e[u1 & 1], (u1 >> 1) & 1,
                           abort_flag, p.wait_ns, lane, rh, rl2);
           ++u1;
           if (DOTS && ok) d_service(d_next + d_quota);
         }
         if (ok && x_last) {
-          ok = drain_unit(tmem + lane_base + 2 * TBN + (ux & 1) * TBN + c0, &xf[ux & 1], &xe[ux & 1], (ux >> 1) & 1,
+          ok = drain_unit(tmem + lane_base + 2 * BN + (ux & 1) * BN + c0, &xf[ux & 1], &xe[ux & 1], (ux >> 1) & 1,
                           abort_flag, p.wait_ns, lane, rh, rl2);
           ++ux;
         }
@@ -567,13 +583,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (!ok) break;
       // store the tile (one rounding of hi + lo)
       const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
-      const int64_t n0 = (int64_t)nb * TBN + c0;
+      const int64_t n0 = (int64_t)nb * BN + c0;
       if (row < PM) {
         if (out_mode == 1) {
           float* crow = (float*)PC + row * scm;
-          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + TN::kCols <= PN;
 #pragma unroll
-          for (int j = 0; j < COLS_PER_WARP; j += 4) {
+          for (int j = 0; j < TN::kCols; j += 4) {
             const float2 c01 = __bfloat1622float2(rl2[j / 2]);
             const float2 c23 = __bfloat1622float2(rl2[j / 2 + 1]);
             const float4 o = make_float4(rh[j] + c01.x, rh[j + 1] + c01.y, rh[j + 2] + c23.x, rh[j + 3] + c23.y);
@@ -588,9 +604,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         } else if (out_mode == 2) {
           float2* crow = (float2*)PC + row * scm;
-          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + TN::kCols <= PN;
 #pragma unroll
-          for (int j = 0; j < COLS_PER_WARP; j += 2) {
+          for (int j = 0; j < TN::kCols; j += 2) {
             const float2 c = __bfloat1622float2(rl2[j / 2]);
             float4 o;
             two_sum(rh[j], c.x, o.x, o.y);
@@ -604,9 +620,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         } else {
           double* crow = (double*)PC + row * scm;
-          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + COLS_PER_WARP <= PN;
+          const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + TN::kCols <= PN;
 #pragma unroll
-          for (int j = 0; j < COLS_PER_WARP; j += 2) {
+          for (int j = 0; j < TN::kCols; j += 2) {
             const float2 c = __bfloat1622float2(rl2[j / 2]);
             const double2 o = make_double2((double)rh[j] + (double)c.x, (double)rh[j + 1] + (double)c.y);
             if (vec) {
@@ -639,7 +655,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   if (warp == 1) {
     __syncwarp();
     ptx::tc_fence_after();
-    ptx::tmem_dealloc(tmem, TMEM_COLS);
+    ptx::tmem_dealloc(tmem, TN::kTmemCols);
   }
 }
 
@@ -684,13 +700,13 @@ tci_status tci_make_piece_map(tci_context ctx, CUtensorMap* map, const void* bas
 
 static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int64_t N, int64_t Kp, const void* Ap,
                                const void* Bp, void* C, int out_mode, int64_t scm, int64_t scn,
-                               int64_t a_plane_rows = 0, int64_t b_plane_rows = 0) {
+                               int64_t a_plane_rows = 0, int64_t b_plane_rows = 0, int bn = TBN) {
   if (M <= 0 || N <= 0 || Kp <= 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: empty problem");
   if (M > (int64_t)INT32_MAX || N > (int64_t)INT32_MAX || Kp > (int64_t)INT32_MAX)
     return tci_fail(ctx, TCI_ERR_UNSUPPORTED, "split gemm: dimension exceeds 2^31");
   memset(pr, 0, sizeof(*pr));
   TCI_TRY(tci_make_piece_map(ctx, &pr->tmA, Ap, M, Kp, TBM, a_plane_rows > 0 ? a_plane_rows : M));
-  TCI_TRY(tci_make_piece_map(ctx, &pr->tmB, Bp, N, Kp, TBN, b_plane_rows > 0 ? b_plane_rows : N));
+  TCI_TRY(tci_make_piece_map(ctx, &pr->tmB, Bp, N, Kp, bn, b_plane_rows > 0 ? b_plane_rows : N));
   pr->C = C;
   pr->M = M;
   pr->N = N;
@@ -698,7 +714,7 @@ static tci_status fill_problem(tci_context ctx, GemmProblem* pr, int64_t M, int6
   pr->scn = scn;
   pr->out_mode = out_mode;
   pr->num_m = (int)((M + TBM - 1) / TBM);
-  pr->num_n = (int)((N + TBN - 1) / TBN);
+  pr->num_n = (int)((N + bn - 1) / bn);
   pr->num_kb = (int)((Kp + TBK - 1) / TBK);
   return TCI_OK;
 }
@@ -707,12 +723,16 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
   if (products != 6 && products != 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: products must be 3 or 6");
   static bool attr_set = false;
   if (!attr_set) {
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    constexpr int S128 = TileN<128>::kSmem, S64 = TileN<64>::kSmem;
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, false, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, false, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 6, true, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, true, 128>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false, 64>, A, S64));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false, 64>, A, S64));
     attr_set = true;
   }
   gp->kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
@@ -745,9 +765,9 @@ tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_
   gp.num_tiles = pr.num_m * pr.num_n;
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
   if (products == 6)
-    k_split_bf16_gemm<false, 6, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 6, false, 128><<<grid, NTHREADS, TileN<128>::kSmem, ctx->stream>>>(pr, gp);
   else
-    k_split_bf16_gemm<false, 3, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 3, false, 128><<<grid, NTHREADS, TileN<128>::kSmem, ctx->stream>>>(pr, gp);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }
@@ -778,9 +798,9 @@ tci_status tci_gemm_split_bf16_dots(tci_context ctx, int64_t M, int64_t N, int64
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
   if (grid > part_stride) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm dots: partial-sum rows too short");
   if (products == 6)
-    k_split_bf16_gemm<false, 6, true><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 6, true, 128><<<grid, NTHREADS, TileN<128>::kSmem, ctx->stream>>>(pr, gp);
   else
-    k_split_bf16_gemm<false, 3, true><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(pr, gp);
+    k_split_bf16_gemm<false, 3, true, 128><<<grid, NTHREADS, TileN<128>::kSmem, ctx->stream>>>(pr, gp);
   TCI_CUDA(ctx, cudaGetLastError());
   if (grid_out) *grid_out = grid;
   return TCI_OK;
@@ -790,13 +810,16 @@ tci_status tci_gemm_split_bf16_dots(tci_context ctx, int64_t M, int64_t N, int64
 struct tci_split_group {
   GemmProblem* d_table = nullptr;
   int2* d_tile_map = nullptr;
+  int bn = TBN;   // tile width of every problem of the group
   int nprob = 0;
   int num_tiles = 0;
   int64_t flops_tc = 0;
 };
 
-tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out) {
+tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out,
+                                  int bn) {
   *out = nullptr;
+  if (bn != 64 && bn != 128) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split group: tile width 64 or 128");
   std::vector<GemmProblem> host;
   host.reserve(n);
   std::vector<int> order;
@@ -809,12 +832,13 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
     const tci_split_problem& q = probs[i];
     GemmProblem pr;
     TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_mode, q.scm, q.scn, q.a_plane_rows,
-                         q.b_plane_rows));
+                         q.b_plane_rows, bn));
     pr.tile_begin = tiles;
     tiles += pr.num_m * pr.num_n;
     host.push_back(pr);
   }
   tci_split_group* g = new tci_split_group();
+  g->bn = bn;
   g->nprob = (int)host.size();
   g->num_tiles = tiles;
   if (g->nprob > 0) {
@@ -866,9 +890,11 @@ tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int
   memset(&dummy, 0, sizeof dummy);
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
   if (products == 6)
-    k_split_bf16_gemm<true, 6, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
+    (g->bn == 64 ? k_split_bf16_gemm<true, 6, false, 64> : k_split_bf16_gemm<true, 6, false, 128>)
+        <<<grid, NTHREADS, g->bn == 64 ? TileN<64>::kSmem : TileN<128>::kSmem, ctx->stream>>>(dummy, gp);
   else
-    k_split_bf16_gemm<true, 3, false><<<grid, NTHREADS, SMEM_BYTES, ctx->stream>>>(dummy, gp);
+    (g->bn == 64 ? k_split_bf16_gemm<true, 3, false, 64> : k_split_bf16_gemm<true, 3, false, 128>)
+        <<<grid, NTHREADS, g->bn == 64 ? TileN<64>::kSmem : TileN<128>::kSmem, ctx->stream>>>(dummy, gp);
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }

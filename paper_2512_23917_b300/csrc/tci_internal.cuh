@@ -182,6 +182,7 @@ struct tci_gemm_cfg {
   int chunk_k = 256;
   int xchunk_k = 1024;
   int raster = 0;
+  int bn = 128;   // tile width (grouped plans may use 64)
 };
 // Time candidate configurations with `run` (which must launch the plan's
 // work with the given configuration on ctx->stream) and return the fastest
@@ -190,7 +191,7 @@ struct tci_gemm_cfg {
 // is used without timing.  raster_candidates: whether tile order is tuned.
 tci_status tci_autotune(tci_context ctx, const std::string& key, int max_chunk_k, bool raster_candidates,
                         tci_status (*run)(void* arg, const tci_gemm_cfg& cfg), void* arg, tci_gemm_cfg* best,
-                        double* best_ms);
+                        double* best_ms, bool bn_candidates = false);
 
 // Grouped split-BF16 GEMM: all problems run in one persistent launch.
 struct tci_split_problem {
@@ -203,7 +204,9 @@ struct tci_split_problem {
   int64_t a_plane_rows = 0, b_plane_rows = 0;   // piece-plane stride in rows (0: M, N)
 };
 struct tci_split_group;
-tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out);
+// bn: tile width (128, or 64 for groups of narrow problems)
+tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out,
+                                  int bn = 128);
 void tci_split_group_destroy(tci_split_group* g);
 tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k,
                                   int raster);

@@ -115,7 +115,9 @@ struct tci_tebd_plan_s {
   void* arena = nullptr;   // bf16 pieces
   float* P = nullptr;      // P1, P2, P3 per bond
   BondJob* d_jobs = nullptr;
-  tci_split_group* group = nullptr;
+  tci_split_group* group = nullptr;    // 128-wide tiles
+  tci_split_group* group_n = nullptr;  // 64-wide tiles (a tile shape the autotuner may choose)
+  int bn = 128;
   tci_graph graph;   // captured split -> grouped GEMM -> gate
   const void *cA = nullptr, *cB = nullptr, *cG = nullptr;
   void* cT = nullptr;
@@ -127,6 +129,7 @@ extern "C" tci_status tci_tebd_plan_destroy(tci_tebd_plan* pp) {
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
   tci_graph_destroy(&p->graph);
   tci_split_group_destroy(p->group);
+  tci_split_group_destroy(p->group_n);
   tci_dev_free(p->arena);
   tci_dev_free(p->P);
   tci_dev_free(p->d_jobs);
@@ -203,7 +206,8 @@ extern "C" tci_status tci_tebd_plan_create(tci_context ctx, int nbonds, const in
     for (int q = 0; q < 3; ++q)
       probs.push_back({A + j.pa[q], A + j.pb[q], 2 * j.chi, 2 * j.chi, j.Kp, p->P + j.pc[q], 1, 2 * j.chi, 1});
   }
-  if ((s = tci_split_group_create(ctx, (int)probs.size(), probs.data(), &p->group)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)probs.size(), probs.data(), &p->group, 128)) != TCI_OK) return fail(s);
+  if ((s = tci_split_group_create(ctx, (int)probs.size(), probs.data(), &p->group_n, 64)) != TCI_OK) return fail(s);
   vs.info = "bonds=" + std::to_string(nbonds) + " max_chi=" + std::to_string(p->max_chi);
   *out = p;
   return TCI_OK;
@@ -221,7 +225,8 @@ static tci_status tebd_launch_all(void* arg) {
   dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)p->cA, (const float2*)p->cB, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
-  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->group_n : p->group, p->products, p->chunk_k, p->xchunk_k,
+                                 p->raster));
   dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)p->cG, (float2*)p->cT);
   TCI_CUDA(ctx, cudaGetLastError());
@@ -274,7 +279,8 @@ extern "C" tci_status tci_tebd_apply_timed(tci_tebd_plan p, const void* A, const
   dim3 g1((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (2 * mc * pad8(mc) + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_split<<<g1, 256, 0, ctx->stream>>>(p->d_jobs, (const float2*)A, (const float2*)B, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
-  TCI_TRY(tci_split_group_launch(ctx, p->group, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->group_n : p->group, p->products, p->chunk_k, p->xchunk_k,
+                                 p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
   dim3 g2((unsigned)std::max<int64_t>(1, std::min<int64_t>(128, (mc * mc + 255) / 256)), (unsigned)p->nbonds);
   k_tebd_gate<<<g2, 256, 0, ctx->stream>>>(p->d_jobs, p->P, (const float2*)G, (float2*)theta);
@@ -299,6 +305,7 @@ tci_status tebd_run_cfg(void* a, const tci_gemm_cfg& cfg) {
   p->chunk_k = cfg.chunk_k;
   p->xchunk_k = cfg.xchunk_k;
   p->raster = cfg.raster;
+  p->bn = cfg.bn;
   return tebd_launch_all(p);
 }
 }  // namespace
@@ -318,10 +325,11 @@ extern "C" tci_status tci_tebd_autotune(tci_tebd_plan p, const void* A, const vo
                           std::to_string((long long)(p->flops / 1e6)) + "|p" + std::to_string(p->products);
   tci_gemm_cfg best;
   double ms = 0.0;
-  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, tebd_run_cfg, p, &best, &ms));
+  TCI_TRY(tci_autotune(ctx, key, max_chunk_k, true, tebd_run_cfg, p, &best, &ms, true));
   p->chunk_k = best.chunk_k;
   p->xchunk_k = best.xchunk_k;
   p->raster = best.raster;
+  p->bn = best.bn;
   tci_graph_destroy(&p->graph);
   if (chosen) {
     chosen[0] = best.chunk_k;
@@ -400,4 +408,21 @@ extern "C" tci_status tci_tebd_theta_batched(tci_context ctx, int n, const tci_t
   for (void* q : {pa, pb, pg, pt}) tci_dev_free(q);
   tci_tebd_plan_destroy(&plan);
   return st;
+}
+
+extern "C" tci_status tci_tebd_set_tile_n(tci_tebd_plan p, int bn) {
+  if (!p || p->magic != kTebdMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "tebd_set_tile_n: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (bn != 64 && bn != 128) return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "tebd_set_tile_n: tile width 64 or 128");
+  if (bn != p->bn) {
+    cudaStreamSynchronize(p->ctx->stream);
+    tci_graph_destroy(&p->graph);   // the next apply captures the new sequence
+    p->bn = bn;
+  }
+  return TCI_OK;
+}
+
+extern "C" int tci_tebd_tile_n(tci_tebd_plan p) {
+  if (!p || p->magic != kTebdMagic) return -1;
+  return p->bn;
 }

@@ -10,7 +10,7 @@ from tci_synth import MPO_CHANNEL_CHARGE, PHYS_CHARGE, blocksparse_inputs, block
 pytestmark = pytest.mark.gpu
 
 
-def run_bs(tci, ctx, inp):
+def run_bs(tci, ctx, inp, tile_n=None):
     import torch
     dims, qmax = inp["dims"], inp["qmax"]
     st = blocksparse_structure(dims, qmax)
@@ -20,6 +20,9 @@ def run_bs(tci, ctx, inp):
     plan = tci.BsHeffPlan(ctx, charges, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE, Lp, Rp, to_dev(inp["W"]))
     psi = to_dev(tci.pack_blocks(inp["psi"], st["psi"]))
     assert plan.psi_size == psi.numel()
+    if tile_n is not None:
+        plan.set_tile_n(tile_n)
+        assert plan.tile_n == tile_n
     out = torch.full_like(psi, float("nan"))
     plan.apply(psi, out)
     torch.cuda.synchronize()
@@ -78,3 +81,35 @@ def test_blocksparse_graph_replay_with_new_buffers(ctx, tci):
         got = tci.unpack_blocks(out.cpu().numpy(), st["psi"], shapes)
         ref, _ = o_bs.bs_heff_apply(dict(inp, psi=psi_blocks))
         assert blocks_err(got, ref) < 1e-6, call
+
+
+@pytest.mark.parametrize("total,qmax,sigma,seed", [(64, 5, 2.0, 3), (97, 15, 5.0, 5), (2048, 15, 5.0, 20251223)])
+def test_blocksparse_narrow_tiles_match_oracle(ctx, tci, total, qmax, sigma, seed):
+    """The 128 x 64 tile shape (an autotuner choice) gives the oracle's blocks, including sectors
+    wider than one tile and ragged last tiles."""
+    inp = blocksparse_inputs(total=total, seed=seed, qmax=qmax, sigma=sigma)
+    got, plan, st = run_bs(tci, ctx, inp, tile_n=64)
+    ref, _ = o_bs.bs_heff_apply(inp)
+    assert blocks_err(got, ref) < 1e-6
+
+
+def test_blocksparse_autotune_chooses_a_tile_shape(ctx, tci):
+    import torch
+    inp = blocksparse_inputs(total=300, seed=4, qmax=9, sigma=3.0)
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    plan = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                          to_dev(tci.pack_blocks(inp["L"], st["L"])), to_dev(tci.pack_blocks(inp["R"], st["R"])),
+                          to_dev(inp["W"]))
+    psi = to_dev(tci.pack_blocks(inp["psi"], st["psi"]))
+    plan.autotune(psi, max_chunk_k=256)
+    assert plan.tile_n in (64, 128)
+    out = torch.full_like(psi, float("nan"))
+    plan.apply(psi, out)
+    torch.cuda.synchronize()
+    shapes = {k: (dims[k[0]], dims[k[3]]) for k in st["psi"]}
+    got = tci.unpack_blocks(out.cpu().numpy(), st["psi"], shapes)
+    ref, _ = o_bs.bs_heff_apply(inp)
+    assert blocks_err(got, ref) < 1e-6
+    with pytest.raises(tci.TciError):
+        plan.set_tile_n(96)

@@ -10,9 +10,12 @@ from tci_synth import tebd_inputs
 pytestmark = pytest.mark.gpu
 
 
-def run_tebd(tci, ctx, chis, A, B, G, precision="split_bf16"):
+def run_tebd(tci, ctx, chis, A, B, G, precision="split_bf16", tile_n=None):
     import torch
     plan = tci.TebdPlan(ctx, chis, precision=precision)
+    if tile_n is not None:
+        plan.set_tile_n(tile_n)
+        assert plan.tile_n == tile_n
     pa = to_dev(np.concatenate([a.ravel() for a in A]))
     pb = to_dev(np.concatenate([b.ravel() for b in B]))
     pg = to_dev(np.concatenate([g.ravel() for g in G]))
@@ -96,3 +99,12 @@ def test_tebd_theta_batched_on_handles(ctx, tci):
         got = t.to_numpy()
         assert got.shape == (a.shape[0], 2, 2, a.shape[0])
         assert rel_frob_err(got, o_tebd.theta(a, b, g)) < 1e-5
+
+
+@pytest.mark.parametrize("nb,lo,hi,seed", [(5, 3, 9, 1), (17, 16, 130, 2), (40, 16, 512, 20251223)])
+def test_tebd_narrow_tiles_match_oracle(ctx, tci, nb, lo, hi, seed):
+    """The 128 x 64 tile shape (an autotuner choice) gives the oracle's theta for every bond."""
+    chis, A, B, G = tebd_inputs(nb, seed=seed, chi_lo=lo, chi_hi=hi)
+    got, plan = run_tebd(tci, ctx, chis, A, B, G, tile_n=64)
+    for g_, a, b, gg in zip(got, A, B, G):
+        assert rel_frob_err(g_, o_tebd.theta(a, b, gg)) < 1e-5
