@@ -31,22 +31,27 @@
 //   warps 2..17 : epilogue; warp w reads TMEM lanes 32*(w%4)..+31 and
 //                 columns 32*((w-2)/4)..+31
 //   warp 18     : watcher: performs every mbarrier wait of the MMA issuer
-//                 (stage landed, accumulator buffers drained) and hands each
-//                 k-block to warp 1 through a named barrier, one per stage.
+//                 (stage landed, accumulator buffers drained) and hands the
+//                 k-blocks of each stage pair (0,1), (2,3) to warp 1 through a
+//                 named barrier per pair, one sync per two k-blocks.
 // The MMA issuer itself never waits on shared memory inside its loop: while
 // the tensor cores stream operands from shared memory, a shared-memory read
 // whose result the issuing thread needs stalls it for about as long as the
 // MMA queue holds work, so the tensor pipe idled ~200 clocks per k-block
 // (measured: 64 -> 80 clocks per 128x128x16 MMA with one mbarrier test per
-// 12 MMAs); a named-barrier sync costs under one clock per MMA.
+// 12 MMAs); a named-barrier sync costs far less, and one per stage pair
+// instead of one per stage took the chi = 2048 GEMM from 1.55 to 1.40 ms
+// (two pairs in flight keep the TMA latency hidden).
 // Named-barrier use cannot deadlock or skew: the MMA warp and the watcher both
 // run the CTA's whole tile / k-block sequence (after an abort the MMA warp
-// still synchronises and commits each k-block, issuing no MMAs); the
-// watcher's arrival for a stage's use u comes after the MMA warp passed its
-// sync for use u - 1: normally because the stage is refilled only after the
-// MMAs that read it completed (full implies empty), and after an abort
-// because the watcher then waits for that commit on the stage's empty
-// barrier itself.  Every wait of the watcher is bounded.
+// still synchronises and commits each k-block, issuing no MMAs), the MMA warp
+// syncing before each even stage and the watcher arriving after each odd
+// stage or after the CTA's last k-block, so the counts match; the watcher's
+// arrival for a pair's use u comes after the MMA warp passed its sync for use
+// u - 1: normally because a stage is refilled only after the MMAs that read it
+// completed (full implies empty), and after an abort because the watcher then
+// waits for that commit on the stage's empty barrier itself.  Every wait of
+// the watcher is bounded.
 // Every wait is bounded (2 s, or the context's wait limit); on expiry the
 // kernel records a status word, lets its in-flight copies and MMAs land
 // (those final drains always allow 2 s), frees TMEM and returns.
@@ -76,7 +81,7 @@ constexpr int TMEM_COLS = 512;                   // D1 x2, X x2 (128 columns eac
 constexpr int NEPI = 16;                         // epilogue warps (4 per TMEM lane quadrant)
 constexpr int kWatchWarp = 2 + NEPI;             // waits on the MMA issuer's barriers for it
 constexpr int NTHREADS = 64 + 32 * NEPI + 32;
-constexpr int kStageBar = 1;                     // named barriers kStageBar + s hand stage s to the MMA warp
+constexpr int kStageBar = 1;                     // named barriers kStageBar + p hand stage pair p to the MMA warp
 constexpr int kMaxDots = 24;                     // fused dot products: basis vectors + 1 (sum of squares)
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 constexpr int COLS_PER_WARP = TBN / (NEPI / 4);  // columns drained by one epilogue warp
@@ -322,8 +327,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         cx = x_last ? 0 : cx + 1;
         const uint32_t b1 = u1 & 1;
         if (x_first) xbuf = ux & 1;
-        // the watcher saw this stage land (and, at a unit start, the buffers drained)
-        named_bar_sync(kStageBar + stage, 64);
+        // the watcher saw this stage pair land (and, at unit starts, the buffers drained)
+        if ((stage & 1) == 0) named_bar_sync(kStageBar + (stage >> 1), 64);   // once per stage pair
         if (lane == 0 && !live) {
           ptx::mma_commit(ptx::smem_u32(&empty[stage]));   // the watcher's abort path waits on it
         } else if (lane == 0) {
@@ -373,8 +378,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     // ------------------------------------------------------------ watcher
     // Same tile / k-block / unit sequence as the MMA warp, run to its end: lane 0
     // waits (bounded) for each k-block's stage, and at a unit start for the
-    // accumulator buffer it reuses; then the warp arrives on the stage's barrier.
-    // After a failed wait (abort) it keeps arriving without waiting.
+    // accumulator buffer it reuses; after the second k-block of a stage pair the
+    // warp arrives on the pair's barrier.  After a failed wait (abort) it waits
+    // only for the stage's previous commit before arriving (see the header).
     int stage = 0;
     uint32_t phase = 0;
     uint32_t u1 = 0, ux = 0;
@@ -405,7 +411,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         __syncwarp();
-        named_bar_arrive(kStageBar + stage, 64);
+        // one arrival per stage pair: after its second stage, or after the CTA's last k-block
+        const bool last_kb = kb + 1 == nkb && tile + (int)gridDim.x >= num_tiles;
+        if ((stage & 1) == 1 || last_kb) named_bar_arrive(kStageBar + (stage >> 1), 64);
         if (d1_last) ++u1;
         if (x_last) ++ux;
         if (++stage == NSTAGE) {
