@@ -611,10 +611,13 @@ double tci_bs_tensor_flops(tci_bs_plan plan);
  * d = 2.  chi[nbonds] is a HOST array of bond dimensions.  Packed device
  * layouts (interleaved re/im, bonds back to back, each row-major):
  * A_i [chi_i,2,chi_i], B_i [chi_i,2,chi_i], G_i [2,2,2,2] (16 values per
- * bond), theta_i [chi_i,2,2,chi_i].  Arithmetic: the context precision at
- * plan creation (SPLIT_BF16 or SPLIT_BF16_3): the complex product uses three
- * real split-BF16 tensor-core GEMMs per bond (3M), all bonds in one grouped
- * persistent launch.  Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision),
+ * bond), theta_i [chi_i,2,2,chi_i]; A, B, theta 8-byte and G 16-byte
+ * aligned (else INVALID_ARG).  Arithmetic: the context precision at
+ * plan creation (SPLIT_BF16 or SPLIT_BF16_3): the complex product is one
+ * real split-BF16 tensor-core GEMM per bond ([Ar | Ai] times [Br | -Bi] and
+ * [Bi | Br], real and imaginary parts in adjacent output columns), all bonds
+ * in one grouped persistent launch whose epilogue applies the gate (AB is
+ * never stored).  Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision),
  * ALLOC, CUDA. */
 tci_status tci_tebd_plan_create(tci_context ctx, int nbonds, const int64_t* chi, tci_tebd_plan* plan);
 tci_status tci_tebd_plan_destroy(tci_tebd_plan* plan);
@@ -632,10 +635,12 @@ double tci_tebd_flops(tci_tebd_plan plan);
 tci_status tci_tebd_theta_batched(tci_context ctx, int n, const tci_tensor* A, const tci_tensor* B,
                                   const tci_tensor* G, tci_tensor* theta);
 /* Profiling form of tci_tebd_apply: stage_ms[0..2] (host) receive the device
- * times of the split, the grouped GEMM and the gate kernel.  Synchronises. */
+ * times of the split and of the grouped GEMM (whose epilogue applies the
+ * gate), and 0 (there is no separate gate stage).  Synchronises. */
 tci_status tci_tebd_apply_timed(tci_tebd_plan plan, const void* A, const void* B, const void* G, void* theta,
                                 float* stage_ms);
-/* BF16 tensor-core flops the grouped launch executes (3 real GEMMs per bond). */
+/* BF16 tensor-core flops the grouped launch executes (one real GEMM per bond,
+ * M = 2 chi, N = 4 chi, K = 2 pad8(chi)). */
 double tci_tebd_tensor_flops(tci_tebd_plan plan);
 
 /* ------------------------------------------- autotuner and plan cache

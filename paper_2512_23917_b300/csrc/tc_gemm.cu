@@ -110,6 +110,9 @@ struct GemmProblem {   // aligned as its tensor maps (TMA descriptors in global 
   int64_t M, N, scm, scn;
   int num_m, num_n, num_kb, tile_begin;
   int out_mode, pad0, pad1, pad2;
+  // out_mode 3 (gate epilogue, see gate16): the bond dimension and the complex
+  // offsets of the bond's gate (16 values) and theta in the launch's buffers
+  int64_t g_chi, g_off, th_off;
 };
 static_assert(alignof(GemmProblem) >= 64 && sizeof(GemmProblem) % 64 == 0, "tensor maps need 64-byte alignment");
 
@@ -130,6 +133,7 @@ struct GemmParams {
   int64_t dot_ldv;
   int dot_nv, dot_stride;
   double* dot_part;
+  const float2* const* gate_ptrs;   // out_mode 3: device array {gate base, theta base} (complex64)
 };
 
 // Local tile index -> (m-block, n-block).  With raster G > 0, consecutive
@@ -160,6 +164,55 @@ template <bool G>
 __device__ __forceinline__ int tile_kblocks(int tile, const GemmProblem* single, const GemmParams& p) {
   if (!G) return single->num_kb;
   return __ldg(&p.tile_map[tile].y);
+}
+
+// Gate epilogue of one TEBD bond (theta formation with the gate applied).  The
+// tile holds AB = A_i B_i with rows (a, t1) and columns (b, t2, c), c = 0 the
+// real and c = 1 the imaginary part, the last index fastest; row (a, 1 - t1)
+// sits in the partner lane (lane ^ 1).  For the 4 b of the 16 columns from
+// ncol0 (ncol0 % 16 == 0) this thread writes
+//   theta[a, s1 = t1, s2, b] = sum_{t1', t2'} G[s1, s2, t1', t2'] AB[a, t1', t2', b].
+// Called by whole warps: lanes past the last row exchange values but store nothing.
+__device__ __forceinline__ void gate16(const float (&v)[16], int64_t row, int64_t ncol0, const GemmProblem* pr,
+                                       const GemmParams& p) {
+  float o[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) o[j] = __shfl_xor_sync(0xffffffffu, v[j], 1);
+  if (row >= pr->M) return;
+  const int64_t chi = pr->g_chi, a = row >> 1, b0 = ncol0 >> 2;
+  const int t1 = (int)(row & 1);
+  // G[s1][s2][t1'][t2'] as float4 pairs over t2': element s1*4 + s2*2 + t1'
+  const float4* gs = reinterpret_cast<const float4*>(p.gate_ptrs[0] + pr->g_off) + t1 * 4;
+  float2* th = const_cast<float2*>(p.gate_ptrs[1]) + pr->th_off + (a * 2 + t1) * 2 * chi;
+#pragma unroll
+  for (int s2 = 0; s2 < 2; ++s2) {
+    const float4 go = __ldg(gs + s2 * 2 + t1);         // t1' = t1 (this lane's row)
+    const float4 gp = __ldg(gs + s2 * 2 + (t1 ^ 1));   // t1' = 1 - t1 (the partner's row)
+    float2 r[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float* x = v + m * 4;   // (t2' = 0: re, im; t2' = 1: re, im)
+      const float* y = o + m * 4;
+      float re = go.x * x[0] - go.y * x[1];
+      float im = go.x * x[1] + go.y * x[0];
+      re = fmaf(go.z, x[2], fmaf(-go.w, x[3], re));
+      im = fmaf(go.z, x[3], fmaf(go.w, x[2], im));
+      re = fmaf(gp.x, y[0], fmaf(-gp.y, y[1], re));
+      im = fmaf(gp.x, y[1], fmaf(gp.y, y[0], im));
+      re = fmaf(gp.z, y[2], fmaf(-gp.w, y[3], re));
+      im = fmaf(gp.z, y[3], fmaf(gp.w, y[2], im));
+      r[m] = make_float2(re, im);
+    }
+    float2* dst = th + s2 * chi + b0;
+    if (b0 + 4 <= chi && (((uintptr_t)dst) & 15) == 0) {
+      reinterpret_cast<float4*>(dst)[0] = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
+      reinterpret_cast<float4*>(dst)[1] = make_float4(r[2].x, r[2].y, r[3].x, r[3].y);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        if (b0 + m < chi) dst[m] = r[m];
+    }
+  }
 }
 
 // Error-free sum in FP32: s + e == a + b exactly (Knuth TwoSum).
@@ -212,7 +265,8 @@ __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, u
   return true;
 }
 
-template <bool G, int NPROD, bool DOTS, int BN>
+// GATE: grouped launches with gate-epilogue problems (out_mode 3)
+template <bool G, int NPROD, bool DOTS, int BN, bool GATE = false>
 __global__ void __launch_bounds__(NTHREADS, 1)
     k_split_bf16_gemm(const __grid_constant__ GemmProblem single, const GemmParams p) {
   using TN = TileN<BN>;
@@ -504,6 +558,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ptx::tmem_ld_32x32b_x16(td + g * 16, vd);
           ptx::tmem_ld_32x32b_x16(tx + g * 16, vx);
           ptx::tmem_ld_wait();
+          if (GATE && out_mode == 3) {   // whole warp: the gate pairs rows of two lanes
+            float v[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(vd[j]) + __uint_as_float(vx[j]);
+            gate16(v, row, n0 + g * 16, pr, p);
+            continue;
+          }
           if (row >= PM) continue;
           const int64_t ng = n0 + g * 16;
           if (out_mode == 1) {
@@ -592,7 +653,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       // store the tile (one rounding of hi + lo)
       const int64_t row = (int64_t)mb * TBM + qd * 32 + lane;
       const int64_t n0 = (int64_t)nb * BN + c0;
-      if (row < PM) {
+      if (GATE && out_mode == 3) {   // gate epilogue (whole warp)
+#pragma unroll
+        for (int g = 0; g < TN::kCols / 16; ++g) {
+          float v[16];
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const float2 c = __bfloat1622float2(rl2[(g * 16 + j) / 2]);
+            v[j] = rh[g * 16 + j] + c.x;
+            v[j + 1] = rh[g * 16 + j + 1] + c.y;
+          }
+          gate16(v, row, n0 + g * 16, pr, p);
+        }
+      } else if (row < PM) {
         if (out_mode == 1) {
           float* crow = (float*)PC + row * scm;
           const bool vec = scn == 1 && ((((uintptr_t)(crow + n0)) & 15) == 0) && n0 + TN::kCols <= PN;
@@ -741,6 +814,10 @@ static tci_status common_params(tci_context ctx, GemmParams* gp, int products, i
     TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<false, 3, true, 128>, A, S128));
     TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false, 64>, A, S64));
     TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false, 64>, A, S64));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false, 128, true>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false, 128, true>, A, S128));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 6, false, 64, true>, A, S64));
+    TCI_CUDA(ctx, cudaFuncSetAttribute(k_split_bf16_gemm<true, 3, false, 64, true>, A, S64));
     attr_set = true;
   }
   gp->kb_d1 = chunk_k < TBK ? 1 : chunk_k / TBK;
@@ -764,6 +841,7 @@ tci_status tci_gemm_split_bf16_sub(tci_context ctx, int64_t M, int64_t N, int64_
                                    int64_t a_plane_rows, const void* Bp, int64_t b_plane_rows, void* C, int out_mode,
                                    int64_t scm, int64_t scn, int products, int chunk_k, int xchunk_k, int raster) {
   if (M <= 0 || N <= 0) return TCI_OK;
+  if (out_mode < 0 || out_mode > 2) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split gemm: out_mode 0, 1 or 2");
   GemmProblem pr;
   TCI_TRY(fill_problem(ctx, &pr, M, N, Kp, Ap, Bp, C, out_mode, scm, scn, a_plane_rows, b_plane_rows));
   GemmParams gp;
@@ -819,6 +897,7 @@ struct tci_split_group {
   GemmProblem* d_table = nullptr;
   int2* d_tile_map = nullptr;
   int bn = TBN;   // tile width of every problem of the group
+  bool gated = false;   // has gate-epilogue problems (the launch needs their pointers)
   int nprob = 0;
   int num_tiles = 0;
   int64_t flops_tc = 0;
@@ -828,6 +907,16 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
                                   int bn) {
   *out = nullptr;
   if (bn != 64 && bn != 128) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split group: tile width 64 or 128");
+  bool gated = false;
+  for (int i = 0; i < n; ++i) {
+    const tci_split_problem& q = probs[i];
+    if (q.out_mode < 0 || q.out_mode > 3) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split group: out_mode 0..3");
+    if (q.out_mode == 3) {   // rows (a, t1), columns (b, t2, re/im)
+      if (q.M != 2 * q.g_chi || q.N != 4 * q.g_chi || q.g_off < 0 || q.th_off < 0)
+        return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split group: malformed gate problem %d", i);
+      gated = true;
+    }
+  }
   std::vector<GemmProblem> host;
   host.reserve(n);
   std::vector<int> order;
@@ -841,12 +930,16 @@ tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_proble
     GemmProblem pr;
     TCI_TRY(fill_problem(ctx, &pr, q.M, q.N, q.Kp, q.Ap, q.Bp, q.C, q.out_mode, q.scm, q.scn, q.a_plane_rows,
                          q.b_plane_rows, bn));
+    pr.g_chi = q.g_chi;
+    pr.g_off = q.g_off;
+    pr.th_off = q.th_off;
     pr.tile_begin = tiles;
     tiles += pr.num_m * pr.num_n;
     host.push_back(pr);
   }
   tci_split_group* g = new tci_split_group();
   g->bn = bn;
+  g->gated = gated;
   g->nprob = (int)host.size();
   g->num_tiles = tiles;
   if (g->nprob > 0) {
@@ -885,24 +978,35 @@ void tci_split_group_destroy(tci_split_group* g) {
 }
 
 tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k,
-                                  int raster) {
+                                  int raster, const void* const* gate_ptrs) {
   if (!g || g->nprob == 0) return TCI_OK;
+  if (g->gated && !gate_ptrs) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "split group: gate pointers required");
   GemmParams gp;
   memset(&gp, 0, sizeof gp);
   TCI_TRY(common_params(ctx, &gp, products, chunk_k, xchunk_k, raster));
   gp.table = g->d_table;
   gp.tile_map = g->d_tile_map;
+  gp.gate_ptrs = reinterpret_cast<const float2* const*>(gate_ptrs);
   gp.nprob = g->nprob;
   gp.num_tiles = g->num_tiles;
   GemmProblem dummy;
   memset(&dummy, 0, sizeof dummy);
   const int grid = gp.num_tiles < ctx->num_sms ? gp.num_tiles : ctx->num_sms;
-  if (products == 6)
+  const int smem = g->bn == 64 ? TileN<64>::kSmem : TileN<128>::kSmem;
+  if (g->gated) {
+    if (products == 6)
+      (g->bn == 64 ? k_split_bf16_gemm<true, 6, false, 64, true> : k_split_bf16_gemm<true, 6, false, 128, true>)
+          <<<grid, NTHREADS, smem, ctx->stream>>>(dummy, gp);
+    else
+      (g->bn == 64 ? k_split_bf16_gemm<true, 3, false, 64, true> : k_split_bf16_gemm<true, 3, false, 128, true>)
+          <<<grid, NTHREADS, smem, ctx->stream>>>(dummy, gp);
+  } else if (products == 6) {
     (g->bn == 64 ? k_split_bf16_gemm<true, 6, false, 64> : k_split_bf16_gemm<true, 6, false, 128>)
-        <<<grid, NTHREADS, g->bn == 64 ? TileN<64>::kSmem : TileN<128>::kSmem, ctx->stream>>>(dummy, gp);
-  else
+        <<<grid, NTHREADS, smem, ctx->stream>>>(dummy, gp);
+  } else {
     (g->bn == 64 ? k_split_bf16_gemm<true, 3, false, 64> : k_split_bf16_gemm<true, 3, false, 128>)
-        <<<grid, NTHREADS, g->bn == 64 ? TileN<64>::kSmem : TileN<128>::kSmem, ctx->stream>>>(dummy, gp);
+        <<<grid, NTHREADS, smem, ctx->stream>>>(dummy, gp);
+  }
   TCI_CUDA(ctx, cudaGetLastError());
   return TCI_OK;
 }

@@ -202,14 +202,20 @@ struct tci_split_problem {
   int out_mode;
   int64_t scm, scn;
   int64_t a_plane_rows = 0, b_plane_rows = 0;   // piece-plane stride in rows (0: M, N)
+  // out_mode 3 (gate epilogue of one TEBD bond: rows (a, t1), columns
+  // (b, t2, re/im), M = 2 g_chi, N = 4 g_chi; C unused): the bond dimension and
+  // the complex offsets of its gate and theta in the buffers the launch is given
+  int64_t g_chi = 0, g_off = 0, th_off = 0;
 };
 struct tci_split_group;
 // bn: tile width (128, or 64 for groups of narrow problems)
 tci_status tci_split_group_create(tci_context ctx, int n, const tci_split_problem* probs, tci_split_group** out,
                                   int bn = 128);
 void tci_split_group_destroy(tci_split_group* g);
+// gate_ptrs: device array {gate base, theta base} (complex64), read by the
+// kernel; required when the group has gate-epilogue problems.
 tci_status tci_split_group_launch(tci_context ctx, const tci_split_group* g, int products, int chunk_k, int xchunk_k,
-                                  int raster);
+                                  int raster, const void* const* gate_ptrs = nullptr);
 
 // Captured launch sequence of a plan.  The sequence is captured once on a
 // private stream (capture is not possible on the legacy default stream) and

@@ -1,4 +1,5 @@
-"""GPU parity of the batched TEBD theta (3M split-BF16 grouped GEMM) vs the complex128 oracle."""
+"""GPU parity of the batched TEBD theta (split-BF16 grouped GEMM with the gate in its epilogue) vs the
+complex128 oracle."""
 import numpy as np
 import pytest
 
@@ -108,3 +109,28 @@ def test_tebd_narrow_tiles_match_oracle(ctx, tci, nb, lo, hi, seed):
     got, plan = run_tebd(tci, ctx, chis, A, B, G, tile_n=64)
     for g_, a, b, gg in zip(got, A, B, G):
         assert rel_frob_err(g_, o_tebd.theta(a, b, gg)) < 1e-5
+
+
+def test_tebd_three_products_match_oracle(ctx, tci):
+    """SPLIT_BF16_3 (hi*hi, hi*mid, mid*hi per real product) through the gate epilogue: both
+    accumulation paths (chi <= 256 fits one hi*hi chunk, chi > 256 does not)."""
+    chis, A, B, G = tebd_inputs(12, seed=31, chi_lo=40, chi_hi=400)
+    got, _ = run_tebd(tci, ctx, chis, A, B, G, precision="split_bf16_3")
+    for g_, a, b, gg in zip(got, A, B, G):
+        assert rel_frob_err(g_, o_tebd.theta(a, b, gg)) < 1e-4
+
+
+def test_tebd_misaligned_gate_is_rejected(ctx, tci):
+    """The gate epilogue reads G as 16-byte vectors: a G base that is only 8-byte aligned is
+    refused on the host (TCI_ERR_INVALID_ARG) before anything launches."""
+    import torch
+    chis, A, B, G = tebd_inputs(2, seed=5, chi_lo=4, chi_hi=6)
+    plan = tci.TebdPlan(ctx, chis)
+    pa = to_dev(np.concatenate([a.ravel() for a in A]))
+    pb = to_dev(np.concatenate([b.ravel() for b in B]))
+    pg = to_dev(np.concatenate([np.zeros(1, np.complex64)] + [g.ravel() for g in G]))[1:]
+    th = torch.zeros(sum(4 * c * c for c in chis), dtype=torch.complex64, device="cuda")
+    assert pg.data_ptr() % 16 == 8
+    with pytest.raises(tci.TciError) as ei:
+        plan.apply(pa, pb, pg, th)
+    assert ei.value.status_name == "TCI_ERR_INVALID_ARG"
