@@ -103,6 +103,7 @@ SIGNATURES = [
     ("tci_heff_set_lanczos_graphs", C.c_int, [_p, C.c_int]),
     ("tci_heff_lanczos_graph_info", C.c_int, [_p, _i64p]),
     ("tci_heff_set_lanczos_fused_dots", C.c_int, [_p, C.c_int]),
+    ("tci_heff_set_lanczos_shadow_dots", C.c_int, [_p, C.c_int]),
     ("tci_bs_set_tile_n", C.c_int, [_p, C.c_int]),
     ("tci_bs_tile_n", C.c_int, [_p]),
     ("tci_tebd_set_tile_n", C.c_int, [_p, C.c_int]),
@@ -637,6 +638,11 @@ class HeffPlan:
         """Form the first projection's dots in the matvec's GEMM2 epilogue (split plans; off by default:
         slower on B300 than the separate pass)."""
         _check(lib.tci_heff_set_lanczos_fused_dots(self.handle, int(bool(enable))), self.ctx.handle)
+
+    def set_lanczos_shadow_dots(self, enable: bool):
+        """First projection's dots from the basis's double-float copy on the FP32 pipes (split plans, FP64
+        vectors; on by default), or (False) in FP64."""
+        _check(lib.tci_heff_set_lanczos_shadow_dots(self.handle, int(bool(enable))), self.ctx.handle)
 
     def set_lanczos_reduced_terms(self, enable: bool):
         """Allow (default) or forbid the FP32 / double-float evaluation of small update terms."""

@@ -554,7 +554,7 @@ extern "C" tci_status tci_heff_plan_destroy(tci_heff_plan* pp) {
   tci_heff_plan p = *pp;
   if (tci_ctx_ok(p->ctx)) cudaStreamSynchronize(p->ctx->stream);
   void* bufs[] = {p->U, p->L64, p->R64, p->V64, p->Lp, p->Rp, p->psip, p->Vp, p->d_stage_in, p->d_stage_out,
-                  p->lz_V, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64, p->ws};
+                  p->lz_V, p->lz_Vs, p->lz_w, p->lz_scal, p->lz_part, p->lz_x64, p->lz_o64, p->ws};
   for (void* b : bufs) tci_dev_free(b);
   for (tci_tensor* t : {&p->cL, &p->cW, &p->cW2, &p->cR, &p->cU[0], &p->cU[1], &p->cU[2], &p->cVin, &p->cVout})
     if (*t) tci_tensor_free(t);

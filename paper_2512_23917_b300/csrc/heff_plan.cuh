@@ -46,6 +46,8 @@ struct tci_heff_plan_s {
   // Lanczos workspace
   double* lz_V = nullptr;     // basis, capacity lz_cap vectors
   int lz_cap = 0;
+  void* lz_Vs = nullptr;      // double-float shadow of the basis (float2), capacity lz_vs_cap vectors
+  int lz_vs_cap = 0;
   double* lz_w = nullptr;
   double* lz_scal = nullptr;  // device scalars
   double* lz_part = nullptr;  // reduction partials
@@ -64,6 +66,7 @@ struct tci_heff_plan_s {
   int64_t lz_graph_launches = 0;
   int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
   int lz_fuse = 0;      // split plans: first Gram-Schmidt projection formed in the matvec's GEMM2 (opt-in)
+  int lz_shadow = 1;    // split plans, FP64 vectors: pass-1 dots from the basis's double-float shadow
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;
 };

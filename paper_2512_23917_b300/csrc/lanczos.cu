@@ -41,10 +41,19 @@
 // the device chose runs.  The second pass's h' are rounding-level after the
 // first projection, so pass 3 is folded into the next-vector kernel (FP32
 // terms), with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h' is
-// orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  Every dot
-// product, and so every alpha, beta and coefficient, stays FP64; the reduced
+// orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  The reduced
 // terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64 of its FP32
 // rate).
+//
+// Dot products.  FP64 in general.  On split plans with FP64 vectors (whose
+// matvec error, ~1e-7 ||w||, dwarfs any rounding of the projections), the
+// first projection's dots <v_i, w> and ||w||^2 are summed in double-float
+// arithmetic from a double-float shadow of the basis (each v_i also stored
+// as an FP32 pair within 2^-47 |v_i|, written with v_i), and the second
+// projection's dots from FP32 pairs split on the integer pipes in the
+// double-float-terms update pass: both passes then run on the FP32 pipes and
+// are bound by HBM, not by the FP64 rate.  Their error is ~2^-46 ||v_i||
+// ||w||; the recurrence scalars alpha, beta and every update stay FP64.
 //
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
@@ -136,6 +145,14 @@ __device__ __forceinline__ void f32_split2(double x, float& h, float& l) {
   const float scale = se > 0 ? __uint_as_float((unsigned)se << 23) : 0.f;
   const float mag = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), scale);
   l = __uint_as_float(__float_as_uint(mag) | (hi & 0x80000000u));
+}
+
+// Shadow element of a basis value y: the FP32 pair of f32_split2 (integer
+// pipes; no FP64 instruction), hi + lo within 2^-47 |y| (|y| <= 1).
+__device__ __forceinline__ float2 shadow_of(double y) {
+  float h, l;
+  f32_split2(y, h, l);
+  return make_float2(h, l);
 }
 
 // ---------------------------------------------------------------- double-float
@@ -286,8 +303,45 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
   }
 }
 
+// Pass 1 from the double-float shadow of the basis (FP64 vectors): partials of
+// <Vs_g, w>, g < nv <= G, into part rows g, and with SQ of ||w||^2; w (FP64) is
+// split into an FP32 pair once per element on the integer pipes (f32_split2,
+// within 2^-47 |w_i| where |w_i| >= 2^-126) and every product and sum runs in
+// double-float arithmetic on the FP32 pipes: no FP64 instruction per element.
+template <int G, bool SQ>
+__global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float2* __restrict__ Vs, int64_t ldv, int nv,
+                                                    const double* __restrict__ w, int64_t n,
+                                                    double* __restrict__ part, double* __restrict__ part_sq,
+                                                    const double* __restrict__ ctrl) {
+  if (ctrl[0] != 0.0) return;
+  ArithDF::Acc a[G];
+#pragma unroll
+  for (int g = 0; g < G; ++g) a[g] = ArithDF::zero();
+  ArithDF::Acc q = ArithDF::zero();
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += (int64_t)gridDim.x * NT) {
+    // every load first (all in flight together), then the arithmetic; rows
+    // g >= nv hold zeros and add nothing
+    float2 vv[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) vv[g] = g < nv ? __ldg(&Vs[(int64_t)g * ldv + i]) : make_float2(0.f, 0.f);
+    const float2 x = shadow_of(__ldg(&w[i]));
+#pragma unroll
+    for (int g = 0; g < G; ++g) ArithDF::acc(a[g], vv[g], x);
+    if (SQ) ArithDF::acc(q, x, x);
+  }
+  block_partials<ArithDF, G>(a, nv, part);
+  if (SQ) {
+    const ArithDF::Acc qa[1] = {q};
+    block_partials<ArithDF, 1>(qa, 1, part_sq);
+  }
+}
+
 // w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
-// into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  TERMS
+// into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  In the
+// double-float-terms variant (FP64 vectors whose update coefficients are at
+// the matvec-error level: split plans) the dots also run in double-float
+// arithmetic on the FP32 pipes, from the FP32 pairs of f32_split2 (integer
+// pipes) of both operands, so the pass stays HBM-bound; ||w||^2 stays FP64.  TERMS
 // (FP64 vectors; v0 = 0, nv = G): the arithmetic of the first nv - 2 terms,
 // kTermsF64, kTermsF32 or kTermsDF with coefficients scaled by lo[LO_SC1]
 // (see the header); with lo the kernel runs only when it is the variant the
@@ -327,9 +381,11 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
   if constexpr (TERMS != kTermsF64) isc = lo[LO_ISC1];
   __syncthreads();
   constexpr int GD = DOTS ? G : 1;
-  typename A::Acc d[GD];
+  constexpr bool kDFDots = kF64 && DOTS && TERMS == kTermsDF;
+  using DA = typename std::conditional<kDFDots, ArithDF, A>::type;
+  typename DA::Acc d[GD];
 #pragma unroll
-  for (int g = 0; g < GD; ++g) d[g] = A::zero();
+  for (int g = 0; g < GD; ++g) d[g] = DA::zero();
   typename A::Acc q = A::zero();
   const Vt* Vb = V + (int64_t)v0 * ldv;
   const int64_t stride = (int64_t)gridDim.x * NT;
@@ -409,14 +465,18 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
       y = A::sub_end(t);
     }
     w[i] = y;
-    if (DOTS) {
+    if constexpr (kDFDots) {
+      const float2 yy = shadow_of(y);
+#pragma unroll
+      for (int g = 0; g < GD; ++g) ArithDF::acc(d[g], shadow_of(v[g]), yy);
+    } else if (DOTS) {
 #pragma unroll
       for (int g = 0; g < GD; ++g)
         if (kF64 || g < nv) A::acc(d[g], v[g], y);
     }
     if (SUMSQ) A::acc(q, y, y);
   }
-  if (DOTS) block_partials<A, GD>(d, nv, part + (int64_t)v0 * NBMAX);
+  if (DOTS) block_partials<DA, GD>(d, nv, part + (int64_t)v0 * NBMAX);
   if (SUMSQ) {
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
@@ -451,20 +511,29 @@ constexpr int kInNone = 0;     // the matvec reads the FP64 basis vector itself
 constexpr int kInPieces = 1;   // bfloat16 pieces of fl32(v), K-major [3][rows][Kp], zero in k >= cols
 constexpr int kInF64 = 2;      // v as FP64 (double-float basis, FP64 matvec)
 
+// two consecutive shadow elements (i even: one 16-byte store)
+__device__ __forceinline__ void store_shadow2(float2* p, double y0, double y1) {
+  const float2 a = shadow_of(y0), b = shadow_of(y1);
+  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+}
+
 template <class A, int MODE>
 __device__ __forceinline__ void emit(typename A::V y, int64_t i, int64_t r, int64_t k, typename A::V* vn,
-                                     __nv_bfloat16* pieces, int64_t Kp, int64_t plane, double* x64) {
+                                     __nv_bfloat16* pieces, int64_t Kp, int64_t plane, double* x64,
+                                     float2* vs = nullptr) {
   vn[i] = y;
+  if (vs) vs[i] = shadow_of(A::to_double(y));
   if (MODE == kInPieces) split3_store(pieces + r * Kp + k, plane, A::f32(y));
   if (MODE == kInF64) x64[i] = A::to_double(y);
 }
 
 // v_{j+1} = w / beta_j (unless stopped or gated off); element (r, k) of [rows][cols].
+// vs (FP64 vectors, may be null): the double-float shadow of v_{j+1}.
 template <class A, int MODE>
 __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w, typename A::V* __restrict__ vn,
                                              int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
-                                             int j, const double* __restrict__ gate) {
+                                             int j, const double* __restrict__ gate, float2* __restrict__ vs) {
   if (scal[OFF_CTRL] != 0.0 || gate[0] != 0.0) return;
   const typename A::Coef c = A::coef(1.0 / scal[OFF_BETA + j]);
   const int64_t plane = rows * Kp;
@@ -478,6 +547,7 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
             const double2 x = *reinterpret_cast<const double2*>(w + i);
             const double y0 = A::mul(x.x, c), y1 = A::mul(x.y, c);
             *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
+            if (vs) store_shadow2(vs + i, y0, y1);
             if (MODE == kInPieces) split3_store2(pieces + r * Kp + k, plane, A::f32(y0), A::f32(y1));
           } else {
             split3_store2(pieces + r * Kp + k, plane, 0.f, 0.f);
@@ -490,7 +560,7 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
     for (int64_t k = threadIdx.x; k < kend; k += NT) {
       if (k < cols) {
         const int64_t i = r * cols + k;
-        emit<A, MODE>(A::mul(w[i], c), i, r, k, vn, pieces, Kp, plane, x64);
+        emit<A, MODE>(A::mul(w[i], c), i, r, k, vn, pieces, Kp, plane, x64, vs);
       } else {
         split3_store(pieces + r * Kp + k, plane, 0.f);
       }
@@ -504,7 +574,7 @@ template <int MODE>
 __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, int64_t ldv, int nv,
                                                   const double* __restrict__ w, double* __restrict__ vn, int64_t rows,
                                                   int64_t cols, __nv_bfloat16* __restrict__ pieces, int64_t Kp,
-                                                  const double* __restrict__ scal, int j) {
+                                                  const double* __restrict__ scal, int j, float2* __restrict__ vs) {
   if (scal[OFF_CTRL] != 0.0 || scal[OFF_LO + LO_GFAST] != 0.0) return;
   __shared__ float cf[MAXM];
   const double sc = scal[OFF_LO + LO_SC3];
@@ -529,6 +599,7 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
           const double2 x = *reinterpret_cast<const double2*>(w + i);
           const double y0 = fma(-(double)s0, isc, x.x) * binv, y1 = fma(-(double)s1, isc, x.y) * binv;
           *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
+          if (vs) store_shadow2(vs + i, y0, y1);
           if (MODE == kInPieces)
             split3_store2(pieces + r * Kp + k, plane, __double2float_rn(y0), __double2float_rn(y1));
         } else {
@@ -545,7 +616,7 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
 #pragma unroll 8
         for (int g = 0; g < nv; ++g) sf = __fmaf_rn(cf[g], f32_trunc(V[(int64_t)g * ldv + i]), sf);
         const double y = fma(-(double)sf, isc, w[i]) * binv;
-        emit<ArithF64, MODE>(y, i, r, k, vn, pieces, Kp, plane, nullptr);
+        emit<ArithF64, MODE>(y, i, r, k, vn, pieces, Kp, plane, nullptr, vs);
       } else {
         split3_store(pieces + r * Kp + k, plane, 0.f);
       }
@@ -556,7 +627,8 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
 template <class A, int MODE>
 __global__ void __launch_bounds__(NT) k_start(const double* __restrict__ psi, typename A::V* __restrict__ v0,
                                               int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
-                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal) {
+                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
+                                              float2* __restrict__ vs) {
   const double inv = 1.0 / sqrt(scal[OFF_CTRL + 3]);
   const int64_t plane = rows * Kp;
   const int64_t kend = MODE == kInPieces ? Kp : cols;
@@ -564,7 +636,7 @@ __global__ void __launch_bounds__(NT) k_start(const double* __restrict__ psi, ty
     for (int64_t k = threadIdx.x; k < kend; k += NT) {
       if (k < cols) {
         const int64_t i = r * cols + k;
-        emit<A, MODE>(A::from_double(psi[i] * inv), i, r, k, v0, pieces, Kp, plane, x64);
+        emit<A, MODE>(A::from_double(psi[i] * inv), i, r, k, v0, pieces, Kp, plane, x64, vs);
       } else {
         split3_store(pieces + r * Kp + k, plane, 0.f);
       }
@@ -1079,6 +1151,42 @@ tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
   return TCI_OK;
 }
 
+template <int G, bool SQ>
+int dots_shadow_g(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n, double* part,
+                  double* part_sq, const double* ctrl) {
+  const int grid = pass_grid(ctx, (const void*)k_dots_shadow<G, SQ>, n);
+  k_dots_shadow<G, SQ><<<grid, NT, 0, ctx->stream>>>(Vs, ldv, nv, w, n, part, part_sq, ctrl);
+  return grid;
+}
+
+template <bool SQ>
+int dots_shadow_launch(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n,
+                       double* part, double* part_sq, const double* ctrl) {
+  if (nv <= 4) return dots_shadow_g<4, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
+  if (nv <= 8) return dots_shadow_g<8, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
+  if (nv <= 12) return dots_shadow_g<12, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
+  if (nv <= 16) return dots_shadow_g<16, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
+  return dots_shadow_g<GMAX, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
+}
+
+// run_dots (v0 = 0) from the basis shadow
+tci_status run_dots_shadow(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n,
+                           double* part, double* out, const double* ctrl, double* sumsq_out) {
+  double* part_sq = part + (int64_t)MAXM * NBMAX;
+  for (int g0 = 0; g0 < nv; g0 += GMAX) {
+    const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
+    const bool sq = sumsq_out && g0 == 0;
+    const float2* Vb = Vs + (int64_t)g0 * ldv;
+    double* pb = part + (int64_t)g0 * NBMAX;
+    const int grid = sq ? dots_shadow_launch<true>(ctx, Vb, ldv, g, w, n, pb, part_sq, ctrl)
+                        : dots_shadow_launch<false>(ctx, Vb, ldv, g, w, n, pb, part_sq, ctrl);
+    k_reduce_parts<<<g, 256, 0, ctx->stream>>>(pb, g, grid, out + g0, ctrl);
+    if (sq) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, grid, sumsq_out, ctrl);
+  }
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
 // Every variant of one pass uses the grid of its FP64 variant, so the partial
 // sums of whichever variant ran are reduced over the same block count.
 template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
@@ -1167,23 +1275,25 @@ tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int 
 
 template <class A, int MODE>
 void launch_start(tci_context ctx, const double* psi0, typename A::V* v0, int64_t rows, int64_t cols,
-                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S) {
+                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, float2* vs) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
-  k_start<A, MODE><<<blocks, NT, 0, ctx->stream>>>(psi0, v0, rows, cols, pieces, Kp, x64, S);
+  k_start<A, MODE><<<blocks, NT, 0, ctx->stream>>>(psi0, v0, rows, cols, pieces, Kp, x64, S, vs);
 }
 
 template <class A, int MODE>
 void launch_next(tci_context ctx, const typename A::V* w, typename A::V* vn, int64_t rows, int64_t cols,
-                 __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j, const double* gate) {
+                 __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j, const double* gate,
+                 float2* vs) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
-  k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j, gate);
+  k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j, gate, vs);
 }
 
 template <int MODE>
 void launch_next_corr(tci_context ctx, const double* V, int64_t ldv, int nv, const double* w, double* vn,
-                      int64_t rows, int64_t cols, __nv_bfloat16* pieces, int64_t Kp, const double* S, int j) {
+                      int64_t rows, int64_t cols, __nv_bfloat16* pieces, int64_t Kp, const double* S, int j,
+                      float2* vs) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
-  k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j);
+  k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j, vs);
 }
 
 // One cluster of the largest size the device runs (16 CTAs where
@@ -1237,7 +1347,11 @@ tci_status launch_step_small(tci_context ctx, double* V, int64_t ldv, double* w,
 // (kInPieces for a split-BF16 plan; kInNone for FP64 vectors on an FP64
 // plan; kInF64 for double-float vectors on an FP64 plan).
 template <class A, int MODE>
-tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol) {
+// Vs (FP64 vectors on a split plan, re-orthogonalised; else null): the
+// double-float shadow of the basis, written with each basis vector and read
+// by pass 1.
+tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol,
+                       float2* Vs) {
   using Vt = typename A::V;
   tci_context ctx = p->ctx;
   // a complex plan runs on the real form: C128 vectors as interleaved FP64 pairs
@@ -1263,7 +1377,8 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   k_init_scal<<<1, 256, 0, ctx->stream>>>(S);
   k_sumsq<<<NBMAX, NT, 0, ctx->stream>>>(psi0, n, part);
   k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
-  launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S);
+  if (kDF || !reorth) Vs = nullptr;
+  launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S, Vs);
   TCI_CUDA(ctx, cudaGetLastError());
   for (int j = 0; j < nsteps; ++j) {
     Vt* vj = V + (int64_t)j * ldv;
@@ -1303,7 +1418,12 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // (below kReducedMinN the FP64 work is smaller than the extra launches)
       const bool reduced = kF32Terms && p->lz_reduced && j + 1 <= GMAX && n >= kReducedMinN;
       const double* lo1 = reduced ? S + OFF_LO : nullptr;
-      if (!fused) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
+      if (!fused) {
+        if constexpr (!kDF) {
+          if (Vs) TCI_TRY(run_dots_shadow(ctx, Vs, ldv, j + 1, (const double*)w, n, part, S + OFF_H, ctrl, ctrl + 4));
+        }
+        if (!Vs) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
+      }
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
@@ -1322,9 +1442,11 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
     if (j + 1 < nsteps) {
       Vt* vn = V + (int64_t)(j + 1) * ldv;
-      launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl);
+      float2* vsn = Vs ? Vs + (int64_t)(j + 1) * ldv : nullptr;
+      launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl,
+                           vsn);
       if constexpr (kF32Terms) {
-        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j);
+        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j, vsn);
       }
     }
     TCI_CUDA(ctx, cudaGetLastError());
@@ -1363,17 +1485,18 @@ struct SolveArgs {
   double tol;
   int arith;
   bool split;
+  float2* Vs;
 };
 
 // One solve's launches on p->ctx->stream (the body a graph captures).
 tci_status solve_body(void* a) {
   const SolveArgs& s = *(const SolveArgs*)a;
   if (s.arith == TCI_LANCZOS_DF32) {
-    if (s.split) return lanczos_run<ArithDF, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
-    return lanczos_run<ArithDF, kInF64>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+    if (s.split) return lanczos_run<ArithDF, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
+    return lanczos_run<ArithDF, kInF64>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
   }
-  if (s.split) return lanczos_run<ArithF64, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
-  return lanczos_run<ArithF64, kInNone>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol);
+  if (s.split) return lanczos_run<ArithF64, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, s.Vs);
+  return lanczos_run<ArithF64, kInNone>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
 }
 }  // namespace
 
@@ -1420,7 +1543,18 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   vs.info = arith == TCI_LANCZOS_DF32 ? "double-float vectors" : "FP64 vectors";
   const double* psi = (const double*)psi0->data;
   double* xd = x ? (double*)x->data : nullptr;
-  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split};
+  // pass 1 from a double-float shadow of the basis: split plans, FP64 vectors,
+  // re-orthogonalised, not fused into GEMM2
+  const bool shadow = split && arith == TCI_LANCZOS_F64 && !p->cplx && reorth && p->lz_shadow && !p->lz_fuse;
+  if (shadow && p->lz_vs_cap < p->lz_cap) {
+    cudaStreamSynchronize(ctx->stream);
+    tci_dev_free(p->lz_Vs);
+    p->lz_Vs = nullptr;
+    p->lz_vs_cap = 0;
+    TCI_TRY(tci_dev_alloc(ctx, sizeof(float2) * ldv * p->lz_cap, &p->lz_Vs));
+    p->lz_vs_cap = p->lz_cap;
+  }
+  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, shadow ? (float2*)p->lz_Vs : nullptr};
   bool done = false;
   p->lz_last_graph = 0;
   if (!p->cplx && p->lz_graphs) {
@@ -1428,7 +1562,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
     // or write x get the call's pointers before every replay
     const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->lz_reduced, p->lz_fuse,
-                                      p->products,
+                                      shadow, (int64_t)(uintptr_t)p->lz_Vs, p->products,
                                       p->chunk_k,
                                       p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
                                       (int64_t)ctx->wait_limit_ns};
@@ -1451,7 +1585,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     if (p->lz_graph.exec && key == p->lz_graph_key) {
       // k_sumsq(psi0, n, part), k_start(psi0, ...), k_ritz(V, ldv, S, x, n)
       TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 0, 3, 0, psi));
-      TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 1, 8, 0, psi));
+      TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 1, 9, 0, psi));
       if (xd) TCI_TRY(graph_set_ptr_arg(ctx, p->lz_graph, 2, 5, 3, xd));
       TCI_CUDA(ctx, cudaGraphLaunch(p->lz_graph.exec, ctx->stream));
       done = true;
@@ -1540,6 +1674,13 @@ extern "C" tci_status tci_heff_set_lanczos_fused_dots(tci_heff_plan p, int enabl
   if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_fused_dots: invalid plan");
   TCI_CHECK_CTX(p->ctx);
   p->lz_fuse = enable ? 1 : 0;
+  return TCI_OK;
+}
+
+extern "C" tci_status tci_heff_set_lanczos_shadow_dots(tci_heff_plan p, int enable) {
+  if (!p || p->magic != kPlanMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "set_lanczos_shadow_dots: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  p->lz_shadow = enable ? 1 : 0;
   return TCI_OK;
 }
 

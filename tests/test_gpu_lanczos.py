@@ -251,6 +251,7 @@ def test_lanczos_fused_dots_equal_separate_pass(ctx, tci, chi, chi_r):
     psi, L, R, W = dense_heff_inputs(chi, seed=21, chi_r=chi_r)
     plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
     plan.set_lanczos_fused_dots(True)
+    plan.set_lanczos_shadow_dots(False)                # both sides form every first-projection dot in FP64
     dpsi = to_dev(psi)
     x = torch.empty_like(dpsi)
     r1 = plan.lanczos(dpsi, 20, True, x)
@@ -268,3 +269,34 @@ def test_lanczos_fused_dots_equal_separate_pass(ctx, tci, chi, chi_r):
     mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
     o = o_lanczos.lanczos(mv, psi, 20)
     assert abs(r1["theta"] - o["theta"]) < 1e-6 * abs(o["theta"])
+
+
+@pytest.mark.parametrize("chi,chi_r", [(64, 64), (75, 61), (256, 256)])
+def test_lanczos_shadow_dots_equal_fp64_pass(ctx, tci, chi, chi_r):
+    """Split-BF16 plan, FP64 vectors: the first projection's dots from the basis's double-float copy
+    (the default) against the FP64 dot pass.  The first step (same v_0, same matvec) agrees to
+    ~1e-14; later steps agree only to the split matvec's own error level, because the matvec rounds
+    its input to FP32 and a 1e-14 change in v can flip such a rounding; theta stays the oracle's to
+    that level either way.  Odd column counts take the element-wise next-vector paths; repeated
+    solves replay the captured graph bit for bit."""
+    import torch
+    psi, L, R, W = dense_heff_inputs(chi, seed=23, chi_r=chi_r)
+    plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
+    dpsi = to_dev(psi)
+    x = torch.empty_like(dpsi)
+    r1 = plan.lanczos(dpsi, 20, True, x)
+    x1 = x.cpu().numpy()
+    for _ in range(2):
+        r1b = plan.lanczos(dpsi, 20, True, x)
+        assert r1b["theta"] == r1["theta"]
+        np.testing.assert_array_equal(x.cpu().numpy(), x1)
+    plan.set_lanczos_shadow_dots(False)
+    r0 = plan.lanczos(dpsi, 20, True, x)
+    assert r0["steps"] == r1["steps"] == 20
+    assert abs(r1["alpha"][0] - r0["alpha"][0]) < 1e-13 * np.abs(r0["alpha"]).max()
+    assert abs(r1["beta"][0] - r0["beta"][0]) < 1e-13 * r0["beta"][0]
+    np.testing.assert_allclose(r1["alpha"], r0["alpha"], rtol=1e-5, atol=1e-5 * np.abs(r0["alpha"]).max())
+    mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
+    o = o_lanczos.lanczos(mv, psi, 20)
+    for r in (r0, r1):
+        assert abs(r["theta"] - o["theta"]) < 1e-6 * abs(o["theta"])
