@@ -12,15 +12,24 @@
 //
 // Per matvec (all block GEMMs of a stage in ONE grouped persistent launch):
 //   1. split psi blocks into bfloat16 pieces (K-major, padded to 8)
-//   2. grouped GEMM1: for each psi block P = (ia', t1, t2, ib'):
+//   2. grouped GEMM1, one problem per sector ib': the psi blocks P = (ia',
+//      t1, t2, ib') that share ib' are stacked along M (their pieces are
+//      split straight into the stack), so one problem computes every
 //        U_P[a', (wr, b)] = sum_b' psi_P[a', b'] Rg_ib'[(wr, b), b']
 //      Rg_ib' stacks the R blocks (ib(wr), wr, ib') along rows (plan time)
 //   3. W.W tasks, one per sector pair (ja, ib): V[(s1 s2, b), (wl, a')] from
 //      the (t1 t2, wr) sub-blocks of the U_P that exist, written as pieces
 //      straight into GEMM2's K-major operand
-//   4. grouped GEMM2: for each output block O = (ia, s1, s2, ib):
+//   4. grouped GEMM2, one problem per sector ia: the output blocks O = (ia,
+//      s1, s2, ib) that share ia (and so Lg_ia) are stacked along N, so one
+//      problem computes every
 //        out_O[a, b] = sum_{wl, a'} Lg_ia[a, (wl, a')] Vg_O[b, (wl, a')]
-//      Lg_ia concatenates the L blocks (ia, wl, ja(wl)) along K (plan time)
+//      Lg_ia concatenates the L blocks (ia, wl, ja(wl)) along K (plan time);
+//      the stacked result lands in a staging buffer and an unpack pass
+//      writes the packed output blocks.
+// Stacking fills the 128-row / 128- or 64-column tiles that single small
+// sector blocks would leave mostly empty (the total chi = 2048, 31-sector
+// workload: 558 -> 361 GEMM1 tiles, 200 -> 116 GEMM2 tiles).
 #include <cuda_bf16.h>
 #include <string.h>
 
@@ -45,12 +54,13 @@ struct SplitJob {
   int64_t src_off;   // element offset of the block in the packed FP32 source
   int64_t rows, K, ld_src, Kp;
   int64_t dst_off;   // bf16 element offset of plane 0 in the destination arena
+  int64_t plane;     // elements between piece planes (the block may sit inside a stack)
 };
 
 __global__ void k_bs_split(const SplitJob* __restrict__ jobs, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
   const SplitJob j = jobs[blockIdx.y];
-  const int64_t plane = j.rows * j.Kp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < plane; i += (int64_t)gridDim.x * blockDim.x) {
+  const int64_t plane = j.plane, n = j.rows * j.Kp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t r = i / j.Kp, k = i - r * j.Kp;
     __nv_bfloat16 h, m, l;
     if (k < j.K) {
@@ -93,6 +103,22 @@ __global__ void k_bs_split_slice(const SliceJob* __restrict__ jobs, const float*
   }
 }
 
+// stacked GEMM2 result -> packed output block: out[dst_off + r*cols + c] =
+// stage[src_off + r*ld_src + c], or 0 where src_off < 0 (no GEMM writes it)
+struct UnpackJob {
+  int64_t src_off, ld_src, rows, cols, dst_off;
+};
+
+__global__ void k_bs_unpack(const UnpackJob* __restrict__ jobs, const float* __restrict__ stage,
+                            float* __restrict__ out) {
+  const UnpackJob j = jobs[blockIdx.y];
+  const int64_t n = j.rows * j.cols;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / j.cols, c = i - r * j.cols;
+    out[j.dst_off + i] = j.src_off >= 0 ? stage[j.src_off + r * j.ld_src + c] : 0.f;
+  }
+}
+
 template <typename Job>
 tci_status run_jobs(tci_context ctx, const std::vector<Job>& jobs, int64_t max_work,
                     void (*kern)(const Job*, const float*, __nv_bfloat16*), const float* src, __nv_bfloat16* dst) {
@@ -127,10 +153,42 @@ struct WWCoef {
   float ww[BS_DW * 4 * BS_DW * 4];   // [wl][s][wr][t]
 };
 
+// The nonzero W.W coefficients by output (wl, s): terms [start[o], start[o+1])
+// multiply input q[k] = t * Dw + wr by c[k] (the Heisenberg MPO has 30 of 400).
+// used: bit q set when input q enters some term.
+struct WWSparse {
+  float c[BS_DW * 4 * BS_DW * 4];
+  unsigned char q[BS_DW * 4 * BS_DW * 4];
+  unsigned char start[4 * BS_DW + 1];
+  unsigned int used;
+};
+
+WWSparse ww_sparse(const WWCoef& w) {
+  WWSparse sp;
+  memset(&sp, 0, sizeof sp);
+  int k = 0;
+  for (int o = 0; o < 4 * BS_DW; ++o) {
+    sp.start[o] = (unsigned char)k;
+    for (int wr = 0; wr < BS_DW; ++wr)
+      for (int t = 0; t < 4; ++t) {
+        const float c = w.ww[(o * BS_DW + wr) * 4 + t];
+        if (c == 0.f) continue;
+        sp.c[k] = c;
+        sp.q[k] = (unsigned char)(t * BS_DW + wr);
+        sp.used |= 1u << (t * BS_DW + wr);
+        ++k;
+      }
+  }
+  sp.start[4 * BS_DW] = (unsigned char)k;
+  return sp;
+}
+
 // One block per (task, 32 a' x 8 b tile).  The tile of every existing input
-// (t, wr) is staged in shared memory with coalesced row reads (8 contiguous
-// b per a' row), then each thread forms the outputs of one (a', b) pair and
-// writes them with a' fastest (contiguous along GEMM2's K dimension).
+// (t, wr) that some coefficient uses is staged in shared memory with
+// coalesced row reads (8 contiguous b per a' row), then each thread forms the
+// outputs of one (a', b) pair from the nonzero coefficients only and writes
+// them with a' fastest (contiguous along GEMM2's K dimension).  Outputs whose
+// coefficients are all zero are not written: the plan zeroes them once.
 struct WWTile {
   int task;
   int a0, b0;
@@ -139,7 +197,7 @@ struct WWTile {
 constexpr int kWA = 32, kWB = 8;
 
 __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ tasks, const WWTile* __restrict__ tiles,
-                                                     const WWCoef coef, __nv_bfloat16* __restrict__ V) {
+                                                     const WWSparse sp, __nv_bfloat16* __restrict__ V) {
   __shared__ float Us[4 * BS_DW][kWA][kWB + 1];
   __shared__ WWTask T;   // the task's pointers and strides, read once per block
   const WWTile tl = tiles[blockIdx.x];
@@ -149,8 +207,9 @@ __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ 
     for (int i = threadIdx.x; i < (int)(sizeof(WWTask) / sizeof(int64_t)); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < 4 * BS_DW * kWA * kWB; idx += kWA * kWB) {
-    const int bl = idx % kWB, al = (idx / kWB) % kWA, q = idx / (kWB * kWA);
+  for (int q = 0; q < 4 * BS_DW; ++q) {   // uniform: only inputs some coefficient uses
+    if (!((sp.used >> q) & 1u)) continue;
+    const int bl = threadIdx.x % kWB, al = threadIdx.x / kWB;
     const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
     float v = 0.f;
     if (T.u[q] && ap < T.na && b < T.nb) v = T.u[q][ap * T.ldu[q] + b];
@@ -160,29 +219,20 @@ __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ 
   const int al = threadIdx.x % kWA, bl = threadIdx.x / kWA;
   const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
   if (ap >= T.na || b >= T.nb) return;
-  float in[4 * BS_DW];
-#pragma unroll
-  for (int q = 0; q < 4 * BS_DW; ++q) in[q] = Us[q][al][bl];
-#pragma unroll
-  for (int wl = 0; wl < BS_DW; ++wl)
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      const int o = wl * 4 + s;
-      if (T.v[o] < 0) continue;
-      float acc = 0.f;
-#pragma unroll
-      for (int wr = 0; wr < BS_DW; ++wr)
-#pragma unroll
-        for (int t = 0; t < 4; ++t) acc = fmaf(coef.ww[((wl * 4 + s) * BS_DW + wr) * 4 + t], in[t * BS_DW + wr], acc);
-      const __nv_bfloat16 h = __float2bfloat16_rn(acc);
-      const float r1 = acc - __bfloat162float(h);
-      const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-      const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-      const int64_t off = T.v[o] + b * T.ldv[o] + ap;
-      V[off] = h;
-      V[T.plane[o] + off] = m;
-      V[2 * T.plane[o] + off] = l;
-    }
+  for (int o = 0; o < 4 * BS_DW; ++o) {
+    const int k0 = sp.start[o], k1 = sp.start[o + 1];
+    if (k0 == k1 || T.v[o] < 0) continue;
+    float acc = 0.f;
+    for (int k = k0; k < k1; ++k) acc = fmaf(sp.c[k], Us[sp.q[k]][al][bl], acc);
+    const __nv_bfloat16 h = __float2bfloat16_rn(acc);
+    const float r1 = acc - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    const int64_t off = T.v[o] + b * T.ldv[o] + ap;
+    V[off] = h;
+    V[T.plane[o] + off] = m;
+    V[2 * T.plane[o] + off] = l;
+  }
 }
 
 __global__ void k_bs_ww_precompute(const double* __restrict__ W, float* __restrict__ out) {
@@ -215,6 +265,9 @@ struct tci_bs_plan_s {
   float* U = nullptr;         // GEMM1 outputs
   float* out_stage = nullptr; // GEMM2 writes here (the group table holds fixed pointers)
   SplitJob* d_psi_jobs = nullptr;
+  UnpackJob* d_unpack = nullptr;   // staged GEMM2 result -> packed output blocks
+  int n_unpack = 0;
+  int64_t max_out_block = 0;
   WWTask* d_tasks = nullptr;
   WWTile* d_tiles = nullptr;
   int n_tiles = 0;
@@ -226,6 +279,7 @@ struct tci_bs_plan_s {
   tci_split_group* g2n = nullptr;
   int bn = 128;
   WWCoef coef;
+  WWSparse ww_sp;   // the nonzero coefficients (the W.W kernel's argument)
   int64_t n_gemm1 = 0, n_gemm2 = 0;
   double tensor_flops = 0.0;
   tci_graph graph;              // captured split -> GEMM1 -> W.W -> GEMM2
@@ -350,29 +404,40 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     S.Kp = pad8(S.K);
     if (S.K) S.off = take(3 * S.rows * S.Kp);
   }
-  // psi pieces per block: [3][dim ia][pad8(dim ib)]
-  std::vector<int64_t> Ppiece(P.size());
+  // psi pieces stacked per sector ib' (GEMM1's A operand): [3][sum of dim ia'][pad8(dim ib')],
+  // block k at rows [prow[k], + dim ia') of every plane
+  std::vector<int64_t> pstack_rows(nsec, 0), pstack_off(nsec, 0), prow(P.size());
+  for (size_t k = 0; k < P.size(); ++k) {
+    prow[k] = pstack_rows[P[k].j];
+    pstack_rows[P[k].j] += dim[P[k].i];
+  }
+  for (int j = 0; j < nsec; ++j)
+    if (pstack_rows[j]) pstack_off[j] = take(3 * pstack_rows[j] * pad8(dim[j]));
   std::vector<SplitJob> psi_jobs;
   for (size_t k = 0; k < P.size(); ++k) {
     const BsBlock& B = P[k];
     const int64_t K = dim[B.j], Kp = pad8(K);
-    Ppiece[k] = take(3 * dim[B.i] * Kp);
-    psi_jobs.push_back({B.off, dim[B.i], K, K, Kp, Ppiece[k]});
+    psi_jobs.push_back({B.off, dim[B.i], K, K, Kp, pstack_off[B.j] + prow[k] * Kp, pstack_rows[B.j] * Kp});
     p->max_psi_plane = std::max(p->max_psi_plane, dim[B.i] * Kp);
   }
-  // Vg per output block O (same structure as psi): [3][dim ib][Lg[ia].Kp]
-  std::vector<int64_t> Vpiece(P.size());
+  // Vg stacked per sector ia (GEMM2's B operand): [3][sum of dim ib][Lg[ia].Kp],
+  // output block k at rows [vcol[k], + dim ib) of every plane
+  std::vector<int64_t> vstack_rows(nsec, 0), vstack_off(nsec, 0), vcol(P.size());
   for (size_t k = 0; k < P.size(); ++k) {
-    const BsBlock& O = P[k];
-    Vpiece[k] = take(3 * dim[O.j] * std::max<int64_t>(Lg[O.i].Kp, 8));
+    vcol[k] = vstack_rows[P[k].i];
+    vstack_rows[P[k].i] += dim[P[k].j];
   }
-  // U per psi block: [dim ia'][Rg[ib'].rows] FP32
-  std::vector<int64_t> Uoff(P.size());
+  for (int ia = 0; ia < nsec; ++ia)
+    if (vstack_rows[ia] && Lg[ia].K) vstack_off[ia] = take(3 * vstack_rows[ia] * Lg[ia].Kp);
+  // U stacked like psi: [sum of dim ia'][Rg[ib'].rows] FP32 per sector ib'
+  std::vector<int64_t> ustack_off(nsec, 0), Uoff(P.size());
   int64_t uelems = 0;
-  for (size_t k = 0; k < P.size(); ++k) {
-    Uoff[k] = uelems;
-    uelems += (al256(dim[P[k].i] * Rg[P[k].j].rows * 4)) / 4;
-  }
+  for (int j = 0; j < nsec; ++j)
+    if (pstack_rows[j] && Rg[j].rows) {
+      ustack_off[j] = uelems;
+      uelems += al256(pstack_rows[j] * Rg[j].rows * 4) / 4;
+    }
+  for (size_t k = 0; k < P.size(); ++k) Uoff[k] = ustack_off[P[k].j] + prow[k] * Rg[P[k].j].rows;
   tci_status s;
   if ((s = tci_dev_alloc(ctx, std::max<int64_t>(arena, 8) * 2, &p->arena)) != TCI_OK) return fail(s);
   if ((s = tci_dev_alloc(ctx, std::max<int64_t>(uelems, 1) * 4, (void**)&p->U)) != TCI_OK) return fail(s);
@@ -401,11 +466,10 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
 
   // ---------------------------------------------------------------- GEMM1 group
   std::vector<tci_split_problem> g1;
-  for (size_t k = 0; k < P.size(); ++k) {
-    const BsBlock& B = P[k];
-    const Stack& S = Rg[B.j];
-    if (!S.rows) continue;
-    g1.push_back({A + Ppiece[k], A + S.off, dim[B.i], S.rows, S.Kp, p->U + Uoff[k], 1, S.rows, 1});
+  for (int j = 0; j < nsec; ++j) {
+    const Stack& S = Rg[j];
+    if (!S.rows || !pstack_rows[j]) continue;
+    g1.push_back({A + pstack_off[j], A + S.off, pstack_rows[j], S.rows, S.Kp, p->U + ustack_off[j], 1, S.rows, 1});
   }
   for (auto& q : g1) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
   if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1, 128)) != TCI_OK) return fail(s);
@@ -449,9 +513,9 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
       auto it = task_of.find((long)ja * 4096 + O.j);
       if (it == task_of.end()) continue;            // no U feeds this V sub-block: it stays zero
       WWTask& T = tasks[it->second];
-      T.v[wl * 4 + sidx] = Vpiece[k] + S.row_off[wl];
+      T.v[wl * 4 + sidx] = vstack_off[O.i] + vcol[k] * S.Kp + S.row_off[wl];
       T.ldv[wl * 4 + sidx] = S.Kp;
-      T.plane[wl * 4 + sidx] = dim[O.j] * S.Kp;
+      T.plane[wl * 4 + sidx] = vstack_rows[O.i] * S.Kp;
     }
   }
   p->n_tasks = (int)tasks.size();
@@ -472,21 +536,38 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W tiles"));
   }
   // ---------------------------------------------------------------- GEMM2 group
+  // the group table holds fixed pointers: GEMM2 writes the plan's staging
+  // buffer, [dim ia][sum of dim ib] row-major per sector ia (same total size as
+  // the packed output), and the unpack pass writes the caller's output blocks
+  std::vector<int64_t> ostage_off(nsec, -1);
+  int64_t ost = 0;
+  for (int ia = 0; ia < nsec; ++ia)
+    if (vstack_rows[ia] && Lg[ia].K) {
+      ostage_off[ia] = ost;
+      ost += dim[ia] * vstack_rows[ia];
+    }
+  if ((s = tci_dev_alloc(ctx, std::max<int64_t>(ost, 1) * 4, (void**)&p->out_stage)) != TCI_OK) return fail(s);
   std::vector<tci_split_problem> g2;
-  std::vector<int64_t> out_off;
+  for (int ia = 0; ia < nsec; ++ia) {
+    const Stack& S = Lg[ia];
+    if (ostage_off[ia] < 0) continue;
+    g2.push_back({A + S.off, A + vstack_off[ia], dim[ia], vstack_rows[ia], S.Kp, p->out_stage + ostage_off[ia], 1,
+                  vstack_rows[ia], 1});
+  }
+  std::vector<UnpackJob> unpack;
   for (size_t k = 0; k < P.size(); ++k) {
     const BsBlock& O = P[k];
-    const Stack& S = Lg[O.i];
-    if (!S.K) continue;
-    // C is filled in per apply (output pointer); store the packed offset for now in C.
-    g2.push_back({A + S.off, A + Vpiece[k], dim[O.i], dim[O.j], S.Kp, (void*)(uintptr_t)(O.off * 4), 1, dim[O.j], 1});
+    const int64_t so = ostage_off[O.i];
+    unpack.push_back({so >= 0 ? so + vcol[k] : -1, vstack_rows[O.i], dim[O.i], dim[O.j], O.off});
+    p->max_out_block = std::max(p->max_out_block, dim[O.i] * dim[O.j]);
   }
-  // the group table holds fixed pointers: GEMM2 writes the plan's output staging buffer
-  if ((s = tci_dev_alloc(ctx, std::max<int64_t>(psi_elems, 1) * 4, (void**)&p->out_stage)) != TCI_OK) return fail(s);
-  for (auto& q : g2) q.C = (char*)p->out_stage + (uintptr_t)q.C;
-  // output blocks that no GEMM writes stay zero
-  e = cudaMemsetAsync(p->out_stage, 0, std::max<int64_t>(psi_elems, 1) * 4, ctx->stream);
-  if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan memset"));
+  p->n_unpack = (int)unpack.size();
+  if (!unpack.empty()) {
+    if ((s = tci_dev_alloc(ctx, sizeof(UnpackJob) * unpack.size(), (void**)&p->d_unpack)) != TCI_OK) return fail(s);
+    e = cudaMemcpyAsync(p->d_unpack, unpack.data(), sizeof(UnpackJob) * unpack.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: unpack jobs"));
+  }
   for (auto& q : g2) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
   if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2, 128)) != TCI_OK) return fail(s);
   if ((s = tci_split_group_create(ctx, (int)g2.size(), g2.data(), &p->g2n, 64)) != TCI_OK) return fail(s);
@@ -508,6 +589,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
     tci_dev_free(d);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W"));
+    p->ww_sp = ww_sparse(p->coef);
   }
   // ---------------------------------------------------------------- algorithmic flops
   {
@@ -552,7 +634,7 @@ extern "C" tci_status tci_bs_plan_destroy(tci_bs_plan* pp) {
   tci_split_group_destroy(p->g2);
   tci_split_group_destroy(p->g1n);
   tci_split_group_destroy(p->g2n);
-  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles};
+  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles, p->d_unpack};
   for (void* b : bufs) tci_dev_free(b);
   p->magic = 0;
   delete p;
@@ -570,6 +652,14 @@ extern "C" int64_t tci_bs_psi_size(tci_bs_plan p) {
   return p->psi_elems;
 }
 
+static tci_status launch_unpack(tci_bs_plan p, float* out) {
+  if (!p->n_unpack) return TCI_OK;
+  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_out_block + 255) / 256)), (unsigned)p->n_unpack);
+  k_bs_unpack<<<grid, 256, 0, p->ctx->stream>>>(p->d_unpack, p->out_stage, out);
+  TCI_CUDA(p->ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
 static tci_status bs_launch_all(void* arg) {
   tci_bs_plan p = (tci_bs_plan)arg;
   tci_context ctx = p->ctx;
@@ -579,7 +669,7 @@ static tci_status bs_launch_all(void* arg) {
   }
   TCI_CUDA(ctx, cudaGetLastError());
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
-  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
+  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->ww_sp, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   return TCI_OK;
@@ -609,12 +699,11 @@ extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* 
     }
     TCI_CUDA(ctx, cudaGraphLaunch(p->graph.exec, ctx->stream));
   }
-  TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
-  return TCI_OK;
+  return launch_unpack(p, out);
 }
 
 // tci_bs_heff_apply with CUDA events between the stages: ms[0..3] = psi split,
-// grouped GEMM1, W.W tasks, grouped GEMM2 (+ the output copy).  Synchronises.
+// grouped GEMM1, W.W tasks, grouped GEMM2 (+ the unpack pass).  Synchronises.
 extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, float* out, float* ms) {
   if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_heff_apply_timed: invalid plan");
   tci_context ctx = p->ctx;
@@ -630,10 +719,10 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->coef, (__nv_bfloat16*)p->arena);
+  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->ww_sp, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
-  TCI_CUDA(ctx, cudaMemcpyAsync(out, p->out_stage, sizeof(float) * p->psi_elems, cudaMemcpyDeviceToDevice, ctx->stream));
+  TCI_TRY(launch_unpack(p, out));
   TCI_CUDA(ctx, cudaEventRecord(ev[4], ctx->stream));
   TCI_CUDA(ctx, cudaEventSynchronize(ev[4]));
   for (int i = 0; i < 4; ++i) cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
