@@ -47,6 +47,9 @@ constexpr int kBsMagic = 0xb5b5e001;
 namespace {
 
 int64_t pad8(int64_t x) { return (x + 7) / 8 * 8; }
+// FP32 row stride of a GEMM output: a multiple of 4 elements keeps every row
+// 16-byte aligned, so the epilogue stores rows as float4 vectors
+int64_t pad4(int64_t x) { return (x + 3) / 4 * 4; }
 int64_t al256(int64_t bytes) { return (bytes + 255) / 256 * 256; }
 
 // split FP32 rows into bf16 piece planes [3][rows][Kp] (zero in k >= K)
@@ -429,15 +432,15 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   }
   for (int ia = 0; ia < nsec; ++ia)
     if (vstack_rows[ia] && Lg[ia].K) vstack_off[ia] = take(3 * vstack_rows[ia] * Lg[ia].Kp);
-  // U stacked like psi: [sum of dim ia'][Rg[ib'].rows] FP32 per sector ib'
+  // U stacked like psi: [sum of dim ia'][pad4(Rg[ib'].rows)] FP32 per sector ib'
   std::vector<int64_t> ustack_off(nsec, 0), Uoff(P.size());
   int64_t uelems = 0;
   for (int j = 0; j < nsec; ++j)
     if (pstack_rows[j] && Rg[j].rows) {
       ustack_off[j] = uelems;
-      uelems += al256(pstack_rows[j] * Rg[j].rows * 4) / 4;
+      uelems += al256(pstack_rows[j] * pad4(Rg[j].rows) * 4) / 4;
     }
-  for (size_t k = 0; k < P.size(); ++k) Uoff[k] = ustack_off[P[k].j] + prow[k] * Rg[P[k].j].rows;
+  for (size_t k = 0; k < P.size(); ++k) Uoff[k] = ustack_off[P[k].j] + prow[k] * pad4(Rg[P[k].j].rows);
   tci_status s;
   if ((s = tci_dev_alloc(ctx, std::max<int64_t>(arena, 8) * 2, &p->arena)) != TCI_OK) return fail(s);
   if ((s = tci_dev_alloc(ctx, std::max<int64_t>(uelems, 1) * 4, (void**)&p->U)) != TCI_OK) return fail(s);
@@ -469,7 +472,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   for (int j = 0; j < nsec; ++j) {
     const Stack& S = Rg[j];
     if (!S.rows || !pstack_rows[j]) continue;
-    g1.push_back({A + pstack_off[j], A + S.off, pstack_rows[j], S.rows, S.Kp, p->U + ustack_off[j], 1, S.rows, 1});
+    g1.push_back({A + pstack_off[j], A + S.off, pstack_rows[j], S.rows, S.Kp, p->U + ustack_off[j], 1, pad4(S.rows), 1});
   }
   for (auto& q : g1) p->tensor_flops += 2.0 * p->products * q.M * q.N * q.Kp;
   if ((s = tci_split_group_create(ctx, (int)g1.size(), g1.data(), &p->g1, 128)) != TCI_OK) return fail(s);
@@ -500,7 +503,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
       const int ib = Rb[S.blk[wr]].i;
       WWTask& T = task(B.i, ib);
       T.u[t * BS_DW + wr] = p->U + Uoff[k] + S.row_off[wr];
-      T.ldu[t * BS_DW + wr] = S.rows;
+      T.ldu[t * BS_DW + wr] = pad4(S.rows);
     }
   }
   for (size_t k = 0; k < P.size(); ++k) {           // outputs
@@ -537,14 +540,14 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   }
   // ---------------------------------------------------------------- GEMM2 group
   // the group table holds fixed pointers: GEMM2 writes the plan's staging
-  // buffer, [dim ia][sum of dim ib] row-major per sector ia (same total size as
-  // the packed output), and the unpack pass writes the caller's output blocks
+  // buffer, [dim ia][pad4(sum of dim ib)] row-major per sector ia, and the
+  // unpack pass writes the caller's output blocks
   std::vector<int64_t> ostage_off(nsec, -1);
   int64_t ost = 0;
   for (int ia = 0; ia < nsec; ++ia)
     if (vstack_rows[ia] && Lg[ia].K) {
       ostage_off[ia] = ost;
-      ost += dim[ia] * vstack_rows[ia];
+      ost += dim[ia] * pad4(vstack_rows[ia]);
     }
   if ((s = tci_dev_alloc(ctx, std::max<int64_t>(ost, 1) * 4, (void**)&p->out_stage)) != TCI_OK) return fail(s);
   std::vector<tci_split_problem> g2;
@@ -552,13 +555,13 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     const Stack& S = Lg[ia];
     if (ostage_off[ia] < 0) continue;
     g2.push_back({A + S.off, A + vstack_off[ia], dim[ia], vstack_rows[ia], S.Kp, p->out_stage + ostage_off[ia], 1,
-                  vstack_rows[ia], 1});
+                  pad4(vstack_rows[ia]), 1});
   }
   std::vector<UnpackJob> unpack;
   for (size_t k = 0; k < P.size(); ++k) {
     const BsBlock& O = P[k];
     const int64_t so = ostage_off[O.i];
-    unpack.push_back({so >= 0 ? so + vcol[k] : -1, vstack_rows[O.i], dim[O.i], dim[O.j], O.off});
+    unpack.push_back({so >= 0 ? so + vcol[k] : -1, pad4(vstack_rows[O.i]), dim[O.i], dim[O.j], O.off});
     p->max_out_block = std::max(p->max_out_block, dim[O.i] * dim[O.j]);
   }
   p->n_unpack = (int)unpack.size();

@@ -32,8 +32,10 @@
 //                 columns 32*((w-2)/4)..+31
 //   warp 18     : watcher: performs every mbarrier wait of the MMA issuer
 //                 (stage landed, accumulator buffers drained) and hands the
-//                 k-blocks of each stage pair (0,1), (2,3) to warp 1 through a
-//                 named barrier per pair, one sync per two k-blocks.
+//                 k-blocks to warp 1 in groups through named barriers: a
+//                 group ends at an odd stage or at a tile's last k-block (so
+//                 mostly stage pairs (0,1), (2,3)), one sync per group, the
+//                 barrier named by the group's first stage.
 // The MMA issuer itself never waits on shared memory inside its loop: while
 // the tensor cores stream operands from shared memory, a shared-memory read
 // whose result the issuing thread needs stalls it for about as long as the
@@ -41,15 +43,18 @@
 // (measured: 64 -> 80 clocks per 128x128x16 MMA with one mbarrier test per
 // 12 MMAs); a named-barrier sync costs far less, and one per stage pair
 // instead of one per stage took the chi = 2048 GEMM from 1.55 to 1.40 ms
-// (two pairs in flight keep the TMA latency hidden).
+// (two pairs in flight keep the TMA latency hidden).  A group never spans two
+// tiles, so a short tile's last k-block is not held back until the next
+// tile's first one lands.
 // Named-barrier use cannot deadlock or skew: the MMA warp and the watcher both
 // run the CTA's whole tile / k-block sequence (after an abort the MMA warp
-// still synchronises and commits each k-block, issuing no MMAs), the MMA warp
-// syncing before each even stage and the watcher arriving after each odd
-// stage or after the CTA's last k-block, so the counts match; the watcher's
-// arrival for a pair's use u comes after the MMA warp passed its sync for use
-// u - 1: normally because a stage is refilled only after the MMAs that read it
-// completed (full implies empty), and after an abort because the watcher then
+// still synchronises and commits each k-block, issuing no MMAs) with the same
+// group boundaries, the MMA warp syncing at each group's first k-block and the
+// watcher arriving after its last, so the counts match.  Barrier s is used at
+// most once per pass over the stages; the watcher's arrival for its use in
+// pass r follows its wait for stage s's refill in pass r, which follows the
+// MMA warp's commit of stage s in pass r - 1 (full implies empty), so the MMA
+// warp has passed every earlier sync on barrier s; after an abort the watcher
 // waits for that commit on the stage's empty barrier itself.  Every wait of
 // the watcher is bounded.
 // Every wait is bounded (2 s, or the context's wait limit); on expiry the
@@ -71,33 +76,33 @@ namespace {
 constexpr int TBM = 128;
 constexpr int TBN = 128;
 constexpr int TBK = 32;   // bf16 elements = 64 B rows, SWIZZLE_64B
-constexpr int NSTAGE = 4;
 constexpr int PIECE_A = TBM * TBK * 2;   // 8 KB
-constexpr int PIECE_B = TBN * TBK * 2;   // 8 KB
 constexpr int STAGE_A = 3 * PIECE_A;
-constexpr int STAGE_B = 3 * PIECE_B;
-constexpr int STAGE_BYTES = STAGE_A + STAGE_B;   // 48 KB
-constexpr int TMEM_COLS = 512;                   // D1 x2, X x2 (128 columns each)
 constexpr int NEPI = 16;                         // epilogue warps (4 per TMEM lane quadrant)
 constexpr int kWatchWarp = 2 + NEPI;             // waits on the MMA issuer's barriers for it
 constexpr int NTHREADS = 64 + 32 * NEPI + 32;
-constexpr int kStageBar = 1;                     // named barriers kStageBar + p hand stage pair p to the MMA warp
+constexpr int kStageBar = 1;                     // named barrier kStageBar + s hands the group starting at stage s
 constexpr int kMaxDots = 24;                     // fused dot products: basis vectors + 1 (sum of squares)
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
-constexpr int COLS_PER_WARP = TBN / (NEPI / 4);  // columns drained by one epilogue warp
 
 // Tile width BN of a launch: 128 (every launch) or 64 (grouped launches of
 // narrow problems, a tile shape the autotuner may choose).  The accumulators
-// take 4 x BN tensor-memory columns (D1 and X, each double-buffered).
+// take 4 x BN tensor-memory columns (D1 and X, each double-buffered).  The
+// narrow tile's smaller stages buy a deeper operand pipeline (6 stages of
+// 36 KB against 4 of 48 KB): short problems are bound by TMA latency.
 template <int BN>
 struct TileN {
   static_assert(BN == 64 || BN == 128, "tile width 64 or 128");
   static constexpr int kPieceB = BN * TBK * 2;
   static constexpr int kStageB = 3 * kPieceB;
   static constexpr int kStageBytes = STAGE_A + kStageB;
+  static constexpr int kStages = BN == 64 ? 6 : 4;   // even: stages are handed over in pairs
   static constexpr int kTmemCols = 4 * BN;
   static constexpr int kCols = BN / (NEPI / 4);
-  static constexpr int kSmem = NSTAGE * kStageBytes + 1024 + 256 + NEPI * kMaxDots * 8;
+  static constexpr int kSmem = kStages * kStageBytes + 1024 + 256 + NEPI * kMaxDots * 8;
+  static_assert(kStages % 2 == 0 && 2 * kStages + 9 <= 32, "barrier block holds the stage barriers");
+  static_assert(kStageBar + kStages <= 15, "named barrier per group start stage");
+  static_assert(kSmem <= 232448, "227 KB of shared memory per CTA");
 };
 
 // One GEMM of a (possibly grouped) launch.  In a grouped launch the table
@@ -230,7 +235,7 @@ __device__ __forceinline__ void named_bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
-// Wait for one accumulation unit, fold its 32-lane x COLS_PER_WARP slice into
+// Wait for one accumulation unit, fold its 32-lane x BN/4-column slice into
 // the double-float running sum (rh + rl), and release the TMEM buffer.  The
 // compensation rl (|rl| <~ 2^-24 |rh| per drain) is kept as packed bfloat16:
 // rounding it to 8 bits costs ~2^-33 |rh| per drain, far below the target,
@@ -274,16 +279,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   static_assert(!(G && DOTS), "fused dot products are for single (non-grouped) FP64 problems");
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* full = (uint64_t*)(smem + NSTAGE * TN::kStageBytes);
-  uint64_t* empty = full + NSTAGE;
-  uint64_t* d1f = empty + NSTAGE;   // D1 buffer full (MMA -> epilogue)
+  uint64_t* full = (uint64_t*)(smem + TN::kStages * TN::kStageBytes);
+  uint64_t* empty = full + TN::kStages;
+  uint64_t* d1f = empty + TN::kStages;   // D1 buffer full (MMA -> epilogue)
   uint64_t* d1e = d1f + 2;          // D1 buffer empty (epilogue -> MMA)
   uint64_t* xf = d1e + 2;
   uint64_t* xe = xf + 2;
   uint64_t* done = xe + 2;
   uint32_t* tmem_slot = (uint32_t*)(done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  double* dacc = (double*)(smem + NSTAGE * TN::kStageBytes + 256);   // [NEPI][kMaxDots] per-warp dot sums
+  double* dacc = (double*)(smem + TN::kStages * TN::kStageBytes + 256);   // [NEPI][kMaxDots] per-warp dot sums
   if (DOTS)
     for (int i = threadIdx.x; i < NEPI * kMaxDots; i += blockDim.x) dacc[i] = 0.0;
 
@@ -291,7 +296,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
+    for (int s = 0; s < TN::kStages; ++s) {
       ptx::mbar_init(ptx::smem_u32(&full[s]), 1);
       ptx::mbar_init(ptx::smem_u32(&empty[s]), 1);
     }
@@ -341,14 +346,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           ptx::tma_load_3d(ptx::smem_u32(sa + STAGE_A), &pr->tmB, fb, kb * TBK, nb * BN, 0);
           issued |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
-          if (++stage == NSTAGE) {
+          if (++stage == TN::kStages) {
             stage = 0;
             phase ^= 1;
           }
         }
       }
       // no copy may still be writing shared memory when the CTA exits
-      for (int s = 0; s < NSTAGE; ++s) {
+      for (int s = 0; s < TN::kStages; ++s) {
         if (!((issued >> s) & 1u)) continue;
         uint64_t t0 = ptx::globaltimer();
         while (!ptx::mbar_try_wait(ptx::smem_u32(&full[s]), (issued_phase >> s) & 1u))
@@ -366,6 +371,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int stage = 0;
     uint32_t u1 = 0, ux = 0;   // D1 / X accumulation-unit counters
     bool live = true;          // false after an abort: keep the barrier sequence, issue nothing
+    bool grp_open = false;     // inside a k-block group the watcher handed over in one sync
     const int kb_d1 = p.kb_d1, kb_x = p.kb_x;   // in registers: the loop reads no memory
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
       if (live && *abort_flag) live = false;   // one shared-memory read per tile
@@ -381,8 +387,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         cx = x_last ? 0 : cx + 1;
         const uint32_t b1 = u1 & 1;
         if (x_first) xbuf = ux & 1;
-        // the watcher saw this stage pair land (and, at unit starts, the buffers drained)
-        if ((stage & 1) == 0) named_bar_sync(kStageBar + (stage >> 1), 64);   // once per stage pair
+        // the watcher saw this group's stages land (and, at unit starts, the buffers drained)
+        if (!grp_open) named_bar_sync(kStageBar + stage, 64);   // once per group
+        grp_open = (stage & 1) == 0 && kb + 1 < nkb;             // the group goes on past this k-block
         if (lane == 0 && !live) {
           ptx::mma_commit(ptx::smem_u32(&empty[stage]));   // the watcher's abort path waits on it
         } else if (lane == 0) {
@@ -417,7 +424,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
         if (d1_last) ++u1;
         if (x_last) ++ux;
-        if (++stage == NSTAGE) stage = 0;
+        if (++stage == TN::kStages) stage = 0;
       }
     }
     if (lane == 0) {
@@ -438,7 +445,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     int stage = 0;
     uint32_t phase = 0;
     uint32_t u1 = 0, ux = 0;
-    int use = 0;   // k-blocks seen so far (use of the current stage = use / NSTAGE)
+    int use = 0;   // k-blocks seen so far (use of the current stage = use / TN::kStages)
+    bool w_open = false;   // inside a group (its barrier is named by its first stage, grp_start)
+    int grp_start = 0;
     bool ok = true;
     for (int tile = blockIdx.x; tile < num_tiles; tile += gridDim.x) {
       const int nkb = tile_kblocks<G>(tile, &single, p);
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           if (ok && x_first)
             ok = ptx::mbar_wait_spin(ptx::smem_u32(&xe[ux & 1]), ((ux >> 1) & 1) ^ 1, abort_flag, p.wait_ns);
           if (ok) ok = ptx::mbar_wait_spin(ptx::smem_u32(&full[stage]), phase, abort_flag, p.wait_ns);
-          if (!ok && use >= NSTAGE) {
+          if (!ok && use >= TN::kStages) {
             // abort: arrive only once the MMA warp committed this stage's previous use
             // (it has passed that sync; the commit lands when the tensor cores finish)
             const uint64_t t0 = ptx::globaltimer();
@@ -465,12 +474,14 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
         }
         __syncwarp();
-        // one arrival per stage pair: after its second stage, or after the CTA's last k-block
-        const bool last_kb = kb + 1 == nkb && tile + (int)gridDim.x >= num_tiles;
-        if ((stage & 1) == 1 || last_kb) named_bar_arrive(kStageBar + (stage >> 1), 64);
+        // one arrival per group, after its last k-block: an odd stage or the tile's last k-block
+        if (!w_open) grp_start = stage;
+        const bool grp_end = (stage & 1) == 1 || kb + 1 == nkb;
+        if (grp_end) named_bar_arrive(kStageBar + grp_start, 64);
+        w_open = !grp_end;
         if (d1_last) ++u1;
         if (x_last) ++ux;
-        if (++stage == NSTAGE) {
+        if (++stage == TN::kStages) {
           stage = 0;
           phase ^= 1;
         }
