@@ -41,10 +41,16 @@ LANCZOS_STEPS = 20
 SEED = 20251223
 
 
-# DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec, the mean
-# of GEMM1 (956 MB) and GEMM2 (1554 MB) from one ncu capture of this kernel build with the
-# autotuned tile order (profiles/dram_heff_chi2048.md).  Set to None whenever the kernel changes.
-GEMM_DRAM_BYTES_PER_LAUNCH = None
+# DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec by tile
+# raster, the mean of GEMM1 (1440 MB) and GEMM2 (1660 MB) from one ncu capture of this
+# kernel build (profiles/dram_heff_chi2048.md); a raster not captured reports null.  Emptied
+# whenever the kernel changes.
+GEMM_DRAM_BYTES_PER_LAUNCH = {8: 1549.8e6}
+
+
+# algorithmic bytes per GEMM launch at chi = 2048: the mean of GEMM1 (operands 227 MB, U^T
+# 336 MB) and GEMM2 (operands 629 MB, out 134 MB)
+GEMM_ALGO_BYTES_PER_LAUNCH = 663e6
 
 
 def heff_flops(chi: int) -> float:
@@ -516,9 +522,14 @@ def run_gpu(args):
     tensor_tflops = 6.0 * gemm_flops(CHI) / (gemm_ms * 1e-3) / 1e12
     roofline = {"bound": "tensor", "kernel": "k_split_bf16_gemm", "achieved": tensor_tflops,
                 "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": tensor_tflops / peaks["bf16_tflops"],
-                "traffic": GEMM_DRAM_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch (DRAM read + write)",
+                "traffic": GEMM_DRAM_BYTES_PER_LAUNCH.get(int(tuned[2])),
+                "traffic_unit": "bytes per launch (DRAM read + write), captured at the tuned tile raster",
+                "traffic_algorithmic": GEMM_ALGO_BYTES_PER_LAUNCH,
                 "peak_source": f"{peak_src} bf16 burst",
                 "flops_per_launch": 6.0 * gemm_flops(CHI),
+                # the same launches run inside the seconds-long solve loop under the power cap,
+                # the condition of the sustained cuBLAS figure: reported beside, not instead
+                "frac_of_sustained_peak": tensor_tflops / peaks["bf16_tflops_sustained"],
                 "note": "achieved counts the 6 BF16 piece products per FP64-equivalent multiply-add"}
 
     # ---- e2e: the same step from host memory: psi copied in from pinned host memory, the
