@@ -42,10 +42,10 @@ SEED = 20251223
 
 
 # DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec by tile
-# raster, the mean of GEMM1 (1440 MB) and GEMM2 (1660 MB) from one ncu capture of this
-# kernel build (profiles/dram_heff_chi2048.md); a raster not captured reports null.  Emptied
-# whenever the kernel changes.
-GEMM_DRAM_BYTES_PER_LAUNCH = {8: 1549.8e6}
+# raster, the mean of GEMM1 and GEMM2 from ncu captures of this kernel build
+# (profiles/dram_heff_chi2048.md: raster 8 1440 / 1660 MB, raster 16 948 / 1555 MB); a raster
+# not captured reports null.  Emptied whenever the kernel changes.
+GEMM_DRAM_BYTES_PER_LAUNCH = {8: 1549.8e6, 16: 1251.3e6}
 
 
 # algorithmic bytes per GEMM launch at chi = 2048: the mean of GEMM1 (operands 227 MB, U^T
@@ -866,6 +866,9 @@ def run_profile_case(args):
     plan = tci.HeffPlan(ctx, t(L), t(W), t(R), precision="split_bf16")
     out = torch.empty_like(dpsi)
     tuned = plan.autotune(dpsi, out, max_chunk_k=256)   # the configuration the bench runs
+    if args.profile_config:   # a pinned configuration (e.g. one whose DRAM bytes the bench reports)
+        c = [int(x) for x in args.profile_config.split(",")]
+        plan.set_config(c[0], c[1], c[2], plan.get_config()[3])
     if args.profile_lanczos:
         for _ in range(args.warmup + args.steps):
             plan.lanczos(dpsi, LANCZOS_STEPS, True, out)
@@ -891,6 +894,7 @@ def main():
                     help="with --profile-chi: run 20-step Lanczos solves instead of single matvecs")
     ap.add_argument("--profile-tebd", action="store_true", help="run only the batched TEBD workload (for ncu)")
     ap.add_argument("--profile-bs", action="store_true", help="run only the block-sparse matvec workload (for ncu)")
+    ap.add_argument("--profile-config", default="", help="chunk_k,xchunk_k,raster for --profile-chi (default: tuned)")
     ap.add_argument("--dmrg", action="store_true", help="time two-site DMRG sweeps (device vs oracle) instead")
     ap.add_argument("--dmrg-sites", type=int, default=32)
     ap.add_argument("--dmrg-chi", type=int, default=64)

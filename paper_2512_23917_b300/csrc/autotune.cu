@@ -10,9 +10,10 @@
 //            for plans whose GEMMs have many tiles per dimension,
 //   bn       tile width in {128, 64} for grouped plans (narrow tiles for
 //            problems of few columns: less padding, half the MMA work per tile).
-// Every candidate is timed over three rounds in alternating order and keeps
-// its best time (one pass favours whichever candidates run before the power
-// cap lowers the clock).  Among the candidates within 2 % of the fastest the
+// The candidates first run in turn for at least 250 ms (the clock settles
+// under the power cap), then every candidate is timed over four rounds in
+// alternating order and keeps its median (the best time would favour whichever
+// candidates ran while the GPU was cool).  Among the candidates within 2 % of the fastest the
 // choice is stable: a grouped tile order (fewer DRAM re-reads), then the
 // longer accumulation chunks (fewer drains), then the wider tile.
 // Winners are cached in memory per (plan kind, shape, device) and, when the
@@ -109,13 +110,31 @@ tci_status tci_autotune(tci_context ctx, const std::string& key_in, int max_chun
   double bms = 1e300;
   tci_gemm_cfg bcfg = cands.front();
   tci_status s = TCI_OK;
-  // Three rounds over all candidates, alternating direction, each candidate's
-  // best time kept: a single pass favours whichever candidates run first,
-  // before the power cap lowers the clock.
-  std::vector<double> times(cands.size(), 1e300);
-  for (const auto& cfg : cands)
-    if ((s = run(arg, cfg)) != TCI_OK) break;   // warm-up (and kernel attributes)
-  for (int round = 0; round < 3 && s == TCI_OK; ++round) {
+  // The clock falls by 15-20 % while a GPU heats into its power cap, so the
+  // candidates are first run in turn until at least kWarmMs of work has passed
+  // (and at most 40 passes), then timed over four rounds in alternating
+  // direction, and each candidate keeps the median of its rounds: a minimum
+  // over rounds would favour whichever candidates ran while the GPU was cool.
+  constexpr float kWarmMs = 250.f;
+  std::vector<std::vector<double>> rounds(cands.size());
+  float warm_total = 0.f;
+  for (int pass = 0; pass < 40 && s == TCI_OK; ++pass) {   // warm-up (and kernel attributes)
+    cudaEventRecord(e0, ctx->stream);
+    for (const auto& cfg : cands)
+      if ((s = run(arg, cfg)) != TCI_OK) break;
+    cudaEventRecord(e1, ctx->stream);
+    if (s != TCI_OK) break;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) {
+      s = tci_cuda_fail(ctx, e, "autotune warm-up");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    warm_total += ms;
+    if (warm_total >= kWarmMs) break;
+  }
+  for (int round = 0; round < 4 && s == TCI_OK; ++round) {
     for (size_t q = 0; q < cands.size() && s == TCI_OK; ++q) {
       const size_t i = (round & 1) ? cands.size() - 1 - q : q;
       float total = 0.f;
@@ -130,9 +149,16 @@ tci_status tci_autotune(tci_context ctx, const std::string& key_in, int max_chun
         break;
       }
       cudaEventElapsedTime(&total, e0, e1);
-      times[i] = std::min(times[i], (double)total / reps);
+      rounds[i].push_back((double)total / reps);
     }
   }
+  std::vector<double> times(cands.size(), 1e300);
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (!rounds[i].empty()) {
+      std::vector<double> r = rounds[i];
+      std::sort(r.begin(), r.end());
+      times[i] = r.size() % 2 ? r[r.size() / 2] : 0.5 * (r[r.size() / 2 - 1] + r[r.size() / 2]);
+    }
   double tmin = 1e300;
   for (size_t i = 0; i < cands.size() && s == TCI_OK; ++i) tmin = std::min(tmin, times[i]);
   // stable choice among the near-fastest: a grouped tile order (re-reads far fewer
