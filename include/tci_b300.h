@@ -669,7 +669,10 @@ double tci_tebd_tensor_flops(tci_tebd_plan plan);
  * max_chunk_k: the measured relative error of the chi = 2048 matvec is
  * 2.2e-7 / 4.3e-7 / 8.8e-7), the cross-product chunk (1024/4096) and the
  * tile order (m-fastest or groups of 8/16 m-blocks) -- and keep the fastest
- * in the plan.  Results are cached per (plan kind, shape, device) in memory
+ * in the plan: the candidates first run in turn for at least 250 ms (the clock
+ * settles under the power cap), then each keeps the median of four timed
+ * rounds, and near ties (2 %) go to the grouped tile order (16, then 8), the
+ * longer chunks and the wider tile.  Results are cached per (plan kind, shape, device) in memory
  * and, when TCI_AUTOTUNE_CACHE names a file, in that file (read first, so a
  * cached shape is not timed again); the W.W kernel variant is timed too
  * (not cached).  chosen (may be NULL) receives 3 ints: chunk_k, xchunk_k,
