@@ -192,6 +192,8 @@ WWSparse ww_sparse(const WWCoef& w) {
 // outputs of one (a', b) pair from the nonzero coefficients only and writes
 // them with a' fastest (contiguous along GEMM2's K dimension).  Outputs whose
 // coefficients are all zero are not written: the plan zeroes them once.
+// Offsets inside a task are 32-bit (the plan checks they fit); only the
+// task's base pointers and plane strides are 64-bit.
 struct WWTile {
   int task;
   int a0, b0;
@@ -210,18 +212,21 @@ __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ 
     for (int i = threadIdx.x; i < (int)(sizeof(WWTask) / sizeof(int64_t)); i += blockDim.x) dst[i] = src[i];
   }
   __syncthreads();
-  for (int q = 0; q < 4 * BS_DW; ++q) {   // uniform: only inputs some coefficient uses
-    if (!((sp.used >> q) & 1u)) continue;
+  const int na = (int)T.na, nb = (int)T.nb;
+  {
     const int bl = threadIdx.x % kWB, al = threadIdx.x / kWB;
-    const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
-    float v = 0.f;
-    if (T.u[q] && ap < T.na && b < T.nb) v = T.u[q][ap * T.ldu[q] + b];
-    Us[q][al][bl] = v;
+    const int ap = tl.a0 + al, b = tl.b0 + bl;
+    const bool in = ap < na && b < nb;
+    for (int q = 0; q < 4 * BS_DW; ++q) {   // uniform: only inputs some coefficient uses
+      if (!((sp.used >> q) & 1u)) continue;
+      const float* u = T.u[q];
+      Us[q][al][bl] = (u && in) ? u[ap * (int)T.ldu[q] + b] : 0.f;
+    }
   }
   __syncthreads();
   const int al = threadIdx.x % kWA, bl = threadIdx.x / kWA;
-  const int64_t ap = tl.a0 + al, b = tl.b0 + bl;
-  if (ap >= T.na || b >= T.nb) return;
+  const int ap = tl.a0 + al, b = tl.b0 + bl;
+  if (ap >= na || b >= nb) return;
   for (int o = 0; o < 4 * BS_DW; ++o) {
     const int k0 = sp.start[o], k1 = sp.start[o + 1];
     if (k0 == k1 || T.v[o] < 0) continue;
@@ -231,10 +236,11 @@ __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ 
     const float r1 = acc - __bfloat162float(h);
     const __nv_bfloat16 m = __float2bfloat16_rn(r1);
     const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-    const int64_t off = T.v[o] + b * T.ldv[o] + ap;
-    V[off] = h;
-    V[T.plane[o] + off] = m;
-    V[2 * T.plane[o] + off] = l;
+    __nv_bfloat16* vo = V + T.v[o] + (b * (int)T.ldv[o] + ap);
+    const int64_t pl = T.plane[o];
+    vo[0] = h;
+    vo[pl] = m;
+    vo[2 * pl] = l;
   }
 }
 
@@ -522,7 +528,13 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     }
   }
   p->n_tasks = (int)tasks.size();
-  for (auto& T : tasks) p->max_task_elems = std::max(p->max_task_elems, T.na * T.nb);
+  for (auto& T : tasks) {
+    p->max_task_elems = std::max(p->max_task_elems, T.na * T.nb);
+    for (int q = 0; q < 4 * BS_DW; ++q)   // the W.W kernel's 32-bit offsets inside a task
+      if ((T.u[q] && T.na * T.ldu[q] + T.nb >= ((int64_t)1 << 31)) ||
+          (T.v[q] >= 0 && T.nb * T.ldv[q] + T.na >= ((int64_t)1 << 31)))
+        return fail(tci_fail(ctx, TCI_ERR_UNSUPPORTED, "bs_heff_plan_create: sector blocks exceed 32-bit offsets"));
+  }
   std::vector<WWTile> wtiles;
   for (int t = 0; t < (int)tasks.size(); ++t)
     for (int64_t a0 = 0; a0 < tasks[t].na; a0 += kWA)
