@@ -303,13 +303,14 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
   }
 }
 
-// Pass 1 from the double-float shadow of the basis (FP64 vectors): partials of
+// Pass 1 from the double-float shadow of the basis (FP64 vectors; vector g's hi
+// plane at Vs + 2 g ldv, its lo plane ldv after it): partials of
 // <Vs_g, w>, g < nv <= G, into part rows g, and with SQ of ||w||^2; w (FP64) is
 // split into an FP32 pair once per element on the integer pipes (f32_split2,
 // within 2^-47 |w_i| where |w_i| >= 2^-126) and every product and sum runs in
 // double-float arithmetic on the FP32 pipes: no FP64 instruction per element.
 template <int G, bool SQ>
-__global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float2* __restrict__ Vs, int64_t ldv, int nv,
+__global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float* __restrict__ Vs, int64_t ldv, int nv,
                                                     const double* __restrict__ w, int64_t n,
                                                     double* __restrict__ part, double* __restrict__ part_sq,
                                                     const double* __restrict__ ctrl) {
@@ -323,7 +324,9 @@ __global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float2* __restrict_
     // g >= nv hold zeros and add nothing
     float2 vv[G];
 #pragma unroll
-    for (int g = 0; g < G; ++g) vv[g] = g < nv ? __ldg(&Vs[(int64_t)g * ldv + i]) : make_float2(0.f, 0.f);
+    for (int g = 0; g < G; ++g)
+      vv[g] = g < nv ? make_float2(__ldg(&Vs[2 * g * ldv + i]), __ldg(&Vs[(2 * g + 1) * ldv + i]))
+                     : make_float2(0.f, 0.f);
     const float2 x = shadow_of(__ldg(&w[i]));
 #pragma unroll
     for (int g = 0; g < G; ++g) ArithDF::acc(a[g], vv[g], x);
@@ -511,18 +514,30 @@ constexpr int kInNone = 0;     // the matvec reads the FP64 basis vector itself
 constexpr int kInPieces = 1;   // bfloat16 pieces of fl32(v), K-major [3][rows][Kp], zero in k >= cols
 constexpr int kInF64 = 2;      // v as FP64 (double-float basis, FP64 matvec)
 
-// two consecutive shadow elements (i even: one 16-byte store)
-__device__ __forceinline__ void store_shadow2(float2* p, double y0, double y1) {
+// Where a pass writes the shadow of the vector it writes: the hi and lo planes
+// (hi == nullptr: no shadow).
+struct ShadowOut {
+  float* hi;
+  float* lo;
+};
+
+// two consecutive shadow elements (i even: one 8-byte store per plane)
+__device__ __forceinline__ void store_shadow2(ShadowOut vs, int64_t i, double y0, double y1) {
   const float2 a = shadow_of(y0), b = shadow_of(y1);
-  *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+  *reinterpret_cast<float2*>(vs.hi + i) = make_float2(a.x, b.x);
+  *reinterpret_cast<float2*>(vs.lo + i) = make_float2(a.y, b.y);
 }
 
 template <class A, int MODE>
 __device__ __forceinline__ void emit(typename A::V y, int64_t i, int64_t r, int64_t k, typename A::V* vn,
                                      __nv_bfloat16* pieces, int64_t Kp, int64_t plane, double* x64,
-                                     float2* vs = nullptr) {
+                                     ShadowOut vs = {nullptr, nullptr}) {
   vn[i] = y;
-  if (vs) vs[i] = shadow_of(A::to_double(y));
+  if (vs.hi) {
+    const float2 sh = shadow_of(A::to_double(y));
+    vs.hi[i] = sh.x;
+    vs.lo[i] = sh.y;
+  }
   if (MODE == kInPieces) split3_store(pieces + r * Kp + k, plane, A::f32(y));
   if (MODE == kInF64) x64[i] = A::to_double(y);
 }
@@ -533,7 +548,7 @@ template <class A, int MODE>
 __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w, typename A::V* __restrict__ vn,
                                              int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
                                              int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
-                                             int j, const double* __restrict__ gate, float2* __restrict__ vs) {
+                                             int j, const double* __restrict__ gate, ShadowOut vs) {
   if (scal[OFF_CTRL] != 0.0 || gate[0] != 0.0) return;
   const typename A::Coef c = A::coef(1.0 / scal[OFF_BETA + j]);
   const int64_t plane = rows * Kp;
@@ -547,7 +562,7 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
             const double2 x = *reinterpret_cast<const double2*>(w + i);
             const double y0 = A::mul(x.x, c), y1 = A::mul(x.y, c);
             *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
-            if (vs) store_shadow2(vs + i, y0, y1);
+            if (vs.hi) store_shadow2(vs, i, y0, y1);
             if (MODE == kInPieces) split3_store2(pieces + r * Kp + k, plane, A::f32(y0), A::f32(y1));
           } else {
             split3_store2(pieces + r * Kp + k, plane, 0.f, 0.f);
@@ -569,12 +584,15 @@ __global__ void __launch_bounds__(NT) k_next(const typename A::V* __restrict__ w
 
 // Pass 3 folded into the next vector (FP64 vectors): v_{j+1} = (w - V h') /
 // beta_j with the rounding-level terms h'_g v_g summed in FP32 (header);
-// runs where k_post_pass2 chose it.
+// runs where k_post_pass2 chose it.  With the basis shadow (Vh: vector 0's hi
+// plane, vector g's at Vh + g vh_ld) the FP32 basis values are read from its hi
+// planes, which hold exactly f32_trunc of the basis, at half the bytes.
 template <int MODE>
 __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, int64_t ldv, int nv,
                                                   const double* __restrict__ w, double* __restrict__ vn, int64_t rows,
                                                   int64_t cols, __nv_bfloat16* __restrict__ pieces, int64_t Kp,
-                                                  const double* __restrict__ scal, int j, float2* __restrict__ vs) {
+                                                  const double* __restrict__ scal, int j, ShadowOut vs,
+                                                  const float* __restrict__ Vh, int64_t vh_ld) {
   if (scal[OFF_CTRL] != 0.0 || scal[OFF_LO + LO_GFAST] != 0.0) return;
   __shared__ float cf[MAXM];
   const double sc = scal[OFF_LO + LO_SC3];
@@ -590,16 +608,25 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
         if (k < cols) {
           const int64_t i = r * cols + k;
           float s0 = 0.f, s1 = 0.f;
+          if (Vh) {
 #pragma unroll 8
-          for (int g = 0; g < nv; ++g) {
-            const double2 v = *reinterpret_cast<const double2*>(V + (int64_t)g * ldv + i);
-            s0 = __fmaf_rn(cf[g], f32_trunc(v.x), s0);
-            s1 = __fmaf_rn(cf[g], f32_trunc(v.y), s1);
+            for (int g = 0; g < nv; ++g) {
+              const float2 v = *reinterpret_cast<const float2*>(Vh + (int64_t)g * vh_ld + i);
+              s0 = __fmaf_rn(cf[g], v.x, s0);
+              s1 = __fmaf_rn(cf[g], v.y, s1);
+            }
+          } else {
+#pragma unroll 8
+            for (int g = 0; g < nv; ++g) {
+              const double2 v = *reinterpret_cast<const double2*>(V + (int64_t)g * ldv + i);
+              s0 = __fmaf_rn(cf[g], f32_trunc(v.x), s0);
+              s1 = __fmaf_rn(cf[g], f32_trunc(v.y), s1);
+            }
           }
           const double2 x = *reinterpret_cast<const double2*>(w + i);
           const double y0 = fma(-(double)s0, isc, x.x) * binv, y1 = fma(-(double)s1, isc, x.y) * binv;
           *reinterpret_cast<double2*>(vn + i) = make_double2(y0, y1);
-          if (vs) store_shadow2(vs + i, y0, y1);
+          if (vs.hi) store_shadow2(vs, i, y0, y1);
           if (MODE == kInPieces)
             split3_store2(pieces + r * Kp + k, plane, __double2float_rn(y0), __double2float_rn(y1));
         } else {
@@ -613,8 +640,13 @@ __global__ void __launch_bounds__(NT) k_next_corr(const double* __restrict__ V, 
       if (k < cols) {
         const int64_t i = r * cols + k;
         float sf = 0.f;
+        if (Vh) {
 #pragma unroll 8
-        for (int g = 0; g < nv; ++g) sf = __fmaf_rn(cf[g], f32_trunc(V[(int64_t)g * ldv + i]), sf);
+          for (int g = 0; g < nv; ++g) sf = __fmaf_rn(cf[g], Vh[(int64_t)g * vh_ld + i], sf);
+        } else {
+#pragma unroll 8
+          for (int g = 0; g < nv; ++g) sf = __fmaf_rn(cf[g], f32_trunc(V[(int64_t)g * ldv + i]), sf);
+        }
         const double y = fma(-(double)sf, isc, w[i]) * binv;
         emit<ArithF64, MODE>(y, i, r, k, vn, pieces, Kp, plane, nullptr, vs);
       } else {
@@ -628,7 +660,7 @@ template <class A, int MODE>
 __global__ void __launch_bounds__(NT) k_start(const double* __restrict__ psi, typename A::V* __restrict__ v0,
                                               int64_t rows, int64_t cols, __nv_bfloat16* __restrict__ pieces,
                                               int64_t Kp, double* __restrict__ x64, const double* __restrict__ scal,
-                                              float2* __restrict__ vs) {
+                                              ShadowOut vs) {
   const double inv = 1.0 / sqrt(scal[OFF_CTRL + 3]);
   const int64_t plane = rows * Kp;
   const int64_t kend = MODE == kInPieces ? Kp : cols;
@@ -1152,7 +1184,7 @@ tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
 }
 
 template <int G, bool SQ>
-int dots_shadow_g(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n, double* part,
+int dots_shadow_g(tci_context ctx, const float* Vs, int64_t ldv, int nv, const double* w, int64_t n, double* part,
                   double* part_sq, const double* ctrl) {
   const int grid = pass_grid(ctx, (const void*)k_dots_shadow<G, SQ>, n);
   k_dots_shadow<G, SQ><<<grid, NT, 0, ctx->stream>>>(Vs, ldv, nv, w, n, part, part_sq, ctrl);
@@ -1160,7 +1192,7 @@ int dots_shadow_g(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const 
 }
 
 template <bool SQ>
-int dots_shadow_launch(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n,
+int dots_shadow_launch(tci_context ctx, const float* Vs, int64_t ldv, int nv, const double* w, int64_t n,
                        double* part, double* part_sq, const double* ctrl) {
   if (nv <= 4) return dots_shadow_g<4, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
   if (nv <= 8) return dots_shadow_g<8, SQ>(ctx, Vs, ldv, nv, w, n, part, part_sq, ctrl);
@@ -1170,13 +1202,13 @@ int dots_shadow_launch(tci_context ctx, const float2* Vs, int64_t ldv, int nv, c
 }
 
 // run_dots (v0 = 0) from the basis shadow
-tci_status run_dots_shadow(tci_context ctx, const float2* Vs, int64_t ldv, int nv, const double* w, int64_t n,
+tci_status run_dots_shadow(tci_context ctx, const float* Vs, int64_t ldv, int nv, const double* w, int64_t n,
                            double* part, double* out, const double* ctrl, double* sumsq_out) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
   for (int g0 = 0; g0 < nv; g0 += GMAX) {
     const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
     const bool sq = sumsq_out && g0 == 0;
-    const float2* Vb = Vs + (int64_t)g0 * ldv;
+    const float* Vb = Vs + 2 * (int64_t)g0 * ldv;
     double* pb = part + (int64_t)g0 * NBMAX;
     const int grid = sq ? dots_shadow_launch<true>(ctx, Vb, ldv, g, w, n, pb, part_sq, ctrl)
                         : dots_shadow_launch<false>(ctx, Vb, ldv, g, w, n, pb, part_sq, ctrl);
@@ -1275,7 +1307,7 @@ tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int 
 
 template <class A, int MODE>
 void launch_start(tci_context ctx, const double* psi0, typename A::V* v0, int64_t rows, int64_t cols,
-                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, float2* vs) {
+                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, ShadowOut vs) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
   k_start<A, MODE><<<blocks, NT, 0, ctx->stream>>>(psi0, v0, rows, cols, pieces, Kp, x64, S, vs);
 }
@@ -1283,7 +1315,7 @@ void launch_start(tci_context ctx, const double* psi0, typename A::V* v0, int64_
 template <class A, int MODE>
 void launch_next(tci_context ctx, const typename A::V* w, typename A::V* vn, int64_t rows, int64_t cols,
                  __nv_bfloat16* pieces, int64_t Kp, double* x64, const double* S, int j, const double* gate,
-                 float2* vs) {
+                 ShadowOut vs) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
   k_next<A, MODE><<<blocks, NT, 0, ctx->stream>>>(w, vn, rows, cols, pieces, Kp, x64, S, j, gate, vs);
 }
@@ -1291,9 +1323,9 @@ void launch_next(tci_context ctx, const typename A::V* w, typename A::V* vn, int
 template <int MODE>
 void launch_next_corr(tci_context ctx, const double* V, int64_t ldv, int nv, const double* w, double* vn,
                       int64_t rows, int64_t cols, __nv_bfloat16* pieces, int64_t Kp, const double* S, int j,
-                      float2* vs) {
+                      ShadowOut vs, const float* Vh, int64_t vh_ld) {
   const int blocks = (int)(rows < (int64_t)NBMAX * 8 ? rows : (int64_t)NBMAX * 8);
-  k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j, vs);
+  k_next_corr<MODE><<<blocks, NT, 0, ctx->stream>>>(V, ldv, nv, w, vn, rows, cols, pieces, Kp, S, j, vs, Vh, vh_ld);
 }
 
 // One cluster of the largest size the device runs (16 CTAs where
@@ -1348,10 +1380,11 @@ tci_status launch_step_small(tci_context ctx, double* V, int64_t ldv, double* w,
 // plan; kInF64 for double-float vectors on an FP64 plan).
 template <class A, int MODE>
 // Vs (FP64 vectors on a split plan, re-orthogonalised; else null): the
-// double-float shadow of the basis, written with each basis vector and read
-// by pass 1.
+// double-float shadow of the basis, written with each basis vector (vector g:
+// hi plane at Vs + 2 g ldv, lo plane ldv after it), read by pass 1 (both
+// planes) and by the pass-3 correction (hi planes).
 tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol,
-                       float2* Vs) {
+                       float* Vs) {
   using Vt = typename A::V;
   tci_context ctx = p->ctx;
   // a complex plan runs on the real form: C128 vectors as interleaved FP64 pairs
@@ -1378,7 +1411,8 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   k_sumsq<<<NBMAX, NT, 0, ctx->stream>>>(psi0, n, part);
   k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
   if (kDF || !reorth) Vs = nullptr;
-  launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S, Vs);
+  launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S,
+                        ShadowOut{Vs, Vs ? Vs + ldv : nullptr});
   TCI_CUDA(ctx, cudaGetLastError());
   for (int j = 0; j < nsteps; ++j) {
     Vt* vj = V + (int64_t)j * ldv;
@@ -1442,11 +1476,12 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
     if (j + 1 < nsteps) {
       Vt* vn = V + (int64_t)(j + 1) * ldv;
-      float2* vsn = Vs ? Vs + (int64_t)(j + 1) * ldv : nullptr;
+      float* vsh = Vs ? Vs + 2 * (int64_t)(j + 1) * ldv : nullptr;
+      const ShadowOut vsn{vsh, vsh ? vsh + ldv : nullptr};
       launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl,
                            vsn);
       if constexpr (kF32Terms) {
-        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j, vsn);
+        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j, vsn, Vs, 2 * ldv);
       }
     }
     TCI_CUDA(ctx, cudaGetLastError());
@@ -1485,7 +1520,7 @@ struct SolveArgs {
   double tol;
   int arith;
   bool split;
-  float2* Vs;
+  float* Vs;
 };
 
 // One solve's launches on p->ctx->stream (the body a graph captures).
@@ -1554,7 +1589,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     TCI_TRY(tci_dev_alloc(ctx, sizeof(float2) * ldv * p->lz_cap, &p->lz_Vs));
     p->lz_vs_cap = p->lz_cap;
   }
-  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, shadow ? (float2*)p->lz_Vs : nullptr};
+  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, shadow ? (float*)p->lz_Vs : nullptr};
   bool done = false;
   p->lz_last_graph = 0;
   if (!p->cplx && p->lz_graphs) {
