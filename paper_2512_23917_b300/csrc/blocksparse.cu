@@ -293,6 +293,7 @@ struct tci_bs_plan_s {
   double tensor_flops = 0.0;
   tci_graph graph;              // captured split -> GEMM1 -> W.W -> GEMM2
   const float* cap_psi = nullptr;
+  float* cap_out = nullptr;     // the unpack's destination (null: stop after GEMM2, e.g. while tuning)
 };
 
 struct BsBlock {
@@ -687,6 +688,7 @@ static tci_status bs_launch_all(void* arg) {
   if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->ww_sp, (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
+  if (p->cap_out) TCI_TRY(launch_unpack(p, p->cap_out));
   return TCI_OK;
 }
 
@@ -697,24 +699,30 @@ extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* 
   TciVerboseScope vs(ctx, "bs_heff_apply");
   if (!psi || !out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_apply: NULL buffer");
   p->cap_psi = psi;
+  p->cap_out = out;
+  if (!p->n_psi_jobs || !p->n_unpack) return bs_launch_all(p);
   if (!p->graph.exec) {
     // first call: run eagerly (sets kernel attributes), then capture the sequence
     TCI_TRY(bs_launch_all(p));
-    if (p->n_psi_jobs) TCI_TRY(tci_graph_capture(ctx, &p->graph, bs_launch_all, p, {(const void*)k_bs_split}));
-  } else {
-    if (p->n_psi_jobs) {
-      const SplitJob* jobs = p->d_psi_jobs;
-      __nv_bfloat16* dst = (__nv_bfloat16*)p->arena;
-      void* args[3] = {(void*)&jobs, (void*)&psi, (void*)&dst};
-      cudaKernelNodeParams kp;
-      TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(p->graph.nodes[0], &kp));
-      kp.kernelParams = args;
-      kp.extra = nullptr;
-      TCI_CUDA(ctx, cudaGraphExecKernelNodeSetParams(p->graph.exec, p->graph.nodes[0], &kp));
-    }
-    TCI_CUDA(ctx, cudaGraphLaunch(p->graph.exec, ctx->stream));
+    return tci_graph_capture(ctx, &p->graph, bs_launch_all, p, {(const void*)k_bs_split, (const void*)k_bs_unpack});
   }
-  return launch_unpack(p, out);
+  // replay with this call's psi (the split's input) and out (the unpack's output)
+  const SplitJob* jobs = p->d_psi_jobs;
+  __nv_bfloat16* dst = (__nv_bfloat16*)p->arena;
+  const UnpackJob* ujobs = p->d_unpack;
+  const float* stage = p->out_stage;
+  void* sargs[3] = {(void*)&jobs, (void*)&psi, (void*)&dst};
+  void* uargs[3] = {(void*)&ujobs, (void*)&stage, (void*)&out};
+  void** argv[2] = {sargs, uargs};
+  for (int i = 0; i < 2; ++i) {
+    cudaKernelNodeParams kp;
+    TCI_CUDA(ctx, cudaGraphKernelNodeGetParams(p->graph.nodes[i], &kp));
+    kp.kernelParams = argv[i];
+    kp.extra = nullptr;
+    TCI_CUDA(ctx, cudaGraphExecKernelNodeSetParams(p->graph.exec, p->graph.nodes[i], &kp));
+  }
+  TCI_CUDA(ctx, cudaGraphLaunch(p->graph.exec, ctx->stream));
+  return TCI_OK;
 }
 
 // tci_bs_heff_apply with CUDA events between the stages: ms[0..3] = psi split,
@@ -765,6 +773,7 @@ tci_status bs_run_cfg(void* a, const tci_gemm_cfg& cfg) {
   t->p->raster = cfg.raster;
   t->p->bn = cfg.bn;
   t->p->cap_psi = t->psi;
+  t->p->cap_out = nullptr;   // candidates stop after GEMM2: the caller's output is not touched
   return bs_launch_all(t->p);
 }
 }  // namespace

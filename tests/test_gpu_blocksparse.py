@@ -72,15 +72,18 @@ def test_blocksparse_graph_replay_with_new_buffers(ctx, tci):
                           to_dev(inp["W"]))
     shapes = {k: (dims[k[0]], dims[k[3]]) for k in st["psi"]}
     rng = np.random.default_rng(5)
+    keep = []   # every call's buffers stay alive, so each call gets new input and output addresses
     for call in range(4):
         psi_blocks = {k: rng.standard_normal(v.shape).astype(np.float32) for k, v in inp["psi"].items()}
         psi = to_dev(tci.pack_blocks(psi_blocks, st["psi"]))
         out = torch.full_like(psi, float("nan"))
+        keep.append((psi, out))
         plan.apply(psi, out)
         torch.cuda.synchronize()
         got = tci.unpack_blocks(out.cpu().numpy(), st["psi"], shapes)
         ref, _ = o_bs.bs_heff_apply(dict(inp, psi=psi_blocks))
         assert blocks_err(got, ref) < 1e-6, call
+    assert len({o.data_ptr() for _, o in keep}) == len(keep)
 
 
 @pytest.mark.parametrize("total,qmax,sigma,seed", [(64, 5, 2.0, 3), (97, 15, 5.0, 5), (2048, 15, 5.0, 20251223)])
