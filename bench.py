@@ -275,7 +275,8 @@ def measure_tebd(tci, ctx, dev, peaks, with_oracle: bool):
     pg = t(np.concatenate([g.ravel() for g in G]))
     th = torch.empty(sum(4 * c * c for c in chis), dtype=torch.complex64, device=dev)
     plan = tci.TebdPlan(ctx, chis)
-    tuned = plan.autotune(pa, pb, pg, th, max_chunk_k=256)
+    # theta's error target is 1e-5 (the dense matvec's 1e-6): the hi*hi chunk may go to 512
+    tuned = plan.autotune(pa, pb, pg, th, max_chunk_k=512)
     for _ in range(3):
         plan.apply(pa, pb, pg, th)
     stream = torch.cuda.current_stream(dev)
@@ -843,7 +844,7 @@ def run_profile_tebd(args):
     th = torch.empty(sum(4 * c * c for c in chis), dtype=torch.complex64, device="cuda")
     ctx = tci.Context(0, precision="split_bf16")
     plan = tci.TebdPlan(ctx, chis)
-    tuned = plan.autotune(pa, pb, pg, th, max_chunk_k=256)
+    tuned = plan.autotune(pa, pb, pg, th, max_chunk_k=512)
     for _ in range(args.warmup + args.steps):
         plan.apply(pa, pb, pg, th)
     torch.cuda.synchronize()

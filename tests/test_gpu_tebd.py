@@ -134,3 +134,22 @@ def test_tebd_misaligned_gate_is_rejected(ctx, tci):
     with pytest.raises(tci.TciError) as ei:
         plan.apply(pa, pb, pg, th)
     assert ei.value.status_name == "TCI_ERR_INVALID_ARG"
+
+
+def test_tebd_config_256_bonds_chunk512(ctx, tci):
+    """The 256-bond batch with a 512-deep hi*hi accumulation chunk (the TEBD row's tuner may pick
+    it: theta's bound is 1e-5) stays within 1e-5 of the oracle, aggregate and worst bond."""
+    chis, A, B, G = tebd_inputs(256, seed=20251223)
+    ctx.set_split_chunks(512, 4096)
+    try:
+        got, _ = run_tebd(tci, ctx, chis, A, B, G)
+    finally:
+        ctx.set_split_chunks(256, 1024)
+    num = den = worst = 0.0
+    for g_, a, b, gg in zip(got, A, B, G):
+        ref = o_tebd.theta(a, b, gg)
+        e = np.sum(np.abs(g_ - ref) ** 2)
+        num += e
+        den += np.sum(np.abs(ref) ** 2)
+        worst = max(worst, np.sqrt(e / np.sum(np.abs(ref) ** 2)))
+    assert np.sqrt(num / den) < 1e-5 and worst < 1e-5
