@@ -598,7 +598,10 @@ tci_status tci_heff_lanczos_graph_info(tci_heff_plan plan, int64_t* info);
  * operand layout once, so the caller may free them after creation.
  * Arithmetic: the context precision (must be SPLIT_BF16 or SPLIT_BF16_3).
  * Every block GEMM of one matvec stage runs in a single grouped persistent
- * launch.  Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision), ALLOC, CUDA. */
+ * launch, the blocks that share a sector stacked into one GEMM problem.
+ * Errors: INVALID_ARG, UNSUPPORTED (NATIVE precision, or sector blocks whose
+ * offsets exceed 32 bits in the W.W step: a sector dimension times five sector
+ * dimensions beyond 2^31), ALLOC, CUDA. */
 tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const int32_t* sector_charge,
                                    const int64_t* sector_dim, const int32_t* phys_charge,
                                    const int32_t* mpo_charge, const float* L_packed,
@@ -615,7 +618,8 @@ double tci_bs_heff_flops(tci_bs_plan plan);
 int64_t tci_bs_psi_size(tci_bs_plan plan);
 /* Profiling form of tci_bs_heff_apply: stage_ms[0..3] (host) receive the
  * device times of the psi split, grouped GEMM1, W.W tasks and grouped GEMM2
- * (with the output copy).  Synchronises. */
+ * (with the unpack of its staged result into the packed output blocks).
+ * Synchronises. */
 tci_status tci_bs_heff_apply_timed(tci_bs_plan plan, const float* psi, float* out, float* stage_ms);
 /* BF16 tensor-core flops the two grouped launches execute per matvec
  * (2 x products x M N Kp summed over block GEMMs). */
