@@ -491,6 +491,17 @@ def run_gpu(args):
     torch.cuda.synchronize()
     lanczos_df_ms = e0.elapsed_time(e1)
     plan.set_lanczos_arith("f64")
+    # ---- the same solve with double-float Gram-Schmidt dot products (FP64 vectors), opt-in
+    plan.set_lanczos_shadow_dots(True)
+    plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    res_dfd = plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lanczos_dfd_ms = e0.elapsed_time(e1)
+    plan.set_lanczos_shadow_dots(False)
     # ---- the same solve with the second Gram-Schmidt pass in every step (CGS2)
     plan.set_gram_schmidt("twice")
     plan.lanczos(dpsi, LANCZOS_STEPS, True, x)
@@ -680,6 +691,9 @@ def run_gpu(args):
             "lanczos_double_float_vectors": {"ms_per_step": lanczos_df_ms, "ritz_value": res_df["theta"],
                                              "ritz_rel_diff_vs_fp64": abs(res_df["theta"] - res["theta"]) / abs(res["theta"])
                                              if res else None},
+            "lanczos_double_float_dots": {"ms_per_step": lanczos_dfd_ms, "ritz_value": res_dfd["theta"],
+                                          "ritz_rel_diff_vs_fp64": abs(res_dfd["theta"] - res["theta"]) / abs(res["theta"])
+                                          if res else None},
             "lanczos_vectors": lanczos_vector_roofline(ms_step, mv_only_ms, psi.size, peaks),
             "matvec": {"gflops": F / (mv_only_ms * 1e-3) / 1e9, "ms": mv_only_ms,
                        "stage_ms": {"split": float(st[0]), "gemm1": float(st[1]), "ww": float(st[2]),

@@ -532,31 +532,29 @@ tci_status tci_heff_lanczos_stats(tci_heff_plan plan, int* stats);
  * accumulator drains.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_fused_dots(tci_heff_plan plan, int enable);
 
-/* First Gram-Schmidt projection of tci_lanczos from a double-float copy of
- * the basis (extension; on by default).  On split-BF16 plans with FP64
- * vectors and re-orthogonalisation, each basis vector v_i is also stored as
- * an FP32 pair hi + lo (|v_i - hi - lo| <= 2^-48 |v_i| per element), written
- * by the pass that writes v_i; the first projection's dot products <v_i, w>
- * and ||w||^2 are then summed in double-float arithmetic (products made exact
- * with FMA, Knuth sums) on the FP32 pipes, which makes that pass bound by HBM
- * instead of B300's FP64 rate.  Each dot product agrees with the FP64 pass to
- * about 1e-14 ||v_i|| ||w||; the update passes and the recurrence scalars
- * stay FP64.  The copy takes 8 bytes per basis element of device memory.
- * enable = 0 runs the FP64 pass.  Ignored when tci_heff_set_lanczos_fused_dots
- * is on.  (The second projection's dots, formed in the update pass whose small
- * terms are double-float, are summed in double-float arithmetic from FP32
- * pairs split on the integer pipes; tci_heff_set_lanczos_reduced_terms(0)
- * keeps them FP64.)  Errors: INVALID_ARG, INVALID_CONTEXT. */
+/* Double-float Gram-Schmidt dot products in tci_lanczos (extension; off by
+ * default: every Lanczos dot product is FP64).  On split-BF16 plans with FP64
+ * vectors and re-orthogonalisation, enable = 1 stores each basis vector v_i
+ * also as an FP32 pair hi + lo (|v_i - hi - lo| <= 2^-47 |v_i| per element,
+ * hi and lo in separate planes), written by the pass that writes v_i; the
+ * first projection's dot products <v_i, w> and ||w||^2 are then summed from
+ * that copy in double-float arithmetic (products made exact with FMA, Knuth
+ * sums) on the FP32 pipes, and the second projection's dots (formed in the
+ * update pass whose small terms are double-float) from FP32 pairs split on the
+ * integer pipes; both passes become bound by HBM instead of B300's FP64 rate,
+ * and the pass-3 correction reads the copy's hi planes.  Each dot product
+ * agrees with the FP64 one to about 1e-14 ||v_i|| ||w||, above FP64
+ * rounding; the update passes and the recurrence scalars stay FP64.  The copy
+ * takes 8 bytes per basis element of device memory.  Ignored when
+ * tci_heff_set_lanczos_fused_dots is on.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_shadow_dots(tci_heff_plan plan, int enable);
 
 /* Reduced-precision small update terms of tci_lanczos with FP64 vectors
  * (extension; on by default): the FP32 and double-float evaluations of
  * rounding-level and matvec-error-level Gram-Schmidt terms counted by
  * tci_heff_lanczos_stats [2] to [4], each under an added error below
- * 2^-56 ||w||; in the double-float-terms pass the second projection's dot
- * products are double-float too (about 1e-14 ||v_i|| ||w||).  enable = 0
- * keeps every update term and those dots in FP64 (slower on B300, equal to
- * rounding).  Errors: INVALID_ARG, INVALID_CONTEXT. */
+ * 2^-56 ||w||.  enable = 0 keeps every update term in FP64 (slower on B300,
+ * equal to rounding).  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_reduced_terms(tci_heff_plan plan, int enable);
 
 /* CUDA-graph replay of tci_lanczos on real plans (extension; on by

@@ -640,8 +640,8 @@ class HeffPlan:
         _check(lib.tci_heff_set_lanczos_fused_dots(self.handle, int(bool(enable))), self.ctx.handle)
 
     def set_lanczos_shadow_dots(self, enable: bool):
-        """First projection's dots from the basis's double-float copy on the FP32 pipes (split plans, FP64
-        vectors; on by default), or (False) in FP64."""
+        """Double-float Gram-Schmidt dots on the FP32 pipes (split plans, FP64 vectors; off by default:
+        the Lanczos dot products are FP64)."""
         _check(lib.tci_heff_set_lanczos_shadow_dots(self.handle, int(bool(enable))), self.ctx.handle)
 
     def set_lanczos_reduced_terms(self, enable: bool):

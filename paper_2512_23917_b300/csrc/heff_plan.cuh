@@ -66,7 +66,8 @@ struct tci_heff_plan_s {
   int64_t lz_graph_launches = 0;
   int lz_reduced = 1;   // reduced-precision small update terms (FP32 / double-float) allowed
   int lz_fuse = 0;      // split plans: first Gram-Schmidt projection formed in the matvec's GEMM2 (opt-in)
-  int lz_shadow = 1;    // split plans, FP64 vectors: pass-1 dots from the basis's double-float shadow
+  int lz_shadow = 0;    // split plans, FP64 vectors: double-float Gram-Schmidt dots (opt-in; the
+                        // first projection's from the basis's double-float shadow)
   tci_graph lz_graph;
   std::vector<int64_t> lz_graph_key, lz_last_key;
 };

@@ -45,15 +45,16 @@
 // terms only spare the FP64 pipe (B300 issues FP64 FMAs at ~1/64 of its FP32
 // rate).
 //
-// Dot products.  FP64 in general.  On split plans with FP64 vectors (whose
-// matvec error, ~1e-7 ||w||, dwarfs any rounding of the projections), the
-// first projection's dots <v_i, w> and ||w||^2 are summed in double-float
+// Dot products.  FP64 (the default).  Opt-in on split plans with FP64 vectors
+// (whose matvec error, ~1e-7 ||w||, dwarfs any rounding of the projections):
+// the first projection's dots <v_i, w> and ||w||^2 summed in double-float
 // arithmetic from a double-float shadow of the basis (each v_i also stored
 // as an FP32 pair within 2^-47 |v_i|, written with v_i), and the second
 // projection's dots from FP32 pairs split on the integer pipes in the
 // double-float-terms update pass: both passes then run on the FP32 pipes and
 // are bound by HBM, not by the FP64 rate.  Their error is ~2^-46 ||v_i||
-// ||w||; the recurrence scalars alpha, beta and every update stay FP64.
+// ||w||, above FP64 rounding; the recurrence scalars alpha, beta and every
+// update stay FP64.
 //
 // Pass 1's update contains the three-term recurrence (h_j = alpha_j, h_{j-1}
 // = beta_{j-1} up to rounding), so the step equals the three-term step
@@ -112,6 +113,9 @@ static_assert(OFF_LO + LO_N2 < NSCAL, "scalar layout");
 constexpr double kF32Bound = 2.3283064365386963e-10;   // 2^-32
 constexpr double kDFBound = 9.765625e-4;                // 2^-10
 constexpr int kTermsF64 = 0, kTermsF32 = 1, kTermsDF = 2;
+// the double-float-terms update whose dots are double-float too (opt-in, split
+// plans): runs where the device chose kTermsDF
+constexpr int kTermsDFDots = 3;
 constexpr int64_t kReducedMinN = 1 << 20;               // vector length from which reduced terms are used
 constexpr int kFusedMax = 23;                           // basis vectors whose dots the split GEMM can fuse
 
@@ -341,10 +345,11 @@ __global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float* __restrict__
 
 // w -= sum_{g<nv} coef[v0+g] V_{v0+g}; then (DOTS) partials of <V_{v0+g}, w>
 // into part rows v0 + g and (SUMSQ) partials of ||w||^2 into part_sq.  In the
-// double-float-terms variant (FP64 vectors whose update coefficients are at
-// the matvec-error level: split plans) the dots also run in double-float
-// arithmetic on the FP32 pipes, from the FP32 pairs of f32_split2 (integer
-// pipes) of both operands, so the pass stays HBM-bound; ||w||^2 stays FP64.  TERMS
+// kTermsDFDots variant (double-float terms; opt-in on split plans, whose
+// update coefficients are at the matvec-error level) the dots also run in
+// double-float arithmetic on the FP32 pipes, from the FP32 pairs of f32_split2
+// (integer pipes) of both operands, so the pass stays HBM-bound; ||w||^2 stays
+// FP64.  TERMS
 // (FP64 vectors; v0 = 0, nv = G): the arithmetic of the first nv - 2 terms,
 // kTermsF64, kTermsF32 or kTermsDF with coefficients scaled by lo[LO_SC1]
 // (see the header); with lo the kernel runs only when it is the variant the
@@ -363,10 +368,11 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
       w[i] = A::from_double(__longlong_as_double(0x7ff8000000000000ll));
     return;
   }
+  constexpr int kArith = TERMS == kTermsDFDots ? kTermsDF : TERMS;   // the term arithmetic
   if constexpr (kF64) {
     int mode = kTermsF64;
     if (lo && nv == G && nv > 2 && (int)lo[LO_NS1] == nv - 2) mode = (int)lo[LO_MODE1];
-    if (mode != TERMS) return;
+    if (mode != kArith) return;
   }
   __shared__ typename A::Coef cs[G];
   __shared__ float csf[G], csl[G];
@@ -384,7 +390,7 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
   if constexpr (TERMS != kTermsF64) isc = lo[LO_ISC1];
   __syncthreads();
   constexpr int GD = DOTS ? G : 1;
-  constexpr bool kDFDots = kF64 && DOTS && TERMS == kTermsDF;
+  constexpr bool kDFDots = kF64 && DOTS && TERMS == kTermsDFDots;
   using DA = typename std::conditional<kDFDots, ArithDF, A>::type;
   typename DA::Acc d[GD];
 #pragma unroll
@@ -430,7 +436,7 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
     // the split point is fixed at compile time (terms 0 .. G-3 reduced, the
     // last two FP64): with a run-time bound the compiler would evaluate both
     // arithmetics for every term and select
-    if constexpr (TERMS == kTermsDF) {
+    if constexpr (kArith == kTermsDF) {
       // double-float sum (sh + sl): c v = ch vh + (ch vl + cl vh) with ch vh
       // split exactly by FMA, the leading parts added by TwoSum
       float sh = 0.f, sl = 0.f;
@@ -449,7 +455,7 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
       for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
       y = A::sub_end(t);
       y = fma(-((double)sh + (double)sl), isc, y);
-    } else if constexpr (TERMS == kTermsF32) {
+    } else if constexpr (kArith == kTermsF32) {
       float sf = 0.f;
 #pragma unroll
       for (int g = 0; g < G - 2; ++g) sf = __fmaf_rn(csf[g], f32_trunc(v[g]), sf);
@@ -1245,14 +1251,19 @@ int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, i
 
 // One update pass; with lo (FP64 vectors) all three term arithmetics are
 // launched and the one the device chose runs (the others exit at once).
+// df_dots: the double-float-terms variant forms its dots in double-float.
 template <class A, bool DOTS, bool SUMSQ>
 int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
-                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo,
+                  bool df_dots) {
   if constexpr (std::is_same<A, ArithF64>::value) {
     const int grid = update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
     if (lo && nv > 2) {
       update_exact<A, DOTS, SUMSQ, kTermsF32>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-      update_exact<A, DOTS, SUMSQ, kTermsDF>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      if (DOTS && df_dots)
+        update_exact<A, DOTS, SUMSQ, kTermsDFDots>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      else
+        update_exact<A, DOTS, SUMSQ, kTermsDF>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
     }
     return grid;
   } else {
@@ -1271,29 +1282,30 @@ int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, 
 template <class A>
 tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                       typename A::V* w, int64_t n, double* part, double* dots_out, double* sumsq_out,
-                      const double* ctrl, const double* lo = nullptr) {
+                      const double* ctrl, const double* lo = nullptr, bool df_dots = false) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
   if (lo && v0 != 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (FP32 terms need v0 = 0)");
   int sq_grid = 0;
   if (nv <= GMAX) {
     int grid = 0;
     if (dots_out && sumsq_out)
-      grid = update_launch<A, true, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      grid = update_launch<A, true, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots);
     else if (dots_out)
-      grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots);
     else if (sumsq_out)
-      grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false);
     else
-      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false);
     if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
     sq_grid = grid;
   } else {
     for (int g0 = 0; g0 < nv; g0 += GMAX) {
       const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
       if (g0 + g == nv && sumsq_out && !dots_out)
-        sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr);
+        sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr,
+                                                false);
       else
-        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr);
+        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr, false);
     }
     if (dots_out) {
       TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl, sumsq_out));
@@ -1462,7 +1474,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,
-                            lo1));
+                            lo1, Vs != nullptr));
       k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, (kF32Terms && p->lz_reduced) ? 1 : 0);
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW));
       // second pass skipped: w -= V h with ||w||^2

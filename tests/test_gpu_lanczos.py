@@ -273,8 +273,8 @@ def test_lanczos_fused_dots_equal_separate_pass(ctx, tci, chi, chi_r):
 
 @pytest.mark.parametrize("chi,chi_r", [(64, 64), (75, 61), (256, 256)])
 def test_lanczos_shadow_dots_equal_fp64_pass(ctx, tci, chi, chi_r):
-    """Split-BF16 plan, FP64 vectors: the first projection's dots from the basis's double-float copy
-    (the default) against the FP64 dot pass.  The first step (same v_0, same matvec) agrees to
+    """Split-BF16 plan, FP64 vectors: the double-float Gram-Schmidt dots (opt-in) against the FP64
+    dot passes (the default).  The first step (same v_0, same matvec) agrees to
     ~1e-14; later steps agree only to the split matvec's own error level, because the matvec rounds
     its input to FP32 and a 1e-14 change in v can flip such a rounding; theta stays the oracle's to
     that level either way.  Odd column counts take the element-wise next-vector paths; repeated
@@ -284,6 +284,7 @@ def test_lanczos_shadow_dots_equal_fp64_pass(ctx, tci, chi, chi_r):
     plan = tci.HeffPlan(ctx, to_dev(L), to_dev(W), to_dev(R), precision="split_bf16")
     dpsi = to_dev(psi)
     x = torch.empty_like(dpsi)
+    plan.set_lanczos_shadow_dots(True)
     r1 = plan.lanczos(dpsi, 20, True, x)
     x1 = x.cpu().numpy()
     for _ in range(2):
