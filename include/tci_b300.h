@@ -707,6 +707,19 @@ tci_status tci_bs_set_tile_n(tci_bs_plan plan, int bn);
 int tci_bs_tile_n(tci_bs_plan plan);
 tci_status tci_tebd_set_tile_n(tci_tebd_plan plan, int bn);
 int tci_tebd_tile_n(tci_tebd_plan plan);
+/* W.W pass of a block-sparse plan (the W.W coefficients applied to GEMM1's
+ * outputs, written as GEMM2's bf16 pieces): variant 0 stages 32 a' x 8 b
+ * tiles in shared memory, one output pair per thread; variants 1, 2, 3 give
+ * each thread a 4 a' x 4 b micro-tile, read as 16-byte rows and written as
+ * 8-byte piece vectors without shared memory, for all 20 outputs (1), or for
+ * a quarter (2) or a tenth (3) of them.  All form every element with the
+ * same terms in the same order, so the results agree bit for bit;
+ * tci_bs_autotune times them inside the matvec sequence.  Set (a captured
+ * graph is dropped and re-captured by the next apply) or read it (-1 for an
+ * invalid plan).  Set errors: INVALID_ARG (invalid plan, variant not in
+ * 0..3), INVALID_CONTEXT. */
+tci_status tci_bs_set_ww_variant(tci_bs_plan plan, int variant);
+int tci_bs_ww_variant(tci_bs_plan plan);
 
 #ifdef __cplusplus
 }

@@ -106,6 +106,8 @@ SIGNATURES = [
     ("tci_heff_set_lanczos_shadow_dots", C.c_int, [_p, C.c_int]),
     ("tci_bs_set_tile_n", C.c_int, [_p, C.c_int]),
     ("tci_bs_tile_n", C.c_int, [_p]),
+    ("tci_bs_set_ww_variant", C.c_int, [_p, C.c_int]),
+    ("tci_bs_ww_variant", C.c_int, [_p]),
     ("tci_tebd_set_tile_n", C.c_int, [_p, C.c_int]),
     ("tci_tebd_tile_n", C.c_int, [_p]),
     ("tci_heff_set_lanczos_reduced_terms", C.c_int, [_p, C.c_int]),
@@ -721,6 +723,13 @@ class BsHeffPlan:
 
     def set_tile_n(self, bn: int):
         _check(lib.tci_bs_set_tile_n(self.handle, int(bn)), self.ctx.handle)
+
+    @property
+    def ww_variant(self) -> int:
+        return lib.tci_bs_ww_variant(self.handle)
+
+    def set_ww_variant(self, variant: int):
+        _check(lib.tci_bs_set_ww_variant(self.handle, int(variant)), self.ctx.handle)
 
     def apply_timed(self, psi_packed, out_packed):
         ms = (C.c_float * 4)()

@@ -60,26 +60,45 @@ struct SplitJob {
   int64_t plane;     // elements between piece planes (the block may sit inside a stack)
 };
 
-__global__ void k_bs_split(const SplitJob* __restrict__ jobs, const float* __restrict__ src, __nv_bfloat16* __restrict__ dst) {
-  const SplitJob j = jobs[blockIdx.y];
-  const int64_t plane = j.plane, n = j.rows * j.Kp;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / j.Kp, k = i - r * j.Kp;
-    __nv_bfloat16 h, m, l;
-    if (k < j.K) {
-      const float x = src[j.src_off + r * j.ld_src + k];
-      h = __float2bfloat16_rn(x);
-      const float r1 = x - __bfloat162float(h);
-      m = __float2bfloat16_rn(r1);
-      l = __float2bfloat16_rn(r1 - __bfloat162float(m));
-    } else {
-      h = m = l = __float2bfloat16_rn(0.f);
-    }
-    __nv_bfloat16* d = dst + j.dst_off;
-    d[i] = h;
-    d[plane + i] = m;
-    d[2 * plane + i] = l;
+// The per-call passes (psi split, output unpack) run over a plan-time table of
+// chunks, each a run of one job's work items: the grid is as large as the work,
+// instead of one grid row per job sized for the largest block (most of whose
+// blocks would find nothing to do).  Offsets inside a job are 32-bit (the plan
+// checks they fit).
+struct BsChunk {
+  int job;
+  int start;   // first work item of the chunk inside its job
+};
+constexpr int kSplitOctets = 256;    // work items (8 consecutive k of one row) per split chunk
+constexpr int kUnpackElems = 1024;   // elements per unpack chunk (4 per thread)
+
+// One work item per thread: eight consecutive k of one row, written as one
+// 16-byte vector per piece plane (Kp, the plane stride and the destination
+// offset are multiples of 8 elements).
+__global__ void __launch_bounds__(kSplitOctets) k_bs_split(const BsChunk* __restrict__ chunks,
+                                                           const SplitJob* __restrict__ jobs,
+                                                           const float* __restrict__ src,
+                                                           __nv_bfloat16* __restrict__ dst) {
+  const BsChunk c = chunks[blockIdx.x];
+  const SplitJob j = jobs[c.job];
+  const int oct = (int)(j.Kp / 8);
+  const int item = c.start + threadIdx.x;
+  if (item >= (int)j.rows * oct) return;
+  const int r = item / oct, k0 = (item - r * oct) * 8, K = (int)j.K;
+  const float* s = src + j.src_off + (int64_t)r * j.ld_src;
+  __align__(16) __nv_bfloat16 h[8], m[8], l[8];
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const float x = k0 + e < K ? s[k0 + e] : 0.f;
+    h[e] = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h[e]);
+    m[e] = __float2bfloat16_rn(r1);
+    l[e] = __float2bfloat16_rn(r1 - __bfloat162float(m[e]));
   }
+  __nv_bfloat16* d = dst + j.dst_off + (int64_t)r * j.Kp + k0;
+  *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(h);
+  *reinterpret_cast<uint4*>(d + j.plane) = *reinterpret_cast<const uint4*>(m);
+  *reinterpret_cast<uint4*>(d + 2 * j.plane) = *reinterpret_cast<const uint4*>(l);
 }
 
 // split a FP32 block [rows][K] (row stride ld_src) into the column slice
@@ -112,13 +131,20 @@ struct UnpackJob {
   int64_t src_off, ld_src, rows, cols, dst_off;
 };
 
-__global__ void k_bs_unpack(const UnpackJob* __restrict__ jobs, const float* __restrict__ stage,
-                            float* __restrict__ out) {
-  const UnpackJob j = jobs[blockIdx.y];
-  const int64_t n = j.rows * j.cols;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = i / j.cols, c = i - r * j.cols;
-    out[j.dst_off + i] = j.src_off >= 0 ? stage[j.src_off + r * j.ld_src + c] : 0.f;
+__global__ void __launch_bounds__(256) k_bs_unpack(const BsChunk* __restrict__ chunks,
+                                                   const UnpackJob* __restrict__ jobs,
+                                                   const float* __restrict__ stage, float* __restrict__ out) {
+  const BsChunk c = chunks[blockIdx.x];
+  const UnpackJob j = jobs[c.job];
+  const int n = (int)(j.rows * j.cols), cols = (int)j.cols;
+  const float* sp = stage + (j.src_off >= 0 ? j.src_off : 0);
+  float* op = out + j.dst_off;
+#pragma unroll
+  for (int e = 0; e < kUnpackElems / 256; ++e) {
+    const int i = c.start + e * 256 + threadIdx.x;
+    if (i >= n) break;
+    const int r = i / cols, cc = i - r * cols;
+    op[i] = j.src_off >= 0 ? sp[(int64_t)r * j.ld_src + cc] : 0.f;
   }
 }
 
@@ -186,19 +212,16 @@ WWSparse ww_sparse(const WWCoef& w) {
   return sp;
 }
 
-// One block per (task, 32 a' x 8 b tile).  The tile of every existing input
-// (t, wr) that some coefficient uses is staged in shared memory with
-// coalesced row reads (8 contiguous b per a' row), then each thread forms the
-// outputs of one (a', b) pair from the nonzero coefficients only and writes
-// them with a' fastest (contiguous along GEMM2's K dimension).  Outputs whose
-// coefficients are all zero are not written: the plan zeroes them once.
-// Offsets inside a task are 32-bit (the plan checks they fit); only the
-// task's base pointers and plane strides are 64-bit.
 struct WWTile {
   int task;
   int a0, b0;
 };
 
+// Variant 0: one block per (task, 32 a' x 8 b tile).  The tile of every
+// existing input (t, wr) that some coefficient uses is staged in shared memory
+// with row reads of 8 contiguous b, then each thread forms the outputs of one
+// (a', b) pair from the nonzero coefficients only and writes them with a'
+// fastest (contiguous along GEMM2's K dimension).
 constexpr int kWA = 32, kWB = 8;
 
 __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ tasks, const WWTile* __restrict__ tiles,
@@ -244,6 +267,81 @@ __global__ void __launch_bounds__(kWA * kWB) k_bs_ww(const WWTask* __restrict__ 
   }
 }
 
+// Variants 1-3: one thread per 4 a' x 4 b micro-tile and group of outputs
+// (outputs o = blockIdx.y, + gridDim.y, ...: 1, 4 or 10 groups, so that more
+// threads each run a shorter chain of dependent loads), one block per (task,
+// 64 a' x 32 b tile, output group); no shared memory.  For each output (wl, s) the thread
+// reads its inputs' micro-tiles as 16-byte rows (U sub-blocks start on
+// 16-byte boundaries and their rows are padded to 4), forms the 16 sums with
+// the terms in the same order as variant 0 (so the results are identical),
+// and writes each b row's 4 a' as one 8-byte vector per piece plane (V
+// sub-blocks start on 4-element K offsets).  Rows a' >= na read nothing and
+// write zeros, which land in the zero K padding after the sub-block; columns
+// b >= nb (read from the padded row) are not written.
+constexpr int kW4A = 16, kW4B = 8;   // micro-tiles per block along a' and b (128 threads)
+constexpr int kWVariants = 4;
+constexpr int kWGroups[kWVariants] = {0, 1, 4, 10};   // output groups of variants 1-3
+
+__device__ __forceinline__ uint2 pack4_bf16(float x0, float x1, float x2, float x3) {
+  const __nv_bfloat162 lo = __floats2bfloat162_rn(x0, x1), hi = __floats2bfloat162_rn(x2, x3);
+  return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+}
+
+__global__ void __launch_bounds__(kW4A * kW4B) k_bs_ww4(const WWTask* __restrict__ tasks,
+                                                        const WWTile* __restrict__ tiles, const WWSparse sp,
+                                                        __nv_bfloat16* __restrict__ V) {
+  const WWTile tl = tiles[blockIdx.x];
+  const WWTask* __restrict__ T = tasks + tl.task;
+  const int na = (int)T->na, nb = (int)T->nb;
+  const int a0 = tl.a0 + 4 * (threadIdx.x % kW4A), b0 = tl.b0 + 4 * (threadIdx.x / kW4A);
+  if (a0 >= na || b0 >= nb) return;
+  for (int o = blockIdx.y; o < 4 * BS_DW; o += gridDim.y) {
+    const int k0 = sp.start[o], k1 = sp.start[o + 1];
+    const int64_t vofs = T->v[o];
+    if (k0 == k1 || vofs < 0) continue;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int k = k0; k < k1; ++k) {
+      const int q = sp.q[k];
+      const float* u = T->u[q];
+      const float c = sp.c[k];
+      const int ld = (int)T->ldu[q];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        // a missing input (or a row past na) contributes c * 0, as in variant 0
+        const float4 x = (u && a0 + i < na) ? __ldg(reinterpret_cast<const float4*>(u + (a0 + i) * ld + b0))
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+        acc[i][0] = fmaf(c, x.x, acc[i][0]);
+        acc[i][1] = fmaf(c, x.y, acc[i][1]);
+        acc[i][2] = fmaf(c, x.z, acc[i][2]);
+        acc[i][3] = fmaf(c, x.w, acc[i][3]);
+      }
+    }
+    const int ldv = (int)T->ldv[o];
+    const int64_t pl = T->plane[o];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      if (b0 + j >= nb) break;
+      float h[4], m[4], l[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float x = acc[i][j];
+        h[i] = __bfloat162float(__float2bfloat16_rn(x));
+        const float r1 = x - h[i];
+        m[i] = __bfloat162float(__float2bfloat16_rn(r1));
+        l[i] = r1 - m[i];
+      }
+      __nv_bfloat16* vp = V + vofs + ((b0 + j) * ldv + a0);
+      *reinterpret_cast<uint2*>(vp) = pack4_bf16(h[0], h[1], h[2], h[3]);
+      *reinterpret_cast<uint2*>(vp + pl) = pack4_bf16(m[0], m[1], m[2], m[3]);
+      *reinterpret_cast<uint2*>(vp + 2 * pl) = pack4_bf16(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
 __global__ void k_bs_ww_precompute(const double* __restrict__ W, float* __restrict__ out) {
   // out[((wl*4 + s1*2+s2)*Dw + wr)*4 + t1*2+t2] = sum_wm W[wl,wm,s1,t1] W[wm,wr,s2,t2]
   for (int i = threadIdx.x; i < BS_DW * 4 * BS_DW * 4; i += blockDim.x) {
@@ -275,13 +373,15 @@ struct tci_bs_plan_s {
   float* out_stage = nullptr; // GEMM2 writes here (the group table holds fixed pointers)
   SplitJob* d_psi_jobs = nullptr;
   UnpackJob* d_unpack = nullptr;   // staged GEMM2 result -> packed output blocks
-  int n_unpack = 0;
-  int64_t max_out_block = 0;
+  BsChunk* d_split_chunks = nullptr;
+  BsChunk* d_unpack_chunks = nullptr;
+  int n_unpack = 0, n_split_chunks = 0, n_unpack_chunks = 0;
   WWTask* d_tasks = nullptr;
-  WWTile* d_tiles = nullptr;
-  int n_tiles = 0;
+  WWTile* d_tiles[2] = {nullptr, nullptr};   // per W.W variant
+  int n_tiles[2] = {0, 0};
+  int ww_var = 2;                            // W.W kernel variant (tuned)
   int n_psi_jobs = 0, n_tasks = 0;
-  int64_t max_psi_plane = 0, max_task_elems = 0;
+  int64_t max_task_elems = 0;
   tci_split_group* g1 = nullptr;     // 128-wide tiles
   tci_split_group* g2 = nullptr;
   tci_split_group* g1n = nullptr;    // 64-wide tiles (a tile shape the autotuner may choose)
@@ -389,7 +489,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
       if (ib < 0) continue;
       S.row_off[w] = S.rows;
       S.blk[w] = Ridx[(long)ib * BS_DW + w];
-      S.rows += dim[ib];
+      S.rows = pad4(S.rows + dim[ib]);   // every U sub-block starts on a 16-byte boundary
     }
     if (S.rows) S.off = take(3 * S.rows * S.Kp);
     for (int w = 0; w < BS_DW; ++w)
@@ -409,7 +509,7 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
       if (it == Lidx.end()) continue;
       S.row_off[w] = S.K;
       S.blk[w] = it->second;
-      S.K += dim[Lb[it->second].j];
+      S.K = pad4(S.K + dim[Lb[it->second].j]);   // every V sub-block starts on an 8-byte boundary
     }
     S.Kp = pad8(S.K);
     if (S.K) S.off = take(3 * S.rows * S.Kp);
@@ -428,7 +528,6 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     const BsBlock& B = P[k];
     const int64_t K = dim[B.j], Kp = pad8(K);
     psi_jobs.push_back({B.off, dim[B.i], K, K, Kp, pstack_off[B.j] + prow[k] * Kp, pstack_rows[B.j] * Kp});
-    p->max_psi_plane = std::max(p->max_psi_plane, dim[B.i] * Kp);
   }
   // Vg stacked per sector ia (GEMM2's B operand): [3][sum of dim ib][Lg[ia].Kp],
   // output block k at rows [vcol[k], + dim ib) of every plane
@@ -536,20 +635,23 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
           (T.v[q] >= 0 && T.nb * T.ldv[q] + T.na >= ((int64_t)1 << 31)))
         return fail(tci_fail(ctx, TCI_ERR_UNSUPPORTED, "bs_heff_plan_create: sector blocks exceed 32-bit offsets"));
   }
-  std::vector<WWTile> wtiles;
-  for (int t = 0; t < (int)tasks.size(); ++t)
-    for (int64_t a0 = 0; a0 < tasks[t].na; a0 += kWA)
-      for (int64_t b0 = 0; b0 < tasks[t].nb; b0 += kWB) wtiles.push_back({t, (int)a0, (int)b0});
-  p->n_tiles = (int)wtiles.size();
   if (!tasks.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(WWTask) * tasks.size(), (void**)&p->d_tasks)) != TCI_OK) return fail(s);
     e = cudaMemcpyAsync(p->d_tasks, tasks.data(), sizeof(WWTask) * tasks.size(), cudaMemcpyHostToDevice,
                         ctx->stream);
     if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: tasks"));
-    if ((s = tci_dev_alloc(ctx, sizeof(WWTile) * wtiles.size(), (void**)&p->d_tiles)) != TCI_OK) return fail(s);
-    e = cudaMemcpyAsync(p->d_tiles, wtiles.data(), sizeof(WWTile) * wtiles.size(), cudaMemcpyHostToDevice,
-                        ctx->stream);
-    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W tiles"));
+    for (int ri = 0; ri < 2; ++ri) {
+      const int ta = ri ? 4 * kW4A : kWA, tb = ri ? 4 * kW4B : kWB;
+      std::vector<WWTile> wtiles;
+      for (int t = 0; t < (int)tasks.size(); ++t)
+        for (int64_t a0 = 0; a0 < tasks[t].na; a0 += ta)
+          for (int64_t b0 = 0; b0 < tasks[t].nb; b0 += tb) wtiles.push_back({t, (int)a0, (int)b0});
+      p->n_tiles[ri] = (int)wtiles.size();
+      if ((s = tci_dev_alloc(ctx, sizeof(WWTile) * wtiles.size(), (void**)&p->d_tiles[ri])) != TCI_OK) return fail(s);
+      e = cudaMemcpyAsync(p->d_tiles[ri], wtiles.data(), sizeof(WWTile) * wtiles.size(), cudaMemcpyHostToDevice,
+                          ctx->stream);
+      if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: W.W tiles"));
+    }
   }
   // ---------------------------------------------------------------- GEMM2 group
   // the group table holds fixed pointers: GEMM2 writes the plan's staging
@@ -575,9 +677,23 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
     const BsBlock& O = P[k];
     const int64_t so = ostage_off[O.i];
     unpack.push_back({so >= 0 ? so + vcol[k] : -1, pad4(vstack_rows[O.i]), dim[O.i], dim[O.j], O.off});
-    p->max_out_block = std::max(p->max_out_block, dim[O.i] * dim[O.j]);
   }
   p->n_unpack = (int)unpack.size();
+  std::vector<BsChunk> uchunks;
+  for (size_t k = 0; k < unpack.size(); ++k) {
+    const int64_t n = unpack[k].rows * unpack[k].cols;
+    if (n >= ((int64_t)1 << 31) - kUnpackElems)
+      return fail(tci_fail(ctx, TCI_ERR_UNSUPPORTED, "bs_heff_plan_create: output block exceeds 32-bit offsets"));
+    for (int64_t st = 0; st < n; st += kUnpackElems) uchunks.push_back({(int)k, (int)st});
+  }
+  p->n_unpack_chunks = (int)uchunks.size();
+  if (!uchunks.empty()) {
+    if ((s = tci_dev_alloc(ctx, sizeof(BsChunk) * uchunks.size(), (void**)&p->d_unpack_chunks)) != TCI_OK)
+      return fail(s);
+    e = cudaMemcpyAsync(p->d_unpack_chunks, uchunks.data(), sizeof(BsChunk) * uchunks.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: unpack chunks"));
+  }
   if (!unpack.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(UnpackJob) * unpack.size(), (void**)&p->d_unpack)) != TCI_OK) return fail(s);
     e = cudaMemcpyAsync(p->d_unpack, unpack.data(), sizeof(UnpackJob) * unpack.size(), cudaMemcpyHostToDevice,
@@ -590,6 +706,25 @@ extern "C" tci_status tci_bs_heff_plan_create(tci_context ctx, int nsec, const i
   p->n_gemm2 = (int64_t)g2.size();
   // psi split jobs
   p->n_psi_jobs = (int)psi_jobs.size();
+  std::vector<BsChunk> schunks;
+  for (size_t k = 0; k < psi_jobs.size(); ++k) {
+    const SplitJob& J = psi_jobs[k];
+    // the split writes 16-byte piece vectors: rows, planes and the stack base on 8-element boundaries
+    if (J.Kp % 8 || J.plane % 8 || J.dst_off % 8)
+      return fail(tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_plan_create: misaligned psi piece stack"));
+    const int64_t n = J.rows * (J.Kp / 8);
+    if (n >= ((int64_t)1 << 31) - kSplitOctets)
+      return fail(tci_fail(ctx, TCI_ERR_UNSUPPORTED, "bs_heff_plan_create: psi block exceeds 32-bit offsets"));
+    for (int64_t st = 0; st < n; st += kSplitOctets) schunks.push_back({(int)k, (int)st});
+  }
+  p->n_split_chunks = (int)schunks.size();
+  if (!schunks.empty()) {
+    if ((s = tci_dev_alloc(ctx, sizeof(BsChunk) * schunks.size(), (void**)&p->d_split_chunks)) != TCI_OK)
+      return fail(s);
+    e = cudaMemcpyAsync(p->d_split_chunks, schunks.data(), sizeof(BsChunk) * schunks.size(), cudaMemcpyHostToDevice,
+                        ctx->stream);
+    if (e != cudaSuccess) return fail(tci_cuda_fail(ctx, e, "bs plan: split chunks"));
+  }
   if (!psi_jobs.empty()) {
     if ((s = tci_dev_alloc(ctx, sizeof(SplitJob) * psi_jobs.size(), (void**)&p->d_psi_jobs)) != TCI_OK) return fail(s);
     e = cudaMemcpyAsync(p->d_psi_jobs, psi_jobs.data(), sizeof(SplitJob) * psi_jobs.size(),
@@ -650,7 +785,8 @@ extern "C" tci_status tci_bs_plan_destroy(tci_bs_plan* pp) {
   tci_split_group_destroy(p->g2);
   tci_split_group_destroy(p->g1n);
   tci_split_group_destroy(p->g2n);
-  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles, p->d_unpack};
+  void* bufs[] = {p->arena, p->U, p->out_stage, p->d_psi_jobs, p->d_tasks, p->d_tiles[0], p->d_tiles[1],
+                  p->d_unpack, p->d_split_chunks, p->d_unpack_chunks};
   for (void* b : bufs) tci_dev_free(b);
   p->magic = 0;
   delete p;
@@ -668,10 +804,22 @@ extern "C" int64_t tci_bs_psi_size(tci_bs_plan p) {
   return p->psi_elems;
 }
 
+static tci_status launch_ww(tci_bs_plan p) {
+  const int v = p->ww_var;
+  if (!p->n_tiles[v ? 1 : 0]) return TCI_OK;
+  tci_context ctx = p->ctx;
+  __nv_bfloat16* V = (__nv_bfloat16*)p->arena;
+  if (v == 0)
+    k_bs_ww<<<p->n_tiles[0], kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles[0], p->ww_sp, V);
+  else
+    k_bs_ww4<<<dim3(p->n_tiles[1], kWGroups[v]), kW4A * kW4B, 0, ctx->stream>>>(p->d_tasks, p->d_tiles[1], p->ww_sp, V);
+  TCI_CUDA(ctx, cudaGetLastError());
+  return TCI_OK;
+}
+
 static tci_status launch_unpack(tci_bs_plan p, float* out) {
-  if (!p->n_unpack) return TCI_OK;
-  dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_out_block + 255) / 256)), (unsigned)p->n_unpack);
-  k_bs_unpack<<<grid, 256, 0, p->ctx->stream>>>(p->d_unpack, p->out_stage, out);
+  if (!p->n_unpack_chunks) return TCI_OK;
+  k_bs_unpack<<<p->n_unpack_chunks, 256, 0, p->ctx->stream>>>(p->d_unpack_chunks, p->d_unpack, p->out_stage, out);
   TCI_CUDA(p->ctx, cudaGetLastError());
   return TCI_OK;
 }
@@ -679,14 +827,13 @@ static tci_status launch_unpack(tci_bs_plan p, float* out) {
 static tci_status bs_launch_all(void* arg) {
   tci_bs_plan p = (tci_bs_plan)arg;
   tci_context ctx = p->ctx;
-  if (p->n_psi_jobs) {
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
-    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, p->cap_psi, (__nv_bfloat16*)p->arena);
-  }
+  if (!p->cap_psi) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs matvec: no input set");
+  if (p->n_split_chunks)
+    k_bs_split<<<p->n_split_chunks, kSplitOctets, 0, ctx->stream>>>(p->d_split_chunks, p->d_psi_jobs, p->cap_psi,
+                                                                      (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaGetLastError());
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
-  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->ww_sp, (__nv_bfloat16*)p->arena);
-  TCI_CUDA(ctx, cudaGetLastError());
+  TCI_TRY(launch_ww(p));
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   if (p->cap_out) TCI_TRY(launch_unpack(p, p->cap_out));
   return TCI_OK;
@@ -700,19 +847,21 @@ extern "C" tci_status tci_bs_heff_apply(tci_bs_plan p, const float* psi, float* 
   if (!psi || !out) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "bs_heff_apply: NULL buffer");
   p->cap_psi = psi;
   p->cap_out = out;
-  if (!p->n_psi_jobs || !p->n_unpack) return bs_launch_all(p);
+  if (!p->n_split_chunks || !p->n_unpack_chunks) return bs_launch_all(p);
   if (!p->graph.exec) {
     // first call: run eagerly (sets kernel attributes), then capture the sequence
     TCI_TRY(bs_launch_all(p));
     return tci_graph_capture(ctx, &p->graph, bs_launch_all, p, {(const void*)k_bs_split, (const void*)k_bs_unpack});
   }
   // replay with this call's psi (the split's input) and out (the unpack's output)
+  const BsChunk* schunks = p->d_split_chunks;
   const SplitJob* jobs = p->d_psi_jobs;
   __nv_bfloat16* dst = (__nv_bfloat16*)p->arena;
+  const BsChunk* uchunks = p->d_unpack_chunks;
   const UnpackJob* ujobs = p->d_unpack;
   const float* stage = p->out_stage;
-  void* sargs[3] = {(void*)&jobs, (void*)&psi, (void*)&dst};
-  void* uargs[3] = {(void*)&ujobs, (void*)&stage, (void*)&out};
+  void* sargs[4] = {(void*)&schunks, (void*)&jobs, (void*)&psi, (void*)&dst};
+  void* uargs[4] = {(void*)&uchunks, (void*)&ujobs, (void*)&stage, (void*)&out};
   void** argv[2] = {sargs, uargs};
   for (int i = 0; i < 2; ++i) {
     cudaKernelNodeParams kp;
@@ -735,14 +884,13 @@ extern "C" tci_status tci_bs_heff_apply_timed(tci_bs_plan p, const float* psi, f
   cudaEvent_t ev[5];
   for (auto& e : ev) TCI_CUDA(ctx, cudaEventCreate(&e));
   TCI_CUDA(ctx, cudaEventRecord(ev[0], ctx->stream));
-  if (p->n_psi_jobs) {
-    dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, (p->max_psi_plane + 255) / 256)), (unsigned)p->n_psi_jobs);
-    k_bs_split<<<grid, 256, 0, ctx->stream>>>(p->d_psi_jobs, psi, (__nv_bfloat16*)p->arena);
-  }
+  if (p->n_split_chunks)
+    k_bs_split<<<p->n_split_chunks, kSplitOctets, 0, ctx->stream>>>(p->d_split_chunks, p->d_psi_jobs, psi,
+                                                                      (__nv_bfloat16*)p->arena);
   TCI_CUDA(ctx, cudaEventRecord(ev[1], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g1n : p->g1, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_CUDA(ctx, cudaEventRecord(ev[2], ctx->stream));
-  if (p->n_tiles) k_bs_ww<<<p->n_tiles, kWA * kWB, 0, ctx->stream>>>(p->d_tasks, p->d_tiles, p->ww_sp, (__nv_bfloat16*)p->arena);
+  TCI_TRY(launch_ww(p));
   TCI_CUDA(ctx, cudaEventRecord(ev[3], ctx->stream));
   TCI_TRY(tci_split_group_launch(ctx, p->bn == 64 ? p->g2n : p->g2, p->products, p->chunk_k, p->xchunk_k, p->raster));
   TCI_TRY(launch_unpack(p, out));
@@ -776,7 +924,73 @@ tci_status bs_run_cfg(void* a, const tci_gemm_cfg& cfg) {
   t->p->cap_out = nullptr;   // candidates stop after GEMM2: the caller's output is not touched
   return bs_launch_all(t->p);
 }
+// W.W kernel variant: the tuned matvec sequence (without the unpack) timed
+// with each, four rounds of 10 in alternating order after a warm-up, median
+// per variant; the lowest-numbered variant within 2 % of the fastest wins.
+tci_status tune_ww(tci_bs_plan p) {
+  tci_context ctx = p->ctx;
+  if (!p->n_tasks) return TCI_OK;
+  float* keep_out = p->cap_out;
+  p->cap_out = nullptr;
+  cudaEvent_t e0, e1;
+  TCI_CUDA(ctx, cudaEventCreate(&e0));
+  TCI_CUDA(ctx, cudaEventCreate(&e1));
+  std::vector<double> rounds[kWVariants];
+  tci_status s = TCI_OK;
+  for (int v = 0; v < kWVariants && s == TCI_OK; ++v) {
+    p->ww_var = v;
+    for (int w = 0; w < 5 && s == TCI_OK; ++w) s = bs_launch_all(p);
+  }
+  for (int round = 0; round < 4 && s == TCI_OK; ++round)
+    for (int q = 0; q < kWVariants && s == TCI_OK; ++q) {
+      const int v = (round & 1) ? kWVariants - 1 - q : q;
+      p->ww_var = v;
+      cudaEventRecord(e0, ctx->stream);
+      for (int r = 0; r < 10 && s == TCI_OK; ++r) s = bs_launch_all(p);
+      cudaEventRecord(e1, ctx->stream);
+      if (s != TCI_OK) break;
+      cudaError_t e = cudaEventSynchronize(e1);
+      if (e != cudaSuccess) {
+        s = tci_cuda_fail(ctx, e, "bs autotune: W.W");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      rounds[v].push_back(ms / 10.0);
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->cap_out = keep_out;
+  if (s != TCI_OK) return s;
+  double med[kWVariants], best = 1e300;
+  for (int v = 0; v < kWVariants; ++v) {
+    std::sort(rounds[v].begin(), rounds[v].end());
+    med[v] = 0.5 * (rounds[v][1] + rounds[v][2]);
+    best = std::min(best, med[v]);
+  }
+  for (int v = kWVariants - 1; v >= 0; --v)
+    if (med[v] <= 1.02 * best) p->ww_var = v;
+  return TCI_OK;
+}
 }  // namespace
+
+extern "C" int tci_bs_ww_variant(tci_bs_plan p) {
+  if (!p || p->magic != kBsMagic) return -1;
+  return p->ww_var;
+}
+
+extern "C" tci_status tci_bs_set_ww_variant(tci_bs_plan p, int variant) {
+  if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_set_ww_variant: invalid plan");
+  TCI_CHECK_CTX(p->ctx);
+  if (variant < 0 || variant >= kWVariants)
+    return tci_fail(p->ctx, TCI_ERR_INVALID_ARG, "bs_set_ww_variant: variant 0..%d", kWVariants - 1);
+  if (variant != p->ww_var) {
+    cudaStreamSynchronize(p->ctx->stream);
+    tci_graph_destroy(&p->graph);   // the next apply captures the new sequence
+    p->ww_var = variant;
+  }
+  return TCI_OK;
+}
 
 extern "C" tci_status tci_bs_autotune(tci_bs_plan p, const float* psi, int max_chunk_k, int* chosen) {
   if (!p || p->magic != kBsMagic) return tci_fail(nullptr, TCI_ERR_INVALID_ARG, "bs_autotune: invalid plan");
@@ -794,6 +1008,8 @@ extern "C" tci_status tci_bs_autotune(tci_bs_plan p, const float* psi, int max_c
   p->xchunk_k = best.xchunk_k;
   p->raster = best.raster;
   p->bn = best.bn;
+  p->cap_psi = psi;   // a cached configuration ran no candidate, which would have set it
+  TCI_TRY(tune_ww(p));
   tci_graph_destroy(&p->graph);   // the next apply captures the tuned sequence
   if (chosen) {
     chosen[0] = best.chunk_k;

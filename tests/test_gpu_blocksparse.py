@@ -116,3 +116,47 @@ def test_blocksparse_autotune_chooses_a_tile_shape(ctx, tci):
     assert blocks_err(got, ref) < 1e-6
     with pytest.raises(tci.TciError):
         plan.set_tile_n(96)
+    assert plan.ww_variant in (0, 1, 2, 3)
+    # a second plan of the same shape takes the cached GEMM configuration (no candidate runs)
+    # and still times its W.W variants on its own input
+    plan2 = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                           to_dev(tci.pack_blocks(inp["L"], st["L"])), to_dev(tci.pack_blocks(inp["R"], st["R"])),
+                           to_dev(inp["W"]))
+    assert plan2.autotune(psi, max_chunk_k=256) == plan.autotune(psi, max_chunk_k=256)
+    out2 = torch.full_like(psi, float("nan"))
+    plan2.apply(psi, out2)
+    torch.cuda.synchronize()
+    assert blocks_err(tci.unpack_blocks(out2.cpu().numpy(), st["psi"], shapes), ref) < 1e-6
+
+
+@pytest.mark.parametrize("total,qmax,sigma,seed", [(64, 5, 2.0, 3), (97, 15, 5.0, 5), (2048, 15, 5.0, 20251223)])
+def test_blocksparse_ww_variants_agree_bit_for_bit(ctx, tci, total, qmax, sigma, seed):
+    """The W.W kernels (shared-memory tiles; 4 x 4 register micro-tiles with vector loads and
+    stores over all outputs or groups of them; an autotuner choice) form every element with the same terms in the same order:
+    identical outputs, equal to the oracle's blocks.  Sector dims 3..162 leave ragged a' and b
+    edges in both tile shapes; the micro-tile writes zeros into the K padding past each sub-block,
+    which GEMM2 must see as zeros."""
+    import torch
+    inp = blocksparse_inputs(total=total, seed=seed, qmax=qmax, sigma=sigma)
+    dims, qmax = inp["dims"], inp["qmax"]
+    st = blocksparse_structure(dims, qmax)
+    plan = tci.BsHeffPlan(ctx, np.arange(len(dims)) - qmax, dims, PHYS_CHARGE, MPO_CHANNEL_CHARGE,
+                          to_dev(tci.pack_blocks(inp["L"], st["L"])), to_dev(tci.pack_blocks(inp["R"], st["R"])),
+                          to_dev(inp["W"]))
+    psi = to_dev(tci.pack_blocks(inp["psi"], st["psi"]))
+    outs = []
+    for variant in (0, 1, 2, 3, 0):
+        plan.set_ww_variant(variant)
+        assert plan.ww_variant == variant
+        out = torch.full_like(psi, float("nan"))
+        plan.apply(psi, out)
+        plan.apply(psi, out)          # the second call replays the captured graph
+        torch.cuda.synchronize()
+        outs.append(out.cpu().numpy())
+    for o in outs[1:]:
+        np.testing.assert_array_equal(outs[0], o)
+    shapes = {k: (dims[k[0]], dims[k[3]]) for k in st["psi"]}
+    ref, _ = o_bs.bs_heff_apply(inp)
+    assert blocks_err(tci.unpack_blocks(outs[0], st["psi"], shapes), ref) < 1e-6
+    with pytest.raises(tci.TciError):
+        plan.set_ww_variant(4)
