@@ -244,7 +244,7 @@ def measure_blocksparse(tci, ctx, dev, peaks, with_oracle: bool):
            "gflops": plan.flops / (ms * 1e-3) / 1e9, "ms_per_matvec": ms, "algorithmic_flops": plan.flops,
            "stage_ms": {"split": float(stg[0]), "gemm1_grouped": float(stg[1]), "ww": float(stg[2]),
                         "gemm2_grouped": float(stg[3])},
-           "launches_per_matvec": 5, "autotune": list(tuned), "tile_n": plan.tile_n, "cuda_graph": True,
+           "launches_per_matvec": 5, "autotune": list(tuned), "tile_n": plan.tile_n, "ww_variant": plan.ww_variant, "cuda_graph": True,
            "roofline": {"bound": "tensor", "kernel": "k_split_bf16_gemm<grouped>", "achieved": ach,
                         "peak": peaks["bf16_tflops"], "unit": "TFLOP/s", "frac": ach / peaks["bf16_tflops"],
                         "flops_per_launch_pair": plan.tensor_flops}}
