@@ -235,6 +235,36 @@ __device__ __forceinline__ void named_bar_arrive(int id, int count) {
   asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Two columns of the drain fold in packed FP32x2 arithmetic (the same IEEE
+// round-to-nearest adds and subtracts as two_sum, two lanes per instruction):
+// (s0, s1) + (e0, e1) == (a0 + b0, a1 + b1) exactly, then the compensation pair
+// rl (packed bfloat16) += (e0, e1), rounded back to bfloat16.
+__device__ __forceinline__ void two_sum2_fold(float& a0, float& a1, uint32_t b0, uint32_t b1, __nv_bfloat162& rl) {
+  uint32_t r = *reinterpret_cast<const uint32_t*>(&rl);
+  asm("{\n\t"
+      ".reg .b64 a, b, s, bp, ap, t1, t2, e, c, q;\n\t"
+      ".reg .b32 cx, cy, q0, q1;\n\t"
+      "mov.b64 a, {%0, %1};\n\t"
+      "mov.b64 b, {%3, %4};\n\t"
+      "add.rn.f32x2 s, a, b;\n\t"
+      "sub.rn.f32x2 bp, s, a;\n\t"
+      "sub.rn.f32x2 ap, s, bp;\n\t"
+      "sub.rn.f32x2 t1, a, ap;\n\t"
+      "sub.rn.f32x2 t2, b, bp;\n\t"
+      "add.rn.f32x2 e, t1, t2;\n\t"
+      "shl.b32 cx, %2, 16;\n\t"
+      "and.b32 cy, %2, 0xffff0000;\n\t"
+      "mov.b64 c, {cx, cy};\n\t"
+      "add.rn.f32x2 q, c, e;\n\t"
+      "mov.b64 {q0, q1}, q;\n\t"
+      "cvt.rn.bf16x2.f32 %2, q1, q0;\n\t"
+      "mov.b64 {%0, %1}, s;\n\t"
+      "}"
+      : "+f"(a0), "+f"(a1), "+r"(r)
+      : "r"(b0), "r"(b1));
+  rl = *reinterpret_cast<const __nv_bfloat162*>(&r);
+}
+
 // Wait for one accumulation unit, fold its 32-lane x BN/4-column slice into
 // the double-float running sum (rh + rl), and release the TMEM buffer.  The
 // compensation rl (|rl| <~ 2^-24 |rh| per drain) is kept as packed bfloat16:
@@ -255,15 +285,8 @@ __device__ __forceinline__ bool drain_unit(uint32_t taddr, uint64_t* full_bar, u
     ptx::tmem_ld_32x32b_x16(taddr + g * 16, v);
     ptx::tmem_ld_wait();
 #pragma unroll
-    for (int j = 0; j < 16; j += 2) {
-      float s0, e0, s1, e1;
-      two_sum(rh[g * 16 + j], __uint_as_float(v[j]), s0, e0);
-      two_sum(rh[g * 16 + j + 1], __uint_as_float(v[j + 1]), s1, e1);
-      rh[g * 16 + j] = s0;
-      rh[g * 16 + j + 1] = s1;
-      const float2 c = __bfloat1622float2(rl[(g * 16 + j) / 2]);
-      rl[(g * 16 + j) / 2] = __floats2bfloat162_rn(__fadd_rn(c.x, e0), __fadd_rn(c.y, e1));
-    }
+    for (int j = 0; j < 16; j += 2)
+      two_sum2_fold(rh[g * 16 + j], rh[g * 16 + j + 1], v[j], v[j + 1], rl[(g * 16 + j) / 2]);
   }
   ptx::tc_fence_before();
   if (lane == 0) ptx::mbar_arrive(ptx::smem_u32(empty_bar));
