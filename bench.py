@@ -43,9 +43,9 @@ SEED = 20251223
 
 # DRAM bytes (read + write) per k_split_bf16_gemm launch of the chi = 2048 matvec by tile
 # raster, the mean of GEMM1 and GEMM2 from ncu captures of this kernel build
-# (profiles/dram_heff_chi2048.md: raster 8 1440 / 1660 MB, raster 16 948 / 1555 MB); a raster
-# not captured reports null.  Emptied whenever the kernel changes.
-GEMM_DRAM_BYTES_PER_LAUNCH = {8: 1549.8e6, 16: 1251.3e6}
+# (profiles/dram_heff_chi2048.md: raster 16 974 / 1564 MB, captured after the packed-FP32x2
+# drain fold); a raster not captured reports null.  Emptied whenever the kernel changes.
+GEMM_DRAM_BYTES_PER_LAUNCH = {16: 1268.9e6}
 
 
 # algorithmic bytes per GEMM launch at chi = 2048: the mean of GEMM1 (operands 227 MB, U^T
