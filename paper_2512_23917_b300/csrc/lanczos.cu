@@ -36,9 +36,9 @@
 //      coefficients split into FP32 pairs, products made exact with FMA,
 //      Dekker / Knuth sums);
 // either way the error added is below 2^-56 ||w||, under the FP64 rounding
-// of the update itself; otherwise the terms stay FP64.  The update kernel is
-// compiled once per term arithmetic; all variants are launched and the one
-// the device chose runs.  The second pass's h' are rounding-level after the
+// of the update itself; otherwise the terms stay FP64.  The update pass is one
+// launch whose blocks read the device's choice and run that arithmetic's
+// body (each body compiled once per term arithmetic).  The second pass's h' are rounding-level after the
 // first projection, so pass 3 is folded into the next-vector kernel (FP32
 // terms), with beta_j^2 = ||w'||^2 - |h'|^2 (Pythagoras: w' - V h' is
 // orthogonal to V up to rounding, and |h'| <= 2^-32 ||w'||).  The reduced
@@ -352,13 +352,13 @@ __global__ void __launch_bounds__(NT, 2) k_dots_shadow(const float* __restrict__
 // FP64.  TERMS
 // (FP64 vectors; v0 = 0, nv = G): the arithmetic of the first nv - 2 terms,
 // kTermsF64, kTermsF32 or kTermsDF with coefficients scaled by lo[LO_SC1]
-// (see the header); with lo the kernel runs only when it is the variant the
+// (see the header); with lo the body runs only when it is the variant the
 // device chose (lo[LO_MODE1] where lo[LO_NS1] = nv - 2, else kTermsF64).
 template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
-__global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::value ? 2 : 1)) k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
-                                               const double* __restrict__ coef, typename A::V* __restrict__ w,
-                                               int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
-                                               const double* __restrict__ ctrl, const double* __restrict__ lo) {
+__device__ __forceinline__ void update_body(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
+                                            const double* __restrict__ coef, typename A::V* __restrict__ w,
+                                            int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
+                                            const double* __restrict__ ctrl, const double* __restrict__ lo) {
   using Vt = typename A::V;
   constexpr bool kF64 = std::is_same<Vt, double>::value;
   static_assert(kF64 || TERMS == kTermsF64, "reduced-precision terms need FP64 vectors");
@@ -490,6 +490,35 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
   }
+}
+
+template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
+__global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::value ? 2 : 1))
+    k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv, const double* __restrict__ coef,
+             typename A::V* __restrict__ w, int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
+             const double* __restrict__ ctrl, const double* __restrict__ lo) {
+  update_body<A, G, DOTS, SUMSQ, TERMS>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+}
+
+// One launch for an FP64 update pass whose term arithmetic the device chooses
+// (lo given): the block reads the choice and runs that variant's body (the
+// choice is uniform over the grid), instead of three launches of which two
+// exit at once.  DFD: the double-float-terms variant forms its dots in
+// double-float (kTermsDFDots).
+template <int G, bool DOTS, bool SUMSQ, bool DFD>
+__global__ void __launch_bounds__(NT, 2)
+    k_update_sel(const double* __restrict__ V, int64_t ldv, int v0, int nv, const double* __restrict__ coef,
+                 double* __restrict__ w, int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
+                 const double* __restrict__ ctrl, const double* __restrict__ lo) {
+  int mode = kTermsF64;
+  if (nv == G && nv > 2 && (int)lo[LO_NS1] == nv - 2) mode = (int)lo[LO_MODE1];
+  if (mode == kTermsF32)
+    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF32>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  else if (mode == kTermsDF)
+    update_body<ArithF64, G, DOTS, SUMSQ, (DOTS && DFD) ? kTermsDFDots : kTermsDF>(V, ldv, v0, nv, coef, w, n, part,
+                                                                                 part_sq, ctrl, lo);
+  else
+    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF64>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
 }
 
 __device__ __forceinline__ void split3_store(__nv_bfloat16* o, int64_t plane, float x) {
@@ -1237,6 +1266,25 @@ int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0
   return grid;
 }
 
+template <int G, bool DOTS, bool SUMSQ, bool DFD>
+int update_sel_g(tci_context ctx, const double* V, int64_t ldv, int v0, int nv, const double* coef, double* w,
+                 int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+  const int grid = pass_grid(ctx, (const void*)k_update_sel<G, DOTS, SUMSQ, DFD>, n);
+  k_update_sel<G, DOTS, SUMSQ, DFD><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  return grid;
+}
+
+template <bool DOTS, bool SUMSQ, bool DFD, int G = 3>
+int update_sel(tci_context ctx, const double* V, int64_t ldv, int v0, int nv, const double* coef, double* w,
+               int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+  if constexpr (G == GMAX) {
+    return update_sel_g<GMAX, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  } else {
+    if (nv <= G) return update_sel_g<G, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_sel<DOTS, SUMSQ, DFD, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  }
+}
+
 template <class A, bool DOTS, bool SUMSQ, int TERMS, int G = 1>
 int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                  typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
@@ -1249,23 +1297,19 @@ int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, i
   }
 }
 
-// One update pass; with lo (FP64 vectors) all three term arithmetics are
-// launched and the one the device chose runs (the others exit at once).
-// df_dots: the double-float-terms variant forms its dots in double-float.
+// One update pass; with lo (FP64 vectors, more than two terms) one launch
+// runs the term arithmetic the device chose (k_update_sel).  df_dots: the
+// double-float-terms variant forms its dots in double-float.
 template <class A, bool DOTS, bool SUMSQ>
 int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                   typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo,
                   bool df_dots) {
   if constexpr (std::is_same<A, ArithF64>::value) {
-    const int grid = update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
     if (lo && nv > 2) {
-      update_exact<A, DOTS, SUMSQ, kTermsF32>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-      if (DOTS && df_dots)
-        update_exact<A, DOTS, SUMSQ, kTermsDFDots>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-      else
-        update_exact<A, DOTS, SUMSQ, kTermsDF>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      if (DOTS && df_dots) return update_sel<DOTS, SUMSQ, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      return update_sel<DOTS, SUMSQ, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
     }
-    return grid;
+    return update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
   } else {
     if (nv <= 8)
       return update_launch_g<A, 8, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
