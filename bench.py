@@ -189,10 +189,11 @@ def lanczos_launches(m: int) -> int:
     n = 4                                           # init scalars, psi0 sum of squares + reduce, start vector
     for j in range(m):
         n += 3                                      # GEMM1, W.W, GEMM2 (the split is fused into the next-vector kernel)
-        n += 3 + 1                                  # pass-1 dots + reduces (dots, sum of squares), alpha / DGKS test
+        # each pass's last block forms its dot and norm totals (no separate reduction launches), and
         # each update pass is one launch (from j = 2 on it runs the term arithmetic the device chose)
-        n += 1 + 2 + 1                              # gated: update + dots + norm and reduces, pass-3 choice
-        n += 2 + 1 + 1                              # gated: FP64 pass 3 + reduce; skipped branch update + reduce
+        n += 1 + 1                                  # pass-1 dots and sum of squares, alpha / DGKS test
+        n += 1 + 1                                  # gated: update + dots + norm, pass-3 choice
+        n += 1 + 1                                  # gated: FP64 pass 3; skipped branch update
         n += 1                                      # beta / stop test
         if j + 1 < m:
             n += 2                                  # v_{j+1} (gated: plain, or with the FP32 pass-3 terms)

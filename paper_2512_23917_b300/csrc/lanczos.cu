@@ -100,13 +100,14 @@ constexpr int OFF_Y = 3 * MAXM + 16;     // Ritz coefficients
 constexpr int OFF_H2 = 4 * MAXM + 32;    // MAXM + 1 entries: pass-2 coefficients
 constexpr int OFF_LO = 5 * MAXM + 40;    // FP32 rounding-level terms (LO_* below)
 constexpr int NSCAL = 5 * MAXM + 64;
+constexpr int OFF_TICKET = NSCAL - 4;    // blocks done in the current pass (as an unsigned; zero between passes)
 // OFF_LO + : pass-2 / 2' FP32 terms (count, scale, inverse scale), pass-2
 // ||w'||^2, pass-3 FP32 scale and inverse, gates (run while 0) of the FP32
 // next-vector kernel, the FP64 pass 3 and the plain next-vector kernel,
 // counters of FP32-term passes and fused pass-3 corrections.
 constexpr int LO_NS1 = 0, LO_SC1 = 1, LO_ISC1 = 2, LO_WN2 = 3, LO_SC3 = 4, LO_ISC3 = 5;
 constexpr int LO_GFAST = 6, LO_GSLOW = 7, LO_GNEXT = 8, LO_N1 = 9, LO_N3 = 10, LO_MODE1 = 11, LO_N2 = 12;
-static_assert(OFF_LO + LO_N2 < NSCAL, "scalar layout");
+static_assert(OFF_LO + LO_N2 < OFF_TICKET, "scalar layout");
 // Terms are summed in FP32 where their coefficients' 1-norm times (k + 8),
 // k the number of such terms, is at most 2^-32 times the norm of the vector
 // they update, and in double-float where it is at most 2^-10 times it.
@@ -257,6 +258,29 @@ struct ArithDF {
 };
 
 // ---------------------------------------------------------------- vector kernels
+// Where a pass's last block puts the totals of its partial sums (dots: one per
+// row, sq: the sum of squares); ticket null: the partials are left for
+// k_reduce_parts.
+struct PassOut {
+  double* dots = nullptr;
+  double* sq = nullptr;
+  unsigned* ticket = nullptr;
+};
+
+// The total of one partial-sum row (nb slots) in k_reduce_parts' order, by one
+// warp: the slices b = t, t + 256, ... of its 256 threads t are summed in
+// sequence, each group of 32 by the same shuffle tree, and the eight group
+// sums in order.  The result is in lane 0.
+__device__ __forceinline__ double warp_reduce_row(const double* row, int nb, int lane) {
+  double r = 0.0;
+  for (int g = 0; g < 256 / 32; ++g) {
+    double s = 0.0;
+    for (int b = 32 * g + lane; b < nb; b += 256) s += __ldcg(row + b);
+    r += warp_sum(s);
+  }
+  return r;
+}
+
 // Per-block partial sums of G accumulators (fixed order): part[g*NBMAX +
 // blockIdx.x] for g < nv.
 // Called by every thread of the block; two calls with the same G in one
@@ -280,12 +304,41 @@ __device__ __forceinline__ void block_partials(const typename A::Acc (&a)[G], in
   }
 }
 
+// With po.ticket: after every block has written its partials, the last block
+// to finish (counted on the ticket) forms the totals the separate
+// k_reduce_parts launches would (same order, so the same values), one warp per
+// row, and clears the ticket for the next pass.  Called by every thread of
+// every block that wrote partials (rows: nrows rows NBMAX apart from part;
+// part_sq: the sum-of-squares row).
+__device__ __forceinline__ void pass_finish(const double* part, int nrows, const double* part_sq, const PassOut& po) {
+  if (!po.ticket) return;
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(po.ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (po.dots)
+    for (int r = wid; r < nrows; r += NT / 32) {
+      const double v = warp_reduce_row(part + (int64_t)r * NBMAX, gridDim.x, lane);
+      if (lane == 0) po.dots[r] = v;
+    }
+  if (po.sq && wid == NT / 32 - 1) {
+    const double v = warp_reduce_row(part_sq, gridDim.x, lane);
+    if (lane == 0) *po.sq = v;
+  }
+  if (threadIdx.x == 0) *po.ticket = 0u;
+}
+
 // partials of <V_{v0+g}, w>, g < nv <= G, into part rows v0 + g; with SQ
 // also the partials of ||w||^2 into part_sq
 template <class A, int G, bool SQ>
 __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                              const typename A::V* __restrict__ w, int64_t n, double* __restrict__ part,
-                                             double* __restrict__ part_sq, const double* __restrict__ ctrl) {
+                                             double* __restrict__ part_sq, const double* __restrict__ ctrl,
+                                             const PassOut po) {
   if (ctrl[0] != 0.0) return;
   typename A::Acc a[G];
 #pragma unroll
@@ -305,6 +358,7 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
   }
+  pass_finish(part + (int64_t)v0 * NBMAX, nv, part_sq, po);
 }
 
 // Pass 1 from the double-float shadow of the basis (FP64 vectors; vector g's hi
@@ -358,7 +412,8 @@ template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
 __device__ __forceinline__ void update_body(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv,
                                             const double* __restrict__ coef, typename A::V* __restrict__ w,
                                             int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
-                                            const double* __restrict__ ctrl, const double* __restrict__ lo) {
+                                            const double* __restrict__ ctrl, const double* __restrict__ lo,
+                                            const PassOut& po) {
   using Vt = typename A::V;
   constexpr bool kF64 = std::is_same<Vt, double>::value;
   static_assert(kF64 || TERMS == kTermsF64, "reduced-precision terms need FP64 vectors");
@@ -490,14 +545,15 @@ __device__ __forceinline__ void update_body(const typename A::V* __restrict__ V,
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
   }
+  if (DOTS || SUMSQ) pass_finish(part + (int64_t)v0 * NBMAX, DOTS ? nv : 0, part_sq, po);
 }
 
 template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
 __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::value ? 2 : 1))
     k_update(const typename A::V* __restrict__ V, int64_t ldv, int v0, int nv, const double* __restrict__ coef,
              typename A::V* __restrict__ w, int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
-             const double* __restrict__ ctrl, const double* __restrict__ lo) {
-  update_body<A, G, DOTS, SUMSQ, TERMS>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+             const double* __restrict__ ctrl, const double* __restrict__ lo, const PassOut po) {
+  update_body<A, G, DOTS, SUMSQ, TERMS>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
 }
 
 // One launch for an FP64 update pass whose term arithmetic the device chooses
@@ -509,16 +565,16 @@ template <int G, bool DOTS, bool SUMSQ, bool DFD>
 __global__ void __launch_bounds__(NT, 2)
     k_update_sel(const double* __restrict__ V, int64_t ldv, int v0, int nv, const double* __restrict__ coef,
                  double* __restrict__ w, int64_t n, double* __restrict__ part, double* __restrict__ part_sq,
-                 const double* __restrict__ ctrl, const double* __restrict__ lo) {
+                 const double* __restrict__ ctrl, const double* __restrict__ lo, const PassOut po) {
   int mode = kTermsF64;
   if (nv == G && nv > 2 && (int)lo[LO_NS1] == nv - 2) mode = (int)lo[LO_MODE1];
   if (mode == kTermsF32)
-    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF32>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF32>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   else if (mode == kTermsDF)
     update_body<ArithF64, G, DOTS, SUMSQ, (DOTS && DFD) ? kTermsDFDots : kTermsDF>(V, ldv, v0, nv, coef, w, n, part,
-                                                                                 part_sq, ctrl, lo);
+                                                                                 part_sq, ctrl, lo, po);
   else
-    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF64>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    update_body<ArithF64, G, DOTS, SUMSQ, kTermsF64>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
 }
 
 __device__ __forceinline__ void split3_store(__nv_bfloat16* o, int64_t plane, float x) {
@@ -1168,9 +1224,9 @@ int pass_grid(tci_context ctx, const void* kernel, int64_t n) {
 
 template <class A, int G, bool SQ>
 int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                  int64_t n, double* part, double* part_sq, const double* ctrl) {
+                  int64_t n, double* part, double* part_sq, const double* ctrl, const PassOut& po) {
   const int grid = pass_grid(ctx, (const void*)k_dots<A, G, SQ>, n);
-  k_dots<A, G, SQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+  k_dots<A, G, SQ><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
   return grid;
 }
 
@@ -1180,37 +1236,43 @@ int dots_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, 
 // needed one.  Double-float passes (FP32 pipes) use G in {8, 16, GMAX}.
 template <class A, bool SQ, int G = 1>
 int dots_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-               int64_t n, double* part, double* part_sq, const double* ctrl) {
+               int64_t n, double* part, double* part_sq, const double* ctrl, const PassOut& po) {
   if constexpr (G == GMAX) {
-    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
   } else {
-    if (nv <= G) return dots_launch_g<A, G, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
-    return dots_exact<A, SQ, G + 1>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    if (nv <= G) return dots_launch_g<A, G, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
+    return dots_exact<A, SQ, G + 1>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
   }
 }
 
 template <class A, bool SQ>
 int dots_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                int64_t n, double* part, double* part_sq, const double* ctrl) {
+                int64_t n, double* part, double* part_sq, const double* ctrl, const PassOut& po) {
   if constexpr (std::is_same<A, ArithF64>::value) {
-    return dots_exact<A, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    return dots_exact<A, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
   } else {
-    if (nv <= 8) return dots_launch_g<A, 8, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
-    if (nv <= 16) return dots_launch_g<A, 16, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
-    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl);
+    if (nv <= 8) return dots_launch_g<A, 8, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
+    if (nv <= 16) return dots_launch_g<A, 16, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
+    return dots_launch_g<A, GMAX, SQ>(ctx, V, ldv, v0, nv, w, n, part, part_sq, ctrl, po);
   }
 }
 
-// out[0..nv) = <V_{v0+v}, w>; *sumsq_out = ||w||^2 when sumsq_out
+// out[0..nv) = <V_{v0+v}, w>; *sumsq_out = ||w||^2 when sumsq_out.  With a
+// ticket (a zero unsigned in device memory) each pass's last block forms the
+// totals; without, k_reduce_parts launches do.
 template <class A>
 tci_status run_dots(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const typename A::V* w,
-                    int64_t n, double* part, double* out, const double* ctrl, double* sumsq_out = nullptr) {
+                    int64_t n, double* part, double* out, const double* ctrl, double* sumsq_out = nullptr,
+                    unsigned* ticket = nullptr) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
   for (int g0 = 0; g0 < nv; g0 += GMAX) {
     const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
     const bool sq = sumsq_out && g0 == 0;
-    const int grid = sq ? dots_launch<A, true>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl)
-                        : dots_launch<A, false>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl);
+    PassOut po;
+    if (ticket) po = {out + g0, sq ? sumsq_out : nullptr, ticket};
+    const int grid = sq ? dots_launch<A, true>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl, po)
+                        : dots_launch<A, false>(ctx, V, ldv, v0 + g0, g, w, n, part, part_sq, ctrl, po);
+    if (ticket) continue;
     k_reduce_parts<<<g, 256, 0, ctx->stream>>>(part + (int64_t)(v0 + g0) * NBMAX, g, grid, out + g0, ctrl);
     if (sq) k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part_sq, 1, grid, sumsq_out, ctrl);
   }
@@ -1259,41 +1321,41 @@ tci_status run_dots_shadow(tci_context ctx, const float* Vs, int64_t ldv, int nv
 template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
 int update_launch_g(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                     typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl,
-                    const double* lo) {
+                    const double* lo, const PassOut& po) {
   const int grid = pass_grid(ctx, (const void*)k_update<A, G, DOTS, SUMSQ, kTermsF64>, n);
   k_update<A, G, DOTS, SUMSQ, TERMS><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl,
-                                                                  lo);
+                                                                  lo, po);
   return grid;
 }
 
 template <int G, bool DOTS, bool SUMSQ, bool DFD>
 int update_sel_g(tci_context ctx, const double* V, int64_t ldv, int v0, int nv, const double* coef, double* w,
-                 int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+                 int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo, const PassOut& po) {
   const int grid = pass_grid(ctx, (const void*)k_update_sel<G, DOTS, SUMSQ, DFD>, n);
-  k_update_sel<G, DOTS, SUMSQ, DFD><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+  k_update_sel<G, DOTS, SUMSQ, DFD><<<grid, NT, 0, ctx->stream>>>(V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   return grid;
 }
 
 template <bool DOTS, bool SUMSQ, bool DFD, int G = 3>
 int update_sel(tci_context ctx, const double* V, int64_t ldv, int v0, int nv, const double* coef, double* w,
-               int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+               int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo, const PassOut& po) {
   if constexpr (G == GMAX) {
-    return update_sel_g<GMAX, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_sel_g<GMAX, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   } else {
-    if (nv <= G) return update_sel_g<G, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-    return update_sel<DOTS, SUMSQ, DFD, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    if (nv <= G) return update_sel_g<G, DOTS, SUMSQ, DFD>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
+    return update_sel<DOTS, SUMSQ, DFD, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   }
 }
 
 template <class A, bool DOTS, bool SUMSQ, int TERMS, int G = 1>
 int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
-                 typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo) {
+                 typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo, const PassOut& po) {
   if constexpr (G == GMAX) {
-    return update_launch_g<A, GMAX, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_launch_g<A, GMAX, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   } else {
     if (nv <= G)
-      return update_launch_g<A, G, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-    return update_exact<A, DOTS, SUMSQ, TERMS, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      return update_launch_g<A, G, DOTS, SUMSQ, TERMS>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
+    return update_exact<A, DOTS, SUMSQ, TERMS, G + 1>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   }
 }
 
@@ -1303,19 +1365,19 @@ int update_exact(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, i
 template <class A, bool DOTS, bool SUMSQ>
 int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                   typename A::V* w, int64_t n, double* part, double* part_sq, const double* ctrl, const double* lo,
-                  bool df_dots) {
+                  bool df_dots, const PassOut& po) {
   if constexpr (std::is_same<A, ArithF64>::value) {
     if (lo && nv > 2) {
-      if (DOTS && df_dots) return update_sel<DOTS, SUMSQ, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-      return update_sel<DOTS, SUMSQ, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      if (DOTS && df_dots) return update_sel<DOTS, SUMSQ, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
+      return update_sel<DOTS, SUMSQ, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
     }
-    return update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+    return update_exact<A, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   } else {
     if (nv <= 8)
-      return update_launch_g<A, 8, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      return update_launch_g<A, 8, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
     if (nv <= 16)
-      return update_launch_g<A, 16, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
-    return update_launch_g<A, GMAX, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo);
+      return update_launch_g<A, 16, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
+    return update_launch_g<A, GMAX, DOTS, SUMSQ, kTermsF64>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, po);
   }
 }
 
@@ -1326,33 +1388,43 @@ int update_launch(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, 
 template <class A>
 tci_status run_update(tci_context ctx, const typename A::V* V, int64_t ldv, int v0, int nv, const double* coef,
                       typename A::V* w, int64_t n, double* part, double* dots_out, double* sumsq_out,
-                      const double* ctrl, const double* lo = nullptr, bool df_dots = false) {
+                      const double* ctrl, const double* lo = nullptr, bool df_dots = false,
+                      unsigned* ticket = nullptr) {
   double* part_sq = part + (int64_t)MAXM * NBMAX;
   if (lo && v0 != 0) return tci_fail(ctx, TCI_ERR_INVALID_ARG, "lanczos: internal (FP32 terms need v0 = 0)");
   int sq_grid = 0;
   if (nv <= GMAX) {
+    PassOut po;
+    if (ticket && (dots_out || sumsq_out)) po = {dots_out, sumsq_out, ticket};
     int grid = 0;
     if (dots_out && sumsq_out)
-      grid = update_launch<A, true, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots);
+      grid = update_launch<A, true, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots, po);
     else if (dots_out)
-      grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots);
+      grid = update_launch<A, true, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, df_dots, po);
     else if (sumsq_out)
-      grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false);
+      grid = update_launch<A, false, true>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false, po);
     else
-      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false);
-    if (dots_out) k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
+      update_launch<A, false, false>(ctx, V, ldv, v0, nv, coef, w, n, part, part_sq, ctrl, lo, false, po);
+    if (ticket) sumsq_out = nullptr;   // reduced by the pass's last block
+    else if (dots_out)
+      k_reduce_parts<<<nv, 256, 0, ctx->stream>>>(part + (int64_t)v0 * NBMAX, nv, grid, dots_out, ctrl);
     sq_grid = grid;
   } else {
     for (int g0 = 0; g0 < nv; g0 += GMAX) {
       const int g = nv - g0 < GMAX ? nv - g0 : GMAX;
-      if (g0 + g == nv && sumsq_out && !dots_out)
+      if (g0 + g == nv && sumsq_out && !dots_out) {
+        PassOut po;
+        if (ticket) po = {nullptr, sumsq_out, ticket};
         sq_grid = update_launch<A, false, true>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr,
-                                                false);
-      else
-        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr, false);
+                                                false, po);
+        if (ticket) sumsq_out = nullptr;
+      } else {
+        update_launch<A, false, false>(ctx, V, ldv, v0 + g0, g, coef, w, n, part, part_sq, ctrl, nullptr, false,
+                                       PassOut{});
+      }
     }
     if (dots_out) {
-      TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl, sumsq_out));
+      TCI_TRY(run_dots<A>(ctx, V, ldv, v0, nv, w, n, part, dots_out, ctrl, sumsq_out, ticket));
       sumsq_out = nullptr;   // reduced by run_dots
     }
   }
@@ -1464,6 +1536,8 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   const int64_t Kp = MODE == kInPieces ? p->Kp1 : 0;
 
   k_init_scal<<<1, 256, 0, ctx->stream>>>(S);
+  // blocks-done counter of the passes whose last block forms the totals (zeroed with S)
+  unsigned* ticket = reinterpret_cast<unsigned*>(S + OFF_TICKET);
   k_sumsq<<<NBMAX, NT, 0, ctx->stream>>>(psi0, n, part);
   k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
   if (kDF || !reorth) Vs = nullptr;
@@ -1512,22 +1586,25 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
         if constexpr (!kDF) {
           if (Vs) TCI_TRY(run_dots_shadow(ctx, Vs, ldv, j + 1, (const double*)w, n, part, S + OFF_H, ctrl, ctrl + 4));
         }
-        if (!Vs) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4));
+        if (!Vs) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4, ticket));
       }
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,
-                            lo1, Vs != nullptr));
+                            lo1, Vs != nullptr, ticket));
       k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, (kF32Terms && p->lz_reduced) ? 1 : 0);
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW));
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW,
+                            nullptr, false, ticket));
       // second pass skipped: w -= V h with ||w||^2
-      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6, lo1));
+      TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl + 6, lo1, false,
+                            ticket));
     } else {
-      TCI_TRY(run_dots<A>(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl));
+      TCI_TRY(run_dots<A>(ctx, V, ldv, j, 1, w, n, part, S + OFF_H + j, ctrl, nullptr, ticket));
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 0, 0, 0);
       const int v0 = j > 0 ? j - 1 : 0;
-      TCI_TRY(run_update<A>(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl));
+      TCI_TRY(run_update<A>(ctx, V, ldv, v0, j + 1 - v0, S + OFF_H, w, n, part, nullptr, ctrl + 3, ctrl, nullptr,
+                            false, ticket));
     }
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
     if (j + 1 < nsteps) {
