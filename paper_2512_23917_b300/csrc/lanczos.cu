@@ -267,20 +267,6 @@ struct PassOut {
   unsigned* ticket = nullptr;
 };
 
-// The total of one partial-sum row (nb slots) in k_reduce_parts' order, by one
-// warp: the slices b = t, t + 256, ... of its 256 threads t are summed in
-// sequence, each group of 32 by the same shuffle tree, and the eight group
-// sums in order.  The result is in lane 0.
-__device__ __forceinline__ double warp_reduce_row(const double* row, int nb, int lane) {
-  double r = 0.0;
-  for (int g = 0; g < 256 / 32; ++g) {
-    double s = 0.0;
-    for (int b = 32 * g + lane; b < nb; b += 256) s += __ldcg(row + b);
-    r += warp_sum(s);
-  }
-  return r;
-}
-
 // Per-block partial sums of G accumulators (fixed order): part[g*NBMAX +
 // blockIdx.x] for g < nv.
 // Called by every thread of the block; two calls with the same G in one
@@ -306,28 +292,49 @@ __device__ __forceinline__ void block_partials(const typename A::Acc (&a)[G], in
 
 // With po.ticket: after every block has written its partials, the last block
 // to finish (counted on the ticket) forms the totals the separate
-// k_reduce_parts launches would (same order, so the same values), one warp per
-// row, and clears the ticket for the next pass.  Called by every thread of
-// every block that wrote partials (rows: nrows rows NBMAX apart from part;
-// part_sq: the sum-of-squares row).
+// k_reduce_parts launches would, in the same order (so the same values): each
+// of its 256 threads sums the slots b = t, t + 256, ... of every row, the
+// rows' loads issued together, then each row goes through the same warp
+// shuffle tree and the eight warp sums are added in order.  The ticket is
+// cleared for the next pass.  Called by every thread of every block that
+// wrote partials (nrows <= G rows NBMAX apart from part; part_sq: the
+// sum-of-squares row).
+template <int G>
 __device__ __forceinline__ void pass_finish(const double* part, int nrows, const double* part_sq, const PassOut& po) {
+  static_assert(NT == 256, "the totals follow k_reduce_parts' 256-thread order");
   if (!po.ticket) return;
   __shared__ int last;
+  __shared__ double sh[NT / 32][G + 1];
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = atomicAdd(po.ticket, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
-  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (po.dots)
-    for (int r = wid; r < nrows; r += NT / 32) {
-      const double v = warp_reduce_row(part + (int64_t)r * NBMAX, gridDim.x, lane);
-      if (lane == 0) po.dots[r] = v;
-    }
-  if (po.sq && wid == NT / 32 - 1) {
-    const double v = warp_reduce_row(part_sq, gridDim.x, lane);
-    if (lane == 0) *po.sq = v;
+  const int nb = gridDim.x, wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nr = po.dots ? nrows : 0;
+  double t[G + 1];
+#pragma unroll
+  for (int r = 0; r <= G; ++r) t[r] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += NT) {
+#pragma unroll
+    for (int r = 0; r < G; ++r)
+      if (r < nr) t[r] += __ldcg(part + (int64_t)r * NBMAX + b);
+    if (po.sq) t[G] += __ldcg(part_sq + b);
+  }
+#pragma unroll
+  for (int r = 0; r <= G; ++r) {
+    if (r < G && r >= nr) continue;
+    if (r == G && !po.sq) continue;
+    const double v = warp_sum(t[r]);
+    if (lane == 0) sh[wid][r] = v;
+  }
+  __syncthreads();
+  if ((int)threadIdx.x < nr || (po.sq && threadIdx.x == G)) {
+    double v = 0.0;
+    for (int k = 0; k < NT / 32; ++k) v += sh[k][threadIdx.x];
+    if ((int)threadIdx.x < nr) po.dots[threadIdx.x] = v;
+    else *po.sq = v;
   }
   if (threadIdx.x == 0) *po.ticket = 0u;
 }
@@ -358,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_dots(const typename A::V* __restrict__ V
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
   }
-  pass_finish(part + (int64_t)v0 * NBMAX, nv, part_sq, po);
+  pass_finish<G>(part + (int64_t)v0 * NBMAX, nv, part_sq, po);
 }
 
 // Pass 1 from the double-float shadow of the basis (FP64 vectors; vector g's hi
@@ -545,7 +552,7 @@ __device__ __forceinline__ void update_body(const typename A::V* __restrict__ V,
     const typename A::Acc qa[1] = {q};
     block_partials<A, 1>(qa, 1, part_sq);
   }
-  if (DOTS || SUMSQ) pass_finish(part + (int64_t)v0 * NBMAX, DOTS ? nv : 0, part_sq, po);
+  if (DOTS || SUMSQ) pass_finish<G>(part + (int64_t)v0 * NBMAX, DOTS ? nv : 0, part_sq, po);
 }
 
 template <class A, int G, bool DOTS, bool SUMSQ, int TERMS>
