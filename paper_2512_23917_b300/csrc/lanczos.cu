@@ -595,6 +595,8 @@ __global__ void __launch_bounds__(NT, (std::is_same<typename A::V, double>::valu
 // choice is uniform over the grid), instead of three launches of which two
 // exit at once.  DFD: the double-float-terms variant forms its dots in
 // double-float (kTermsDFDots).
+// (Two blocks per SM: the DGKS variants of the largest bases spill a few
+// registers there, and measured faster so than with one block's registers.)
 template <int G, bool DOTS, bool SUMSQ, bool DFD>
 __global__ void __launch_bounds__(NT, 2)
     k_update_sel(const double* __restrict__ V, int64_t ldv, int v0, int nv, const double* __restrict__ coef,
