@@ -642,7 +642,8 @@ constexpr int kInPieces = 1;   // bfloat16 pieces of fl32(v), K-major [3][rows][
 constexpr int kInF64 = 2;      // v as FP64 (double-float basis, FP64 matvec)
 
 // Where a pass writes the shadow of the vector it writes: the hi and lo planes
-// (hi == nullptr: no shadow).
+// (hi == nullptr: no shadow; lo == nullptr: the hi plane only, the FP32
+// truncation the pass-3 correction reads).
 struct ShadowOut {
   float* hi;
   float* lo;
@@ -652,7 +653,7 @@ struct ShadowOut {
 __device__ __forceinline__ void store_shadow2(ShadowOut vs, int64_t i, double y0, double y1) {
   const float2 a = shadow_of(y0), b = shadow_of(y1);
   *reinterpret_cast<float2*>(vs.hi + i) = make_float2(a.x, b.x);
-  *reinterpret_cast<float2*>(vs.lo + i) = make_float2(a.y, b.y);
+  if (vs.lo) *reinterpret_cast<float2*>(vs.lo + i) = make_float2(a.y, b.y);
 }
 
 template <class A, int MODE>
@@ -663,7 +664,7 @@ __device__ __forceinline__ void emit(typename A::V y, int64_t i, int64_t r, int6
   if (vs.hi) {
     const float2 sh = shadow_of(A::to_double(y));
     vs.hi[i] = sh.x;
-    vs.lo[i] = sh.y;
+    if (vs.lo) vs.lo[i] = sh.y;
   }
   if (MODE == kInPieces) split3_store(pieces + r * Kp + k, plane, A::f32(y));
   if (MODE == kInF64) x64[i] = A::to_double(y);
@@ -1543,12 +1544,14 @@ tci_status launch_step_small(tci_context ctx, double* V, int64_t ldv, double* w,
 // (kInPieces for a split-BF16 plan; kInNone for FP64 vectors on an FP64
 // plan; kInF64 for double-float vectors on an FP64 plan).
 template <class A, int MODE>
-// Vs (FP64 vectors on a split plan, re-orthogonalised; else null): the
-// double-float shadow of the basis, written with each basis vector (vector g:
-// hi plane at Vs + 2 g ldv, lo plane ldv after it), read by pass 1 (both
-// planes) and by the pass-3 correction (hi planes).
+// Vs (FP64 vectors on a split plan, re-orthogonalised; else null): a copy of
+// the basis written with each basis vector (vector g: hi plane at Vs + 2 g
+// ldv, lo plane ldv after it).  The pass-3 correction reads the hi planes (the
+// FP32 truncation its rounding-level terms use: half the bytes of the FP64
+// basis); with dfdots the lo planes are written too and pass 1 and the second
+// pass's dots run in double-float from the copy.
 tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol,
-                       float* Vs) {
+                       float* Vs, bool dfdots) {
   using Vt = typename A::V;
   tci_context ctx = p->ctx;
   // a complex plan runs on the real form: C128 vectors as interleaved FP64 pairs
@@ -1577,8 +1580,9 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   k_sumsq<<<NBMAX, NT, 0, ctx->stream>>>(psi0, n, part);
   k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
   if (kDF || !reorth) Vs = nullptr;
+  if (!Vs) dfdots = false;
   launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S,
-                        ShadowOut{Vs, Vs ? Vs + ldv : nullptr});
+                        ShadowOut{Vs, dfdots ? Vs + ldv : nullptr});
   TCI_CUDA(ctx, cudaGetLastError());
   for (int j = 0; j < nsteps; ++j) {
     Vt* vj = V + (int64_t)j * ldv;
@@ -1620,15 +1624,15 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
       const double* lo1 = reduced ? S + OFF_LO : nullptr;
       if (!fused) {
         if constexpr (!kDF) {
-          if (Vs) TCI_TRY(run_dots_shadow(ctx, Vs, ldv, j + 1, (const double*)w, n, part, S + OFF_H, ctrl, ctrl + 4));
+          if (dfdots) TCI_TRY(run_dots_shadow(ctx, Vs, ldv, j + 1, (const double*)w, n, part, S + OFF_H, ctrl, ctrl + 4));
         }
-        if (!Vs) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4, ticket));
+        if (!dfdots) TCI_TRY(run_dots<A>(ctx, V, ldv, 0, j + 1, w, n, part, S + OFF_H, ctrl, ctrl + 4, ticket));
       }
       k_post_pass1<<<1, 1, 0, ctx->stream>>>(S, j, 1, dgks, reduced ? 1 : 0);
       // second pass taken: w -= V h, then its dots and ||w'||^2; then w -= V h'
       // with ||w||^2 in FP64, or folded into the next-vector kernel
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H, w, n, part, S + OFF_H2, S + OFF_LO + LO_WN2, ctrl + 5,
-                            lo1, Vs != nullptr, ticket));
+                            lo1, dfdots, ticket));
       k_post_pass2<<<1, 1, 0, ctx->stream>>>(S, j, (kF32Terms && p->lz_reduced) ? 1 : 0);
       TCI_TRY(run_update<A>(ctx, V, ldv, 0, j + 1, S + OFF_H2, w, n, part, nullptr, ctrl + 3, S + OFF_LO + LO_GSLOW,
                             nullptr, false, ticket));
@@ -1646,7 +1650,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     if (j + 1 < nsteps) {
       Vt* vn = V + (int64_t)(j + 1) * ldv;
       float* vsh = Vs ? Vs + 2 * (int64_t)(j + 1) * ldv : nullptr;
-      const ShadowOut vsn{vsh, vsh ? vsh + ldv : nullptr};
+      const ShadowOut vsn{vsh, (vsh && dfdots) ? vsh + ldv : nullptr};
       launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl,
                            vsn);
       if constexpr (kF32Terms) {
@@ -1690,17 +1694,18 @@ struct SolveArgs {
   int arith;
   bool split;
   float* Vs;
+  bool dfdots;
 };
 
 // One solve's launches on p->ctx->stream (the body a graph captures).
 tci_status solve_body(void* a) {
   const SolveArgs& s = *(const SolveArgs*)a;
   if (s.arith == TCI_LANCZOS_DF32) {
-    if (s.split) return lanczos_run<ArithDF, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
-    return lanczos_run<ArithDF, kInF64>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
+    if (s.split) return lanczos_run<ArithDF, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr, false);
+    return lanczos_run<ArithDF, kInF64>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr, false);
   }
-  if (s.split) return lanczos_run<ArithF64, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, s.Vs);
-  return lanczos_run<ArithF64, kInNone>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr);
+  if (s.split) return lanczos_run<ArithF64, kInPieces>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, s.Vs, s.dfdots);
+  return lanczos_run<ArithF64, kInNone>(s.p, s.psi, s.nsteps, s.reorth, s.x, s.tol, nullptr, false);
 }
 }  // namespace
 
@@ -1747,10 +1752,12 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   vs.info = arith == TCI_LANCZOS_DF32 ? "double-float vectors" : "FP64 vectors";
   const double* psi = (const double*)psi0->data;
   double* xd = x ? (double*)x->data : nullptr;
-  // pass 1 from a double-float shadow of the basis: split plans, FP64 vectors,
-  // re-orthogonalised, not fused into GEMM2
-  const bool shadow = split && arith == TCI_LANCZOS_F64 && !p->cplx && reorth && p->lz_shadow && !p->lz_fuse;
-  if (shadow && p->lz_vs_cap < p->lz_cap) {
+  // the basis copy (split plans, FP64 vectors, re-orthogonalised, dots not
+  // fused into GEMM2): its FP32 planes serve the pass-3 correction, and with
+  // shadow (the opt-in double-float dots) its lo planes too
+  const bool copy = split && arith == TCI_LANCZOS_F64 && !p->cplx && reorth && !p->lz_fuse;
+  const bool shadow = copy && p->lz_shadow;
+  if (copy && p->lz_vs_cap < p->lz_cap) {
     cudaStreamSynchronize(ctx->stream);
     tci_dev_free(p->lz_Vs);
     p->lz_Vs = nullptr;
@@ -1758,7 +1765,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     TCI_TRY(tci_dev_alloc(ctx, sizeof(float2) * ldv * p->lz_cap, &p->lz_Vs));
     p->lz_vs_cap = p->lz_cap;
   }
-  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, shadow ? (float*)p->lz_Vs : nullptr};
+  SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, copy ? (float*)p->lz_Vs : nullptr, shadow};
   bool done = false;
   p->lz_last_graph = 0;
   if (!p->cplx && p->lz_graphs) {
@@ -1766,7 +1773,7 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
     // psi0 and x are not part of the key: the three kernel nodes that read psi0
     // or write x get the call's pointers before every replay
     const std::vector<int64_t> key = {xd != nullptr, nsteps, reorth, arith, p->gs_mode, p->lz_reduced, p->lz_fuse,
-                                      shadow, (int64_t)(uintptr_t)p->lz_Vs, p->products,
+                                      shadow, copy, (int64_t)(uintptr_t)p->lz_Vs, p->products,
                                       p->chunk_k,
                                       p->xchunk_k, p->raster, p->ww_na, (int64_t)(uintptr_t)p->lz_V,
                                       (int64_t)ctx->wait_limit_ns};
