@@ -46,7 +46,8 @@ struct tci_heff_plan_s {
   // Lanczos workspace
   double* lz_V = nullptr;     // basis, capacity lz_cap vectors
   int lz_cap = 0;
-  void* lz_Vs = nullptr;      // double-float shadow of the basis (float2), capacity lz_vs_cap vectors
+  void* lz_Vs = nullptr;      // FP32 copy of the basis (hi planes, and lo planes with the double-float dots)
+                              // capacity lz_vs_cap planes of ldv floats
   int lz_vs_cap = 0;
   double* lz_w = nullptr;
   double* lz_scal = nullptr;  // device scalars

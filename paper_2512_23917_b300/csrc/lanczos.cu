@@ -1545,11 +1545,11 @@ tci_status launch_step_small(tci_context ctx, double* V, int64_t ldv, double* w,
 // plan; kInF64 for double-float vectors on an FP64 plan).
 template <class A, int MODE>
 // Vs (FP64 vectors on a split plan, re-orthogonalised; else null): a copy of
-// the basis written with each basis vector (vector g: hi plane at Vs + 2 g
-// ldv, lo plane ldv after it).  The pass-3 correction reads the hi planes (the
-// FP32 truncation its rounding-level terms use: half the bytes of the FP64
-// basis); with dfdots the lo planes are written too and pass 1 and the second
-// pass's dots run in double-float from the copy.
+// the basis written with each basis vector.  The pass-3 correction reads its
+// hi planes (the FP32 truncation its rounding-level terms use: half the bytes
+// of the FP64 basis; vector g's at Vs + g ldv).  With dfdots each vector also
+// has a lo plane (vector g: hi at Vs + 2 g ldv, lo ldv after it) and pass 1
+// and the second pass's dots run in double-float from the copy.
 tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reorth, double* x, double tol,
                        float* Vs, bool dfdots) {
   using Vt = typename A::V;
@@ -1581,6 +1581,7 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
   k_reduce_parts<<<1, 256, 0, ctx->stream>>>(part, 1, NBMAX, ctrl + 3, ctrl);
   if (kDF || !reorth) Vs = nullptr;
   if (!Vs) dfdots = false;
+  const int64_t vs_ld = dfdots ? 2 * ldv : ldv;   // between consecutive vectors' hi planes
   launch_start<A, MODE>(ctx, psi0, V, rows, cols, pieces, Kp, p->lz_x64, S,
                         ShadowOut{Vs, dfdots ? Vs + ldv : nullptr});
   TCI_CUDA(ctx, cudaGetLastError());
@@ -1649,12 +1650,12 @@ tci_status lanczos_run(tci_heff_plan p, const double* psi0, int nsteps, int reor
     k_finish_beta<<<1, 1, 0, ctx->stream>>>(S, j, nsteps, tol);
     if (j + 1 < nsteps) {
       Vt* vn = V + (int64_t)(j + 1) * ldv;
-      float* vsh = Vs ? Vs + 2 * (int64_t)(j + 1) * ldv : nullptr;
+      float* vsh = Vs ? Vs + (int64_t)(j + 1) * vs_ld : nullptr;
       const ShadowOut vsn{vsh, (vsh && dfdots) ? vsh + ldv : nullptr};
       launch_next<A, MODE>(ctx, w, vn, rows, cols, pieces, Kp, p->lz_x64, S, j, reorth ? S + OFF_LO + LO_GNEXT : ctrl,
                            vsn);
       if constexpr (kF32Terms) {
-        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j, vsn, Vs, 2 * ldv);
+        if (reorth) launch_next_corr<MODE>(ctx, V, ldv, j + 1, w, vn, rows, cols, pieces, Kp, S, j, vsn, Vs, vs_ld);
       }
     }
     TCI_CUDA(ctx, cudaGetLastError());
@@ -1757,13 +1758,14 @@ extern "C" tci_status tci_lanczos(tci_heff_plan p, tci_tensor psi0, int nsteps, 
   // shadow (the opt-in double-float dots) its lo planes too
   const bool copy = split && arith == TCI_LANCZOS_F64 && !p->cplx && reorth && !p->lz_fuse;
   const bool shadow = copy && p->lz_shadow;
-  if (copy && p->lz_vs_cap < p->lz_cap) {
+  const int vs_planes = copy ? p->lz_cap * (shadow ? 2 : 1) : 0;   // FP32 planes of ldv elements
+  if (copy && p->lz_vs_cap < vs_planes) {
     cudaStreamSynchronize(ctx->stream);
     tci_dev_free(p->lz_Vs);
     p->lz_Vs = nullptr;
     p->lz_vs_cap = 0;
-    TCI_TRY(tci_dev_alloc(ctx, sizeof(float2) * ldv * p->lz_cap, &p->lz_Vs));
-    p->lz_vs_cap = p->lz_cap;
+    TCI_TRY(tci_dev_alloc(ctx, sizeof(float) * ldv * vs_planes, &p->lz_Vs));
+    p->lz_vs_cap = vs_planes;
   }
   SolveArgs sa{p, psi, nsteps, reorth, xd, tol, arith, split, copy ? (float*)p->lz_Vs : nullptr, shadow};
   bool done = false;
