@@ -545,7 +545,9 @@ tci_status tci_heff_set_lanczos_fused_dots(tci_heff_plan plan, int enable);
  * and the pass-3 correction reads the copy's hi planes.  Each dot product
  * agrees with the FP64 one to about 1e-14 ||v_i|| ||w||, above FP64
  * rounding; the update passes and the recurrence scalars stay FP64.  The copy
- * takes 8 bytes per basis element of device memory.  Ignored when
+ * takes 8 bytes per basis element of device memory (without this option a
+ * split plan keeps the hi planes only, 4 bytes per element, which the pass-3
+ * correction reads).  Ignored when
  * tci_heff_set_lanczos_fused_dots is on.  Errors: INVALID_ARG, INVALID_CONTEXT. */
 tci_status tci_heff_set_lanczos_shadow_dots(tci_heff_plan plan, int enable);
 
