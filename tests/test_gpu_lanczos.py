@@ -68,6 +68,24 @@ def test_lanczos_chi1024_ritz_value(ctx, tci, arith):
     assert abs(r["theta"] - o["theta"]) < 1e-10 * abs(o["theta"])
 
 
+@pytest.mark.parametrize("arith", ARITH)
+@pytest.mark.parametrize("gs", ["dgks", "twice"])
+def test_lanczos_basis_beyond_one_pass_matches_oracle(ctx, tci, arith, gs):
+    """chi = 128 (n = 2^16), 32 steps: from step 7 on the vector work runs as separate passes, and
+    from step 20 on the basis (over 20 vectors) is updated and projected in groups of passes, each
+    forming its dot and norm totals in its last block; alpha, beta, theta and the Ritz vector
+    equal the oracle's."""
+    psi, L, R, W = dense_heff_inputs(128, seed=31)
+    r = gpu_lanczos(tci, ctx, L, W, R, psi, 32, arith=arith, gs=gs)
+    mv = lambda v: o_heff.heff_apply(L, W, R, v.reshape(psi.shape))
+    o = o_lanczos.lanczos(mv, psi, 32)
+    assert r["steps"] == o["steps"] == 32
+    np.testing.assert_allclose(r["alpha"], o["alpha"], rtol=1e-9, atol=1e-9 * np.abs(o["alpha"]).max())
+    np.testing.assert_allclose(r["beta"], o["beta"], rtol=1e-9, atol=1e-9 * np.abs(o["beta"]).max())
+    assert abs(r["theta"] - o["theta"]) < 1e-10 * abs(o["theta"])
+    assert np.linalg.norm(r["x"].ravel() - o["x"]) < 1e-7
+
+
 def test_lanczos_split_bf16_ritz_close(ctx, tci):
     psi, L, R, W = dense_heff_inputs(256, seed=7)
     r = gpu_lanczos(tci, ctx, L, W, R, psi, 20, precision="split_bf16")
