@@ -132,6 +132,18 @@ __device__ __forceinline__ double warp_sum(double v) {
 // size with x's sign (an absolute error below 2^-125) and |x| >= 2^128 the
 // largest binade; NaN and infinity are not preserved (only basis vectors,
 // |x| <= 1, come here).
+// FP32 -> FP64 on the integer pipes for normal numbers and zero (the exact
+// conversion: exponent rebiased by 896, fraction shifted by 29); subnormals,
+// infinities and NaN take the conversion instruction (FP64 pipe).
+__device__ __forceinline__ double f64_of_f32(float f) {
+  const unsigned b = __float_as_uint(f), e = (b >> 23) & 0xffu;
+  const unsigned long long sign = (unsigned long long)(b & 0x80000000u) << 32;
+  if (e == 0u && (b & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
+  if (e == 0u || e == 0xffu) return (double)f;
+  return __longlong_as_double(
+      (long long)(sign | ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
 __device__ __forceinline__ float f32_trunc(double x) {
   const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
   unsigned a = min(max(hi & 0x7fffffffu, 0x38100000u), 0x47efffffu);   // exponent in [897, 1150]
@@ -543,7 +555,11 @@ __device__ __forceinline__ void update_body(const typename A::V* __restrict__ V,
 #pragma unroll
       for (int g = G - 2 > 0 ? G - 2 : 0; g < G; ++g) A::sub(t, cs[g], v[g]);
       y = A::sub_end(t);
-      y = fma(-((double)sh + (double)sl), isc, y);
+      // with dots the pass is bound by the FP64 pipe: its conversions run on the integer pipes
+      if constexpr (DOTS)
+        y = fma(-(f64_of_f32(sh) + f64_of_f32(sl)), isc, y);
+      else
+        y = fma(-((double)sh + (double)sl), isc, y);
     } else if constexpr (kArith == kTermsF32) {
       float sf = 0.f;
 #pragma unroll
